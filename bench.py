@@ -1,0 +1,362 @@
+"""Benchmark: CP-ALS-QR sweeps per second on one GB300 (per rank; replicas for N > 1).
+
+Workload (the configuration the headline metric is quoted on): a 3-way
+400 x 400 x 400 FP64 tensor (512 MB, larger than the 129 MB L2), planted rank 10,
+factor columns with pairwise congruence 0.99, weights logspace 1..1e-4, 0.1%
+Gaussian noise, rank-10 CP-ALS-QR with the QR solve.  One "step" is one full
+sweep over the three modes: KRP of the R-factors and its QR, the Multi-TTM,
+W = Y_(n) Q0, the R0 substitution, normalisation, the factor QR, and the
+efficient fit.  The timed steps run through cpals_iterate (one CUDA graph per
+sweep) with X resident in HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1, run under torch.distributed.run.  Every rank runs its own
+independent replica (different seed), and value = the sum of sweeps/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CP-ALS-QR iters/s"
+UNIT = "iters/s"
+WORKLOAD = ("3-way 400x400x400 FP64 (512 MB), rank 10, planted factors with column congruence 0.99, "
+            "weights logspace 1..1e-4, 0.1% Gaussian noise; CP-ALS-QR sweeps (QR solve)")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_PER_SM = 4       # 2 DFMA/clk/SM on this part (measured: 1.195 TFLOP/s at ~1.95 GHz)
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=400)
+    ap.add_argument("--rank", type=int, default=10)
+    ap.add_argument("--solve", choices=["qr", "svd", "normal"], default="qr")
+    ap.add_argument("--no-variants", action="store_true", help="skip the SVD/NORMAL/FP32 side measurements")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling (every 200 ms) during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    maxes.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def workload(size, rank, seed):
+    from paper_2112_10855_gb300 import inputs
+    return inputs.workload_c2(seed=seed, init_seed=10855 + seed - 2112, size=size, rank=rank)
+
+
+def cpu_oracle_rate(p, sweeps=2, solve=0):
+    """The oracle as it stands (1 host thread), `sweeps` full sweeps."""
+    import oracle
+    o = oracle.OracleCPALS(p.X, p.dims, p.rank)
+    o.set_factors(p.init_factors)
+    t0 = time.perf_counter()
+    o.iterate(sweeps, solve=solve)
+    dt = time.perf_counter() - t0
+    return sweeps / dt, dt
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 CPU oracle timed on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    p = workload(args.size, args.rank, 2112)
+    solve = {"qr": 0, "svd": 1, "normal": 2}[args.solve]
+    o = oracle.OracleCPALS(p.X, p.dims, p.rank)
+    o.set_factors(p.init_factors)
+    for _ in range(args.warmup):
+        o.iterate(1, solve=solve, rtol=1e-10)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.iterate(1, solve=solve, rtol=1e-10)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("400x400x400", f"{args.size}x{args.size}x{args.size}")
+                   .replace("rank 10", f"rank {args.rank}"), "solve": args.solve, "parallelism": "replicas"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full sweeps of the same workload, single-threaded plain C FP64"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_2112_10855_gb300 import _build, cpals
+
+    if world == 1:
+        torch.cuda.set_device(0)
+    _build.build()
+    cpals.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    p = workload(args.size, args.rank, 2112 + rank)
+    P = int(np.prod(p.dims))
+    R = p.rank
+    stream = torch.cuda.Stream(device=dev)
+
+    Xd = torch.from_numpy(p.X).to(dev)
+    h = cpals.CPALS(p.dims, R, "f64")
+    h.set_stream(stream)
+    h.set_tensor(Xd)
+    h.set_factors([np.asfortranarray(a) for a in p.init_factors])
+
+    # warm-up (also captures the sweep graph)
+    h.iterate(args.warmup, solve=args.solve, svd_rtol=1e-10, want_fits=False)
+    torch.cuda.synchronize()
+
+    launches0 = h.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        h.iterate(args.steps, solve=args.solve, svd_rtol=1e-10, want_fits=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    gpu_launches = h.launch_count() - launches0
+    ms_max = max_over_ranks(ms, world)
+    value = world * args.steps / (ms_max * 1e-3)
+    fit_now = h.fit()
+
+    # dominant kernel: the first TTM of each mode's Multi-TTM (streams X), timed alone
+    reps = 5
+    ttm_ms = []
+    for n in range(3):
+        h.ttm_first(n)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            h.ttm_first(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ttm_ms.append(e0.elapsed_time(e1) / reps)
+    ttm_avg_ms = sum(ttm_ms) / len(ttm_ms)
+    flops = 2.0 * P * R
+    achieved_tflops = flops / (ttm_avg_ms * 1e-3) / 1e12
+    peak_fp64 = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    probe64, probe32 = cpals.probe_fma_peak(30.0)
+    hbm = measured_peaks().get("hbm_gbs")
+    ttm_gbs = 8.0 * P / (ttm_avg_ms * 1e-3) / 1e9
+
+    # end to end through the C-ABI with host buffers: X and the factors copied in
+    # from pinned host memory, one sweep, factors + fit read back, every step
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 5))
+    Xh = torch.from_numpy(p.X).pin_memory()
+    Ah = [torch.from_numpy(np.asfortranarray(a)).pin_memory() for a in p.init_factors]
+    Ah = [a.t().contiguous().t() if a.stride() != (1, a.shape[0]) else a for a in Ah]
+    he = cpals.CPALS(p.dims, R, "f64")
+    he.set_stream(stream)
+    he.set_tensor(Xh)
+    he.set_factors(Ah)
+    he.iterate(1, solve=args.solve, svd_rtol=1e-10, want_fits=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        he.set_tensor(Xh)
+        he.set_factors(Ah)
+        he.iterate(1, solve=args.solve, svd_rtol=1e-10, want_fits=False)
+        outA, lam = he.get_factors()
+        f = he.fit()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    fac_bytes = 8 * sum(d * R for d in p.dims)
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * P + fac_bytes,
+           "d2h_bytes_per_step": fac_bytes + 8 * R + 8, "steps": e2e_steps,
+           "what": "per step: pinned-host X and factors in, one sweep, factors, lambda and fit out"}
+    del he
+
+    variants = {}
+    if not args.no_variants:
+        for solve in ("svd", "normal"):
+            if solve == args.solve:
+                continue
+            hv = cpals.CPALS(p.dims, R, "f64")
+            hv.set_stream(stream)
+            hv.set_tensor(Xd)
+            hv.set_factors([np.asfortranarray(a) for a in p.init_factors])
+            hv.iterate(2, solve=solve, svd_rtol=1e-10, want_fits=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hv.iterate(5, solve=solve, svd_rtol=1e-10, want_fits=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            variants[f"f64_{solve}"] = 5 / (e0.elapsed_time(e1) * 1e-3)
+            del hv
+        hf = cpals.CPALS(p.dims, R, "f32")
+        hf.set_stream(stream)
+        hf.set_tensor(Xd)
+        hf.set_factors([np.asfortranarray(a) for a in p.init_factors])
+        hf.iterate(2, solve=args.solve, want_fits=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hf.iterate(args.steps, solve=args.solve, want_fits=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        variants[f"f32_{args.solve}"] = args.steps / (e0.elapsed_time(e1) * 1e-3)
+        del hf
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(p, sweeps=2, solve={"qr": 0, "svd": 1, "normal": 2}[args.solve])
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"2 full sweeps of the same workload ({dt:.1f} s), plain C FP64, 1 host thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("400x400x400", "x".join(map(str, p.dims)))
+                       .replace("rank 10", f"rank {R}"), "dims": list(p.dims), "rank": R, "solve": args.solve,
+                       "l2": "inputs larger than L2 (X is 8*P bytes > 129 MB); no flush needed",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_fp64, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_fp64, "traffic": None,
+                         "kernel": "ttm_rows_kernel<double> (first TTM of the Multi-TTM, streams X)",
+                         "peak_source": "152 SMs x 2 DFMA/clk x 2070 MHz (derived); live FMA probe below",
+                         "probe_fp64_tflops": probe64, "probe_fp32_tflops": probe32,
+                         "ms_per_launch": ttm_avg_ms, "flops_per_launch": flops},
+            "multi_ttm": {"gbs": ttm_gbs, "hbm_peak_gbs": hbm, "frac_hbm": (ttm_gbs / hbm) if hbm else None},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "clocks": clk.summary(),
+            "fit_after": fit_now,
+            "variants_iters_per_s": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

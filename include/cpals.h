@@ -1,0 +1,196 @@
+/*
+ * cpals.h -- C-ABI of the GB300 (sm_103a) CP-ALS-QR hot path.
+ *
+ * Method: Minster, Viviano, Liu, Ballard, "CP Decomposition for Tensors via
+ * Alternating Least Squares with QR Decomposition" (arXiv 2112.10855).
+ * For mode n, Alg. cp-als-qr solves the least-squares problem of Eq. ls_n,
+ *     min || X_(n) - Ahat_n Z_n^T ||_F,  Z_n = A_N (.) ... (.) A_{n+1} (.) A_{n-1} (.) ... (.) A_1,
+ * through the structured QR Z_n = [(Q_N (x) ... (x) Q_1) Q0] R0 of Eq. Z_qr.
+ * Alg. cp-als gives the normal-equations baseline (MTTKRP + Cholesky).
+ *
+ * Conventions
+ *  - Modes are 0-based: `mode` = n - 1 in the paper's numbering.
+ *  - X has dims I_0..I_{N-1} and is stored with mode 0 fastest: element
+ *    (i_0..i_{N-1}) sits at sum_m i_m prod_{k<m} I_k.
+ *  - Matrices are column-major (element (i,j) of an m x n matrix at i + m*j).
+ *    Factor A_m and Q_m are I_m x R.  R_m, R0 and S are R x R.  Q0 is R^{N-1} x R.
+ *  - The unfolding Y_(n) is I_n x R^{N-1}.  Its column index is
+ *    sum_{m != n} r_m R^{pos(m)}, where pos counts the modes below m other
+ *    than n (mode 0 fastest, as in Eq. multittm with the Kronecker rule of
+ *    Sec. 2.2).  The rows of V_n and Q0 use the same order.
+ *  - Every call returns a cpals_status.  cpals_last_error() gives a message.
+ *  - Work is enqueued on the stream set with cpals_set_stream (default: the
+ *    legacy default stream) and is asynchronous, except where a call says it
+ *    synchronises.
+ *  - Pointer arguments carry a `mem` flag: CPALS_MEM_DEVICE means device
+ *    memory that the caller owns; CPALS_MEM_HOST means host memory.  Host
+ *    transfers are synchronous with respect to the host.
+ *  - Errors found on the device (a singular R0, an S that is not positive
+ *    definite, a device wait that ran out) are recorded in a device status
+ *    word.  After one is recorded, every later kernel of the handle becomes
+ *    a no-op, so the factors stay as they were when the failure happened.
+ *    The word is reported, and then cleared, by the next synchronising call:
+ *    cpals_sync, cpals_fit, cpals_iterate, or a get call with host memory.
+ *  - A handle is not thread-safe.  Use one handle per host thread.
+ */
+#ifndef CPALS_H
+#define CPALS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cpals_handle cpals_handle;
+
+typedef enum {
+    CPALS_OK = 0,
+    CPALS_ERR_ARG = 1,       /* invalid argument (dims, rank, mode, null pointer, sizes) */
+    CPALS_ERR_NOMEM = 2,     /* device or host allocation failed */
+    CPALS_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    CPALS_ERR_SINGULAR = 4,  /* R0 numerically singular (QR solve) or S not SPD (normal equations) */
+    CPALS_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+    CPALS_ERR_STATE = 6      /* call order violated (e.g. no tensor, no factors) */
+} cpals_status;
+
+/* Arithmetic of the passes over X (Multi-TTM and MTTKRP).  The small
+ * factors (QR of A_m and of V_n, the R0 solve or SVD, normalisation, fit)
+ * always run in FP64. */
+typedef enum {
+    CPALS_F64 = 0,     /* X read as FP64, FP64 FMA */
+    CPALS_F32 = 1,     /* X read as an FP32 copy, FP32 FMA; Y promoted to FP64 */
+    CPALS_BF16X3 = 2   /* FP32 copy split into bf16 hi/lo parts; hi*hi+hi*lo+lo*hi on tensor cores, FP32 accumulate */
+} cpals_precision;
+
+typedef enum {
+    CPALS_SOLVE_QR = 0,     /* CP-ALS-QR: substitution with R0 (Eq. ls-qr-q0-step) */
+    CPALS_SOLVE_SVD = 1,    /* CP-ALS-QR-SVD: Ahat = W U pinv(Sigma) V^T with R0 = U Sigma V^T (Sec. 3.1) */
+    CPALS_SOLVE_NORMAL = 2  /* CP-ALS: MTTKRP and Cholesky of the Hadamard product of Grams (Alg. cp-als) */
+} cpals_solve;
+
+typedef enum { CPALS_MEM_DEVICE = 0, CPALS_MEM_HOST = 1 } cpals_mem;
+typedef enum { CPALS_ELEM_F64 = 0, CPALS_ELEM_F32 = 1 } cpals_elem;
+
+/* Create a rank-`rank` CP-ALS problem for an N-way tensor of the given dims
+ * (Sec. 3.1).  Requires 2 <= N <= 8, 1 <= rank <= 64 and rank <= dims[m]
+ * for every m.  The compact QR A_m = Q_m R_m with Q_m of size I_m x R
+ * (Sec. 3.1) needs I_m >= R, and that also keeps every Z_n from being wide.
+ * Allocates every device workspace buffer now (cudaMalloc), on the current
+ * device.  On success, *out receives the handle.
+ * Errors: CPALS_ERR_ARG, CPALS_ERR_NOMEM, CPALS_ERR_CUDA. */
+int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_handle** out);
+
+/* Free the handle and every buffer it owns.  Synchronises its stream.  NULL is a no-op. */
+int cpals_destroy(cpals_handle* h);
+
+/* Static message for the last failing call on h (or on creation when h is NULL). */
+const char* cpals_last_error(const cpals_handle* h);
+
+/* Enqueue all later work on `stream` (a cudaStream_t; NULL = legacy default stream). */
+int cpals_set_stream(cpals_handle* h, void* stream);
+
+/* Bytes of device memory the handle owns (workspace plus any owned copy of X). */
+int cpals_workspace_bytes(const cpals_handle* h, size_t* bytes);
+
+/* Attach the data tensor X (prod(dims) elements, mode 0 fastest).
+ *  elem = CPALS_ELEM_F64: with precision F64 and mem DEVICE, the pointer is
+ *    borrowed and must stay valid until the handle is destroyed or another
+ *    tensor is set; with mem HOST, X is copied into a device buffer that the
+ *    handle owns.  With precision F32/BF16X3, X is rounded (round to nearest
+ *    even) into an FP32 copy that the handle owns.
+ *  elem = CPALS_ELEM_F32: allowed only with precision F32/BF16X3; borrowed
+ *    (DEVICE) or copied (HOST).
+ * Also computes ||X||_F^2 in FP64 (Sec. 3.3.1: it is pre-computed once). */
+int cpals_set_tensor(cpals_handle* h, const void* X, int elem, int mem);
+
+/* Set the factors A_m (N pointers, I_m x R, FP64) and weights lambda (R values,
+ * or NULL for ones).  Alg. cp-als-qr initialisation: the compact QR
+ * A_m = Q_m R_m (diag(R_m) >= 0) is computed for every m, and so is the Gram
+ * A_m^T A_m (Alg. cp-als initialisation).  The data is copied. */
+int cpals_set_factors(cpals_handle* h, const double* const* A, const double* lambda, int mem);
+
+/* Copy out the current factors A_m (entries of A may be NULL to skip a mode)
+ * and lambda (may be NULL). */
+int cpals_get_factors(cpals_handle* h, double* const* A, double* lambda, int mem);
+
+/* Copy out Q_m (I_m x R) and R_m (R x R) of the current factor of `mode`
+ * (Alg. cp-als-qr factor-QR step).  Either output may be NULL. */
+int cpals_get_factor_qr(cpals_handle* h, int mode, double* Q, double* R, int mem);
+
+/* Override Q_m and R_m of every mode (N pointers each, FP64, mem as given),
+ * without touching A_m.  This feeds externally computed orthonormal factors
+ * to the Multi-TTM and KRP steps, for checking them one at a time. */
+int cpals_set_factor_qr(cpals_handle* h, const double* const* Q, const double* const* R, int mem);
+
+/* Alg. cp-als-qr, KRP and Q0 steps: V_n = R_{N-1} (.) ... (.) R_0 without
+ * `mode`, then its compact QR V_n = Q0 R0 with diag(R0) >= 0 (Eq. Z_qr).
+ * Q0 (R^{N-1} x R) and R0 (R x R) may be NULL.  The result is kept in the
+ * handle for the W step of cpals_multi_ttm on the same mode. */
+int cpals_krp_qr(cpals_handle* h, int mode, double* Q0, double* R0, int mem);
+
+/* Alg. cp-als-qr, Multi-TTM step (Eq. multittm): Y = X x_m Q_m^T for every m != mode,
+ * as single TTMs in decreasing-dimension order (Sec. 3.2).
+ *  Y (may be NULL): I_n x R^{N-1} unfolding Y_(n), FP64.
+ *  W (may be NULL): W_n = Y_(n) Q0 (Eq. ls-qr-q0-step), I_n x R, FP64.  It
+ *    needs a cpals_krp_qr on the same mode first (CPALS_ERR_STATE otherwise). */
+int cpals_multi_ttm(cpals_handle* h, int mode, double* Y, double* W, int mem);
+
+/* Measurement entry point: the first single TTM of the Multi-TTM of `mode`
+ * alone.  It is the pass that streams X from HBM (2 P R flops, Eq. TTMcost
+ * leading term).  Its output goes to the handle's workspace.  The benchmark
+ * times this kernel with events for the roofline figure. */
+int cpals_ttm_first(cpals_handle* h, int mode);
+
+/* Alg. cp-als, MTTKRP step: M_n = X_(n) Z_n (I_n x R, FP64) with the current
+ * factors; the arithmetic follows the handle's precision. */
+int cpals_mttkrp(cpals_handle* h, int mode, double* M, int mem);
+
+/* One mode update.
+ *  QR/SVD: the mode-loop body of Alg. cp-als-qr (KRP, QR of V_n, Multi-TTM,
+ *    apply Q0, solve by substitution or by the truncated SVD of R0 keeping
+ *    sigma_i > svd_rtol * sigma_1, normalise columns with the 2-norm into A_n
+ *    and lambda, re-QR A_n = Q_n R_n).
+ *  NORMAL: the mode-loop body of Alg. cp-als (Hadamard product of Grams S_n,
+ *    MTTKRP, Cholesky solve, normalise, re-Gram); Q_n and R_n are refreshed
+ *    too, so that solves can be mixed.
+ * svd_rtol <= 0 selects R * eps.  Asynchronous; a singular solve is recorded
+ * in the device status word and leaves the factor unchanged. */
+int cpals_solve_mode(cpals_handle* h, int mode, int solve, double svd_rtol);
+
+/* Run sweeps over all modes (the outer loop of Alg. cp-als-qr / cp-als).
+ * Each sweep ends with the efficient fit of Sec. 3.3.1.
+ *  tol > 0: stop once |fit - previous fit| < tol.  This reads the fit on the
+ *    host after every sweep.
+ *  tol == 0: run exactly `iters` sweeps, with no host synchronisation until
+ *    the end.
+ * The sweep is captured once per solve kind into a CUDA graph and replayed.
+ * fits_host (may be NULL) receives one fit per sweep that ran.
+ * *done (may be NULL) receives the number of sweeps run.  Synchronises at the end. */
+int cpals_iterate(cpals_handle* h, int iters, double tol, int solve, double svd_rtol, int* done,
+                  double* fits_host);
+
+/* fit = 1 - ||X - Xhat|| / ||X||.  direct = 0: the efficient form of
+ * Sec. 3.3.1 from the last sweep's W_N, Ahat_N, R0 and R_N (or, after a
+ * NORMAL sweep, from M_N and S_N).  It is accurate to about sqrt(eps) and
+ * needs a finished sweep (CPALS_ERR_STATE otherwise).  direct = 1: one pass
+ * over X that forms Xhat entry by entry.  Synchronises. */
+int cpals_fit(cpals_handle* h, int direct, double* fit_host);
+
+/* Synchronise the handle's stream and report (then clear) the device status word. */
+int cpals_sync(cpals_handle* h);
+
+/* Number of kernel launches the handle has issued so far (graph replays count
+ * each kernel node once per replay). */
+int64_t cpals_launch_count(const cpals_handle* h);
+
+/* Measured FMA throughput probe (not part of the method): runs dependent
+ * FMA chains on every SM for `ms_target` ms and writes the achieved
+ * TFLOP/s for FP64 and FP32.  Used to state the ALU roofline.  Synchronises. */
+int cpals_probe_fma_peak(double ms_target, double* fp64_tflops, double* fp32_tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPALS_H */

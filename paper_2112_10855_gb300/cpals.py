@@ -1,0 +1,286 @@
+"""Thin Python binding of libcpals (include/cpals.h), by ctypes.
+
+Only argument marshalling happens here.  Every step of CP-ALS-QR runs inside
+the CUDA library.  There is no CPU fallback: if the library is missing or no
+GPU is present, the calls raise.
+
+Arrays: torch CUDA tensors are passed as device pointers (CPALS_MEM_DEVICE),
+numpy arrays as host pointers (CPALS_MEM_HOST).  Matrices are column-major: an
+I x R factor is a tensor of shape (I, R) with strides (1, I)
+(``A.t().contiguous().t()``) or a numpy array with order='F'.  The data tensor
+is a flat array with mode 0 fastest.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE = range(7)
+F64, F32, BF16X3 = 0, 1, 2
+SOLVE_QR, SOLVE_SVD, SOLVE_NORMAL = 0, 1, 2
+MEM_DEVICE, MEM_HOST = 0, 1
+ELEM_F64, ELEM_F32 = 0, 1
+
+PRECISIONS = {"f64": F64, "f32": F32, "bf16x3": BF16X3}
+SOLVES = {"qr": SOLVE_QR, "svd": SOLVE_SVD, "normal": SOLVE_NORMAL}
+
+_vp = C.c_void_p
+_lib = None
+
+
+class CPALSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cpals error {code}: {msg}")
+        self.code = code
+
+
+class SingularError(CPALSError):
+    pass
+
+
+def load(path: str | None = None):
+    """Load libcpals.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcpals.so not found at {path}; build it first (python -c 'import "
+                           "__graft_entry__ as g; g.build()')")
+    L = C.CDLL(path)
+    i64p = C.POINTER(C.c_int64)
+    L.cpals_create.argtypes = [i64p, C.c_int, C.c_int, C.c_int, C.POINTER(_vp)]
+    L.cpals_destroy.argtypes = [_vp]
+    L.cpals_last_error.argtypes = [_vp]
+    L.cpals_last_error.restype = C.c_char_p
+    L.cpals_set_stream.argtypes = [_vp, _vp]
+    L.cpals_workspace_bytes.argtypes = [_vp, C.POINTER(C.c_size_t)]
+    L.cpals_set_tensor.argtypes = [_vp, _vp, C.c_int, C.c_int]
+    L.cpals_set_factors.argtypes = [_vp, C.POINTER(_vp), _vp, C.c_int]
+    L.cpals_get_factors.argtypes = [_vp, C.POINTER(_vp), _vp, C.c_int]
+    L.cpals_get_factor_qr.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
+    L.cpals_set_factor_qr.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_vp), C.c_int]
+    L.cpals_krp_qr.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
+    L.cpals_multi_ttm.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
+    L.cpals_mttkrp.argtypes = [_vp, C.c_int, _vp, C.c_int]
+    L.cpals_ttm_first.argtypes = [_vp, C.c_int]
+    L.cpals_solve_mode.argtypes = [_vp, C.c_int, C.c_int, C.c_double]
+    L.cpals_iterate.argtypes = [_vp, C.c_int, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_int),
+                                C.POINTER(C.c_double)]
+    L.cpals_fit.argtypes = [_vp, C.c_int, C.POINTER(C.c_double)]
+    L.cpals_sync.argtypes = [_vp]
+    L.cpals_launch_count.argtypes = [_vp]
+    L.cpals_launch_count.restype = C.c_int64
+    L.cpals_probe_fma_peak.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names of the C-ABI entry points declared in include/cpals.h."""
+    import re
+    hdr = os.path.join(_build.ROOT, "include", "cpals.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(cpals_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(h, rc):
+    if rc != OK:
+        msg = load().cpals_last_error(h).decode(errors="replace")
+        if rc == ERR_SINGULAR:
+            raise SingularError(rc, msg)
+        raise CPALSError(rc, msg)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, mem flag) of a torch tensor or numpy array."""
+    if x is None:
+        return None, MEM_DEVICE
+    if _is_torch(x):
+        if x.is_cuda:
+            return C.c_void_p(x.data_ptr()), MEM_DEVICE
+        return C.c_void_p(x.data_ptr()), MEM_HOST
+    if isinstance(x, np.ndarray):
+        return C.c_void_p(x.ctypes.data), MEM_HOST
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+def _colmajor_ok(x, rows, cols):
+    if _is_torch(x):
+        return tuple(x.shape) == (rows, cols) and (cols == 1 or x.stride() == (1, rows) or rows == 1) \
+            and x.dtype.is_floating_point and x.element_size() == 8
+    return x.shape == (rows, cols) and x.dtype == np.float64 and (x.flags.f_contiguous or cols == 1)
+
+
+class CPALS:
+    """One CP-ALS(-QR) problem: cpals_create / cpals_destroy and the calls of include/cpals.h."""
+
+    def __init__(self, dims, rank, precision="f64"):
+        import torch  # noqa: F401  (the library shares the device and context with torch)
+        L = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.N = len(self.dims)
+        self.R = int(rank)
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        d = (C.c_int64 * self.N)(*self.dims)
+        h = _vp()
+        rc = L.cpals_create(d, self.N, self.R, self.precision, C.byref(h))
+        if rc != OK:
+            raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
+        self._h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cpals_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- plumbing
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(self._h, load().cpals_set_stream(self._h, C.c_void_p(raw or 0)))
+
+    def workspace_bytes(self):
+        b = C.c_size_t()
+        _check(self._h, load().cpals_workspace_bytes(self._h, C.byref(b)))
+        return b.value
+
+    def launch_count(self):
+        return load().cpals_launch_count(self._h)
+
+    def sync(self):
+        _check(self._h, load().cpals_sync(self._h))
+
+    # -- data
+    def set_tensor(self, X):
+        """X: flat float64/float32 array of prod(dims) entries, mode 0 fastest."""
+        n = int(np.prod(self.dims))
+        if _is_torch(X):
+            if not X.is_contiguous() or X.numel() != n:
+                raise ValueError("X must be a contiguous tensor with prod(dims) entries")
+            elem = ELEM_F64 if X.element_size() == 8 else ELEM_F32
+        else:
+            X = np.ascontiguousarray(X)
+            if X.size != n:
+                raise ValueError("X must have prod(dims) entries")
+            elem = ELEM_F64 if X.dtype == np.float64 else ELEM_F32
+        p, mem = _ptr(X)
+        self._X = X   # a borrowed device pointer must stay alive
+        _check(self._h, load().cpals_set_tensor(self._h, p, elem, mem))
+
+    def _mats_in(self, mats, rows):
+        ptrs, mem = [], None
+        for m, A in enumerate(mats):
+            if not _colmajor_ok(A, rows[m], self.R):
+                raise ValueError(f"matrix {m} must be a column-major float64 {rows[m]} x {self.R} array")
+            p, mm = _ptr(A)
+            if mem is not None and mm != mem:
+                raise ValueError("mix of host and device matrices")
+            mem = mm
+            ptrs.append(p)
+        return (_vp * len(ptrs))(*ptrs), mem
+
+    def set_factors(self, A, lam=None):
+        arr, mem = self._mats_in(A, self.dims)
+        lp = None
+        if lam is not None:
+            lp, lm = _ptr(lam)
+            if lm != mem:
+                raise ValueError("lambda must live where the factors live")
+        _check(self._h, load().cpals_set_factors(self._h, arr, lp, mem))
+
+    def set_factor_qr(self, Q, R):
+        qa, mem = self._mats_in(Q, self.dims)
+        ra, mem2 = self._mats_in(R, [self.R] * self.N)
+        if mem != mem2:
+            raise ValueError("Q and R must live in the same memory")
+        _check(self._h, load().cpals_set_factor_qr(self._h, qa, ra, mem))
+
+    def _out(self, rows, cols, device):
+        if device:
+            import torch
+            return torch.empty((cols, rows), dtype=torch.float64, device="cuda").t()
+        return np.zeros((rows, cols), order="F")
+
+    def get_factors(self, device=False):
+        outs = [self._out(d, self.R, device) for d in self.dims]
+        lam = self._out(self.R, 1, device)[:, 0] if device else np.zeros(self.R)
+        ptrs = [_ptr(o)[0] for o in outs]
+        lp, mem = _ptr(lam)
+        _check(self._h, load().cpals_get_factors(self._h, (_vp * self.N)(*ptrs), lp, mem))
+        return outs, lam
+
+    def get_factor_qr(self, mode, device=False):
+        Q = self._out(self.dims[mode], self.R, device)
+        R = self._out(self.R, self.R, device)
+        _check(self._h, load().cpals_get_factor_qr(self._h, mode, _ptr(Q)[0], _ptr(R)[0],
+                                                   MEM_DEVICE if device else MEM_HOST))
+        return Q, R
+
+    # -- the hot path
+    def krp_qr(self, mode, device=False):
+        RN1 = self.R ** (self.N - 1)
+        Q0 = self._out(RN1, self.R, device)
+        R0 = self._out(self.R, self.R, device)
+        _check(self._h, load().cpals_krp_qr(self._h, mode, _ptr(Q0)[0], _ptr(R0)[0],
+                                            MEM_DEVICE if device else MEM_HOST))
+        return Q0, R0
+
+    def multi_ttm(self, mode, want_Y=True, want_W=False, device=False):
+        RN1 = self.R ** (self.N - 1)
+        In = self.dims[mode]
+        Y = self._out(In, RN1, device) if want_Y else None
+        W = self._out(In, self.R, device) if want_W else None
+        _check(self._h, load().cpals_multi_ttm(self._h, mode, _ptr(Y)[0], _ptr(W)[0],
+                                               MEM_DEVICE if device else MEM_HOST))
+        return Y, W
+
+    def ttm_first(self, mode):
+        _check(self._h, load().cpals_ttm_first(self._h, mode))
+
+    def mttkrp(self, mode, device=False):
+        M = self._out(self.dims[mode], self.R, device)
+        _check(self._h, load().cpals_mttkrp(self._h, mode, _ptr(M)[0], MEM_DEVICE if device else MEM_HOST))
+        return M
+
+    def solve_mode(self, mode, solve="qr", svd_rtol=0.0):
+        s = SOLVES[solve] if isinstance(solve, str) else int(solve)
+        _check(self._h, load().cpals_solve_mode(self._h, mode, s, float(svd_rtol)))
+
+    def iterate(self, iters, tol=0.0, solve="qr", svd_rtol=0.0, want_fits=True):
+        s = SOLVES[solve] if isinstance(solve, str) else int(solve)
+        done = C.c_int(0)
+        fits = (C.c_double * max(int(iters), 1))() if want_fits else None
+        _check(self._h, load().cpals_iterate(self._h, int(iters), float(tol), s, float(svd_rtol),
+                                             C.byref(done), fits))
+        return np.array(fits[:done.value]) if want_fits else done.value
+
+    def fit(self, direct=False):
+        f = C.c_double()
+        _check(self._h, load().cpals_fit(self._h, 1 if direct else 0, C.byref(f)))
+        return f.value
+
+
+def probe_fma_peak(ms_target=50.0):
+    """Measured FP64 and FP32 FMA throughput in TFLOP/s (dependent-chain probe)."""
+    a, b = C.c_double(), C.c_double()
+    rc = load().cpals_probe_fma_peak(float(ms_target), C.byref(a), C.byref(b))
+    if rc != OK:
+        raise CPALSError(rc, "FMA probe failed")
+    return a.value, b.value

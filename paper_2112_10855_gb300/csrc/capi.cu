@@ -1,0 +1,630 @@
+// capi.cu -- the extern "C" entry points of include/cpals.h: handle lifecycle,
+// data movement, the per-mode update of Alg. cp-als-qr / Alg. cp-als, and
+// the sweep loop replayed as one CUDA graph per solve kind.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+using cpals::Handle;
+
+namespace {
+
+thread_local char g_create_err[512] = "";
+
+int fail(Handle* h, int code, const char* fmt, const char* detail = "")
+{
+    char* dst = h ? h->err : g_create_err;
+    snprintf(dst, 512, fmt, detail);
+    return code;
+}
+
+int cuda_fail(Handle* h, cudaError_t e, const char* where)
+{
+    char* dst = h ? h->err : g_create_err;
+    snprintf(dst, 512, "%s: %s", where, cudaGetErrorString(e));
+    return CPALS_ERR_CUDA;
+}
+
+#define CUDA_OR_FAIL(h, expr, where)                 \
+    do {                                             \
+        cudaError_t _e = (expr);                     \
+        if (_e != cudaSuccess) return cuda_fail((h), _e, (where)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(Handle* h, T** p, size_t elems)
+{
+    const size_t bytes = std::max<size_t>(elems, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess) h->owned_bytes += bytes;
+    return e;
+}
+
+void free_all(Handle* h)
+{
+    auto f = [](void* p) { if (p) cudaFree(p); };
+    for (int m = 0; m < cpals::kMaxN; ++m) { f(h->A[m]); f(h->Q[m]); f(h->Rf[m]); f(h->G[m]); }
+    f(h->lambda); f(h->V); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
+    f(h->tbuf[0]); f(h->tbuf[1]); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
+    f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned);
+    for (int s = 0; s < 3; ++s) if (h->graph[s]) cudaGraphExecDestroy(h->graph[s]);
+}
+
+// Largest TTM intermediate over all modes and steps of the Multi-TTM (and MTTKRP).
+int64_t max_intermediate(const Handle* h)
+{
+    int64_t best = 1;
+    for (int n = 0; n < h->N; ++n) {
+        int order[cpals::kMaxN];
+        cpals::ttm_order(h->N, h->dims, n, order);
+        int64_t d[cpals::kMaxN];
+        for (int m = 0; m < h->N; ++m) d[m] = h->dims[m];
+        int64_t P = h->P;
+        for (int k = 0; k < h->N - 1; ++k) {
+            const int m = order[k];
+            P = P / d[m] * h->R;
+            d[m] = h->R;
+            best = std::max(best, P);
+        }
+    }
+    return best;
+}
+
+bool mem_ok(int mem) { return mem == CPALS_MEM_DEVICE || mem == CPALS_MEM_HOST; }
+
+cudaMemcpyKind kind_in(int mem) { return mem == CPALS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind kind_out(int mem) { return mem == CPALS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+// Reads and clears the device status word (synchronises).
+int take_status(Handle* h)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (st != cpals::kStatusOk) {
+        const int zero = 0;
+        cudaMemcpy(h->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        if (st == CPALS_ERR_SINGULAR)
+            return fail(h, CPALS_ERR_SINGULAR, "%s", "singular least-squares system (R0 or S); factor left unchanged");
+        if (st == CPALS_ERR_TIMEOUT) return fail(h, CPALS_ERR_TIMEOUT, "%s", "a bounded device wait gave up");
+        return fail(h, st, "%s", "device error");
+    }
+    return CPALS_OK;
+}
+
+// Make the derived data (Q_m, R_m for QR/SVD; G_m for NORMAL) of every mode
+// other than `skip` current.
+cudaError_t refresh_derived(Handle* h, int solve, int skip)
+{
+    for (int m = 0; m < h->N; ++m) {
+        if (m == skip) continue;
+        if (solve == CPALS_SOLVE_NORMAL) {
+            if (!h->gram_valid[m]) {
+                CPALS_CUDA_TRY(cpals::gram(h, h->A[m], h->dims[m], h->G[m]));
+                h->gram_valid[m] = true;
+            }
+        } else {
+            if (!h->qr_valid[m]) {
+                CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], h->dims[m], h->R, h->Q[m], h->Rf[m]));
+                h->qr_valid[m] = true;
+            }
+        }
+    }
+    return cudaSuccess;
+}
+
+// One mode update (Alg. cp-als-qr mode-loop body, or Alg. cp-als for NORMAL).
+cudaError_t mode_update(Handle* h, int n, int solve, double rtol)
+{
+    CPALS_CUDA_TRY(refresh_derived(h, solve, n));
+    const int64_t In = h->dims[n];
+    if (solve == CPALS_SOLVE_NORMAL) {
+        CPALS_CUDA_TRY(cpals::mttkrp(h, n));
+        CPALS_CUDA_TRY(cpals::solve_normal(h, n));
+    } else {
+        CPALS_CUDA_TRY(cpals::krp_qr(h, n));
+        h->krp_mode = n;
+        CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
+        CPALS_CUDA_TRY(cpals::gemm_nn(h, h->Yn, h->Q0, h->W, In, h->RN1, h->R));
+        if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
+        else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol));
+    }
+    CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
+    if (solve == CPALS_SOLVE_NORMAL) {
+        CPALS_CUDA_TRY(cpals::gram(h, h->A[n], In, h->G[n]));
+        h->gram_valid[n] = true;
+        h->qr_valid[n] = false;
+    } else {
+        CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n]));
+        h->qr_valid[n] = true;
+        h->gram_valid[n] = false;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t sweep(Handle* h, int solve, double rtol)
+{
+    for (int n = 0; n < h->N; ++n) CPALS_CUDA_TRY(mode_update(h, n, solve, rtol));
+    return cpals::fit_efficient(h, solve);
+}
+
+// FMA throughput probe kernels (dependent chains, 8 independent accumulators).
+template <typename T>
+__global__ void fma_probe_kernel(T* out, int iters, T a, T b)
+{
+    T acc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc[i] = (T)(threadIdx.x + i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = acc[i] * a + b;
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += acc[i];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_handle** out)
+{
+    if (!out) return fail(nullptr, CPALS_ERR_ARG, "%s", "out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, CPALS_ERR_ARG, "%s", "dims is NULL");
+    if (N < 2 || N > cpals::kMaxN) return fail(nullptr, CPALS_ERR_ARG, "%s", "N must be in [2, 8]");
+    if (rank < 1 || rank > cpals::kMaxRank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must be in [1, 64]");
+    if (precision != CPALS_F64 && precision != CPALS_F32 && precision != CPALS_BF16X3)
+        return fail(nullptr, CPALS_ERR_ARG, "%s", "unknown precision");
+    for (int m = 0; m < N; ++m)
+        if (dims[m] < 1) return fail(nullptr, CPALS_ERR_ARG, "%s", "dims must be >= 1");
+    for (int m = 0; m < N; ++m)
+        if (dims[m] < rank)
+            return fail(nullptr, CPALS_ERR_ARG, "%s",
+                        "rank must not exceed any dim (the compact QR of each I_m x R factor needs I_m >= R)");
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return fail(nullptr, CPALS_ERR_NOMEM, "%s", "host allocation failed");
+    h->N = N; h->R = rank; h->prec = precision;
+    h->P = 1; h->RN1 = 1; h->Imax = 0;
+    for (int m = 0; m < N; ++m) {
+        h->dims[m] = dims[m];
+        h->P *= dims[m];
+        h->Imax = std::max(h->Imax, dims[m]);
+    }
+    for (int m = 0; m < N - 1; ++m) h->RN1 *= rank;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { int rc = cuda_fail(nullptr, e, "device query"); delete h; return rc; }
+
+    const int R = rank;
+    const int64_t big = std::max(h->Imax, h->RN1);
+    h->tbuf_elems = max_intermediate(h);
+    const size_t tsz = (precision == CPALS_F64) ? sizeof(double) : sizeof(float);
+    h->scratch_elems = std::max<int64_t>({4 * big * R + 64 * R * R, 4096, (int64_t)h->num_sms * 2 * h->Imax * R});
+    h->fit_cap = 4096;
+    bool ok = true;
+    for (int m = 0; m < N && ok; ++m) {
+        ok = dalloc(h, &h->A[m], dims[m] * R) == cudaSuccess && dalloc(h, &h->Q[m], dims[m] * R) == cudaSuccess &&
+             dalloc(h, &h->Rf[m], (size_t)R * R) == cudaSuccess && dalloc(h, &h->G[m], (size_t)R * R) == cudaSuccess;
+    }
+    ok = ok && dalloc(h, &h->lambda, R) == cudaSuccess && dalloc(h, &h->V, h->RN1 * R) == cudaSuccess &&
+         dalloc(h, &h->Q0, h->RN1 * R) == cudaSuccess && dalloc(h, &h->R0, (size_t)R * R) == cudaSuccess &&
+         dalloc(h, &h->Yn, h->Imax * h->RN1) == cudaSuccess && dalloc(h, &h->W, h->Imax * R) == cudaSuccess &&
+         dalloc(h, &h->Ahat, h->Imax * R) == cudaSuccess && dalloc(h, &h->M, h->Imax * R) == cudaSuccess &&
+         dalloc(h, &h->S, (size_t)R * R) == cudaSuccess && dalloc(h, &h->T, (size_t)R * R) == cudaSuccess &&
+         dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
+         dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
+         dalloc(h, &h->d_fit_count, 1) == cudaSuccess;
+    if (ok) {
+        void* p0 = nullptr; void* p1 = nullptr;
+        ok = cudaMalloc(&p0, tsz * h->tbuf_elems) == cudaSuccess && cudaMalloc(&p1, tsz * h->tbuf_elems) == cudaSuccess;
+        h->tbuf[0] = p0; h->tbuf[1] = p1;
+        if (ok) h->owned_bytes += 2 * tsz * h->tbuf_elems;
+    }
+    if (!ok) {
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return fail(nullptr, CPALS_ERR_NOMEM, "%s", "device allocation failed");
+    }
+    e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_fit_count, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->lambda, 0, sizeof(double) * R);
+    if (e != cudaSuccess) { int rc = cuda_fail(nullptr, e, "memset"); free_all(h); delete h; return rc; }
+    *out = reinterpret_cast<cpals_handle*>(h);
+    return CPALS_OK;
+}
+
+int cpals_destroy(cpals_handle* hh)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return CPALS_OK;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return CPALS_OK;
+}
+
+const char* cpals_last_error(const cpals_handle* hh)
+{
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    return h ? h->err : g_create_err;
+}
+
+int cpals_set_stream(cpals_handle* hh, void* stream)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    return CPALS_OK;
+}
+
+int cpals_workspace_bytes(const cpals_handle* hh, size_t* bytes)
+{
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    if (!h || !bytes) return CPALS_ERR_ARG;
+    *bytes = h->owned_bytes;
+    return CPALS_OK;
+}
+
+int cpals_set_tensor(cpals_handle* hh, const void* X, int elem, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (!X) return fail(h, CPALS_ERR_ARG, "%s", "X is NULL");
+    if (!mem_ok(mem) || (elem != CPALS_ELEM_F64 && elem != CPALS_ELEM_F32))
+        return fail(h, CPALS_ERR_ARG, "%s", "bad elem or mem flag");
+    if (elem == CPALS_ELEM_F32 && h->prec == CPALS_F64)
+        return fail(h, CPALS_ERR_ARG, "%s", "an FP32 tensor needs precision F32 or BF16X3");
+    h->X64 = nullptr; h->X32 = nullptr; h->have_X = false;
+    if (h->prec == CPALS_F64) {
+        if (mem == CPALS_MEM_DEVICE) {
+            h->X64 = static_cast<const double*>(X);
+        } else {
+            if (!h->X64_owned) CUDA_OR_FAIL(h, dalloc(h, &h->X64_owned, h->P), "allocate X");
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(h->X64_owned, X, sizeof(double) * h->P, cudaMemcpyHostToDevice, h->stream),
+                         "copy X");
+            h->X64 = h->X64_owned;
+        }
+    } else {
+        if (!h->X32_owned && !(elem == CPALS_ELEM_F32 && mem == CPALS_MEM_DEVICE))
+            CUDA_OR_FAIL(h, dalloc(h, &h->X32_owned, h->P), "allocate FP32 X");
+        if (elem == CPALS_ELEM_F32) {
+            if (mem == CPALS_MEM_DEVICE) {
+                h->X32 = static_cast<const float*>(X);
+            } else {
+                CUDA_OR_FAIL(h, cudaMemcpyAsync(h->X32_owned, X, sizeof(float) * h->P, cudaMemcpyHostToDevice,
+                                                h->stream), "copy X");
+                h->X32 = h->X32_owned;
+            }
+        } else {
+            const double* src = static_cast<const double*>(X);
+            if (mem == CPALS_MEM_HOST) {
+                // stage through the owned FP64 buffer
+                if (!h->X64_owned) CUDA_OR_FAIL(h, dalloc(h, &h->X64_owned, h->P), "allocate X staging");
+                CUDA_OR_FAIL(h, cudaMemcpyAsync(h->X64_owned, X, sizeof(double) * h->P, cudaMemcpyHostToDevice,
+                                                h->stream), "copy X");
+                src = h->X64_owned;
+            }
+            CUDA_OR_FAIL(h, cpals::cast_f64_f32(h, src, h->X32_owned, h->P), "cast X");
+            h->X32 = h->X32_owned;
+            h->X64 = src;   // the norm uses the FP64 values
+        }
+    }
+    CUDA_OR_FAIL(h, cpals::norm2(h), "norm of X");
+    if (h->prec != CPALS_F64) h->X64 = nullptr;   // passes over X read the FP32 copy only
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->normX2_host, h->d_normX2, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                 "norm read");
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "set_tensor sync");
+    h->have_X = true;
+    h->last_sweep_solve = -1;
+    return CPALS_OK;
+}
+
+int cpals_set_factors(cpals_handle* hh, const double* const* A, const double* lambda, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (!A || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad factor pointers or mem flag");
+    for (int m = 0; m < h->N; ++m)
+        if (!A[m]) return fail(h, CPALS_ERR_ARG, "%s", "a factor pointer is NULL");
+    const int R = h->R;
+    for (int m = 0; m < h->N; ++m)
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->A[m], A[m], sizeof(double) * h->dims[m] * R, kind_in(mem), h->stream),
+                     "copy factor");
+    if (lambda) {
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->lambda, lambda, sizeof(double) * R, kind_in(mem), h->stream), "copy lambda");
+    } else {
+        std::vector<double> ones(R, 1.0);
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->lambda, ones.data(), sizeof(double) * R, cudaMemcpyHostToDevice, h->stream),
+                     "copy lambda");
+        CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "sync");
+    }
+    for (int m = 0; m < h->N; ++m) {
+        CUDA_OR_FAIL(h, cpals::householder_qr(h, h->A[m], h->dims[m], R, h->Q[m], h->Rf[m]), "factor QR");
+        CUDA_OR_FAIL(h, cpals::gram(h, h->A[m], h->dims[m], h->G[m]), "factor Gram");
+        h->qr_valid[m] = true;
+        h->gram_valid[m] = true;
+    }
+    if (mem == CPALS_MEM_HOST) CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "sync");
+    h->have_factors = true;
+    h->krp_mode = -1;
+    h->last_sweep_solve = -1;
+    return CPALS_OK;
+}
+
+int cpals_get_factors(cpals_handle* hh, double* const* A, double* lambda, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (!mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad mem flag");
+    for (int m = 0; m < h->N && A; ++m)
+        if (A[m])
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(A[m], h->A[m], sizeof(double) * h->dims[m] * h->R, kind_out(mem),
+                                            h->stream), "copy factor out");
+    if (lambda)
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(lambda, h->lambda, sizeof(double) * h->R, kind_out(mem), h->stream),
+                     "copy lambda out");
+    if (mem == CPALS_MEM_HOST) return take_status(h);
+    return CPALS_OK;
+}
+
+int cpals_get_factor_qr(cpals_handle* hh, int mode, double* Q, double* R, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (mode < 0 || mode >= h->N || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad mode or mem flag");
+    if (!h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "no factors set");
+    CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, -1), "refresh QR");
+    if (Q) CUDA_OR_FAIL(h, cudaMemcpyAsync(Q, h->Q[mode], sizeof(double) * h->dims[mode] * h->R, kind_out(mem),
+                                           h->stream), "copy Q");
+    if (R) CUDA_OR_FAIL(h, cudaMemcpyAsync(R, h->Rf[mode], sizeof(double) * h->R * h->R, kind_out(mem), h->stream),
+                        "copy R");
+    if (mem == CPALS_MEM_HOST) return take_status(h);
+    return CPALS_OK;
+}
+
+int cpals_set_factor_qr(cpals_handle* hh, const double* const* Q, const double* const* R, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (!Q || !R || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad pointers or mem flag");
+    for (int m = 0; m < h->N; ++m) {
+        if (!Q[m] || !R[m]) return fail(h, CPALS_ERR_ARG, "%s", "a Q or R pointer is NULL");
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->Q[m], Q[m], sizeof(double) * h->dims[m] * h->R, kind_in(mem), h->stream),
+                     "copy Q");
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->Rf[m], R[m], sizeof(double) * h->R * h->R, kind_in(mem), h->stream),
+                     "copy R");
+        h->qr_valid[m] = true;
+    }
+    if (mem == CPALS_MEM_HOST) CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "sync");
+    h->have_factors = true;
+    h->krp_mode = -1;
+    return CPALS_OK;
+}
+
+int cpals_krp_qr(cpals_handle* hh, int mode, double* Q0, double* R0, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (mode < 0 || mode >= h->N || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad mode or mem flag");
+    if (!h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "no factors set");
+    CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, mode), "refresh QR");
+    CUDA_OR_FAIL(h, cpals::krp_qr(h, mode), "KRP QR");
+    h->krp_mode = mode;
+    if (Q0) CUDA_OR_FAIL(h, cudaMemcpyAsync(Q0, h->Q0, sizeof(double) * h->RN1 * h->R, kind_out(mem), h->stream),
+                         "copy Q0");
+    if (R0) CUDA_OR_FAIL(h, cudaMemcpyAsync(R0, h->R0, sizeof(double) * h->R * h->R, kind_out(mem), h->stream),
+                         "copy R0");
+    if (mem == CPALS_MEM_HOST) return take_status(h);
+    return CPALS_OK;
+}
+
+int cpals_multi_ttm(cpals_handle* hh, int mode, double* Y, double* W, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (mode < 0 || mode >= h->N || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad mode or mem flag");
+    if (!h->have_X) return fail(h, CPALS_ERR_STATE, "%s", "no tensor set");
+    if (!h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "no factors set");
+    if (W && h->krp_mode != mode) return fail(h, CPALS_ERR_STATE, "%s", "W needs cpals_krp_qr on this mode first");
+    CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, mode), "refresh QR");
+    CUDA_OR_FAIL(h, cpals::multi_ttm(h, mode, h->Q), "Multi-TTM");
+    const int64_t In = h->dims[mode];
+    if (W) CUDA_OR_FAIL(h, cpals::gemm_nn(h, h->Yn, h->Q0, h->W, In, h->RN1, h->R), "apply Q0");
+    if (Y) CUDA_OR_FAIL(h, cudaMemcpyAsync(Y, h->Yn, sizeof(double) * In * h->RN1, kind_out(mem), h->stream), "copy Y");
+    if (W) CUDA_OR_FAIL(h, cudaMemcpyAsync(W, h->W, sizeof(double) * In * h->R, kind_out(mem), h->stream), "copy W");
+    if (mem == CPALS_MEM_HOST) return take_status(h);
+    return CPALS_OK;
+}
+
+int cpals_ttm_first(cpals_handle* hh, int mode)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (mode < 0 || mode >= h->N) return fail(h, CPALS_ERR_ARG, "%s", "bad mode");
+    if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
+    CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, mode), "refresh QR");
+    CUDA_OR_FAIL(h, cpals::ttm_first(h, mode), "first TTM");
+    return CPALS_OK;
+}
+
+int cpals_mttkrp(cpals_handle* hh, int mode, double* M, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (mode < 0 || mode >= h->N || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad mode or mem flag");
+    if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
+    CUDA_OR_FAIL(h, cpals::mttkrp(h, mode), "MTTKRP");
+    if (M) CUDA_OR_FAIL(h, cudaMemcpyAsync(M, h->M, sizeof(double) * h->dims[mode] * h->R, kind_out(mem), h->stream),
+                        "copy M");
+    if (mem == CPALS_MEM_HOST) return take_status(h);
+    return CPALS_OK;
+}
+
+int cpals_solve_mode(cpals_handle* hh, int mode, int solve, double svd_rtol)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (mode < 0 || mode >= h->N) return fail(h, CPALS_ERR_ARG, "%s", "bad mode");
+    if (solve < CPALS_SOLVE_QR || solve > CPALS_SOLVE_NORMAL) return fail(h, CPALS_ERR_ARG, "%s", "bad solve kind");
+    if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
+    CUDA_OR_FAIL(h, mode_update(h, mode, solve, svd_rtol), "mode update");
+    h->last_sweep_solve = -1;
+    return CPALS_OK;
+}
+
+int cpals_iterate(cpals_handle* hh, int iters, double tol, int solve, double svd_rtol, int* done, double* fits_host)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (done) *done = 0;
+    if (iters < 0 || tol < 0.0) return fail(h, CPALS_ERR_ARG, "%s", "iters and tol must be >= 0");
+    if (solve < CPALS_SOLVE_QR || solve > CPALS_SOLVE_NORMAL) return fail(h, CPALS_ERR_ARG, "%s", "bad solve kind");
+    if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
+    if (iters == 0) return CPALS_OK;
+    // derived data valid for every mode, so that one captured sweep fits all
+    CUDA_OR_FAIL(h, refresh_derived(h, solve, -1), "refresh derived factors");
+    CUDA_OR_FAIL(h, cudaMemsetAsync(h->d_fit_count, 0, sizeof(int), h->stream), "reset fit count");
+    if (h->graph[solve] && h->graph_rtol[solve] != svd_rtol) {
+        cudaGraphExecDestroy(h->graph[solve]);
+        h->graph[solve] = nullptr;
+    }
+    if (!h->graph[solve]) {
+        // capture one sweep
+        cudaStream_t cap = h->stream;
+        bool own = false;
+        if (cap == nullptr) {
+            CUDA_OR_FAIL(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+            own = true;
+            CUDA_OR_FAIL(h, cudaDeviceSynchronize(), "sync before capture");
+        }
+        cudaStream_t saved = h->stream;
+        h->stream = cap;
+        const int64_t l0 = h->launches;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e2 = cudaSuccess;
+        if (e == cudaSuccess) {
+            e2 = sweep(h, solve, svd_rtol);
+            e = cudaStreamEndCapture(cap, &g);
+        }
+        h->stream = saved;
+        if (own) cudaStreamDestroy(cap);
+        if (e2 != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, e2, "capture sweep"); }
+        CUDA_OR_FAIL(h, e, "end capture");
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_OR_FAIL(h, e, "instantiate sweep graph");
+        h->graph[solve] = ge;
+        h->graph_rtol[solve] = svd_rtol;
+        h->graph_nodes[solve] = h->launches - l0;
+        h->launches = l0;
+    }
+    int ran = 0;
+    double prev = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        CUDA_OR_FAIL(h, cudaGraphLaunch(h->graph[solve], h->stream), "launch sweep graph");
+        h->launches += h->graph_nodes[solve];
+        ++ran;
+        if (tol > 0.0) {
+            double f = 0.0;
+            CUDA_OR_FAIL(h, cudaMemcpyAsync(&f, h->d_fit + h->fit_cap, sizeof(double), cudaMemcpyDeviceToHost,
+                                            h->stream), "fit read");
+            int st = take_status(h);
+            if (st != CPALS_OK) { if (done) *done = ran; return st; }
+            if (it > 0 && fabs(f - prev) < tol) break;
+            prev = f;
+        }
+    }
+    h->last_sweep_solve = solve;
+    if (done) *done = ran;
+    if (fits_host) {
+        const int n = std::min(ran, h->fit_cap);
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(fits_host, h->d_fit, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream),
+                     "fit history read");
+    }
+    return take_status(h);
+}
+
+int cpals_fit(cpals_handle* hh, int direct, double* fit_host)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (!fit_host) return fail(h, CPALS_ERR_ARG, "%s", "fit_host is NULL");
+    if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
+    if (direct) {
+        double* d_res = h->d_fit + h->fit_cap;   // reuse the "last fit" slot for the residual
+        double res2 = 0.0;
+        CUDA_OR_FAIL(h, cpals::residual_direct(h, d_res), "direct residual");
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(&res2, d_res, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read");
+        int st = take_status(h);
+        if (st != CPALS_OK) return st;
+        *fit_host = 1.0 - sqrt(std::max(res2, 0.0)) / sqrt(h->normX2_host);
+        return CPALS_OK;
+    }
+    if (h->last_sweep_solve < 0) return fail(h, CPALS_ERR_STATE, "%s", "the efficient fit needs a finished sweep");
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(fit_host, h->d_fit + h->fit_cap, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                 "fit read");
+    return take_status(h);
+}
+
+int cpals_sync(cpals_handle* hh)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    return take_status(h);
+}
+
+int64_t cpals_launch_count(const cpals_handle* hh)
+{
+    const Handle* h = reinterpret_cast<const Handle*>(hh);
+    return h ? h->launches : -1;
+}
+
+int cpals_probe_fma_peak(double ms_target, double* fp64_tflops, double* fp32_tflops)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CPALS_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CPALS_ERR_CUDA;
+    const int blocks = sms * 4, threads = 256;
+    void* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * threads) != cudaSuccess) return CPALS_ERR_NOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double res[2] = {0, 0};
+    for (int which = 0; which < 2; ++which) {
+        int iters = which == 0 ? 2000 : 100000;
+        float ms = 0.f;
+        for (int rep = 0; rep < 8; ++rep) {
+            cudaEventRecord(e0);
+            if (which == 0) fma_probe_kernel<double><<<blocks, threads>>>((double*)out, iters, 0.999999, 1e-7);
+            else fma_probe_kernel<float><<<blocks, threads>>>((float*)out, iters, 0.999999f, 1e-7f);
+            cudaEventRecord(e1);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < 0.5 * ms_target && iters < (1 << 28)) { iters *= 2; continue; }
+            const double flops = 2.0 * 8 * (double)iters * blocks * threads;
+            res[which] = std::max(res[which], flops / (ms * 1e-3) / 1e12);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (cudaGetLastError() != cudaSuccess) return CPALS_ERR_CUDA;
+    if (fp64_tflops) *fp64_tflops = res[0];
+    if (fp32_tflops) *fp32_tflops = res[1];
+    return CPALS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// internal.cuh -- handle layout and kernel launchers shared by the CUDA
+// translation units of libcpals.  Not part of the public C-ABI (include/cpals.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/cpals.h"
+
+namespace cpals {
+
+constexpr int kMaxN = 8;
+constexpr int kMaxRank = 64;
+
+// Device status word values (a subset of cpals_status).
+constexpr int kStatusOk = 0;
+
+// ------------------------------------------------------------------ layout
+// A TTM over mode m of a tensor with (current) dims d views it as
+// [L, K, T] with L = prod_{k<m} d_k, K = d_m, T = prod_{k>m} d_k (Sec. 2.2).
+struct TtmShape {
+    int64_t L, K, T;
+};
+
+inline TtmShape ttm_shape(int N, const int64_t* d, int m) {
+    TtmShape s{1, d[m], 1};
+    for (int k = 0; k < m; ++k) s.L *= d[k];
+    for (int k = m + 1; k < N; ++k) s.T *= d[k];
+    return s;
+}
+
+// Decreasing-dimension TTM order of Sec. 3.2 (ties: higher mode first).
+inline void ttm_order(int N, const int64_t* dims, int n, int* order) {
+    int cnt = 0;
+    for (int m = 0; m < N; ++m)
+        if (m != n) order[cnt++] = m;
+    for (int a = 0; a < cnt; ++a)
+        for (int b = a + 1; b < cnt; ++b) {
+            int x = order[a], y = order[b];
+            if (dims[y] > dims[x] || (dims[y] == dims[x] && y > x)) { order[a] = y; order[b] = x; }
+        }
+}
+
+// ------------------------------------------------------------------ handle
+struct Handle {
+    int N = 0, R = 0, prec = CPALS_F64;
+    int64_t dims[kMaxN] = {0};
+    int64_t P = 0;        // prod dims
+    int64_t RN1 = 0;      // R^{N-1}
+    int64_t Imax = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+
+    // data tensor
+    const double* X64 = nullptr;
+    const float* X32 = nullptr;
+    double* X64_owned = nullptr;
+    float* X32_owned = nullptr;
+    bool have_X = false, have_factors = false;
+    double normX2_host = 0.0;
+
+    // factors and their QR / Gram (device, FP64)
+    double* A[kMaxN] = {nullptr};
+    double* Q[kMaxN] = {nullptr};
+    double* Rf[kMaxN] = {nullptr};
+    double* G[kMaxN] = {nullptr};
+    double* lambda = nullptr;
+    // host-side validity of the derived data of each factor (the QR for the
+    // QR/SVD solves, the Gram for the normal equations)
+    bool qr_valid[kMaxN] = {false};
+    bool gram_valid[kMaxN] = {false};
+
+    // per-mode-update buffers
+    double* V = nullptr;     // R^{N-1} x R
+    double* Q0 = nullptr;    // R^{N-1} x R
+    double* R0 = nullptr;    // R x R
+    double* Yn = nullptr;    // Imax x R^{N-1} (unfolding, FP64)
+    double* W = nullptr;     // Imax x R
+    double* Ahat = nullptr;  // Imax x R
+    double* M = nullptr;     // Imax x R (MTTKRP)
+    double* S = nullptr;     // R x R (Hadamard of Grams)
+    double* T = nullptr;     // R x R solve operator (SVD path)
+    int krp_mode = -1;       // mode whose Q0/R0 are current
+
+    // TTM intermediates (ping-pong), in the Multi-TTM's arithmetic type
+    void* tbuf[2] = {nullptr, nullptr};
+    int64_t tbuf_elems = 0;
+    // generic FP64 scratch for split reductions and TSQR
+    double* scratch = nullptr;
+    int64_t scratch_elems = 0;
+
+    // device scalars
+    int* d_status = nullptr;
+    double* d_normX2 = nullptr;
+    double* d_fit = nullptr;        // fit history ring
+    int* d_fit_count = nullptr;
+    int fit_cap = 0;
+    int last_sweep_solve = -1;      // solve kind of the last finished sweep
+
+    // graphs, one per solve kind
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    double graph_rtol[3] = {0, 0, 0};
+    int64_t graph_nodes[3] = {0, 0, 0};
+
+    int64_t launches = 0;
+    size_t owned_bytes = 0;
+    char err[512] = {0};
+};
+
+// ------------------------------------------------------------------ launchers
+// All launchers enqueue on h->stream, count their launches in h->launches
+// and return cudaGetLastError().
+
+// Multi-TTM (Alg. cp-als-qr Multi-TTM step): writes the FP64 unfolding Y_(n)
+// into h->Yn using Q_m = h->Q[m] (or the given override array).
+cudaError_t multi_ttm(Handle* h, int n, const double* const* Q);
+// Only the first TTM of the Multi-TTM of mode n (the pass over X).
+cudaError_t ttm_first(Handle* h, int n);
+// MTTKRP M_n = X_(n) Z_n (Alg. cp-als) into h->M.
+cudaError_t mttkrp(Handle* h, int n);
+// Squared Frobenius norm of X into h->d_normX2.
+cudaError_t norm2(Handle* h);
+// FP64 -> FP32 copy with round-to-nearest-even.
+cudaError_t cast_f64_f32(Handle* h, const double* src, float* dst, int64_t n);
+// Direct residual ||X - Xhat||^2 into *d_out.
+cudaError_t residual_direct(Handle* h, double* d_out);
+
+// Householder QR with explicit Q and diag(R) >= 0 (Sec. 2.1).  A is m x n
+// (lda = m), Q is m x n, R is n x n.  A may alias Q.
+cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R);
+// V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->V and its QR into h->Q0, h->R0.
+cudaError_t krp_qr(Handle* h, int n);
+// C (m x n) = A (m x k) * B (k x n), FP64, column-major.
+cudaError_t gemm_nn(Handle* h, const double* A, const double* B, double* C, int64_t m, int64_t k, int64_t n);
+// Solve Ahat R0^T = W (QR) or Ahat = W U pinv(S) V^T (SVD) into h->Ahat.
+cudaError_t solve_qr(Handle* h, int64_t In);
+cudaError_t solve_svd(Handle* h, int64_t In, double rtol);
+// S_n = Hadamard product of the other Grams, then Cholesky solve Ahat S = M.
+cudaError_t solve_normal(Handle* h, int n);
+// Normalise columns of h->Ahat into A_n and lambda; then QR and Gram of A_n.
+cudaError_t normalize_and_refactor(Handle* h, int n);
+// Gram G = A^T A for an I x R factor.
+cudaError_t gram(Handle* h, const double* A, int64_t I, double* G);
+// Efficient fit after the last mode of a sweep; appends to the fit ring.
+cudaError_t fit_efficient(Handle* h, int solve);
+
+}  // namespace cpals
+
+#define CPALS_CUDA_TRY(expr)                                  \
+    do {                                                      \
+        cudaError_t _e = (expr);                              \
+        if (_e != cudaSuccess) return _e;                     \
+    } while (0)

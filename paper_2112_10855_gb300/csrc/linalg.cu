@@ -1,0 +1,698 @@
+// linalg.cu -- the small FP64 linear algebra of a CP-ALS-QR mode update
+// (Alg. cp-als-qr): Householder QR of the factors and of the Khatri-Rao
+// product V_n (Sec. 3.1, Eq. Z_qr), W_n = Y_(n) Q0, the R0 substitution or the
+// truncated SVD solve, column normalisation, Grams and Cholesky for the
+// normal-equations baseline (Alg. cp-als), and the efficient fit (Sec. 3.3.1).
+//
+// FP64 on this part runs at 2 DFMA/clk/SM, so every step that is not O(R^3)
+// is spread over many CTAs: tall QRs go through a recursive TSQR whose leaves
+// are Householder QRs in shared memory, and the GEMM and fit reductions are
+// split over row blocks and then reduced in a fixed order (deterministic).
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace cpals {
+
+namespace {
+
+constexpr int kQrThreads = 256;
+constexpr double kEps = 2.220446049250313e-16;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- Householder
+// CTA b factors rows [off_b, off_{b+1}) of the m x n matrix A (lda), with
+// off_b = b*m/nb, into an explicit Q_b (written to the same rows of Qout, ldq)
+// and R_b (written to rows [b*n, (b+1)*n) of Rout, ldr).  Reflectors follow
+// LAPACK's dlarfg form H = I - tau v v^T with v(0) = 1; the diagonal of R is
+// made non-negative by flipping the matching row of R and column of Q.
+__global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
+    const double* __restrict__ A, int64_t lda, int64_t m, int n, int nb, double* __restrict__ Qout,
+    int64_t ldq, double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    extern __shared__ double sm[];
+    const int b = blockIdx.x;
+    const int64_t off = (int64_t)b * m / nb, end = (int64_t)(b + 1) * m / nb;
+    const int mb = (int)(end - off);
+    double* W = sm;                       // mb x n (reflectors below the diagonal, R above)
+    double* Qs = sm + (size_t)mb * n;     // mb x n
+    double* tau = Qs + (size_t)mb * n;    // n
+    double* red = tau + n;                // 32 scratch
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kQrThreads / 32;
+
+    for (int64_t e = tid; e < (int64_t)mb * n; e += kQrThreads) {
+        const int j = (int)(e / mb), i = (int)(e - (int64_t)j * mb);
+        W[e] = A[(off + i) + lda * j];
+    }
+    __syncthreads();
+
+    const int kmax = min(mb, n);
+    for (int j = 0; j < kmax; ++j) {
+        // norm of W(j+1:mb, j) -- warp 0
+        if (warp == 0) {
+            double s = 0.0;
+            for (int i = j + 1 + lane; i < mb; i += 32) s = fma(W[i + mb * j], W[i + mb * j], s);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double alpha = W[j + mb * j];
+                double t = 0.0, scale = 0.0, beta = alpha;
+                if (s > 0.0) {
+                    const double nrm = sqrt(fma(alpha, alpha, s));
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    t = (beta - alpha) / beta;
+                    scale = 1.0 / (alpha - beta);
+                }
+                tau[j] = t;
+                red[0] = scale;
+                W[j + mb * j] = beta;
+            }
+        }
+        __syncthreads();
+        const double scale = red[0];
+        if (tau[j] != 0.0)
+            for (int i = j + 1 + tid; i < mb; i += kQrThreads) W[i + mb * j] *= scale;
+        __syncthreads();
+        // apply H_j to columns j+1..n-1 (one warp per column)
+        const double tj = tau[j];
+        if (tj != 0.0) {
+            for (int k = j + 1 + warp; k < n; k += nwarps) {
+                double s = 0.0;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    s = fma(v, W[i + mb * k], s);
+                }
+                s = warp_sum(s) * tj;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    W[i + mb * k] = fma(-s, v, W[i + mb * k]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int j = kmax; j < n; ++j) if (tid == 0) tau[j] = 0.0;
+    // explicit Q = H_0 ... H_{k-1} [I; 0], backward accumulation
+    for (int64_t e = tid; e < (int64_t)mb * n; e += kQrThreads) {
+        const int j = (int)(e / mb), i = (int)(e - (int64_t)j * mb);
+        Qs[e] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = kmax - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        if (tj != 0.0) {
+            for (int k = j + warp; k < n; k += nwarps) {
+                double s = 0.0;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    s = fma(v, Qs[i + mb * k], s);
+                }
+                s = warp_sum(s) * tj;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    Qs[i + mb * k] = fma(-s, v, Qs[i + mb * k]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // sign convention diag(R) >= 0, write out
+    for (int64_t e = tid; e < (int64_t)mb * n; e += kQrThreads) {
+        const int j = (int)(e / mb), i = (int)(e - (int64_t)j * mb);
+        const double sgn = (j < kmax && W[j + mb * j] < 0.0) ? -1.0 : 1.0;
+        Qout[(off + i) + ldq * j] = sgn * Qs[e];
+    }
+    for (int e = tid; e < n * n; e += kQrThreads) {
+        const int j = e / n, i = e - j * n;     // R(i, j)
+        double v = 0.0;
+        if (i <= j && i < kmax) {
+            const double sgn = (W[i + mb * i] < 0.0) ? -1.0 : 1.0;
+            v = sgn * W[i + mb * j];
+        }
+        Rout[((int64_t)b * n + i) + ldr * j] = v;
+    }
+}
+
+// Qout(block rows of b) = Qi(block rows of b) * Qtop(b*n:(b+1)*n, :)  (TSQR combine)
+__global__ void tsqr_combine_kernel(const double* __restrict__ Qi, int64_t m, int n, int nb,
+                                    const double* __restrict__ Qtop, int64_t ldt, double* __restrict__ Qout,
+                                    const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t total = m * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / m, row = e - c * m;
+        // block of this row: largest b with b*m/nb <= row
+        int64_t b = (row * nb) / m;
+        while (b + 1 < nb && (b + 1) * m / nb <= row) ++b;
+        while (b > 0 && b * m / nb > row) --b;
+        const double* t = Qtop + b * n + ldt * c;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s = fma(Qi[row + m * k], t[k], s);
+        Qout[e] = s;
+    }
+}
+
+inline size_t qr_smem_bytes(int mb, int n) { return sizeof(double) * ((size_t)2 * mb * n + n + 32); }
+
+constexpr int kQrSmemLimitDoubles = 24000;   // 2*mb*n doubles of the leaf QR (<= ~192 KB)
+
+// ---------------------------------------------------------------- Khatri-Rao
+struct RPtrs {
+    const double* R[kMaxN];
+};
+
+// V(row, r) = prod_{m != n} R_m(i_m, r), row = sum_{m != n} i_m R^{pos(m)} (mode 0 fastest).
+__global__ void krp_kernel(RPtrs rp, int N, int n, int R, int64_t rows, double* __restrict__ V,
+                           const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t total = rows * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / rows, row = e - r * rows;
+        int64_t rem = row;
+        double p = 1.0;
+        for (int m = 0; m < N; ++m) {
+            if (m == n) continue;
+            const int64_t i = rem % R;
+            rem /= R;
+            p *= rp.R[m][i + (int64_t)R * r];
+        }
+        V[e] = p;
+    }
+}
+
+// ---------------------------------------------------------------- GEMM (split-K)
+// C (m x n) = A (m x k) B (k x n).  Block: 32 rows x 8 column groups; blockIdx.y
+// splits k.  With ks > 1 the partials go to part[ks][m][n] and a second kernel
+// sums them in split order.
+constexpr int kGemmRows = 32;
+constexpr int kGemmColGroups = 8;
+
+__global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                                      double* __restrict__ out, int64_t m, int64_t k, int64_t n,
+                                                      int64_t kchunk, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t row = (int64_t)blockIdx.x * kGemmRows + (threadIdx.x & 31);
+    const int cg = threadIdx.x >> 5;
+    const int64_t k0 = (int64_t)blockIdx.y * kchunk;
+    const int64_t k1 = min(k, k0 + kchunk);
+    double acc[kMaxRank / kGemmColGroups];
+#pragma unroll
+    for (int q = 0; q < kMaxRank / kGemmColGroups; ++q) acc[q] = 0.0;
+    if (row < m) {
+        for (int64_t p = k0; p < k1; ++p) {
+            const double a = A[row + m * p];
+#pragma unroll
+            for (int q = 0; q < kMaxRank / kGemmColGroups; ++q) {
+                const int64_t j = cg + (int64_t)kGemmColGroups * q;
+                if (j < n) acc[q] = fma(a, B[p + k * j], acc[q]);
+            }
+        }
+        double* o = out + (int64_t)blockIdx.y * m * n;
+#pragma unroll
+        for (int q = 0; q < kMaxRank / kGemmColGroups; ++q) {
+            const int64_t j = cg + (int64_t)kGemmColGroups * q;
+            if (j < n) o[row + m * j] = acc[q];
+        }
+    }
+}
+
+__global__ void sum_splits_kernel(const double* __restrict__ part, int ks, int64_t mn, double* __restrict__ C,
+                                  const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < ks; ++q) s += part[(int64_t)q * mn + e];
+        C[e] = s;
+    }
+}
+
+// ---------------------------------------------------------------- solves
+// Ahat R0^T = W by substitution, one thread per row.  Singularity test:
+// |R0(k,k)| <= R * eps * max_j |R0(j,j)| sets the status word and writes nothing.
+__global__ void trsm_qr_kernel(const double* __restrict__ W, const double* __restrict__ R0, int64_t I, int R,
+                               double* __restrict__ Ahat, int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double r0[kMaxRank * kMaxRank];
+    __shared__ int singular;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) r0[e] = R0[e];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double dmax = 0.0;
+        for (int k = 0; k < R; ++k) dmax = fmax(dmax, fabs(r0[k + R * k]));
+        int s = 0;
+        for (int k = 0; k < R; ++k)
+            if (!(fabs(r0[k + R * k]) > (double)R * kEps * dmax)) s = 1;
+        singular = s;
+        if (s && blockIdx.x == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_SINGULAR);
+    }
+    __syncthreads();
+    if (singular) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+        double x[kMaxRank];
+        for (int k = R - 1; k >= 0; --k) {
+            double s = W[i + I * k];
+            for (int j = k + 1; j < R; ++j) s = fma(-r0[k + R * j], x[j], s);
+            x[k] = s / r0[k + R * k];
+        }
+        for (int k = 0; k < R; ++k) Ahat[i + I * k] = x[k];
+    }
+}
+
+// One-sided Jacobi SVD of R0 (Hestenes), then T = U pinv(Sigma) V^T keeping
+// sigma_j > rtol * sigma_max.  Pairs are visited in round-robin order so that
+// the R/2 rotations of a round are independent (one warp per pair).
+__global__ void __launch_bounds__(256) jacobi_pinv_kernel(const double* __restrict__ R0, int R, double rtol,
+                                                          double* __restrict__ T, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    extern __shared__ double jsm[];
+    double* B = jsm;                          // R x Rp, leading dimension R
+    double* V = jsm + kMaxRank * kMaxRank;    // R x Rp
+    double* sig = V + kMaxRank * kMaxRank;    // R
+    __shared__ int rotated;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int Rp = (R + 1) & ~1;   // padded to even; column R (if any) is a zero dummy
+    for (int e = tid; e < Rp * R; e += blockDim.x) {
+        const int j = e / R, i = e - j * R;
+        B[i + R * j] = (j < R) ? R0[i + R * j] : 0.0;
+    }
+    for (int e = tid; e < Rp * Rp; e += blockDim.x) {
+        const int j = e / Rp, i = e - j * Rp;
+        if (i < R && j < Rp) V[i + R * j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        if (tid == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < Rp - 1; ++round) {
+            for (int pi = warp; pi < Rp / 2; pi += nwarps) {
+                // round-robin pairing: position 0 fixed, others rotate
+                int a = (pi == 0) ? 0 : 1 + (pi - 1 + round) % (Rp - 1);
+                int b = 1 + (Rp - 2 - pi + round) % (Rp - 1);
+                int p = min(a, b), q = max(a, b);
+                if (q >= R) continue;   // dummy column
+                double sa = 0.0, sb = 0.0, sg = 0.0;
+                for (int i = lane; i < R; i += 32) {
+                    const double bp = B[i + R * p], bq = B[i + R * q];
+                    sa = fma(bp, bp, sa);
+                    sb = fma(bq, bq, sb);
+                    sg = fma(bp, bq, sg);
+                }
+                sa = warp_sum(sa); sb = warp_sum(sb); sg = warp_sum(sg);
+                if (sg == 0.0 || fabs(sg) <= kEps * sqrt(sa * sb)) continue;
+                const double zeta = (sb - sa) / (2.0 * sg);
+                const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int i = lane; i < R; i += 32) {
+                    const double bp = B[i + R * p], bq = B[i + R * q];
+                    B[i + R * p] = c * bp - s * bq;
+                    B[i + R * q] = s * bp + c * bq;
+                    const double vp = V[i + R * p], vq = V[i + R * q];
+                    V[i + R * p] = c * vp - s * vq;
+                    V[i + R * q] = s * vp + c * vq;
+                }
+                if (lane == 0) rotated = 1;
+            }
+            __syncthreads();
+        }
+        const int any = rotated;
+        __syncthreads();
+        if (!any) break;
+    }
+    for (int j = warp; j < R; j += nwarps) {
+        double s = 0.0;
+        for (int i = lane; i < R; i += 32) s = fma(B[i + R * j], B[i + R * j], s);
+        s = warp_sum(s);
+        if (lane == 0) sig[j] = sqrt(s);
+    }
+    __syncthreads();
+    double smax = 0.0;
+    for (int j = 0; j < R; ++j) smax = fmax(smax, sig[j]);
+    for (int e = tid; e < R * R; e += blockDim.x) {
+        const int bcol = e / R, a = e - bcol * R;   // T(a, bcol) = sum_j B(a,j) V(bcol,j) / sig_j^2
+        double s = 0.0;
+        for (int j = 0; j < R; ++j)
+            if (sig[j] > rtol * smax && sig[j] > 0.0) s = fma(B[a + R * j] / (sig[j] * sig[j]), V[bcol + R * j], s);
+        T[a + R * bcol] = s;
+    }
+}
+
+// S = Hadamard product of the Grams G_m, m != n; then its Cholesky factor L
+// (lower) into Lout.  Not SPD sets the status word.
+struct GPtrs {
+    const double* G[kMaxN];
+};
+
+__global__ void hadamard_cholesky_kernel(GPtrs gp, int N, int n, int R, double* __restrict__ S,
+                                         double* __restrict__ Lout, int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double L[kMaxRank * kMaxRank];
+    __shared__ int bad;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < R * R; e += blockDim.x) {
+        double s = 1.0;
+        for (int m = 0; m < N; ++m)
+            if (m != n) s *= gp.G[m][e];
+        S[e] = s;
+        L[e] = s;
+    }
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < R; ++j) {
+        if (tid == 0) {
+            double d = L[j + R * j];
+            for (int k = 0; k < j; ++k) d -= L[j + R * k] * L[j + R * k];
+            if (!(d > 0.0)) bad = 1;
+            L[j + R * j] = (d > 0.0) ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        for (int i = j + 1 + tid; i < R; i += blockDim.x) {
+            double s = L[i + R * j];
+            for (int k = 0; k < j; ++k) s -= L[i + R * k] * L[j + R * k];
+            L[i + R * j] = s / L[j + R * j];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_SINGULAR);
+        return;
+    }
+    for (int e = tid; e < R * R; e += blockDim.x) {
+        const int j = e / R, i = e - j * R;
+        Lout[e] = (i >= j) ? L[e] : 0.0;
+    }
+}
+
+// Ahat S = M with S = L L^T: per row, L y = m, L^T x = y.
+__global__ void chol_rows_kernel(const double* __restrict__ Mm, const double* __restrict__ Lg, int64_t I, int R,
+                                 double* __restrict__ Ahat, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double L[kMaxRank * kMaxRank];
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) L[e] = Lg[e];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+        double y[kMaxRank];
+        for (int k = 0; k < R; ++k) {
+            double s = Mm[i + I * k];
+            for (int j = 0; j < k; ++j) s = fma(-L[k + R * j], y[j], s);
+            y[k] = s / L[k + R * k];
+        }
+        for (int k = R - 1; k >= 0; --k) {
+            double s = y[k];
+            for (int j = k + 1; j < R; ++j) s = fma(-L[j + R * k], y[j], s);
+            y[k] = s / L[k + R * k];
+        }
+        for (int k = 0; k < R; ++k) Ahat[i + I * k] = y[k];
+    }
+}
+
+// lambda_r = ||Ahat(:, r)||_2, A(:, r) = Ahat(:, r) / lambda_r (one CTA per column).
+__global__ void normalize_kernel(const double* __restrict__ Ahat, int64_t I, double* __restrict__ A,
+                                 double* __restrict__ lambda, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double sh[32];
+    __shared__ double lam;
+    const int r = blockIdx.x;
+    const double* col = Ahat + I * r;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < I; i += blockDim.x) s = fma(col[i], col[i], s);
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) { lam = sqrt(v); lambda[r] = lam; }
+    }
+    __syncthreads();
+    const double l = lam;
+    for (int64_t i = threadIdx.x; i < I; i += blockDim.x) A[i + I * r] = (l > 0.0) ? col[i] / l : col[i];
+}
+
+// G = A^T A (R x R), one thread per entry, summing over the I rows in order.
+__global__ void gram_kernel(const double* __restrict__ A, int64_t I, int R, double* __restrict__ G,
+                            const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= R * R) return;
+    const int b = e / R, a = e - b * R;
+    double s = 0.0;
+    for (int64_t i = 0; i < I; ++i) s = fma(A[i + I * a], A[i + I * b], s);
+    G[e] = s;
+}
+
+// ---------------------------------------------------------------- fit (Sec. 3.3.1)
+// Partial inner products over row blocks of 32:
+//  QR:     sum_{i,k} W(i,k) (Ahat R0^T)(i,k)
+//  NORMAL: sum_{i,k} M(i,k) Ahat(i,k)
+__global__ void fit_inner_kernel(const double* __restrict__ Wm, const double* __restrict__ Ahat,
+                                 const double* __restrict__ R0, int64_t I, int R, int qr,
+                                 double* __restrict__ part, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double sh[32];
+    double s = 0.0;
+    const int64_t i = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    if (i < I) {
+        for (int k = (threadIdx.x >> 5); k < R; k += (blockDim.x >> 5)) {
+            double v;
+            if (qr) {
+                v = 0.0;
+                for (int j = 0; j < R; ++j) v = fma(Ahat[i + I * j], R0[k + R * j], v);
+            } else {
+                v = Ahat[i + I * k];
+            }
+            s = fma(Wm[i + I * k], v, s);
+        }
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// Final: inner = sum of partials; model norm
+//  QR:     <R0^T R0, diag(l) R_N^T R_N diag(l)>
+//  NORMAL: <S_N, diag(l) G_N diag(l)>
+// fit = 1 - sqrt(max(||X||^2 - 2 inner + nrm, 0)) / ||X||, appended to the ring.
+__global__ void fit_final_kernel(const double* __restrict__ part, int nparts, const double* __restrict__ R0orS,
+                                 const double* __restrict__ RNorG, const double* __restrict__ lambda, int R, int qr,
+                                 const double* __restrict__ normX2, double* __restrict__ ring, int cap,
+                                 int* __restrict__ count, double* __restrict__ last, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double sh[32];
+    double nrm = 0.0;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+        const int b = e / R, a = e - b * R;
+        double g0, gN;
+        if (qr) {
+            g0 = 0.0; gN = 0.0;
+            for (int k = 0; k < R; ++k) {
+                g0 = fma(R0orS[k + R * a], R0orS[k + R * b], g0);
+                gN = fma(RNorG[k + R * a], RNorG[k + R * b], gN);
+            }
+        } else {
+            g0 = R0orS[e];
+            gN = RNorG[e];
+        }
+        nrm = fma(g0 * lambda[a], gN * lambda[b], nrm);
+    }
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
+        double inner = 0.0;
+        for (int p = 0; p < nparts; ++p) inner += part[p];
+        double res2 = *normX2 - 2.0 * inner + tot;
+        if (res2 < 0.0) res2 = 0.0;
+        const double f = 1.0 - sqrt(res2) / sqrt(*normX2);
+        const int c = *count;
+        ring[c % cap] = f;
+        *count = c + 1;
+        *last = f;
+    }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int num_sms)
+{
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+// Recursive TSQR.  ws must hold 3*m*n doubles for the top call (geometric sum).
+cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, double* ws, int64_t ws_elems)
+{
+    // leaf: the whole matrix in one CTA's shared memory when it is short
+    const int64_t leaf_rows = std::max<int64_t>(2 * n, 32);
+    if (m <= std::max<int64_t>(leaf_rows, 2 * (int64_t)n) || (int64_t)2 * m * n <= 1024) {
+        const size_t smem = qr_smem_bytes((int)m, n);
+        hh_qr_blocks_kernel<<<1, kQrThreads, smem, h->stream>>>(A, m, m, n, 1, Q, m, R, n, h->d_status);
+        h->launches++;
+        return cudaGetLastError();
+    }
+    int64_t nb = (m + leaf_rows - 1) / leaf_rows;
+    if (nb > 4096) nb = 4096;
+    // each block must keep >= n rows: balanced blocks have floor(m/nb) rows
+    while (nb > 1 && m / nb < n) --nb;
+    const int64_t mbmax = (m + nb - 1) / nb;
+    if ((int64_t)2 * mbmax * n > kQrSmemLimitDoubles) return cudaErrorInvalidValue;
+    double* Qi = ws;                        // m x n
+    double* Rs = Qi + m * n;                // (nb*n) x n
+    double* Qt = Rs + nb * n * n;           // (nb*n) x n
+    double* rest = Qt + nb * n * n;
+    const int64_t used = m * n + 2 * nb * n * n;
+    if (used > ws_elems) return cudaErrorInvalidValue;
+    hh_qr_blocks_kernel<<<(unsigned)nb, kQrThreads, qr_smem_bytes((int)mbmax, n), h->stream>>>(
+        A, m, m, n, (int)nb, Qi, m, Rs, nb * n, h->d_status);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    CPALS_CUDA_TRY(tsqr(h, Rs, nb * n, n, Qt, R, rest, ws_elems - used));
+    tsqr_combine_kernel<<<grid_for(m * n, 256, h->num_sms), 256, 0, h->stream>>>(Qi, m, n, (int)nb, Qt, nb * n, Q,
+                                                                                  h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        CPALS_CUDA_TRY(cudaFuncSetAttribute(hh_qr_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(double) * (kQrSmemLimitDoubles + 64 + 32))));
+        attr_set = true;
+    }
+    return tsqr(h, A, m, n, Q, R, h->scratch, h->scratch_elems);
+}
+
+cudaError_t krp_qr(Handle* h, int n)
+{
+    RPtrs rp;
+    for (int m = 0; m < h->N; ++m) rp.R[m] = h->Rf[m];
+    const int64_t total = h->RN1 * h->R;
+    krp_kernel<<<grid_for(total, 256, h->num_sms), 256, 0, h->stream>>>(rp, h->N, n, h->R, h->RN1, h->V,
+                                                                         h->d_status);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    return householder_qr(h, h->V, h->RN1, h->R, h->Q0, h->R0);
+}
+
+cudaError_t gemm_nn(Handle* h, const double* A, const double* B, double* C, int64_t m, int64_t k, int64_t n)
+{
+    const int64_t mt = (m + kGemmRows - 1) / kGemmRows;
+    int64_t ks = 1;
+    const int64_t want = (int64_t)h->num_sms * 2;
+    if (mt < want && k >= 64) {
+        ks = std::min<int64_t>((want + mt - 1) / mt, k / 32);
+        const int64_t cap = h->scratch_elems / std::max<int64_t>(m * n, 1);
+        if (ks > cap) ks = cap;
+        if (ks < 1) ks = 1;
+    }
+    const int64_t kchunk = (k + ks - 1) / ks;
+    ks = (k + kchunk - 1) / kchunk;
+    dim3 grid((unsigned)mt, (unsigned)ks);
+    if (ks == 1) {
+        gemm_nn_kernel<<<grid, 256, 0, h->stream>>>(A, B, C, m, k, n, kchunk, h->d_status);
+        h->launches++;
+        return cudaGetLastError();
+    }
+    gemm_nn_kernel<<<grid, 256, 0, h->stream>>>(A, B, h->scratch, m, k, n, kchunk, h->d_status);
+    sum_splits_kernel<<<grid_for(m * n, 256, h->num_sms), 256, 0, h->stream>>>(h->scratch, (int)ks, m * n, C,
+                                                                                h->d_status);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t solve_qr(Handle* h, int64_t In)
+{
+    trsm_qr_kernel<<<grid_for(In, 128, h->num_sms), 128, 0, h->stream>>>(h->W, h->R0, In, h->R, h->Ahat,
+                                                                          h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t solve_svd(Handle* h, int64_t In, double rtol)
+{
+    if (!(rtol > 0.0)) rtol = (double)h->R * kEps;
+    constexpr size_t smem = sizeof(double) * (2 * kMaxRank * kMaxRank + kMaxRank);
+    static bool attr_set = false;
+    if (!attr_set) {
+        CPALS_CUDA_TRY(cudaFuncSetAttribute(jacobi_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        attr_set = true;
+    }
+    jacobi_pinv_kernel<<<1, 256, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    return gemm_nn(h, h->W, h->T, h->Ahat, In, h->R, h->R);
+}
+
+cudaError_t solve_normal(Handle* h, int n)
+{
+    GPtrs gp;
+    for (int m = 0; m < h->N; ++m) gp.G[m] = h->G[m];
+    hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status);
+    chol_rows_kernel<<<grid_for(h->dims[n], 128, h->num_sms), 128, 0, h->stream>>>(h->M, h->T, h->dims[n], h->R,
+                                                                                   h->Ahat, h->d_status);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t gram(Handle* h, const double* A, int64_t I, double* G)
+{
+    const int RR = h->R * h->R;
+    gram_kernel<<<(RR + 127) / 128, 128, 0, h->stream>>>(A, I, h->R, G, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t normalize_and_refactor(Handle* h, int n)
+{
+    normalize_kernel<<<h->R, 256, 0, h->stream>>>(h->Ahat, h->dims[n], h->A[n], h->lambda, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t fit_efficient(Handle* h, int solve)
+{
+    const int n = h->N - 1;
+    const int64_t I = h->dims[n];
+    const int qr = (solve != CPALS_SOLVE_NORMAL);
+    const unsigned nb = (unsigned)((I + 31) / 32);
+    fit_inner_kernel<<<nb, 256, 0, h->stream>>>(qr ? h->W : h->M, h->Ahat, h->R0, I, h->R, qr, h->scratch,
+                                                h->d_status);
+    fit_final_kernel<<<1, 256, 0, h->stream>>>(h->scratch, (int)nb, qr ? h->R0 : h->S, qr ? h->Rf[n] : h->G[n],
+                                               h->lambda, h->R, qr, h->d_normX2, h->d_fit, h->fit_cap,
+                                               h->d_fit_count, h->d_fit + h->fit_cap, h->d_status);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace cpals

@@ -1,0 +1,380 @@
+// ttm.cu -- passes over the data tensor X: Multi-TTM (Eq. multittm, Alg.
+// cp-als-qr Multi-TTM step), MTTKRP (Alg. cp-als), ||X||^2 and the direct
+// residual (Sec. 3.3.1).
+//
+// A single TTM over mode m views the current tensor as [L, K, T] (L = prod of
+// the dims before m, K = I_m, T = prod of the dims after m) and computes
+//     Out(l, r, t) = sum_k In(l, k, t) * Q(k, r),     Q = Q_m (K x R)
+// i.e. Y = X x_m Q_m^T.  The Multi-TTM applies the N-1 TTMs in
+// decreasing-dimension order (Sec. 3.2), ping-ponging between two workspace
+// buffers; the first one streams X from HBM, the later ones read the shrunken
+// intermediate (R/I of the previous size), which usually stays in L2.
+#include "internal.cuh"
+
+namespace cpals {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kKC = 32;   // k-chunk of Q staged in shared memory
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return fma(a, b, c); }
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+// One thread per flattened output row f = l + L*t; RC output columns per
+// thread (grid.y covers R in chunks of RC).  Q(k, r) for a k-chunk is staged in
+// shared memory as qs[k][r] and read as a broadcast.  Loads of In along k are
+// coalesced across the warp whenever L >= 32; for small L each thread walks
+// its own fiber and the lines are reused from L1.
+template <typename T, int RC>
+__global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
+    const T* __restrict__ in, const double* __restrict__ Q, int64_t ldq, T* __restrict__ out,
+    int64_t L, int64_t K, int64_t Tn, int R, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ T qs[kKC][RC];
+    const int64_t rows = L * Tn;
+    const int64_t f = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int r0 = blockIdx.y * RC;
+    const int rc = min(RC, R - r0);
+    const bool active = f < rows;
+    int64_t t = 0, l = 0;
+    if (active) { t = f / L; l = f - t * L; }
+    const T* p = in + l + L * K * t;
+
+    T acc[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) acc[r] = T(0);
+
+    for (int64_t k0 = 0; k0 < K; k0 += kKC) {
+        const int kc = (int)((K - k0) < (int64_t)kKC ? (K - k0) : (int64_t)kKC);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kKC * RC; i += kThreads) {
+            const int kk = i / RC, rr = i - kk * RC;
+            qs[kk][rr] = (kk < kc && rr < rc) ? (T)Q[(k0 + kk) + ldq * (int64_t)(r0 + rr)] : T(0);
+        }
+        __syncthreads();
+        if (!active) continue;
+        const T* pk = p + L * k0;
+        int kk = 0;
+        for (; kk + 8 <= kc; kk += 8) {
+            T x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = __ldg(pk + L * (kk + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[r] = fma_t(x[u], qs[kk + u][r], acc[r]);
+        }
+        for (; kk < kc; ++kk) {
+            const T x = __ldg(pk + L * kk);
+#pragma unroll
+            for (int r = 0; r < RC; ++r) acc[r] = fma_t(x, qs[kk][r], acc[r]);
+        }
+    }
+    if (active) {
+        T* o = out + l + L * (int64_t)R * t;
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+            if (r < rc) o[L * (int64_t)(r0 + r)] = acc[r];
+    }
+}
+
+template <typename T>
+cudaError_t launch_ttm(Handle* h, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s, int R)
+{
+    const int64_t rows = s.L * s.T;
+    if (rows == 0) return cudaSuccess;
+    dim3 block(kThreads);
+    const int64_t gx = (rows + kThreads - 1) / kThreads;
+    if (R <= 4) {
+        dim3 grid((unsigned)gx, 1);
+        ttm_rows_kernel<T, 4><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
+    } else if (R <= 8) {
+        dim3 grid((unsigned)gx, 1);
+        ttm_rows_kernel<T, 8><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
+    } else if (R <= 16) {
+        dim3 grid((unsigned)gx, 1);
+        ttm_rows_kernel<T, 16><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
+    } else {
+        dim3 grid((unsigned)gx, (unsigned)((R + 31) / 32));
+        ttm_rows_kernel<T, 32><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
+    }
+    h->launches++;
+    return cudaGetLastError();
+}
+
+// Final Multi-TTM tensor (dims R for m != n, I_n at n; mode 0 fastest) to the
+// FP64 unfolding Y_(n): element e = a + Rn*(i + In*c) with a < Rn = R^n maps to
+// column a + Rn*c.
+template <typename T>
+__global__ void unfold_kernel(const T* __restrict__ in, double* __restrict__ Yn, int64_t Rn, int64_t In,
+                              int64_t total, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = e % Rn;
+        const int64_t q = e / Rn;
+        const int64_t i = q % In;
+        const int64_t c = q / In;
+        Yn[i + In * (a + Rn * c)] = (double)in[e];
+    }
+}
+
+// Diagonal contraction of the MTTKRP: after the first TTM one mode (position
+// cpos) holds the rank index r; contracting mode m with A_m(:, r) keeps r:
+//   Out(l, t) = sum_k In(l, k, t) * A(k, r(l, t)).
+template <typename T>
+__global__ void diag_contract_kernel(const T* __restrict__ in, const double* __restrict__ A, int64_t lda,
+                                     T* __restrict__ out, int64_t L, int64_t K, int64_t Tn, int r_in_l,
+                                     int64_t r_div, int R, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t rows = L * Tn;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < rows;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = f / L, l = f - t * L;
+        const int r = (int)(((r_in_l ? l : t) / r_div) % R);
+        const T* p = in + l + L * K * t;
+        const double* a = A + lda * r;
+        T acc = T(0);
+        for (int64_t k = 0; k < K; ++k) acc = fma_t(p[L * k], (T)a[k], acc);
+        out[f] = acc;
+    }
+}
+
+// out(i, r) = in[i*si + r*sr] as FP64 (I x R, column-major).
+template <typename T>
+__global__ void gather2d_kernel(const T* __restrict__ in, double* __restrict__ out, int64_t I, int R,
+                                int64_t si, int64_t sr, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t total = I * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / I, i = e - r * I;
+        out[e] = (double)in[i * si + r * sr];
+    }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int num_sms) {
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+template <typename T>
+const T* x_ptr(Handle* h);
+template <>
+const double* x_ptr<double>(Handle* h) { return h->X64; }
+template <>
+const float* x_ptr<float>(Handle* h) { return h->X32; }
+
+template <typename T>
+cudaError_t multi_ttm_impl(Handle* h, int n, const double* const* Q)
+{
+    const int N = h->N, R = h->R;
+    int order[kMaxN];
+    ttm_order(N, h->dims, n, order);
+    int64_t d[kMaxN];
+    for (int m = 0; m < N; ++m) d[m] = h->dims[m];
+    const T* in = x_ptr<T>(h);
+    int cur = 0;
+    for (int k = 0; k < N - 1; ++k) {
+        const int m = order[k];
+        const TtmShape s = ttm_shape(N, d, m);
+        T* out = (T*)h->tbuf[cur];
+        CPALS_CUDA_TRY(launch_ttm<T>(h, in, Q[m], h->dims[m], out, s, R));
+        d[m] = R;
+        in = out;
+        cur ^= 1;
+    }
+    int64_t Rn = 1;
+    for (int m = 0; m < n; ++m) Rn *= R;
+    const int64_t total = h->dims[n] * h->RN1;
+    unfold_kernel<T><<<grid_for(total, 256, h->num_sms), 256, 0, h->stream>>>(in, h->Yn, Rn, h->dims[n], total,
+                                                                               h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mttkrp_impl(Handle* h, int n)
+{
+    const int N = h->N, R = h->R;
+    int order[kMaxN];
+    ttm_order(N, h->dims, n, order);
+    int64_t d[kMaxN];
+    for (int m = 0; m < N; ++m) d[m] = h->dims[m];
+    // first contraction: a full TTM with A_c (cost 2 P R, as the MTTKRP of Alg. cp-als)
+    const int c = order[0];
+    TtmShape s = ttm_shape(N, d, c);
+    T* buf = (T*)h->tbuf[0];
+    CPALS_CUDA_TRY(launch_ttm<T>(h, x_ptr<T>(h), h->A[c], h->dims[c], buf, s, R));
+    d[c] = R;
+    const T* in = buf;
+    int cur = 1;
+    for (int k = 1; k < N - 1; ++k) {
+        const int m = order[k];
+        s = ttm_shape(N, d, m);
+        int64_t div = 1;
+        int r_in_l;
+        if (c < m) { r_in_l = 1; for (int q = 0; q < c; ++q) div *= d[q]; }
+        else { r_in_l = 0; for (int q = m + 1; q < c; ++q) div *= d[q]; }
+        T* out = (T*)h->tbuf[cur];
+        const int64_t rows = s.L * s.T;
+        diag_contract_kernel<T><<<grid_for(rows, 256, h->num_sms), 256, 0, h->stream>>>(
+            in, h->A[m], h->dims[m], out, s.L, s.K, s.T, r_in_l, div, R, h->d_status);
+        h->launches++;
+        CPALS_CUDA_TRY(cudaGetLastError());
+        d[m] = 1;
+        in = out;
+        cur ^= 1;
+    }
+    // remaining dims: I_n at n, R at c, ones elsewhere
+    int64_t sn = 1, sc = 1;
+    for (int q = 0; q < n; ++q) sn *= d[q];
+    for (int q = 0; q < c; ++q) sc *= d[q];
+    gather2d_kernel<T><<<grid_for(h->dims[n] * R, 256, h->num_sms), 256, 0, h->stream>>>(
+        in, h->M, h->dims[n], R, sn, sc, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reductions
+// Deterministic two-phase sum: fixed grid, per-block tree, then one block.
+constexpr int kRedBlocks = 1024;
+
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+template <typename T>
+__global__ void sumsq_partial_kernel(const T* __restrict__ x, int64_t n, double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)x[i];
+        s = fma(v, v, s);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void sum_final_kernel(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// (X - Xhat)^2 summed, Xhat(i) = sum_r lambda_r prod_m A_m(i_m, r).
+struct FactorPtrs {
+    const double* A[kMaxN];
+    int64_t dims[kMaxN];
+};
+
+template <typename T>
+__global__ void residual_partial_kernel(const T* __restrict__ x, int64_t P, int N, int R, FactorPtrs f,
+                                        const double* __restrict__ lambda, double* __restrict__ part)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t idx[kMaxN];
+        int64_t rem = e;
+        for (int m = 0; m < N; ++m) { idx[m] = rem % f.dims[m]; rem /= f.dims[m]; }
+        double xh = 0.0;
+        for (int r = 0; r < R; ++r) {
+            double p = lambda[r];
+            for (int m = 0; m < N; ++m) p *= f.A[m][idx[m] + f.dims[m] * r];
+            xh += p;
+        }
+        const double dlt = (double)x[e] - xh;
+        s = fma(dlt, dlt, s);
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void cast_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __double2float_rn(src[i]);
+}
+
+}  // namespace
+
+cudaError_t multi_ttm(Handle* h, int n, const double* const* Q)
+{
+    if (h->prec == CPALS_F64) return multi_ttm_impl<double>(h, n, Q);
+    return multi_ttm_impl<float>(h, n, Q);
+}
+
+cudaError_t ttm_first(Handle* h, int n)
+{
+    int order[kMaxN];
+    ttm_order(h->N, h->dims, n, order);
+    const TtmShape s = ttm_shape(h->N, h->dims, order[0]);
+    if (h->prec == CPALS_F64)
+        return launch_ttm<double>(h, h->X64, h->Q[order[0]], h->dims[order[0]], (double*)h->tbuf[0], s, h->R);
+    return launch_ttm<float>(h, h->X32, h->Q[order[0]], h->dims[order[0]], (float*)h->tbuf[0], s, h->R);
+}
+
+cudaError_t mttkrp(Handle* h, int n)
+{
+    if (h->prec == CPALS_F64) return mttkrp_impl<double>(h, n);
+    return mttkrp_impl<float>(h, n);
+}
+
+cudaError_t norm2(Handle* h)
+{
+    if (h->X64) sumsq_partial_kernel<double><<<kRedBlocks, 256, 0, h->stream>>>(h->X64, h->P, h->scratch);
+    else sumsq_partial_kernel<float><<<kRedBlocks, 256, 0, h->stream>>>(h->X32, h->P, h->scratch);
+    sum_final_kernel<<<1, 1024, 0, h->stream>>>(h->scratch, kRedBlocks, h->d_normX2);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t residual_direct(Handle* h, double* d_out)
+{
+    FactorPtrs f;
+    for (int m = 0; m < h->N; ++m) { f.A[m] = h->A[m]; f.dims[m] = h->dims[m]; }
+    if (h->X64)
+        residual_partial_kernel<double><<<kRedBlocks, 256, 0, h->stream>>>(h->X64, h->P, h->N, h->R, f, h->lambda,
+                                                                           h->scratch);
+    else
+        residual_partial_kernel<float><<<kRedBlocks, 256, 0, h->stream>>>(h->X32, h->P, h->N, h->R, f, h->lambda,
+                                                                          h->scratch);
+    sum_final_kernel<<<1, 1024, 0, h->stream>>>(h->scratch, kRedBlocks, d_out);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t cast_f64_f32(Handle* h, const double* src, float* dst, int64_t n)
+{
+    cast_kernel<<<grid_for(n, 256, h->num_sms), 256, 0, h->stream>>>(src, dst, n);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace cpals

@@ -1,0 +1,264 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Every case feeds both sides identical seeded inputs.  FP64 bars:
+  - Multi-TTM Y_(n), W_n, Q0/R0 and factor QR: relative Frobenius <= 1e-12;
+  - one mode update (A_n, lambda): <= 1e-10;
+  - fit per sweep: |gpu - oracle| <= 1e-10.
+Integer-valued inputs make the index bookkeeping bit-exact.  FP32 bars are
+stated per test (the error bound of an FP32 dot product of length K).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2112_10855_gb300 import cpals, inputs
+from tests import npforms as F
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def gaussian_problem(dims, R, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal(int(np.prod(dims)))
+    A = [np.asfortranarray(rng.standard_normal((d, R))) for d in dims]
+    return X, A
+
+
+def gpu_handle(dims, R, X, A=None, precision="f64", device_x=True):
+    h = cpals.CPALS(dims, R, precision)
+    if device_x:
+        h.set_tensor(torch.from_numpy(np.ascontiguousarray(X)).cuda())
+    else:
+        h.set_tensor(np.ascontiguousarray(X))
+    if A is not None:
+        h.set_factors([np.asfortranarray(a) for a in A])
+    return h
+
+
+# shapes spanning several 256-row tiles with ragged tails, all orders 2..5
+SHAPES = [((50, 33), 4), ((37, 29, 41), 5), ((23, 19, 17), 3), ((12, 11, 10, 9), 3), ((7, 6, 5, 4, 3), 2),
+          ((64, 64, 64), 16), ((40, 35, 30), 20), ((9, 8, 7), 7)]
+
+
+@pytest.mark.parametrize("dims,R", SHAPES)
+def test_multi_ttm_matches_oracle(cuda_lib, dims, R):
+    X, A = gaussian_problem(dims, R, seed=sum(dims) + R)
+    QR = [oracle.qr(a) for a in A]
+    h = gpu_handle(dims, R, X)
+    h.set_factor_qr([q for q, _ in QR], [r for _, r in QR])
+    for n in range(len(dims)):
+        Y, _ = h.multi_ttm(n)
+        ref = oracle.multi_ttm(X, dims, n, [q for q, _ in QR])
+        assert Y.shape == ref.shape
+        assert rel(Y, ref) <= 1e-12, (n, rel(Y, ref))
+
+
+@pytest.mark.parametrize("dims,R", [((5, 4, 3), 2), ((3, 4, 2, 3), 3), ((40, 30, 20), 6), ((300, 7), 5)])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_multi_ttm_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision):
+    # integer X and 0/1 Q: every partial sum is an integer below 2^24, exact in
+    # FP64 and FP32, so the two sides must agree bit for bit
+    P = int(np.prod(dims))
+    X = (np.arange(P) * 37 % 97 - 48).astype(np.float64)
+    rng = np.random.default_rng(7)
+    Q = [np.asfortranarray((rng.random((d, R)) < 0.5).astype(np.float64)) for d in dims]
+    Rm = [np.asfortranarray(np.triu(np.ones((R, R)))) for _ in dims]
+    h = gpu_handle(dims, R, X, precision=precision)
+    h.set_factor_qr(Q, Rm)
+    for n in range(len(dims)):
+        Y, _ = h.multi_ttm(n)
+        np.testing.assert_array_equal(Y, oracle.multi_ttm(X, dims, n, Q))
+
+
+@pytest.mark.parametrize("m,R", [(10, 10), (50, 5), (400, 10), (1000, 10), (3000, 20), (500, 64), (1, 1), (129, 64)])
+def test_factor_qr_matches_oracle(cuda_lib, m, R):
+    rng = np.random.default_rng(m + R)
+    A = np.asfortranarray(rng.standard_normal((m, R)))
+    dims = (m, R, R)
+    X = np.zeros(m * R * R)
+    h = gpu_handle(dims, R, X, [A, np.eye(R), np.eye(R)])
+    Q, Rm = h.get_factor_qr(0)
+    Qo, Ro = oracle.qr(A)
+    assert rel(Q, Qo) <= 1e-12 and rel(Rm, Ro) <= 1e-12
+    assert (np.diag(Rm) >= 0).all()
+
+
+@pytest.mark.parametrize("dims,R", [((6, 5, 7), 3), ((20, 20, 20), 10), ((12, 11, 10, 9), 5), ((30, 30, 30), 16),
+                                    ((7, 6, 5, 4, 3), 3), ((20, 20, 20, 20), 20)])
+def test_krp_qr_matches_oracle(cuda_lib, dims, R):
+    X, A = gaussian_problem(dims, R, seed=3)
+    o = oracle.OracleCPALS(X, dims, R)
+    o.set_factors(A)
+    h = gpu_handle(dims, R, X, A)
+    for n in range(len(dims)):
+        Q0, R0 = h.krp_qr(n)
+        Q0o, R0o = o.krp_qr(n)
+        assert rel(Q0, Q0o) <= 1e-12 and rel(R0, R0o) <= 1e-12, n
+
+
+@pytest.mark.parametrize("dims,R", [((37, 29, 41), 5), ((12, 11, 10, 9), 3), ((50, 33), 4)])
+def test_apply_q0_matches_oracle(cuda_lib, dims, R):
+    X, A = gaussian_problem(dims, R, seed=5)
+    for n in range(len(dims)):
+        o = oracle.OracleCPALS(X, dims, R)
+        o.set_factors(A)
+        o.update_mode(n, oracle.QR)
+        ref = o.last(n)
+        h = gpu_handle(dims, R, X, A)
+        h.krp_qr(n)
+        Y, W = h.multi_ttm(n, want_W=True)
+        assert rel(Y, ref["Y"]) <= 1e-12
+        assert rel(W, ref["W"]) <= 1e-12
+
+
+@pytest.mark.parametrize("solve", ["qr", "svd", "normal"])
+@pytest.mark.parametrize("dims,R", [((37, 29, 41), 5), ((12, 11, 10, 9), 3), ((60, 50, 40), 10)])
+def test_mode_update_matches_oracle(cuda_lib, solve, dims, R):
+    X, A = gaussian_problem(dims, R, seed=11)
+    osolve = {"qr": oracle.QR, "svd": oracle.SVD, "normal": oracle.NORMAL}[solve]
+    for n in range(len(dims)):
+        o = oracle.OracleCPALS(X, dims, R)
+        o.set_factors(A)
+        assert o.update_mode(n, osolve, 1e-12) == 0
+        h = gpu_handle(dims, R, X, A)
+        h.solve_mode(n, solve, 1e-12)
+        Ag, lam = h.get_factors()
+        assert rel(Ag[n], o.factor(n)) <= 1e-10, (n, rel(Ag[n], o.factor(n)))
+        assert rel(lam, o.lam()) <= 1e-10
+        Qg, Rg = h.get_factor_qr(n)
+        Qo, Ro = o.qr_factor(n)
+        assert rel(Rg, Ro) <= 1e-10
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_mttkrp_matches_oracle(cuda_lib, mode):
+    dims, R = (33, 27, 45), 6
+    X, A = gaussian_problem(dims, R, seed=13)
+    h = gpu_handle(dims, R, X, A)
+    M = h.mttkrp(mode)
+    assert rel(M, oracle.mttkrp(X, dims, mode, A)) <= 1e-12
+
+
+@pytest.mark.parametrize("solve", ["qr", "svd", "normal"])
+def test_sweeps_match_oracle_c1_shape(cuda_lib, solve):
+    # 50^3, rank 5, N(0,1) factors, unit weights, 1% noise, 20 sweeps
+    p = inputs.workload_c1()
+    osolve = {"qr": oracle.QR, "svd": oracle.SVD, "normal": oracle.NORMAL}[solve]
+    o = oracle.OracleCPALS(p.X, p.dims, p.rank)
+    o.set_factors(p.init_factors)
+    k, fits_o = o.iterate(20, solve=osolve, rtol=1e-10)
+    assert k == 20
+    h = gpu_handle(p.dims, p.rank, p.X, p.init_factors)
+    fits = h.iterate(20, solve=solve, svd_rtol=1e-10)
+    assert len(fits) == 20
+    assert np.abs(fits - fits_o).max() <= 1e-10
+    Ag, lam = h.get_factors()
+    for m in range(3):
+        assert rel(Ag[m], o.factor(m)) <= 1e-8
+    assert abs(h.fit(direct=True) - o.fit_direct()) <= 1e-10
+
+
+def test_direct_fit_and_resume(cuda_lib):
+    # 10 + 10 sweeps equal 20 sweeps bit for bit (checkpoint = get/set factors)
+    p = inputs.workload_c1(size=24, rank=4)
+    h1 = gpu_handle(p.dims, p.rank, p.X, p.init_factors)
+    h1.iterate(20)
+    A20, l20 = h1.get_factors()
+    h2 = gpu_handle(p.dims, p.rank, p.X, p.init_factors)
+    h2.iterate(10)
+    A10, l10 = h2.get_factors()
+    h3 = gpu_handle(p.dims, p.rank, p.X)
+    h3.set_factors(A10, l10)
+    h3.iterate(10)
+    A, l = h3.get_factors()
+    for m in range(3):
+        np.testing.assert_array_equal(A[m], A20[m])
+    np.testing.assert_array_equal(l, l20)
+    o = oracle.OracleCPALS(p.X, p.dims, p.rank)
+    o.set_factors(A20, l20)
+    assert abs(h1.fit(direct=True) - o.fit_direct()) <= 1e-12
+
+
+def test_singular_qr_solve_is_reported_and_factor_kept(cuda_lib):
+    dims, R = (16, 15, 14), 3
+    X, A = gaussian_problem(dims, R, seed=9)
+    for m in range(3):
+        A[m][:, 2] = A[m][:, 1]
+    h = gpu_handle(dims, R, X, A)
+    before, _ = h.get_factors()
+    h.solve_mode(0, "qr")
+    with pytest.raises(cpals.SingularError):
+        h.sync()
+    after, _ = h.get_factors()
+    np.testing.assert_array_equal(after[0], before[0])
+    # the SVD solve truncates the rank-deficient direction: min-norm lstsq
+    h.solve_mode(0, "svd", 1e-10)
+    h.sync()
+    Ag, lam = h.get_factors()
+    o = oracle.OracleCPALS(X, dims, R)
+    o.set_factors(A)
+    o.update_mode(0, oracle.SVD, 1e-10)
+    assert rel(Ag[0] * lam[None, :], o.factor(0) * o.lam()[None, :]) <= 1e-8
+
+
+def test_host_tensor_path_and_edge_shapes(cuda_lib):
+    # host X (copied by the library), rank 1, order 2, rank == a dim
+    for dims, R in [((9, 1 + 8), 1), ((5, 5), 5), ((3, 4, 5), 3)]:
+        X, A = gaussian_problem(dims, R, seed=17)
+        h = gpu_handle(dims, R, X, A, device_x=False)
+        o = oracle.OracleCPALS(X, dims, R)
+        o.set_factors(A)
+        for n in range(len(dims)):
+            h.solve_mode(n, "qr")
+            o.update_mode(n, oracle.QR)
+        h.sync()
+        Ag, lam = h.get_factors()
+        for n in range(len(dims)):
+            assert rel(Ag[n], o.factor(n)) <= 1e-9
+
+
+@pytest.mark.parametrize("dims,R", [((37, 29, 41), 5), ((40, 35, 30), 20), ((12, 11, 10, 9), 3)])
+def test_f32_multi_ttm_error_bound(cuda_lib, dims, R):
+    # FP32 copy of X and FP32 accumulation: each entry of Y is a sum of
+    # prod_{m != n} I_m products; relative Frobenius error stays below
+    # ~sqrt(K) * 2^-24 per TTM, bounded here by 2e-6.
+    X, A = gaussian_problem(dims, R, seed=19)
+    QR = [oracle.qr(a) for a in A]
+    h = gpu_handle(dims, R, X, precision="f32")
+    h.set_factor_qr([q for q, _ in QR], [r for _, r in QR])
+    for n in range(len(dims)):
+        Y, _ = h.multi_ttm(n)
+        assert rel(Y, oracle.multi_ttm(X, dims, n, [q for q, _ in QR])) <= 2e-6
+
+
+def test_full_size_multi_ttm_c2(cuda_lib):
+    # 400^3 FP64 rank 10 (the benchmark configuration), same launch path:
+    # full parity of Y_(n) for every mode against the oracle
+    p = inputs.workload_c2()
+    QR = [oracle.qr(a) for a in p.init_factors]
+    h = gpu_handle(p.dims, p.rank, p.X)
+    h.set_factor_qr([q for q, _ in QR], [r for _, r in QR])
+    for n in range(3):
+        Y, _ = h.multi_ttm(n)
+        ref = oracle.multi_ttm(p.X, p.dims, n, [q for q, _ in QR])
+        assert rel(Y, ref) <= 1e-12
+
+
+def test_full_size_sweep_c2(cuda_lib):
+    # one full QR sweep at 400^3 rank 10 from the same start: factors and fit
+    p = inputs.workload_c2()
+    o = oracle.OracleCPALS(p.X, p.dims, p.rank)
+    o.set_factors(p.init_factors)
+    o.iterate(1, solve=oracle.QR)
+    h = gpu_handle(p.dims, p.rank, p.X, p.init_factors)
+    fits = h.iterate(1, solve="qr")
+    assert abs(fits[0] - o.fit_last()) <= 1e-10
+    Ag, lam = h.get_factors()
+    for m in range(3):
+        assert rel(Ag[m], o.factor(m)) <= 1e-9
