@@ -59,7 +59,7 @@ def test_multi_ttm_matches_oracle(cuda_lib, dims, R):
         assert rel(Y, ref) <= 1e-12, (n, rel(Y, ref))
 
 
-@pytest.mark.parametrize("dims,R", [((5, 4, 3), 2), ((3, 4, 2, 3), 3), ((40, 30, 20), 6), ((300, 7), 5)])
+@pytest.mark.parametrize("dims,R", [((5, 4, 3), 2), ((3, 4, 3, 3), 3), ((40, 30, 20), 6), ((300, 7), 5)])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_multi_ttm_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision):
     # integer X and 0/1 Q: every partial sum is an integer below 2^24, exact in
