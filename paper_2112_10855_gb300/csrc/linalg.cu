@@ -546,18 +546,19 @@ inline unsigned grid_for(int64_t n, int threads, int num_sms)
 }
 
 // Recursive TSQR.  ws must hold 3*m*n doubles for the top call (geometric sum).
+// A leaf QR is latency-bound (n sequential reflector steps), so a matrix that
+// fits one CTA's shared memory is factored by a single leaf; taller ones are
+// split into blocks of max(2n, 32, m / #SMs) rows.
 cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, double* ws, int64_t ws_elems)
 {
-    // leaf: the whole matrix in one CTA's shared memory when it is short
-    const int64_t leaf_rows = std::max<int64_t>(2 * n, 32);
-    if (m <= std::max<int64_t>(leaf_rows, 2 * (int64_t)n) || (int64_t)2 * m * n <= 1024) {
+    if ((int64_t)2 * m * n <= kQrSmemLimitDoubles) {
         const size_t smem = qr_smem_bytes((int)m, n);
         hh_qr_blocks_kernel<<<1, kQrThreads, smem, h->stream>>>(A, m, m, n, 1, Q, m, R, n, h->d_status);
         h->launches++;
         return cudaGetLastError();
     }
+    const int64_t leaf_rows = std::max<int64_t>({2 * (int64_t)n, 32, (m + h->num_sms - 1) / h->num_sms});
     int64_t nb = (m + leaf_rows - 1) / leaf_rows;
-    if (nb > 4096) nb = 4096;
     // each block must keep >= n rows: balanced blocks have floor(m/nb) rows
     while (nb > 1 && m / nb < n) --nb;
     const int64_t mbmax = (m + nb - 1) / nb;

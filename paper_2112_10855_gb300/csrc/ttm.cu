@@ -9,6 +9,8 @@
 // decreasing-dimension order (Sec. 3.2), ping-ponging between two workspace
 // buffers; the first one streams X from HBM, the later ones read the shrunken
 // intermediate (R/I of the previous size), which usually stays in L2.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace cpals {
@@ -25,15 +27,18 @@ __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { 
 template <>
 __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return fmaf(a, b, c); }
 
-// One thread per flattened output row f = l + L*t; RC output columns per
-// thread (grid.y covers R in chunks of RC).  Q(k, r) for a k-chunk is staged in
-// shared memory as qs[k][r] and read as a broadcast.  Loads of In along k are
-// coalesced across the warp whenever L >= 32; for small L each thread walks
-// its own fiber and the lines are reused from L1.
+// One thread per flattened output row f = l + L*t and RC output columns
+// (RC = R rounded up to an instantiated width; grid.y covers wider R in
+// chunks).  Q(k, r) for a k-chunk is staged in shared memory as qs[k][r] and
+// read as a broadcast.  Loads of In along k are coalesced across the warp
+// whenever L >= 32; for small L each thread walks its own fiber and the lines
+// are reused from L1.  grid.z splits K: with gridDim.z > 1 each split writes
+// its partial sums to part + z * (L*R*T) in the output layout, and
+// reduce_splits_kernel adds them in split order (deterministic).
 template <typename T, int RC>
 __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
     const T* __restrict__ in, const double* __restrict__ Q, int64_t ldq, T* __restrict__ out,
-    int64_t L, int64_t K, int64_t Tn, int R, const int* __restrict__ status)
+    int64_t L, int64_t K, int64_t Tn, int R, int64_t kchunk, const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     __shared__ T qs[kKC][RC];
@@ -42,6 +47,8 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
     const int r0 = blockIdx.y * RC;
     const int rc = min(RC, R - r0);
     const bool active = f < rows;
+    const int64_t kb = (int64_t)blockIdx.z * kchunk;
+    const int64_t ke = (kb + kchunk < K) ? kb + kchunk : K;
     int64_t t = 0, l = 0;
     if (active) { t = f / L; l = f - t * L; }
     const T* p = in + l + L * K * t;
@@ -50,8 +57,8 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
 #pragma unroll
     for (int r = 0; r < RC; ++r) acc[r] = T(0);
 
-    for (int64_t k0 = 0; k0 < K; k0 += kKC) {
-        const int kc = (int)((K - k0) < (int64_t)kKC ? (K - k0) : (int64_t)kKC);
+    for (int64_t k0 = kb; k0 < ke; k0 += kKC) {
+        const int kc = (int)((ke - k0) < (int64_t)kKC ? (ke - k0) : (int64_t)kKC);
         __syncthreads();
         for (int i = threadIdx.x; i < kKC * RC; i += kThreads) {
             const int kk = i / RC, rr = i - kk * RC;
@@ -77,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
         }
     }
     if (active) {
-        T* o = out + l + L * (int64_t)R * t;
+        T* o = out + (int64_t)blockIdx.z * (L * (int64_t)R * Tn) + l + L * (int64_t)R * t;
 #pragma unroll
         for (int r = 0; r < RC; ++r)
             if (r < rc) o[L * (int64_t)(r0 + r)] = acc[r];
@@ -85,27 +92,81 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
 }
 
 template <typename T>
-cudaError_t launch_ttm(Handle* h, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s, int R)
+__global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int64_t n, T* __restrict__ out,
+                                     const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        T s = part[e];
+        for (int q = 1; q < ks; ++q) s += part[(int64_t)q * n + e];
+        out[e] = s;
+    }
+}
+
+template <typename T, int RC>
+void launch_rows(dim3 grid, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s,
+                 int R, int64_t kchunk, const int* status)
+{
+    ttm_rows_kernel<T, RC><<<grid, kThreads, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
+}
+
+// Register width per thread: R itself up to 16, then 20, 24, 32 (wider R in chunks of 32).
+inline int ttm_width(int R) {
+    if (R <= 16) return R;
+    if (R <= 20) return 20;
+    if (R <= 24) return 24;
+    return 32;
+}
+
+template <typename T>
+cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s, int R,
+                             T* part, int64_t part_elems)
 {
     const int64_t rows = s.L * s.T;
     if (rows == 0) return cudaSuccess;
-    dim3 block(kThreads);
+    const int rc = ttm_width(R);
     const int64_t gx = (rows + kThreads - 1) / kThreads;
-    if (R <= 4) {
-        dim3 grid((unsigned)gx, 1);
-        ttm_rows_kernel<T, 4><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
-    } else if (R <= 8) {
-        dim3 grid((unsigned)gx, 1);
-        ttm_rows_kernel<T, 8><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
-    } else if (R <= 16) {
-        dim3 grid((unsigned)gx, 1);
-        ttm_rows_kernel<T, 16><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
-    } else {
-        dim3 grid((unsigned)gx, (unsigned)((R + 31) / 32));
-        ttm_rows_kernel<T, 32><<<grid, block, 0, h->stream>>>(in, Q, ldq, out, s.L, s.K, s.T, R, h->d_status);
+    const int64_t gy = (R + rc - 1) / rc;
+    // split K when the row blocks alone cannot fill two waves of the SMs
+    int64_t ks = 1;
+    const int64_t want = 2LL * h->num_sms;
+    const int64_t outn = rows * R;
+    if (gx * gy < want && s.K >= 2 * kKC && part != nullptr) {
+        ks = (want + gx * gy - 1) / (gx * gy);
+        ks = std::min<int64_t>(ks, s.K / kKC);
+        ks = std::min<int64_t>(ks, part_elems / std::max<int64_t>(outn, 1));
+        if (ks < 2) ks = 1;
+    }
+    int64_t kchunk = (s.K + ks - 1) / ks;
+    kchunk = ((kchunk + kKC - 1) / kKC) * kKC;     // whole k-chunks per split
+    ks = (s.K + kchunk - 1) / kchunk;
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
+    T* dst = (ks > 1) ? part : out;
+    switch (rc) {
+#define CPALS_RC(W) case W: launch_rows<T, W>(grid, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
+        CPALS_RC(1) CPALS_RC(2) CPALS_RC(3) CPALS_RC(4) CPALS_RC(5) CPALS_RC(6) CPALS_RC(7) CPALS_RC(8)
+        CPALS_RC(9) CPALS_RC(10) CPALS_RC(11) CPALS_RC(12) CPALS_RC(13) CPALS_RC(14) CPALS_RC(15) CPALS_RC(16)
+        CPALS_RC(20) CPALS_RC(24) CPALS_RC(32)
+#undef CPALS_RC
+        default: return cudaErrorInvalidValue;
     }
     h->launches++;
-    return cudaGetLastError();
+    CPALS_CUDA_TRY(cudaGetLastError());
+    if (ks > 1) {
+        int64_t g = (outn + 255) / 256;
+        if (g > 16LL * h->num_sms) g = 16LL * h->num_sms;
+        reduce_splits_kernel<T><<<(unsigned)g, 256, 0, h->stream>>>(part, (int)ks, outn, out, h->d_status);
+        h->launches++;
+        CPALS_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_ttm(Handle* h, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s, int R)
+{
+    return launch_ttm_split<T>(h, in, Q, ldq, out, s, R, (T*)h->scratch,
+                               h->scratch_elems * (int64_t)(sizeof(double) / sizeof(T)));
 }
 
 // Final Multi-TTM tensor (dims R for m != n, I_n at n; mode 0 fastest) to the
