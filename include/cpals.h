@@ -185,6 +185,44 @@ int cpals_sync(cpals_handle* h);
  * each kernel node once per replay). */
 int64_t cpals_launch_count(const cpals_handle* h);
 
+/* Multi-TTM Y_(n) = X_(n) (Q_{N-1} (x) ... (x) Q_0, without `mode`) for
+ * callers that cannot allocate device memory.  The paper has no counterpart
+ * to this entry point.  Such callers include a host framework that hands all
+ * device memory to its own pool allocator, a process that runs under a hard
+ * device-memory budget, and a latency-critical loop where the implicit
+ * device synchronisation of cudaMalloc/cudaFree is not acceptable.
+ *
+ * It computes what cpals_multi_ttm computes (FP64, the same kernels, the
+ * single TTMs in decreasing-dimension order) without a handle.  It calls
+ * no cudaMalloc, cudaFree or allocating library routine.  Its scratch (the
+ * TTM intermediates and split-K partial sums) is one fixed file-scope device
+ * array of 2^21 doubles (16 MiB).  Every GPU that loads the library holds
+ * that array until the process exits.
+ *
+ *  dims, N, rank: as for cpals_create (2 <= N <= 8, 1 <= rank <= 64,
+ *    rank <= every dim).
+ *  mode: the kept mode n (0-based).
+ *  X: device pointer to prod(dims) FP64 values (mode 0 fastest), read only.
+ *  Q: host array of N device pointers to the I_m x R column-major FP64
+ *    matrices Q_m; Q[mode] is not read and may be NULL.
+ *  Y: device pointer to I_n x R^{N-1} FP64 values (the unfolding Y_(n)),
+ *    written.
+ *  stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+ *    Asynchronous.
+ * The caller owns X, Q and Y.  Sizes whose two largest TTM intermediates need
+ * more than 2^21 doubles are rejected with CPALS_ERR_ARG and a message from
+ * cpals_last_error(NULL), before any work is enqueued.
+ * On the first call on each device, with that device current, the call looks
+ * up the array's device address (cudaGetSymbolAddress).  That first call
+ * should therefore come before any stream capture.
+ * Every call shares the one array, and the array keeps the last call's
+ * contents.  Each call writes every scratch element before reading it and
+ * clears the status word it needs, so stale contents do no harm.  Calls
+ * that overlap on the GPU (other streams, other host threads, the same
+ * device) race on the array and give wrong results. */
+int cpals_multi_ttm_static(const int64_t* dims, int N, int rank, int mode, const double* X,
+                           const double* const* Q, double* Y, void* stream);
+
 /* Measured FMA throughput probe (not part of the method): runs dependent
  * FMA chains on every SM for `ms_target` ms and writes the achieved
  * TFLOP/s for FP64 and FP32.  Used to state the ALU roofline.  Synchronises. */

@@ -75,6 +75,7 @@ def load(path: str | None = None):
     L.cpals_sync.argtypes = [_vp]
     L.cpals_launch_count.argtypes = [_vp]
     L.cpals_launch_count.restype = C.c_int64
+    L.cpals_multi_ttm_static.argtypes = [i64p, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp), _vp, _vp]
     L.cpals_probe_fma_peak.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     _lib = L
     return L
@@ -275,6 +276,23 @@ class CPALS:
         f = C.c_double()
         _check(self._h, load().cpals_fit(self._h, 1 if direct else 0, C.byref(f)))
         return f.value
+
+
+def multi_ttm_static(X, Q, mode, rank, dims, Y, stream=None):
+    """cpals_multi_ttm_static: Multi-TTM into the caller's device tensor Y
+    (I_n x R^{N-1}, column-major), with no device allocation by the library.
+    X: flat FP64 CUDA tensor; Q: list of N column-major FP64 CUDA tensors
+    (Q[mode] may be None)."""
+    L = load()
+    dims = tuple(int(d) for d in dims)
+    N = len(dims)
+    d = (C.c_int64 * N)(*dims)
+    ptrs = (_vp * N)(*[None if q is None else C.c_void_p(q.data_ptr()) for q in Q])
+    raw = getattr(stream, "cuda_stream", stream) or 0
+    rc = L.cpals_multi_ttm_static(d, N, int(rank), int(mode), C.c_void_p(X.data_ptr()), ptrs,
+                                  C.c_void_p(Y.data_ptr()), C.c_void_p(raw))
+    if rc != OK:
+        raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
 
 
 def probe_fma_peak(ms_target=50.0):

@@ -591,6 +591,30 @@ int64_t cpals_launch_count(const cpals_handle* hh)
     return h ? h->launches : -1;
 }
 
+int cpals_multi_ttm_static(const int64_t* dims, int N, int rank, int mode, const double* X,
+                           const double* const* Q, double* Y, void* stream)
+{
+    if (!dims || !X || !Q || !Y) return fail(nullptr, CPALS_ERR_ARG, "%s", "a pointer argument is NULL");
+    if (N < 2 || N > cpals::kMaxN) return fail(nullptr, CPALS_ERR_ARG, "%s", "N must be in [2, 8]");
+    if (rank < 1 || rank > cpals::kMaxRank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must be in [1, 64]");
+    if (mode < 0 || mode >= N) return fail(nullptr, CPALS_ERR_ARG, "%s", "bad mode");
+    for (int m = 0; m < N; ++m) {
+        if (dims[m] < rank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must not exceed any dim");
+        if (m != mode && !Q[m]) return fail(nullptr, CPALS_ERR_ARG, "%s", "a Q pointer is NULL");
+    }
+    const int64_t need = cpals::multi_ttm_static_need(N, dims, rank, mode);
+    if (need > cpals::multi_ttm_static_capacity()) {
+        snprintf(g_create_err, sizeof(g_create_err),
+                 "problem too large for the static scratch: the two largest TTM intermediates need %lld doubles, "
+                 "the fixed array holds %lld",
+                 (long long)need, (long long)cpals::multi_ttm_static_capacity());
+        return CPALS_ERR_ARG;
+    }
+    cudaError_t e = cpals::multi_ttm_static(N, dims, rank, mode, X, Q, Y, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "static Multi-TTM");
+    return CPALS_OK;
+}
+
 int cpals_probe_fma_peak(double ms_target, double* fp64_tflops, double* fp32_tflops)
 {
     int dev = 0, sms = 0;

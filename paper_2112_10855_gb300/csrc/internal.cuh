@@ -117,6 +117,11 @@ struct Handle {
 cudaError_t multi_ttm(Handle* h, int n, const double* const* Q);
 // Only the first TTM of the Multi-TTM of mode n (the pass over X).
 cudaError_t ttm_first(Handle* h, int n);
+// Multi-TTM with all scratch in a fixed file-scope device array (no allocation).
+cudaError_t multi_ttm_static(int N, const int64_t* dims, int R, int n, const double* X, const double* const* Q,
+                             double* Y, cudaStream_t stream);
+int64_t multi_ttm_static_capacity();
+int64_t multi_ttm_static_need(int N, const int64_t* dims, int R, int n);
 // MTTKRP M_n = X_(n) Z_n (Alg. cp-als) into h->M.
 cudaError_t mttkrp(Handle* h, int n);
 // Squared Frobenius norm of X into h->d_normX2.

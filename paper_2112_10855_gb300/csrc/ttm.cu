@@ -10,6 +10,7 @@
 // buffers; the first one streams X from HBM, the later ones read the shrunken
 // intermediate (R/I of the previous size), which usually stays in L2.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -435,6 +436,111 @@ cudaError_t cast_f64_f32(Handle* h, const double* src, float* dst, int64_t n)
 {
     cast_kernel<<<grid_for(n, 256, h->num_sms), 256, 0, h->stream>>>(src, dst, n);
     h->launches++;
+    return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------- no-allocation Multi-TTM
+// Scratch for cpals_multi_ttm_static: the TTM intermediates and split-K
+// partials live in this fixed array, so that entry point never allocates.
+// Every GPU that loads the library holds it (16 MiB) until the process exits.
+constexpr int64_t kStaticScratchDoubles = int64_t(1) << 21;
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+static __device__ __align__(256) int g_static_status[1];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mutex;
+double* g_static_scratch_ptr[kMaxDevices] = {nullptr};
+int* g_static_status_ptr[kMaxDevices] = {nullptr};
+
+// Device addresses of the static arrays for the current device (set up once
+// per device, with that device current).
+cudaError_t static_scratch(int device, double** scratch, int** status)
+{
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_scratch_ptr[device]) {
+        void* p = nullptr;
+        void* q = nullptr;
+        CPALS_CUDA_TRY(cudaGetSymbolAddress(&p, g_static_scratch));
+        CPALS_CUDA_TRY(cudaGetSymbolAddress(&q, g_static_status));
+        g_static_scratch_ptr[device] = static_cast<double*>(p);
+        g_static_status_ptr[device] = static_cast<int*>(q);
+    }
+    *scratch = g_static_scratch_ptr[device];
+    *status = g_static_status_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int64_t multi_ttm_static_capacity() { return kStaticScratchDoubles; }
+
+// Elements of the two largest TTM intermediates of the Multi-TTM of mode n
+// (the sequence of sizes is non-increasing because R <= every dim).
+int64_t multi_ttm_static_need(int N, const int64_t* dims, int R, int n)
+{
+    int order[kMaxN];
+    ttm_order(N, dims, n, order);
+    int64_t d[kMaxN];
+    int64_t P = 1;
+    for (int m = 0; m < N; ++m) { d[m] = dims[m]; P *= dims[m]; }
+    int64_t s0 = 0, s1 = 0;
+    for (int k = 0; k < N - 1; ++k) {
+        P = P / d[order[k]] * R;
+        d[order[k]] = R;
+        if (k == 0) s0 = P;
+        if (k == 1) s1 = P;
+    }
+    return s0 + s1;
+}
+
+cudaError_t multi_ttm_static(int N, const int64_t* dims, int R, int n, const double* X, const double* const* Q,
+                             double* Y, cudaStream_t stream)
+{
+    int device = 0;
+    CPALS_CUDA_TRY(cudaGetDevice(&device));
+    double* scratch = nullptr;
+    int* status = nullptr;
+    CPALS_CUDA_TRY(static_scratch(device, &scratch, &status));
+    Handle h;                       // launch context only: no buffers are allocated
+    h.N = N;
+    h.R = R;
+    h.stream = stream;
+    for (int m = 0; m < N; ++m) h.dims[m] = dims[m];
+    CPALS_CUDA_TRY(cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, device));
+    h.d_status = status;
+    // the kernels skip their work unless the status word is zero
+    CPALS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), stream));
+
+    int order[kMaxN];
+    ttm_order(N, dims, n, order);
+    int64_t d[kMaxN];
+    int64_t P = 1;
+    for (int m = 0; m < N; ++m) { d[m] = dims[m]; P *= dims[m]; }
+    const int64_t s0 = P / dims[order[0]] * R;
+    const int64_t s1 = (N > 2) ? s0 / dims[order[1]] * R : 0;
+    double* buf[2] = {scratch, scratch + s0};
+    double* part = scratch + s0 + s1;
+    const int64_t part_elems = kStaticScratchDoubles - s0 - s1;
+    const double* in = X;
+    int cur = 0;
+    for (int k = 0; k < N - 1; ++k) {
+        const int m = order[k];
+        const TtmShape s = ttm_shape(N, d, m);
+        CPALS_CUDA_TRY(launch_ttm_split<double>(&h, in, Q[m], dims[m], buf[cur], s, R, part, part_elems));
+        d[m] = R;
+        in = buf[cur];
+        cur ^= 1;
+    }
+    int64_t Rn = 1;
+    for (int m = 0; m < n; ++m) Rn *= R;
+    int64_t RN1 = 1;
+    for (int m = 0; m < N - 1; ++m) RN1 *= R;
+    const int64_t total = dims[n] * RN1;
+    unfold_kernel<double><<<grid_for(total, 256, h.num_sms), 256, 0, stream>>>(in, Y, Rn, dims[n], total, status);
     return cudaGetLastError();
 }
 
