@@ -31,8 +31,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "CP-ALS-QR iters/s"
 UNIT = "iters/s"
-WORKLOAD = ("3-way 400x400x400 FP64 (512 MB), rank 10, planted factors with column congruence 0.99, "
-            "weights logspace 1..1e-4, 0.1% Gaussian noise; CP-ALS-QR sweeps (QR solve)")
+def workload_name(size, rank, solve="qr"):
+    mb = 8 * size ** 3 / 1e6
+    return (f"3-way {size}x{size}x{size} FP64 ({mb:.0f} MB), rank {rank}, planted factors with column congruence "
+            f"0.99, weights logspace 1..1e-4, 0.1% Gaussian noise; CP-ALS-QR sweeps ({solve.upper()} solve)")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP64_FLOP_PER_CLK_PER_SM = 4       # 2 DFMA/clk/SM on this part (measured: 1.195 TFLOP/s at ~1.95 GHz)
@@ -177,21 +179,30 @@ def run_reference(args, world, rank):
     solve = {"qr": 0, "svd": 1, "normal": 2}[args.solve]
     o = oracle.OracleCPALS(p.X, p.dims, p.rank)
     o.set_factors(p.init_factors)
+    # warm-up and timed steps, each one full oracle sweep; the run is bounded to
+    # about three minutes of host time (fewer steps are timed if needed)
+    budget_s = 180.0
+    t_start = time.perf_counter()
     for _ in range(args.warmup):
         o.iterate(1, solve=solve, rtol=1e-10)
+        if time.perf_counter() - t_start > budget_s / 4:
+            break
+    per = (time.perf_counter() - t_start) / max(args.warmup, 1)
+    steps = max(1, min(args.steps, int(budget_s / max(per, 1e-9))))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         o.iterate(1, solve=solve, rtol=1e-10)
     dt = time.perf_counter() - t0
-    v = args.steps / dt
+    v = steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD.replace("400x400x400", f"{args.size}x{args.size}x{args.size}")
-                   .replace("rank 10", f"rank {args.rank}"), "solve": args.solve, "parallelism": "replicas"},
+        "config": {"workload": workload_name(args.size, args.rank, args.solve), "dims": [args.size] * 3,
+                   "rank": args.rank, "solve": args.solve, "parallelism": "replicas"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full sweeps of the same workload, single-threaded plain C FP64"},
+                         "sample": f"{steps} full sweeps of the same workload (of {args.steps} asked; bounded to "
+                                   f"~{budget_s:.0f} s), single-threaded plain C FP64"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -337,8 +348,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("400x400x400", "x".join(map(str, p.dims)))
-                       .replace("rank 10", f"rank {R}"), "dims": list(p.dims), "rank": R, "solve": args.solve,
+            "config": {"workload": workload_name(p.dims[0], R, args.solve), "dims": list(p.dims), "rank": R,
+                       "solve": args.solve,
                        "l2": "inputs larger than L2 (X is 8*P bytes > 129 MB); no flush needed",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_fp64, "unit": "TFLOP/s",

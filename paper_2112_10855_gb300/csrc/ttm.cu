@@ -44,51 +44,59 @@ __global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
     if (*status != kStatusOk) return;
     __shared__ T qs[kKC][RC];
     const int64_t rows = L * Tn;
-    const int64_t f = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    // each CTA owns an equal contiguous share of the rows, so that every SM
+    // gets the same amount of FMA work (the grid is #SMs x resident CTAs)
+    const int64_t rb = rows * blockIdx.x / gridDim.x;
+    const int64_t re = rows * (blockIdx.x + 1) / gridDim.x;
     const int r0 = blockIdx.y * RC;
     const int rc = min(RC, R - r0);
-    const bool active = f < rows;
     const int64_t kb = (int64_t)blockIdx.z * kchunk;
     const int64_t ke = (kb + kchunk < K) ? kb + kchunk : K;
-    int64_t t = 0, l = 0;
-    if (active) { t = f / L; l = f - t * L; }
-    const T* p = in + l + L * K * t;
+    T* const outz = out + (int64_t)blockIdx.z * (L * (int64_t)R * Tn);
 
-    T acc[RC];
-#pragma unroll
-    for (int r = 0; r < RC; ++r) acc[r] = T(0);
+    for (int64_t f0 = rb; f0 < re; f0 += kThreads) {
+        const int64_t f = f0 + threadIdx.x;
+        const bool active = f < re;
+        int64_t t = 0, l = 0;
+        if (active) { t = f / L; l = f - t * L; }
+        const T* p = in + l + L * K * t;
 
-    for (int64_t k0 = kb; k0 < ke; k0 += kKC) {
-        const int kc = (int)((ke - k0) < (int64_t)kKC ? (ke - k0) : (int64_t)kKC);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kKC * RC; i += kThreads) {
-            const int kk = i / RC, rr = i - kk * RC;
-            qs[kk][rr] = (kk < kc && rr < rc) ? (T)Q[(k0 + kk) + ldq * (int64_t)(r0 + rr)] : T(0);
+        T acc[RC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) acc[r] = T(0);
+
+        for (int64_t k0 = kb; k0 < ke; k0 += kKC) {
+            const int kc = (int)((ke - k0) < (int64_t)kKC ? (ke - k0) : (int64_t)kKC);
+            __syncthreads();
+            for (int i = threadIdx.x; i < kKC * RC; i += kThreads) {
+                const int kk = i / RC, rr = i - kk * RC;
+                qs[kk][rr] = (kk < kc && rr < rc) ? (T)Q[(k0 + kk) + ldq * (int64_t)(r0 + rr)] : T(0);
+            }
+            __syncthreads();
+            if (!active) continue;
+            const T* pk = p + L * k0;
+            int kk = 0;
+            for (; kk + 8 <= kc; kk += 8) {
+                T x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) x[u] = __ldg(pk + L * (kk + u));
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) acc[r] = fma_t(x[u], qs[kk + u][r], acc[r]);
+            }
+            for (; kk < kc; ++kk) {
+                const T x = __ldg(pk + L * kk);
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[r] = fma_t(x, qs[kk][r], acc[r]);
+            }
         }
-        __syncthreads();
-        if (!active) continue;
-        const T* pk = p + L * k0;
-        int kk = 0;
-        for (; kk + 8 <= kc; kk += 8) {
-            T x[8];
+        if (active) {
+            T* o = outz + l + L * (int64_t)R * t;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = __ldg(pk + L * (kk + u));
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma_t(x[u], qs[kk + u][r], acc[r]);
+            for (int r = 0; r < RC; ++r)
+                if (r < rc) o[L * (int64_t)(r0 + r)] = acc[r];
         }
-        for (; kk < kc; ++kk) {
-            const T x = __ldg(pk + L * kk);
-#pragma unroll
-            for (int r = 0; r < RC; ++r) acc[r] = fma_t(x, qs[kk][r], acc[r]);
-        }
-    }
-    if (active) {
-        T* o = out + (int64_t)blockIdx.z * (L * (int64_t)R * Tn) + l + L * (int64_t)R * t;
-#pragma unroll
-        for (int r = 0; r < RC; ++r)
-            if (r < rc) o[L * (int64_t)(r0 + r)] = acc[r];
     }
 }
 
@@ -105,9 +113,26 @@ __global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int64_t
 }
 
 template <typename T, int RC>
-void launch_rows(dim3 grid, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s,
-                 int R, int64_t kchunk, const int* status)
+int resident_ctas()
 {
+    static int occ = 0;
+    if (occ == 0) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, ttm_rows_kernel<T, RC>, kThreads, 0) != cudaSuccess ||
+            v < 1)
+            v = 1;
+        occ = v;
+    }
+    return occ;
+}
+
+template <typename T, int RC>
+void launch_rows(dim3 grid, int num_sms, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out,
+                 TtmShape s, int R, int64_t kchunk, const int* status)
+{
+    // one wave: at most #SMs x resident CTAs, rows split evenly between them
+    const int64_t cap = (int64_t)num_sms * resident_ctas<T, RC>();
+    if ((int64_t)grid.x > cap) grid.x = (unsigned)cap;
     ttm_rows_kernel<T, RC><<<grid, kThreads, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
 }
 
@@ -144,7 +169,8 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
     T* dst = (ks > 1) ? part : out;
     switch (rc) {
-#define CPALS_RC(W) case W: launch_rows<T, W>(grid, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
+#define CPALS_RC(W) \
+    case W: launch_rows<T, W>(grid, h->num_sms, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
         CPALS_RC(1) CPALS_RC(2) CPALS_RC(3) CPALS_RC(4) CPALS_RC(5) CPALS_RC(6) CPALS_RC(7) CPALS_RC(8)
         CPALS_RC(9) CPALS_RC(10) CPALS_RC(11) CPALS_RC(12) CPALS_RC(13) CPALS_RC(14) CPALS_RC(15) CPALS_RC(16)
         CPALS_RC(20) CPALS_RC(24) CPALS_RC(32)
