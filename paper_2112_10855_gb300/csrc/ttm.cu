@@ -18,7 +18,6 @@ namespace cpals {
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int kKC = 32;   // k-chunk of Q staged in shared memory
 
 template <typename T>
@@ -36,67 +35,59 @@ __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { retur
 // are reused from L1.  grid.z splits K: with gridDim.z > 1 each split writes
 // its partial sums to part + z * (L*R*T) in the output layout, and
 // reduce_splits_kernel adds them in split order (deterministic).
-template <typename T, int RC>
-__global__ void __launch_bounds__(kThreads) ttm_rows_kernel(
+template <typename T, int RC, int TPB>
+__global__ void __launch_bounds__(TPB) ttm_rows_kernel(
     const T* __restrict__ in, const double* __restrict__ Q, int64_t ldq, T* __restrict__ out,
     int64_t L, int64_t K, int64_t Tn, int R, int64_t kchunk, const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     __shared__ T qs[kKC][RC];
     const int64_t rows = L * Tn;
-    // each CTA owns an equal contiguous share of the rows, so that every SM
-    // gets the same amount of FMA work (the grid is #SMs x resident CTAs)
-    const int64_t rb = rows * blockIdx.x / gridDim.x;
-    const int64_t re = rows * (blockIdx.x + 1) / gridDim.x;
+    const int64_t f = (int64_t)blockIdx.x * TPB + threadIdx.x;
     const int r0 = blockIdx.y * RC;
     const int rc = min(RC, R - r0);
+    const bool active = f < rows;
     const int64_t kb = (int64_t)blockIdx.z * kchunk;
     const int64_t ke = (kb + kchunk < K) ? kb + kchunk : K;
-    T* const outz = out + (int64_t)blockIdx.z * (L * (int64_t)R * Tn);
+    int64_t t = 0, l = 0;
+    if (active) { t = f / L; l = f - t * L; }
+    const T* p = in + l + L * K * t;
 
-    for (int64_t f0 = rb; f0 < re; f0 += kThreads) {
-        const int64_t f = f0 + threadIdx.x;
-        const bool active = f < re;
-        int64_t t = 0, l = 0;
-        if (active) { t = f / L; l = f - t * L; }
-        const T* p = in + l + L * K * t;
+    T acc[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) acc[r] = T(0);
 
-        T acc[RC];
-#pragma unroll
-        for (int r = 0; r < RC; ++r) acc[r] = T(0);
-
-        for (int64_t k0 = kb; k0 < ke; k0 += kKC) {
-            const int kc = (int)((ke - k0) < (int64_t)kKC ? (ke - k0) : (int64_t)kKC);
-            __syncthreads();
-            for (int i = threadIdx.x; i < kKC * RC; i += kThreads) {
-                const int kk = i / RC, rr = i - kk * RC;
-                qs[kk][rr] = (kk < kc && rr < rc) ? (T)Q[(k0 + kk) + ldq * (int64_t)(r0 + rr)] : T(0);
-            }
-            __syncthreads();
-            if (!active) continue;
-            const T* pk = p + L * k0;
-            int kk = 0;
-            for (; kk + 8 <= kc; kk += 8) {
-                T x[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) x[u] = __ldg(pk + L * (kk + u));
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) acc[r] = fma_t(x[u], qs[kk + u][r], acc[r]);
-            }
-            for (; kk < kc; ++kk) {
-                const T x = __ldg(pk + L * kk);
-#pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = fma_t(x, qs[kk][r], acc[r]);
-            }
+    for (int64_t k0 = kb; k0 < ke; k0 += kKC) {
+        const int kc = (int)((ke - k0) < (int64_t)kKC ? (ke - k0) : (int64_t)kKC);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kKC * RC; i += TPB) {
+            const int kk = i / RC, rr = i - kk * RC;
+            qs[kk][rr] = (kk < kc && rr < rc) ? (T)Q[(k0 + kk) + ldq * (int64_t)(r0 + rr)] : T(0);
         }
-        if (active) {
-            T* o = outz + l + L * (int64_t)R * t;
+        __syncthreads();
+        if (!active) continue;
+        const T* pk = p + L * k0;
+        int kk = 0;
+        for (; kk + 8 <= kc; kk += 8) {
+            T x[8];
 #pragma unroll
-            for (int r = 0; r < RC; ++r)
-                if (r < rc) o[L * (int64_t)(r0 + r)] = acc[r];
+            for (int u = 0; u < 8; ++u) x[u] = __ldg(pk + L * (kk + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[r] = fma_t(x[u], qs[kk + u][r], acc[r]);
         }
+        for (; kk < kc; ++kk) {
+            const T x = __ldg(pk + L * kk);
+#pragma unroll
+            for (int r = 0; r < RC; ++r) acc[r] = fma_t(x, qs[kk][r], acc[r]);
+        }
+    }
+    if (active) {
+        T* o = out + (int64_t)blockIdx.z * (L * (int64_t)R * Tn) + l + L * (int64_t)R * t;
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+            if (r < rc) o[L * (int64_t)(r0 + r)] = acc[r];
     }
 }
 
@@ -112,28 +103,20 @@ __global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int64_t
     }
 }
 
-template <typename T, int RC>
-int resident_ctas()
-{
-    static int occ = 0;
-    if (occ == 0) {
-        int v = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, ttm_rows_kernel<T, RC>, kThreads, 0) != cudaSuccess ||
-            v < 1)
-            v = 1;
-        occ = v;
-    }
-    return occ;
-}
+// CTA size: FP64 is bound by the FP64 pipe of each SM, so small CTAs (64
+// rows) keep the per-SM row counts within ~3% of each other with every CTA
+// resident in one wave; FP32 is bound by HBM and uses 256-row CTAs.
+template <typename T>
+struct TtmTpb { static constexpr int value = 256; };
+template <>
+struct TtmTpb<double> { static constexpr int value = 64; };
 
 template <typename T, int RC>
-void launch_rows(dim3 grid, int num_sms, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out,
-                 TtmShape s, int R, int64_t kchunk, const int* status)
+void launch_rows(dim3 grid, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s,
+                 int R, int64_t kchunk, const int* status)
 {
-    // one wave: at most #SMs x resident CTAs, rows split evenly between them
-    const int64_t cap = (int64_t)num_sms * resident_ctas<T, RC>();
-    if ((int64_t)grid.x > cap) grid.x = (unsigned)cap;
-    ttm_rows_kernel<T, RC><<<grid, kThreads, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
+    constexpr int TPB = TtmTpb<T>::value;
+    ttm_rows_kernel<T, RC, TPB><<<grid, TPB, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
 }
 
 // Register width per thread: R itself up to 16, then 20, 24, 32 (wider R in chunks of 32).
@@ -151,11 +134,12 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     const int64_t rows = s.L * s.T;
     if (rows == 0) return cudaSuccess;
     const int rc = ttm_width(R);
-    const int64_t gx = (rows + kThreads - 1) / kThreads;
+    const int tpb = sizeof(T) == 8 ? TtmTpb<double>::value : TtmTpb<float>::value;
+    const int64_t gx = (rows + tpb - 1) / tpb;
     const int64_t gy = (R + rc - 1) / rc;
     // split K when the row blocks alone cannot fill two waves of the SMs
     int64_t ks = 1;
-    const int64_t want = 2LL * h->num_sms;
+    const int64_t want = (int64_t)h->num_sms * (2048 / tpb);   // about 2048 threads per SM
     const int64_t outn = rows * R;
     if (gx * gy < want && s.K >= 2 * kKC && part != nullptr) {
         ks = (want + gx * gy - 1) / (gx * gy);
@@ -169,8 +153,7 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
     T* dst = (ks > 1) ? part : out;
     switch (rc) {
-#define CPALS_RC(W) \
-    case W: launch_rows<T, W>(grid, h->num_sms, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
+#define CPALS_RC(W) case W: launch_rows<T, W>(grid, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
         CPALS_RC(1) CPALS_RC(2) CPALS_RC(3) CPALS_RC(4) CPALS_RC(5) CPALS_RC(6) CPALS_RC(7) CPALS_RC(8)
         CPALS_RC(9) CPALS_RC(10) CPALS_RC(11) CPALS_RC(12) CPALS_RC(13) CPALS_RC(14) CPALS_RC(15) CPALS_RC(16)
         CPALS_RC(20) CPALS_RC(24) CPALS_RC(32)
