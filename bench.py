@@ -145,6 +145,24 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def recorded_traffic(profile="ttm_rows_f64_400cubed_r10.md"):
+    """DRAM traffic per launch of the dominant kernel from the committed ncu
+    summary, or None if the kernel source changed since it was captured."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", profile)) as f:
+            text = f.read()
+        want = re.search(r"sha256\[:16\] = ([0-9a-f]+)", text).group(1)
+        with open(os.path.join(ROOT, "paper_2112_10855_gb300", "csrc", "ttm.cu"), "rb") as f:
+            have = hashlib.sha256(f.read()).hexdigest()[:16]
+        if want != have:
+            return None
+        return int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -353,7 +371,9 @@ def main():
                        "l2": "inputs larger than L2 (X is 8*P bytes > 129 MB); no flush needed",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_fp64, "unit": "TFLOP/s",
-                         "frac": achieved_tflops / peak_fp64, "traffic": None,
+                         "frac": achieved_tflops / peak_fp64,
+                         "traffic": recorded_traffic() if (p.dims == (400, 400, 400) and R == 10) else None,
+                         "algorithmic_bytes": 8 * P,
                          "kernel": "ttm_rows_kernel<double> (first TTM of the Multi-TTM, streams X)",
                          "peak_source": "152 SMs x 2 DFMA/clk x 2070 MHz (derived); live FMA probe below",
                          "probe_fp64_tflops": probe64, "probe_fp32_tflops": probe32,
