@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the SVD/NORMAL/FP32 side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--workload", choices=["c2", "c3", "c5b"], default="c2",
+                    help="c2: the headline 400^3 rank-10 FP64 workload; c3: 4-way 120^4 rank 20 and c5b: 5-way "
+                         "40^5 rank 8, both comparing FP64, FP32 and 3xBF16 passes over X")
+    ap.add_argument("--fit-sweeps", type=int, default=20, help="sweeps for the equal-fit comparison")
     return ap.parse_args()
 
 
@@ -226,11 +230,113 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def mixed_workload(name, seed=2112):
+    from paper_2112_10855_gb300 import inputs
+    if name == "c3":
+        p = inputs.workload_c3(seed=seed)
+        desc = ("4-way 120x120x120x120 (FP64 master 1.66 GB + FP32 copy 0.83 GB), rank 20, factor columns with "
+                "congruence 0.9, 1% noise; CP-ALS-QR (QR solve)")
+    else:
+        p = inputs.planted((40,) * 5, 8, seed=seed, noise=0.01)
+        desc = "5-way 40^5 (FP64 master 819 MB + FP32 copy 410 MB), rank 8, N(0,1) factors, 1% noise; CP-ALS-QR"
+    return p, desc
+
+
+def run_mixed(args, world, rank):
+    """FP64 vs FP32 vs 3xBF16 (tensor cores) passes over X on one workload:
+    sweeps/s, first-TTM GB/s against HBM, Multi-TTM error against FP64 with
+    the same Q_m, factor error after one sweep, and the fit after
+    --fit-sweeps sweeps from the same start."""
+    import torch
+    from paper_2112_10855_gb300 import _build, cpals
+    torch.cuda.set_device(0)
+    _build.build()
+    cpals.load()
+    p, desc = mixed_workload(args.workload, 2112 + rank)
+    P = int(np.prod(p.dims))
+    R = p.rank
+    stream = torch.cuda.Stream()
+    Xd = torch.from_numpy(p.X).cuda()
+    init = [np.asfortranarray(a) for a in p.init_factors]
+    hbm = measured_peaks().get("hbm_gbs")
+    out = {}
+    ref = {}
+    for prec in ["f64", "f32", "bf16x3"]:
+        # throughput
+        h = cpals.CPALS(p.dims, R, prec)
+        h.set_stream(stream)
+        h.set_tensor(Xd)
+        h.set_factors(init)
+        h.iterate(args.warmup, want_fits=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = h.launch_count()
+        e0.record(stream)
+        h.iterate(args.steps, want_fits=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        its = args.steps / (e0.elapsed_time(e1) * 1e-3)
+        launches = h.launch_count() - l0
+        ttm_ms = []
+        for n in range(len(p.dims)):
+            h.ttm_first(n)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(5):
+                h.ttm_first(n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ttm_ms.append(e0.elapsed_time(e1) / 5)
+        ms = sum(ttm_ms) / len(ttm_ms)
+        xbytes = (8 if prec == "f64" else 4) * P
+        del h
+        # accuracy: Multi-TTM with identical Q_m, one sweep, and the fit after S sweeps
+        ha = cpals.CPALS(p.dims, R, prec)
+        ha.set_stream(stream)
+        ha.set_tensor(Xd)
+        ha.set_factors(init)
+        Ys = [ha.multi_ttm(n)[0] for n in range(len(p.dims))]
+        fits1 = ha.iterate(1)
+        A1, l1 = ha.get_factors()
+        fitsS = ha.iterate(max(args.fit_sweeps - 1, 0))
+        fit_final = float(fitsS[-1]) if len(fitsS) else float(fits1[-1])
+        del ha
+        entry = {"iters_per_s": its, "gpu_launches_per_sweep": launches / args.steps,
+                 "first_ttm_ms": ms, "first_ttm_gbs": xbytes / (ms * 1e-3) / 1e9,
+                 "first_ttm_frac_hbm": (xbytes / (ms * 1e-3) / 1e9 / hbm) if hbm else None,
+                 "first_ttm_tflops": 2.0 * P * R / (ms * 1e-3) / 1e12,
+                 "fit_after_sweeps": fit_final}
+        if prec == "f64":
+            ref = {"Y": Ys, "A": A1, "fit": fit_final}
+        else:
+            entry["multi_ttm_rel_err_vs_f64"] = max(
+                float(np.linalg.norm(Ys[n] - ref["Y"][n]) / np.linalg.norm(ref["Y"][n])) for n in range(len(Ys)))
+            entry["factor_rel_err_vs_f64_after_1_sweep"] = max(
+                float(np.linalg.norm(A1[m] - ref["A"][m]) / np.linalg.norm(ref["A"][m])) for m in range(len(A1)))
+            entry["fit_rel_diff_vs_f64"] = abs(fit_final - ref["fit"]) / abs(ref["fit"])
+        out[prec] = entry
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": out["bf16x3"]["iters_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3 (first TTM on tcgen05 when R >= 16) / fp32 / fp64",
+            "data": "synthetic",
+            "config": {"workload": desc, "dims": list(p.dims), "rank": R, "fit_sweeps": args.fit_sweeps},
+            "precisions": out,
+            "speedup_vs_f64": {k: out[k]["iters_per_s"] / out["f64"]["iters_per_s"] for k in out},
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload != "c2":
+        run_mixed(args, world, rank)
         return
     import torch
     from paper_2112_10855_gb300 import _build, cpals

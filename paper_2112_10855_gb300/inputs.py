@@ -50,13 +50,28 @@ def uniform(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
     return ((z >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
 
 
-def normal(seed: int, stream: int, n: int, chunk: int = 1 << 24) -> np.ndarray:
-    """n i.i.d. N(0,1) draws: Box-Muller on uniform pairs (2k, 2k+1)."""
+def normal(seed: int, stream: int, n: int, chunk: int = 1 << 22) -> np.ndarray:
+    """n i.i.d. N(0,1) draws: Box-Muller on uniform pairs (2k, 2k+1).
+
+    Chunks are filled by a thread pool (numpy releases the GIL); each chunk
+    writes its own slice, so the result does not depend on the thread count.
+    """
     out = np.empty(n, dtype=np.float64)
-    for s in range(0, n, chunk):
+
+    def fill(s):
         m = min(chunk, n - s)
         u = uniform(seed, stream, 2 * m, offset=2 * s)
         out[s:s + m] = np.sqrt(-2.0 * np.log(u[0::2])) * np.cos(2.0 * math.pi * u[1::2])
+
+    starts = list(range(0, n, chunk))
+    if len(starts) <= 1:
+        for s in starts:
+            fill(s)
+    else:
+        import concurrent.futures as cf
+        import os
+        with cf.ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, starts))
     return out
 
 
