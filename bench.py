@@ -261,7 +261,7 @@ def run_mixed(args, world, rank):
     hbm = measured_peaks().get("hbm_gbs")
     out = {}
     ref = {}
-    for prec in ["f64", "f32", "bf16x3"]:
+    for prec in ["f64", "f32", "bf16x3", "tf32x3"]:
         # throughput
         h = cpals.CPALS(p.dims, R, prec)
         h.set_stream(stream)
@@ -318,9 +318,9 @@ def run_mixed(args, world, rank):
         out[prec] = entry
     if rank == 0:
         line = {
-            "metric": METRIC, "value": out["bf16x3"]["iters_per_s"], "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": out["tf32x3"]["iters_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3 (first TTM on tcgen05 when R >= 16) / fp32 / fp64",
+            "vs_baseline": None, "dtype": "tf32x3 (value); bf16x3, fp32 and fp64 beside it (tensor cores when R >= 16)",
             "data": "synthetic",
             "config": {"workload": desc, "dims": list(p.dims), "rank": R, "fit_sweeps": args.fit_sweeps},
             "precisions": out,

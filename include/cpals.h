@@ -60,8 +60,11 @@ typedef enum {
  * always run in FP64. */
 typedef enum {
     CPALS_F64 = 0,     /* X read as FP64, FP64 FMA */
-    CPALS_F32 = 1,     /* X read as an FP32 copy, FP32 FMA; Y promoted to FP64 */
-    CPALS_BF16X3 = 2   /* FP32 copy split into bf16 hi/lo parts; hi*hi+hi*lo+lo*hi on tensor cores, FP32 accumulate */
+    CPALS_F32 = 1,     /* X read as an FP32 copy (round to nearest even), FP32 FMA; Y promoted to FP64 */
+    CPALS_BF16X3 = 2,  /* FP32 copy split into bf16 hi/lo parts; hi*hi+hi*lo+lo*hi on tcgen05 tensor cores
+                          (kind::f16), FP32 accumulate; ~2^-16 relative per product.  Tensor cores for
+                          the first TTM when rank >= 16, FP32 FMA otherwise */
+    CPALS_TF32X3 = 3   /* the same with tf32 hi/lo parts (kind::tf32): ~2^-21 relative per product */
 } cpals_precision;
 
 typedef enum {
@@ -98,10 +101,10 @@ int cpals_workspace_bytes(const cpals_handle* h, size_t* bytes);
  *  elem = CPALS_ELEM_F64: with precision F64 and mem DEVICE, the pointer is
  *    borrowed and must stay valid until the handle is destroyed or another
  *    tensor is set; with mem HOST, X is copied into a device buffer that the
- *    handle owns.  With precision F32/BF16X3, X is rounded (round to nearest
- *    even) into an FP32 copy that the handle owns.
- *  elem = CPALS_ELEM_F32: allowed only with precision F32/BF16X3; borrowed
- *    (DEVICE) or copied (HOST).
+ *    handle owns.  With precision F32/BF16X3/TF32X3, X is rounded (round to
+ *    nearest even) into an FP32 copy that the handle owns.
+ *  elem = CPALS_ELEM_F32: allowed only with precision F32/BF16X3/TF32X3;
+ *    borrowed (DEVICE) or copied (HOST).
  * Also computes ||X||_F^2 in FP64 (Sec. 3.3.1: it is pre-computed once). */
 int cpals_set_tensor(cpals_handle* h, const void* X, int elem, int mem);
 

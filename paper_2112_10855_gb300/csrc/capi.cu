@@ -182,7 +182,7 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
     if (!dims) return fail(nullptr, CPALS_ERR_ARG, "%s", "dims is NULL");
     if (N < 2 || N > cpals::kMaxN) return fail(nullptr, CPALS_ERR_ARG, "%s", "N must be in [2, 8]");
     if (rank < 1 || rank > cpals::kMaxRank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must be in [1, 64]");
-    if (precision != CPALS_F64 && precision != CPALS_F32 && precision != CPALS_BF16X3)
+    if (precision != CPALS_F64 && precision != CPALS_F32 && precision != CPALS_BF16X3 && precision != CPALS_TF32X3)
         return fail(nullptr, CPALS_ERR_ARG, "%s", "unknown precision");
     for (int m = 0; m < N; ++m)
         if (dims[m] < 1) return fail(nullptr, CPALS_ERR_ARG, "%s", "dims must be >= 1");
@@ -283,7 +283,7 @@ int cpals_set_tensor(cpals_handle* hh, const void* X, int elem, int mem)
     if (!mem_ok(mem) || (elem != CPALS_ELEM_F64 && elem != CPALS_ELEM_F32))
         return fail(h, CPALS_ERR_ARG, "%s", "bad elem or mem flag");
     if (elem == CPALS_ELEM_F32 && h->prec == CPALS_F64)
-        return fail(h, CPALS_ERR_ARG, "%s", "an FP32 tensor needs precision F32 or BF16X3");
+        return fail(h, CPALS_ERR_ARG, "%s", "an FP32 tensor needs precision F32, BF16X3 or TF32X3");
     h->X64 = nullptr; h->X32 = nullptr; h->have_X = false;
     if (h->prec == CPALS_F64) {
         if (mem == CPALS_MEM_DEVICE) {

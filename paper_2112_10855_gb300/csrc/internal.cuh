@@ -122,9 +122,11 @@ cudaError_t multi_ttm_static(int N, const int64_t* dims, int R, int n, const dou
                              double* Y, cudaStream_t stream);
 int64_t multi_ttm_static_capacity();
 int64_t multi_ttm_static_need(int N, const int64_t* dims, int R, int n);
-// First TTM on the tcgen05 tensor cores with 3xBF16 split products (FP32 X).
+// First TTM on the tcgen05 tensor cores with split products (FP32 X):
+// 3 x bf16 (kind::f16) or, with tf32 = true, 3 x tf32 (kind::tf32).
 bool tc_supported(int R);
-cudaError_t ttm_bf16x3(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R);
+cudaError_t ttm_split_tc(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R,
+                         bool tf32);
 // MTTKRP M_n = X_(n) Z_n (Alg. cp-als) into h->M.
 cudaError_t mttkrp(Handle* h, int n);
 // Squared Frobenius norm of X into h->d_normX2.

@@ -1,0 +1,481 @@
+// tc_split.cu -- the first TTM of the Multi-TTM (the pass that streams X) on
+// the tcgen05 tensor cores with split-precision products:
+//     Out(l, r, t) = sum_k X(l, k, t) * Q(k, r)            (Y = X x_m Q_m^T)
+// X is the FP32 copy of the tensor.  Each x and each q are split into two
+// parts of the operand type, x = x_hi + x_lo (x_hi = round(x),
+// x_lo = round(x - x_hi)), and x*q ~ x_hi*q_hi + x_hi*q_lo + x_lo*q_hi.  Three
+// MMAs per K step accumulate the products (exact in FP32) into one FP32
+// accumulator in tensor memory.
+//   BF16X3 (kind::f16, bf16 parts of 8 significant bits): the dropped
+//     x_lo*q_lo and the rounding of the lo parts leave ~2^-16 per product.
+//   TF32X3 (kind::tf32, tf32 parts of 11 bits): ~2^-21 per product, the level
+//     of FP32 arithmetic.
+//
+// Tiling: a CTA of 128 threads owns 128 consecutive flattened rows f = l + L*t
+// (M = 128) and all R outputs (N = R rounded up to a multiple of 16).  It walks
+// K in chunks of 128 bytes per row (64 bf16 or 32 tf32 values).  Operands live
+// in shared memory in the K-major no-swizzle canonical layout: 8-row x 16-byte
+// core matrices, K-adjacent cores 128 B apart (LBO), 8-row groups 1024 B apart
+// (SBO).  Q_m is split once per launch into tiles already in that layout.
+// Every thread splits two (4-row, 16-byte K group) units of X per chunk, loading
+// four rows at once with 128-bit loads when L % 4 == 0.  Two stages are in
+// flight: the loads of chunk c+1 are issued before the CTA waits on the MMAs
+// of chunk c-1.  One thread issues the 3 tcgen05.mma per K step (M=128) and
+// commits each chunk to that stage's mbarrier.  The epilogue reads the
+// accumulator with tcgen05.ld (one warp per 32 TMEM lanes) and stores the R
+// valid columns.
+//
+// Every wait is bounded.  On timeout the kernel records CPALS_ERR_TIMEOUT in
+// the status word, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace cpals {
+
+namespace {
+
+constexpr int kTcRows = 128;     // M
+constexpr int kTcThreads = 128;
+constexpr uint32_t kSbo = 1024;  // bytes between 8-row core groups (a 128-byte K chunk = 8 cores x 128 B)
+constexpr uint32_t kLbo = 128;   // bytes between K-adjacent core matrices
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, LBO and SBO in 16-byte
+// units, descriptor version 1 (bit 46), no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((kLbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((kSbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :
+                 : "r"(smem_u32(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" : : "r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false after ~2^24 failed polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < (1u << 24); ++it) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+template <int NCOLS>
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :
+                 : "r"(smem_u32(dst)), "r"((uint32_t)NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+template <int NCOLS>
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" : : "r"(taddr), "r"((uint32_t)NCOLS)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// 16 consecutive f32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Operand element type of the split: bf16 (kind::f16) or tf32 (kind::tf32).
+// A K-chunk is 128 bytes of one row (64 bf16 or 32 tf32), so both share one
+// byte layout: 8 core matrices of 16 bytes per 8-row group.
+template <bool TF32>
+struct Elem {
+    static constexpr int kBytes = TF32 ? 4 : 2;
+    static constexpr int kPerGroup = 16 / kBytes;          // elements per 16-byte core row
+    static constexpr int kChunk = 128 / kBytes;            // K elements per stage
+    static constexpr int kStep = 32 / kBytes;              // K per MMA (two core matrices)
+};
+
+// Byte offset of element (row, k) of a [rows x chunk] K-major no-swizzle tile.
+template <bool TF32>
+__host__ __device__ __forceinline__ uint32_t tile_off_e(int row, int k)
+{
+    using E = Elem<TF32>;
+    return (uint32_t)(row >> 3) * kSbo + (uint32_t)(k / E::kPerGroup) * kLbo + (uint32_t)(row & 7) * 16u +
+           (uint32_t)(k % E::kPerGroup) * (uint32_t)E::kBytes;
+}
+
+// hi = round(x), lo = round(x - hi) in the operand type, packed for a 16-byte
+// core row (4 values for tf32: one uint4 each for hi and lo; 8 for bf16).
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+template <bool TF32>
+__device__ __forceinline__ void split_group(const float* x, uint4& hi, uint4& lo)
+{
+    if constexpr (TF32) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = to_tf32(x[e]);
+            l[e] = to_tf32(x[e] - __uint_as_float(h[e]));
+        }
+        hi = make_uint4(h[0], h[1], h[2], h[3]);
+        lo = make_uint4(l[0], l[1], l[2], l[3]);
+    } else {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x[2 * e]);
+            const __nv_bfloat16 h1 = __float2bfloat16_rn(x[2 * e + 1]);
+            h[e] = pack2(h0, h1);
+            l[e] = pack2(__float2bfloat16_rn(x[2 * e] - __bfloat162float(h0)),
+                         __float2bfloat16_rn(x[2 * e + 1] - __bfloat162float(h1)));
+        }
+        hi = make_uint4(h[0], h[1], h[2], h[3]);
+        lo = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// Instruction descriptor: D f32; A and B bf16 (format 1, kind::f16) or tf32
+// (format 2, kind::tf32); both K-major; N>>3 at bits 17-22, M>>4 at 24-28.
+template <bool TF32>
+__host__ __device__ constexpr uint32_t make_idesc_e(int M, int N)
+{
+    return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma_split(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+            :
+            : "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
+    }
+}
+
+template <int N>
+struct TcCfg {
+    static constexpr int kNcols = (N <= 32) ? 32 : (N <= 64 ? 64 : 128);   // TMEM columns (power of 2 >= 32)
+    static constexpr uint32_t kABytes = kTcRows * 128;                    // one A tile: 128 rows x 128 B (16 KB)
+    static constexpr uint32_t kBBytes = N * 128;                          // one B tile
+    static constexpr uint32_t kStage = 2 * kABytes + 2 * kBBytes;         // hi + lo of A and B
+    static constexpr uint32_t kSmem = 2 * kStage + 64 + 1024;             // two stages + barriers + alignment
+};
+
+// Q_m split into hi/lo B tiles once per launch, already in the shared-memory
+// layout: tiles[c][0|1] is the hi|lo tile of K-chunk c (N x chunk, zero past R
+// and past K).
+template <int N, bool TF32>
+__global__ void split_q_kernel(const double* __restrict__ Q, int64_t ldq, int64_t K, int R,
+                               uint8_t* __restrict__ tiles, int nchunks, const int* __restrict__ status)
+{
+    using E = Elem<TF32>;
+    using Cfg = TcCfg<N>;
+    if (*status != kStatusOk) return;
+    const int64_t groups = (int64_t)nchunks * N * (E::kChunk / E::kPerGroup);
+    for (int64_t gidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gidx < groups;
+         gidx += (int64_t)gridDim.x * blockDim.x) {
+        const int perc = N * (E::kChunk / E::kPerGroup);
+        const int c = (int)(gidx / perc);
+        const int rem = (int)(gidx - (int64_t)c * perc);
+        const int n = rem / (E::kChunk / E::kPerGroup), g = rem - n * (E::kChunk / E::kPerGroup);
+        float xv[8];
+        for (int e = 0; e < E::kPerGroup; ++e) {
+            const int64_t k = (int64_t)c * E::kChunk + g * E::kPerGroup + e;
+            xv[e] = (n < R && k < K) ? (float)Q[k + ldq * (int64_t)n] : 0.0f;
+        }
+        uint4 hi, lo;
+        split_group<TF32>(xv, hi, lo);
+        uint8_t* base = tiles + (size_t)c * 2 * Cfg::kBBytes;
+        const uint32_t off = tile_off_e<TF32>(n, g * E::kPerGroup);
+        *reinterpret_cast<uint4*>(base + off) = hi;
+        *reinterpret_cast<uint4*>(base + Cfg::kBBytes + off) = lo;
+    }
+}
+
+// Main kernel.  Work unit for the A operand: (row quad q, 16-byte K group g);
+// 32 quads x 8 groups per stage, two units per thread.  With L % 4 == 0 the
+// four rows of a quad are contiguous and 16-byte aligned, so each k needs one
+// 128-bit load; otherwise four scalar loads.  Stages are double-buffered: the
+// loads of chunk c+1 are issued before the CTA waits on the MMAs of chunk c-1.
+template <int N, bool TF32>
+__global__ void __launch_bounds__(kTcThreads) ttm_split_tc_kernel(
+    const float* __restrict__ in, const uint8_t* __restrict__ btiles, float* __restrict__ out, int64_t L,
+    int64_t K, int64_t Tn, int R, int nchunks, int* __restrict__ status)
+{
+    using E = Elem<TF32>;
+    using Cfg = TcCfg<N>;
+    if (*status != kStatusOk) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* mbar = (uint64_t*)(smem + 2 * Cfg::kStage);
+    uint32_t* tmem_slot = (uint32_t*)(mbar + 2);
+    __shared__ int timed_out;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t rows = L * Tn;
+    const int64_t f_base = (int64_t)blockIdx.x * kTcRows;
+    const bool vec = (L % 4) == 0 && (((uintptr_t)in) & 15) == 0;
+
+    // this thread's two units: unit u = tid + 128*j, quad = u & 31, group = u >> 5
+    int64_t rowoff[2][4];
+    bool rowok[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int u = tid + kTcThreads * j;
+        const int q = u & 31;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t f = f_base + 4 * q + i;
+            rowok[j][i] = f < rows;
+            const int64_t t = rowok[j][i] ? f / L : 0;
+            const int64_t l = rowok[j][i] ? f - t * L : 0;
+            rowoff[j][i] = l + L * K * t;
+        }
+    }
+
+    if (warp == 0) tmem_alloc<Cfg::kNcols>(tmem_slot);
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+        timed_out = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = make_idesc_e<TF32>(kTcRows, N);
+
+    float xr[2][E::kPerGroup][4];   // [unit][k in group][row in quad]
+    auto load_chunk = [&](int c) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int g = (tid + kTcThreads * j) >> 5;
+#pragma unroll
+            for (int e = 0; e < E::kPerGroup; ++e) {
+                const int64_t k = (int64_t)c * E::kChunk + g * E::kPerGroup + e;
+                const bool kok = k < K;
+                if (vec && rowok[j][0] && rowok[j][3] && rowoff[j][3] == rowoff[j][0] + 3) {
+                    float4 v = kok ? __ldg(reinterpret_cast<const float4*>(in + rowoff[j][0] + L * k))
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                    xr[j][e][0] = v.x; xr[j][e][1] = v.y; xr[j][e][2] = v.z; xr[j][e][3] = v.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        xr[j][e][i] = (kok && rowok[j][i]) ? __ldg(in + rowoff[j][i] + L * k) : 0.0f;
+                }
+            }
+        }
+    };
+
+    load_chunk(0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int b = c & 1;
+        uint8_t* stage = smem + (size_t)b * Cfg::kStage;
+        uint8_t* a_hi = stage;
+        uint8_t* a_lo = a_hi + Cfg::kABytes;
+        uint8_t* b_hi = a_lo + Cfg::kABytes;
+        uint8_t* b_lo = b_hi + Cfg::kBBytes;
+        if (c >= 2) {                       // MMAs of chunk c-2 read this stage
+            if (!mbar_wait_bounded(&mbar[b], (uint32_t)((c - 2) >> 1) & 1u)) timed_out = 1;
+        }
+        // A: split the registers of chunk c into this stage
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int u = tid + kTcThreads * j;
+            const int q = u & 31, g = u >> 5;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float xv[8];
+#pragma unroll
+                for (int e = 0; e < E::kPerGroup; ++e) xv[e] = xr[j][e][i];
+                uint4 hi, lo;
+                split_group<TF32>(xv, hi, lo);
+                const uint32_t off = tile_off_e<TF32>(4 * q + i, g * E::kPerGroup);
+                *reinterpret_cast<uint4*>(a_hi + off) = hi;
+                *reinterpret_cast<uint4*>(a_lo + off) = lo;
+            }
+        }
+        // B: copy the pre-split tiles of chunk c
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(btiles + (size_t)c * 2 * Cfg::kBBytes);
+            uint4* dst = reinterpret_cast<uint4*>(b_hi);
+            for (int i = tid; i < (int)(2 * Cfg::kBBytes / 16); i += kTcThreads) dst[i] = __ldg(src + i);
+        }
+        if (c + 1 < nchunks) load_chunk(c + 1);   // in flight while the MMAs run
+        fence_proxy_async();
+        __syncthreads();
+        if (timed_out) break;
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+            for (int ks = 0; ks < E::kChunk / E::kStep; ++ks) {
+                const uint32_t step = (uint32_t)ks * 2u * kLbo;
+                mma_split<TF32>(tmem, make_desc(ah + step), make_desc(bh + step), idesc, (c | ks) ? 1u : 0u);
+                mma_split<TF32>(tmem, make_desc(ah + step), make_desc(bl + step), idesc, 1u);
+                mma_split<TF32>(tmem, make_desc(al + step), make_desc(bh + step), idesc, 1u);
+            }
+            mma_commit(&mbar[b]);
+        }
+    }
+    // the last commit covers every MMA of this thread
+    if (!timed_out && nchunks > 0) {
+        const int c = nchunks - 1;
+        if (!mbar_wait_bounded(&mbar[c & 1], (uint32_t)(c >> 1) & 1u)) timed_out = 1;
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (!timed_out) {
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            const int64_t f = f_base + tid;
+            if (f < rows) {
+                const int64_t t = f / L, l = f - t * L;
+                float* o = out + l + L * (int64_t)R * t;
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj)
+                    if (c0 + jj < R) o[L * (int64_t)(c0 + jj)] = v[jj];
+            }
+        }
+    } else {
+        if (tid == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_TIMEOUT);
+        // once more (bounded) for MMAs still in flight before the memory is freed
+        if (nchunks > 0) mbar_wait_bounded(&mbar[(nchunks - 1) & 1], (uint32_t)((nchunks - 1) >> 1) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc<Cfg::kNcols>(tmem);
+}
+
+template <int N, bool TF32>
+cudaError_t launch_tc(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R)
+{
+    using Cfg = TcCfg<N>;
+    using E = Elem<TF32>;
+    static bool attr = false;
+    if (!attr) {
+        CPALS_CUDA_TRY(cudaFuncSetAttribute(ttm_split_tc_kernel<N, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)Cfg::kSmem));
+        attr = true;
+    }
+    const int nchunks = (int)((s.K + E::kChunk - 1) / E::kChunk);
+    const size_t tile_bytes = (size_t)nchunks * 2 * Cfg::kBBytes;
+    if (tile_bytes > (size_t)h->scratch_elems * sizeof(double)) return cudaErrorInvalidValue;
+    uint8_t* tiles = reinterpret_cast<uint8_t*>(h->scratch);
+    const int64_t groups = (int64_t)nchunks * N * (E::kChunk / E::kPerGroup);
+    split_q_kernel<N, TF32><<<(unsigned)std::min<int64_t>((groups + 255) / 256, 4096), 256, 0, h->stream>>>(
+        Q, ldq, s.K, R, tiles, nchunks, h->d_status);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    const int64_t rows = s.L * s.T;
+    const int64_t grid = (rows + kTcRows - 1) / kTcRows;
+    ttm_split_tc_kernel<N, TF32><<<(unsigned)grid, kTcThreads, Cfg::kSmem, h->stream>>>(
+        in, tiles, out, s.L, s.K, s.T, R, nchunks, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_supported(int R) { return R >= 16 && R <= 64; }
+
+cudaError_t ttm_split_tc(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R,
+                         bool tf32)
+{
+    if (s.L * s.T == 0) return cudaSuccess;
+    if (tf32) {
+        if (R <= 16) return launch_tc<16, true>(h, in, Q, ldq, out, s, R);
+        if (R <= 32) return launch_tc<32, true>(h, in, Q, ldq, out, s, R);
+        if (R <= 48) return launch_tc<48, true>(h, in, Q, ldq, out, s, R);
+        return launch_tc<64, true>(h, in, Q, ldq, out, s, R);
+    }
+    if (R <= 16) return launch_tc<16, false>(h, in, Q, ldq, out, s, R);
+    if (R <= 32) return launch_tc<32, false>(h, in, Q, ldq, out, s, R);
+    if (R <= 48) return launch_tc<48, false>(h, in, Q, ldq, out, s, R);
+    return launch_tc<64, false>(h, in, Q, ldq, out, s, R);
+}
+
+}  // namespace cpals

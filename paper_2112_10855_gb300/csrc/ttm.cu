@@ -248,12 +248,12 @@ const double* x_ptr<double>(Handle* h) { return h->X64; }
 template <>
 const float* x_ptr<float>(Handle* h) { return h->X32; }
 
-// The BF16X3 precision runs the first TTM (the pass over X) on the tensor
-// cores when the rank fills an MMA tile (R >= 16); otherwise FP32 FMA.
+// The BF16X3 and TF32X3 precisions run the first TTM (the pass over X) on the
+// tensor cores when the rank fills an MMA tile (R >= 16); otherwise FP32 FMA.
 template <typename T>
 bool first_on_tensor_cores(const Handle* h)
 {
-    return sizeof(T) == 4 && h->prec == CPALS_BF16X3 && tc_supported(h->R);
+    return sizeof(T) == 4 && (h->prec == CPALS_BF16X3 || h->prec == CPALS_TF32X3) && tc_supported(h->R);
 }
 
 template <typename T>
@@ -271,7 +271,8 @@ cudaError_t multi_ttm_impl(Handle* h, int n, const double* const* Q)
         const TtmShape s = ttm_shape(N, d, m);
         T* out = (T*)h->tbuf[cur];
         if (k == 0 && first_on_tensor_cores<T>(h))
-            CPALS_CUDA_TRY(ttm_bf16x3(h, (const float*)in, Q[m], h->dims[m], (float*)out, s, R));
+            CPALS_CUDA_TRY(ttm_split_tc(h, (const float*)in, Q[m], h->dims[m], (float*)out, s, R,
+                                        h->prec == CPALS_TF32X3));
         else
             CPALS_CUDA_TRY(launch_ttm<T>(h, in, Q[m], h->dims[m], out, s, R));
         d[m] = R;
@@ -420,7 +421,8 @@ cudaError_t ttm_first(Handle* h, int n)
     if (h->prec == CPALS_F64)
         return launch_ttm<double>(h, h->X64, h->Q[order[0]], h->dims[order[0]], (double*)h->tbuf[0], s, h->R);
     if (first_on_tensor_cores<float>(h))
-        return ttm_bf16x3(h, h->X32, h->Q[order[0]], h->dims[order[0]], (float*)h->tbuf[0], s, h->R);
+        return ttm_split_tc(h, h->X32, h->Q[order[0]], h->dims[order[0]], (float*)h->tbuf[0], s, h->R,
+                            h->prec == CPALS_TF32X3);
     return launch_ttm<float>(h, h->X32, h->Q[order[0]], h->dims[order[0]], (float*)h->tbuf[0], s, h->R);
 }
 

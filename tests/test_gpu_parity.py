@@ -264,38 +264,44 @@ def test_full_size_sweep_c2(cuda_lib):
         assert rel(Ag[m], o.factor(m)) <= 1e-9
 
 
-# ---------------------------------------------------------------- tensor cores (BF16X3)
+# ---------------------------------------------------------------- tensor cores (BF16X3, TF32X3)
+# shapes cover the 128-bit load path (L % 4 == 0: (40,30,20) mode 0, (64,48,40),
+# (36,36,36,36)) and the scalar path (L = 1 fibers, odd L such as (70,45,33))
 TC_SHAPES = [((40, 30, 20), 16), ((300, 20), 16), ((20, 18, 17, 16), 16), ((70, 45, 33), 20), ((129, 64, 40), 32),
-             ((66, 65, 64), 64)]
+             ((64, 48, 40), 32), ((36, 36, 36, 36), 16), ((66, 65, 64), 64)]
+TC_TOL = {"bf16x3": 5e-5, "tf32x3": 2e-6}
 
 
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("dims,R", TC_SHAPES)
-def test_bf16x3_index_bookkeeping_bit_exact(cuda_lib, dims, R):
-    # integers |x| <= 48 are exact in bf16 (lo parts are zero) and 0/1 factors keep
-    # every product and partial sum exact in FP32, so the tensor-core path must
-    # agree bit for bit with the oracle; a wrong operand layout cannot pass
+def test_split_tc_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision):
+    # integers |x| <= 48 are exact in bf16 and tf32 (lo parts are zero) and 0/1
+    # factors keep every product and partial sum exact in FP32, so the
+    # tensor-core path must agree bit for bit with the oracle; a wrong operand
+    # layout cannot pass
     P = int(np.prod(dims))
     X = (np.arange(P) * 37 % 97 - 48).astype(np.float64)
     rng = np.random.default_rng(R + len(dims))
     Q = [np.asfortranarray((rng.random((d, R)) < 0.5).astype(np.float64)) for d in dims]
     Rm = [np.asfortranarray(np.triu(np.ones((R, R)))) for _ in dims]
-    h = gpu_handle(dims, R, X, precision="bf16x3")
+    h = gpu_handle(dims, R, X, precision=precision)
     h.set_factor_qr(Q, Rm)
     for n in range(len(dims)):
         Y, _ = h.multi_ttm(n)
         np.testing.assert_array_equal(Y, oracle.multi_ttm(X, dims, n, Q))
 
 
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("dims,R", TC_SHAPES)
-def test_bf16x3_multi_ttm_error_bound(cuda_lib, dims, R):
+def test_split_tc_multi_ttm_error_bound(cuda_lib, dims, R, precision):
     # hi*hi + hi*lo + lo*hi drops lo*lo and rounds the lo parts: about 2^-16
-    # relative per product; with FP32 accumulation the relative Frobenius error
-    # of Y_(n) stays below 5e-5
+    # (bf16) or 2^-21 (tf32) relative per product; with FP32 accumulation the
+    # relative Frobenius error of Y_(n) stays below 5e-5 (bf16) / 2e-6 (tf32)
     X, A = gaussian_problem(dims, R, seed=23)
     QR = [oracle.qr(a) for a in A]
-    h = gpu_handle(dims, R, X, precision="bf16x3")
+    h = gpu_handle(dims, R, X, precision=precision)
     h.set_factor_qr([q for q, _ in QR], [r for _, r in QR])
     for n in range(len(dims)):
         Y, _ = h.multi_ttm(n)
         err = rel(Y, oracle.multi_ttm(X, dims, n, [q for q, _ in QR]))
-        assert err <= 5e-5, (n, err)
+        assert err <= TC_TOL[precision], (n, err)
