@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--workload", choices=["c2", "c3", "c5b"], default="c2",
                     help="c2: the headline 400^3 rank-10 FP64 workload; c3: 4-way 120^4 rank 20 and c5b: 5-way "
                          "40^5 rank 8, both comparing FP64, FP32 and 3xBF16 passes over X")
-    ap.add_argument("--fit-sweeps", type=int, default=20, help="sweeps for the equal-fit comparison")
+    ap.add_argument("--fit-sweeps", type=int, default=300,
+                    help="at most this many sweeps (stop at |fit change| < 1e-10) for the equal-fit comparison")
     return ap.parse_args()
 
 
@@ -299,17 +300,23 @@ def run_mixed(args, world, rank):
         Ys = [ha.multi_ttm(n)[0] for n in range(len(p.dims))]
         fits1 = ha.iterate(1)
         A1, l1 = ha.get_factors()
-        fitsS = ha.iterate(max(args.fit_sweeps - 1, 0))
-        fit_final = float(fitsS[-1]) if len(fitsS) else float(fits1[-1])
+        # run to convergence (|fit change| < 1e-10, at most --fit-sweeps), then
+        # the direct fit: FP64 residual against the FP64 tensor
+        fitsS = ha.iterate(max(args.fit_sweeps - 1, 1), tol=1e-10)
+        sweeps_run = 1 + len(fitsS)
+        fit_final = ha.fit(direct=True)
+        traj = np.concatenate([fits1, fitsS])
         del ha
         entry = {"iters_per_s": its, "gpu_launches_per_sweep": launches / args.steps,
                  "first_ttm_ms": ms, "first_ttm_gbs": xbytes / (ms * 1e-3) / 1e9,
                  "first_ttm_frac_hbm": (xbytes / (ms * 1e-3) / 1e9 / hbm) if hbm else None,
                  "first_ttm_tflops": 2.0 * P * R / (ms * 1e-3) / 1e12,
-                 "fit_after_sweeps": fit_final}
+                 "fit_direct_converged": fit_final, "sweeps_to_converge": sweeps_run}
         if prec == "f64":
-            ref = {"Y": Ys, "A": A1, "fit": fit_final}
+            ref = {"Y": Ys, "A": A1, "fit": fit_final, "traj": traj}
         else:
+            m5 = min(5, len(traj), len(ref["traj"]))
+            entry["fit_traj_max_diff_first5"] = float(np.abs(traj[:m5] - ref["traj"][:m5]).max())
             entry["multi_ttm_rel_err_vs_f64"] = max(
                 float(np.linalg.norm(Ys[n] - ref["Y"][n]) / np.linalg.norm(ref["Y"][n])) for n in range(len(Ys)))
             entry["factor_rel_err_vs_f64_after_1_sweep"] = max(

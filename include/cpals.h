@@ -102,7 +102,9 @@ int cpals_workspace_bytes(const cpals_handle* h, size_t* bytes);
  *    borrowed and must stay valid until the handle is destroyed or another
  *    tensor is set; with mem HOST, X is copied into a device buffer that the
  *    handle owns.  With precision F32/BF16X3/TF32X3, X is rounded (round to
- *    nearest even) into an FP32 copy that the handle owns.
+ *    nearest even) into an FP32 copy that the handle owns.  The passes over X
+ *    read only that copy.  ||X||^2 and the direct fit use the FP64 values, so
+ *    a device FP64 pointer stays borrowed in that case too.
  *  elem = CPALS_ELEM_F32: allowed only with precision F32/BF16X3/TF32X3;
  *    borrowed (DEVICE) or copied (HOST).
  * Also computes ||X||_F^2 in FP64 (Sec. 3.3.1: it is pre-computed once). */

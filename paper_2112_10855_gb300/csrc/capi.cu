@@ -319,8 +319,9 @@ int cpals_set_tensor(cpals_handle* hh, const void* X, int elem, int mem)
             h->X64 = src;   // the norm uses the FP64 values
         }
     }
+    // ||X||^2 and the direct fit use the FP64 values when the caller gave them;
+    // the passes over X (Multi-TTM, MTTKRP) read the FP32 copy only
     CUDA_OR_FAIL(h, cpals::norm2(h), "norm of X");
-    if (h->prec != CPALS_F64) h->X64 = nullptr;   // passes over X read the FP32 copy only
     CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->normX2_host, h->d_normX2, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
                  "norm read");
     CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "set_tensor sync");

@@ -91,6 +91,82 @@ __global__ void __launch_bounds__(TPB) ttm_rows_kernel(
     }
 }
 
+// FP32 variant with four rows per thread (L % 4 == 0, so the four rows share
+// t and are contiguous): one 128-bit load and RC broadcast reads of Q per k
+// feed 4*RC FMAs.  This makes the kernel FMA-bound instead of bound by the
+// shared-memory broadcasts.
+template <int RC, int TPB>
+__global__ void __launch_bounds__(TPB) ttm_rows4_kernel(
+    const float* __restrict__ in, const double* __restrict__ Q, int64_t ldq, float* __restrict__ out,
+    int64_t L, int64_t K, int64_t Tn, int R, int64_t kchunk, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ float qs[kKC][RC];
+    const int64_t rows = L * Tn;
+    const int64_t f = 4 * ((int64_t)blockIdx.x * TPB + threadIdx.x);
+    const int r0 = blockIdx.y * RC;
+    const int rc = min(RC, R - r0);
+    const bool active = f < rows;          // rows % 4 == 0, so all four rows exist
+    const int64_t kb = (int64_t)blockIdx.z * kchunk;
+    const int64_t ke = (kb + kchunk < K) ? kb + kchunk : K;
+    int64_t t = 0, l = 0;
+    if (active) { t = f / L; l = f - t * L; }
+    const float* p = in + l + L * K * t;
+
+    float acc[4][RC];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int r = 0; r < RC; ++r) acc[i][r] = 0.0f;
+
+    for (int64_t k0 = kb; k0 < ke; k0 += kKC) {
+        const int kc = (int)((ke - k0) < (int64_t)kKC ? (ke - k0) : (int64_t)kKC);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kKC * RC; i += TPB) {
+            const int kk = i / RC, rr = i - kk * RC;
+            qs[kk][rr] = (kk < kc && rr < rc) ? (float)Q[(k0 + kk) + ldq * (int64_t)(r0 + rr)] : 0.0f;
+        }
+        __syncthreads();
+        if (!active) continue;
+        const float* pk = p + L * k0;
+        int kk = 0;
+        for (; kk + 4 <= kc; kk += 4) {
+            float4 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(reinterpret_cast<const float4*>(pk + L * (kk + u)));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
+                    const float q = qs[kk + u][r];
+                    acc[0][r] = fmaf(x[u].x, q, acc[0][r]);
+                    acc[1][r] = fmaf(x[u].y, q, acc[1][r]);
+                    acc[2][r] = fmaf(x[u].z, q, acc[2][r]);
+                    acc[3][r] = fmaf(x[u].w, q, acc[3][r]);
+                }
+        }
+        for (; kk < kc; ++kk) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(pk + L * kk));
+#pragma unroll
+            for (int r = 0; r < RC; ++r) {
+                const float q = qs[kk][r];
+                acc[0][r] = fmaf(x.x, q, acc[0][r]);
+                acc[1][r] = fmaf(x.y, q, acc[1][r]);
+                acc[2][r] = fmaf(x.z, q, acc[2][r]);
+                acc[3][r] = fmaf(x.w, q, acc[3][r]);
+            }
+        }
+    }
+    if (active) {
+        float* o = out + (int64_t)blockIdx.z * (L * (int64_t)R * Tn) + l + L * (int64_t)R * t;
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+            if (r < rc)
+                *reinterpret_cast<float4*>(o + L * (int64_t)(r0 + r)) =
+                    make_float4(acc[0][r], acc[1][r], acc[2][r], acc[3][r]);
+    }
+}
+
 template <typename T>
 __global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int64_t n, T* __restrict__ out,
                                      const int* __restrict__ status)
@@ -108,6 +184,7 @@ __global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int64_t
 // resident in one wave; FP32 is bound by HBM and uses 256-row CTAs.
 template <typename T>
 struct TtmTpb { static constexpr int value = 256; };
+constexpr int kQuadTpb = 128;   // FP32 row-quad kernel: 512 rows per CTA
 template <>
 struct TtmTpb<double> { static constexpr int value = 64; };
 
@@ -135,7 +212,11 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     if (rows == 0) return cudaSuccess;
     const int rc = ttm_width(R);
     const int tpb = sizeof(T) == 8 ? TtmTpb<double>::value : TtmTpb<float>::value;
-    const int64_t gx = (rows + tpb - 1) / tpb;
+    // FP32 with four rows per thread when the rows come in aligned quads
+    const bool quad = sizeof(T) == 4 && (s.L % 4) == 0 && rc <= 24 &&
+                      (((uintptr_t)in) & 15) == 0 && (((uintptr_t)out) & 15) == 0 && (((uintptr_t)part) & 15) == 0;
+    const int64_t rows_per_cta = quad ? 4 * kQuadTpb : tpb;
+    const int64_t gx = (rows + rows_per_cta - 1) / rows_per_cta;
     const int64_t gy = (R + rc - 1) / rc;
     // split K when the row blocks alone cannot fill two waves of the SMs
     int64_t ks = 1;
@@ -152,7 +233,22 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     ks = (s.K + kchunk - 1) / kchunk;
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
     T* dst = (ks > 1) ? part : out;
-    switch (rc) {
+    if (quad) {
+        const float* fin = reinterpret_cast<const float*>(in);
+        float* fdst = reinterpret_cast<float*>(dst);
+        switch (rc) {
+#define CPALS_RQ(W)                                                                                            \
+    case W:                                                                                                    \
+        ttm_rows4_kernel<W, kQuadTpb><<<grid, kQuadTpb, 0, h->stream>>>(fin, Q, ldq, fdst, s.L, s.K, s.T, R,   \
+                                                                        kchunk, h->d_status);                  \
+        break;
+            CPALS_RQ(1) CPALS_RQ(2) CPALS_RQ(3) CPALS_RQ(4) CPALS_RQ(5) CPALS_RQ(6) CPALS_RQ(7) CPALS_RQ(8)
+            CPALS_RQ(9) CPALS_RQ(10) CPALS_RQ(11) CPALS_RQ(12) CPALS_RQ(13) CPALS_RQ(14) CPALS_RQ(15) CPALS_RQ(16)
+            CPALS_RQ(20) CPALS_RQ(24)
+#undef CPALS_RQ
+            default: return cudaErrorInvalidValue;
+        }
+    } else switch (rc) {
 #define CPALS_RC(W) case W: launch_rows<T, W>(grid, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
         CPALS_RC(1) CPALS_RC(2) CPALS_RC(3) CPALS_RC(4) CPALS_RC(5) CPALS_RC(6) CPALS_RC(7) CPALS_RC(8)
         CPALS_RC(9) CPALS_RC(10) CPALS_RC(11) CPALS_RC(12) CPALS_RC(13) CPALS_RC(14) CPALS_RC(15) CPALS_RC(16)
