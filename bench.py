@@ -150,6 +150,20 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def kernel_source(name, path=os.path.join(ROOT, "paper_2112_10855_gb300", "csrc", "ttm.cu")):
+    """Source text of one __global__ kernel (its template line through the
+    closing brace), used to tell whether recorded counters still apply."""
+    with open(path) as f:
+        lines = f.read().split("\n")
+    for i, ln in enumerate(lines):
+        if "__global__" in ln and (name + "(") in ln:
+            start = i - 1 if i > 0 and lines[i - 1].startswith("template") else i
+            for j in range(i, len(lines)):
+                if lines[j] == "}":
+                    return "\n".join(lines[start:j + 1])
+    return ""
+
+
 def recorded_traffic(profile="ttm_rows_f64_400cubed_r10.md"):
     """DRAM traffic per launch of the dominant kernel from the committed ncu
     summary, or None if the kernel source changed since it was captured."""
@@ -159,8 +173,7 @@ def recorded_traffic(profile="ttm_rows_f64_400cubed_r10.md"):
         with open(os.path.join(ROOT, "profiles", profile)) as f:
             text = f.read()
         want = re.search(r"sha256\[:16\] = ([0-9a-f]+)", text).group(1)
-        with open(os.path.join(ROOT, "paper_2112_10855_gb300", "csrc", "ttm.cu"), "rb") as f:
-            have = hashlib.sha256(f.read()).hexdigest()[:16]
+        have = hashlib.sha256(kernel_source("ttm_rows_kernel").encode()).hexdigest()[:16]
         if want != have:
             return None
         return int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
