@@ -48,7 +48,8 @@ void free_all(Handle* h)
 {
     auto f = [](void* p) { if (p) cudaFree(p); };
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->A[m]); f(h->Q[m]); f(h->Rf[m]); f(h->G[m]); }
-    f(h->lambda); f(h->V); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
+    f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
+    f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
     f(h->tbuf[0]); f(h->tbuf[1]); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned);
     for (int s = 0; s < 3; ++s) if (h->graph[s]) cudaGraphExecDestroy(h->graph[s]);
@@ -215,11 +216,14 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
         ok = dalloc(h, &h->A[m], dims[m] * R) == cudaSuccess && dalloc(h, &h->Q[m], dims[m] * R) == cudaSuccess &&
              dalloc(h, &h->Rf[m], (size_t)R * R) == cudaSuccess && dalloc(h, &h->G[m], (size_t)R * R) == cudaSuccess;
     }
-    ok = ok && dalloc(h, &h->lambda, R) == cudaSuccess && dalloc(h, &h->V, h->RN1 * R) == cudaSuccess &&
+    ok = ok && dalloc(h, &h->lambda, R) == cudaSuccess &&
          dalloc(h, &h->Q0, h->RN1 * R) == cudaSuccess && dalloc(h, &h->R0, (size_t)R * R) == cudaSuccess &&
          dalloc(h, &h->Yn, h->Imax * h->RN1) == cudaSuccess && dalloc(h, &h->W, h->Imax * R) == cudaSuccess &&
          dalloc(h, &h->Ahat, h->Imax * R) == cudaSuccess && dalloc(h, &h->M, h->Imax * R) == cudaSuccess &&
          dalloc(h, &h->S, (size_t)R * R) == cudaSuccess && dalloc(h, &h->T, (size_t)R * R) == cudaSuccess &&
+         dalloc(h, &h->KM, (size_t)R * R * R) == cudaSuccess && dalloc(h, &h->KQ, (size_t)R * R * R) == cudaSuccess &&
+         dalloc(h, &h->KR[0], (size_t)R * R) == cudaSuccess && dalloc(h, &h->KR[1], (size_t)R * R) == cudaSuccess &&
+         dalloc(h, &h->KQb[0], h->RN1 * R) == cudaSuccess && dalloc(h, &h->KQb[1], h->RN1 * R) == cudaSuccess &&
          dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
          dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
          dalloc(h, &h->d_fit_count, 1) == cudaSuccess;

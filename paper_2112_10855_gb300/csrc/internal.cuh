@@ -72,7 +72,6 @@ struct Handle {
     bool gram_valid[kMaxN] = {false};
 
     // per-mode-update buffers
-    double* V = nullptr;     // R^{N-1} x R
     double* Q0 = nullptr;    // R^{N-1} x R
     double* R0 = nullptr;    // R x R
     double* Yn = nullptr;    // Imax x R^{N-1} (unfolding, FP64)
@@ -81,6 +80,12 @@ struct Handle {
     double* M = nullptr;     // Imax x R (MTTKRP)
     double* S = nullptr;     // R x R (Hadamard of Grams)
     double* T = nullptr;     // R x R solve operator (SVD path)
+    // structured QR of V_n: Khatri-Rao of two R x R factors, its Q, the two
+    // ping-pong R factors, and the ping-pong partial Q0 (up to R^{N-1} x R)
+    double* KM = nullptr;    // R^2 x R
+    double* KQ = nullptr;    // R^2 x R
+    double* KR[2] = {nullptr, nullptr};
+    double* KQb[2] = {nullptr, nullptr};
     int krp_mode = -1;       // mode whose Q0/R0 are current
 
     // TTM intermediates (ping-pong), in the Multi-TTM's arithmetic type
@@ -139,7 +144,7 @@ cudaError_t residual_direct(Handle* h, double* d_out);
 // Householder QR with explicit Q and diag(R) >= 0 (Sec. 2.1).  A is m x n
 // (lda = m), Q is m x n, R is n x n.  A may alias Q.
 cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R);
-// V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->V and its QR into h->Q0, h->R0.
+// QR of V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->Q0, h->R0 (structured, V_n not formed).
 cudaError_t krp_qr(Handle* h, int n);
 // C (m x n) = A (m x k) * B (k x n), FP64, column-major.
 cudaError_t gemm_nn(Handle* h, const double* A, const double* B, double* C, int64_t m, int64_t k, int64_t n);

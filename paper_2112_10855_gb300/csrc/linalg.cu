@@ -164,28 +164,36 @@ inline size_t qr_smem_bytes(int mb, int n) { return sizeof(double) * ((size_t)2 
 constexpr int kQrSmemLimitDoubles = 24000;   // 2*mb*n doubles of the leaf QR (<= ~192 KB)
 
 // ---------------------------------------------------------------- Khatri-Rao
-struct RPtrs {
-    const double* R[kMaxN];
-};
-
-// V(row, r) = prod_{m != n} R_m(i_m, r), row = sum_{m != n} i_m R^{pos(m)} (mode 0 fastest).
-__global__ void krp_kernel(RPtrs rp, int N, int n, int R, int64_t rows, double* __restrict__ V,
-                           const int* __restrict__ status)
+// M(i*R + j, c) = F(i, c) * G(j, c): the Khatri-Rao product F (.) G of two
+// R x R factors, the right factor's row index fastest (Sec. 2.2).
+__global__ void krp2_kernel(const double* __restrict__ F, const double* __restrict__ G, int R,
+                            double* __restrict__ M, const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
-    const int64_t total = rows * R;
+    const int64_t rows = (int64_t)R * R, total = rows * R;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = e / rows, row = e - r * rows;
-        int64_t rem = row;
-        double p = 1.0;
-        for (int m = 0; m < N; ++m) {
-            if (m == n) continue;
-            const int64_t i = rem % R;
-            rem /= R;
-            p *= rp.R[m][i + (int64_t)R * r];
-        }
-        V[e] = p;
+        const int64_t c = e / rows, row = e - c * rows;
+        const int64_t i = row / R, j = row - i * R;
+        M[e] = F[i + (int64_t)R * c] * G[j + (int64_t)R * c];
+    }
+}
+
+// out = (I_R (x) Qb) Qp: out(i*S + j, c) = sum_c' Qb(j, c') Qp(i*R + c', c),
+// with Qb of size S x R and Qp of size R^2 x R (Kronecker index rule, Sec. 2.2).
+__global__ void kron_left_apply_kernel(const double* __restrict__ Qb, int64_t S, const double* __restrict__ Qp,
+                                       int R, double* __restrict__ out, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t rows = (int64_t)R * S, total = rows * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / rows, row = e - c * rows;
+        const int64_t i = row / S, j = row - i * S;
+        const double* qp = Qp + i * R + (int64_t)R * R * c;
+        double acc = 0.0;
+        for (int cp = 0; cp < R; ++cp) acc = fma(Qb[j + S * cp], qp[cp], acc);
+        out[e] = acc;
     }
 }
 
@@ -593,16 +601,51 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
     return tsqr(h, A, m, n, Q, R, h->scratch, h->scratch_elems);
 }
 
+// QR of V_n = F_1 (.) F_2 (.) ... (.) F_{N-1} (the R_m of every mode m != n, highest
+// mode first; Sec. 3.1) without forming V_n.  If B = Q_B R_B is the thin QR
+// of the trailing Khatri-Rao product, then by Eq. kr-id
+//     F (.) B = (I_R (x) Q_B) (F (.) R_B),
+// and I_R (x) Q_B has orthonormal columns, so QR(F (.) B) needs only the QR of
+// the R^2 x R matrix F (.) R_B.  Folding from the lowest mode upward, the QR of V_n
+// takes N-2 QRs of R^2 x R matrices and one Kronecker-structured product per
+// step to build the explicit Q0 (R^{N-1} x R).  The thin QR with diag(R0) >= 0
+// is unique, so this equals the Householder QR of the explicit V_n up to
+// rounding.
 cudaError_t krp_qr(Handle* h, int n)
 {
-    RPtrs rp;
-    for (int m = 0; m < h->N; ++m) rp.R[m] = h->Rf[m];
-    const int64_t total = h->RN1 * h->R;
-    krp_kernel<<<grid_for(total, 256, h->num_sms), 256, 0, h->stream>>>(rp, h->N, n, h->R, h->RN1, h->V,
-                                                                         h->d_status);
-    h->launches++;
-    CPALS_CUDA_TRY(cudaGetLastError());
-    return householder_qr(h, h->V, h->RN1, h->R, h->Q0, h->R0);
+    const int R = h->R;
+    int modes[kMaxN];
+    int cnt = 0;
+    for (int m = 0; m < h->N; ++m)
+        if (m != n) modes[cnt++] = m;   // ascending: modes[0] is the fastest (rightmost) factor
+    if (cnt == 1) return householder_qr(h, h->Rf[modes[0]], R, R, h->Q0, h->R0);
+    const double* curR = h->Rf[modes[0]];
+    int64_t S = 0;                       // rows of the current Q_B (0: Q_B = I)
+    for (int k = 1; k < cnt; ++k) {
+        const bool last = (k == cnt - 1);
+        krp2_kernel<<<grid_for((int64_t)R * R * R, 256, h->num_sms), 256, 0, h->stream>>>(h->Rf[modes[k]], curR, R,
+                                                                                          h->KM, h->d_status);
+        h->launches++;
+        CPALS_CUDA_TRY(cudaGetLastError());
+        double* Rout = last ? h->R0 : h->KR[k & 1];
+        if (S == 0) {
+            // Q_B = I: the QR of F (.) R_B is already Q0 (or the next Q_B)
+            double* Qout = last ? h->Q0 : h->KQb[k & 1];
+            CPALS_CUDA_TRY(householder_qr(h, h->KM, (int64_t)R * R, R, Qout, Rout));
+            S = (int64_t)R * R;
+        } else {
+            CPALS_CUDA_TRY(householder_qr(h, h->KM, (int64_t)R * R, R, h->KQ, Rout));
+            const double* Qb = h->KQb[(k - 1) & 1];
+            double* Qout = last ? h->Q0 : h->KQb[k & 1];
+            kron_left_apply_kernel<<<grid_for((int64_t)R * S * R, 256, h->num_sms), 256, 0, h->stream>>>(
+                Qb, S, h->KQ, R, Qout, h->d_status);
+            h->launches++;
+            CPALS_CUDA_TRY(cudaGetLastError());
+            S *= R;
+        }
+        curR = Rout;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t gemm_nn(Handle* h, const double* A, const double* B, double* C, int64_t m, int64_t k, int64_t n)
