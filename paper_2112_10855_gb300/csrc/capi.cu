@@ -51,7 +51,10 @@ void free_all(Handle* h)
     f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
     f(h->tbuf[0]); f(h->tbuf[1]); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
-    f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned);
+    f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (int s = 0; s < 3; ++s) if (h->graph[s]) cudaGraphExecDestroy(h->graph[s]);
 }
 
@@ -129,9 +132,19 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol)
         CPALS_CUDA_TRY(cpals::mttkrp(h, n));
         CPALS_CUDA_TRY(cpals::solve_normal(h, n));
     } else {
-        CPALS_CUDA_TRY(cpals::krp_qr(h, n));
+        // The QR of V_n needs only the R_m and the Multi-TTM only the Q_m: run the
+        // QR on the side stream meanwhile and join before W = Y_(n) Q0.
+        CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+        CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        cudaStream_t main = h->stream;
+        h->stream = h->side;
+        cudaError_t e = cpals::krp_qr(h, n);
+        h->stream = main;
+        CPALS_CUDA_TRY(e);
+        CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
         h->krp_mode = n;
         CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
+        CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
         CPALS_CUDA_TRY(cpals::gemm_nn(h, h->Yn, h->Q0, h->W, In, h->RN1, h->R));
         if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
         else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol));
@@ -227,6 +240,15 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
          dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
          dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
          dalloc(h, &h->d_fit_count, 1) == cudaSuccess;
+    h->qr_ws_elems = std::max<int64_t>(4 * big * R + 64 * R * R, 4096);
+    ok = ok && dalloc(h, &h->qr_ws, h->qr_ws_elems) == cudaSuccess;
+    if (ok) {
+        int lo = 0, hi = 0;
+        ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    }
     if (ok) {
         void* p0 = nullptr; void* p1 = nullptr;
         ok = cudaMalloc(&p0, tsz * h->tbuf_elems) == cudaSuccess && cudaMalloc(&p1, tsz * h->tbuf_elems) == cudaSuccess;
@@ -252,6 +274,7 @@ int cpals_destroy(cpals_handle* hh)
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return CPALS_OK;
     cudaStreamSynchronize(h->stream);
+    if (h->side) cudaStreamSynchronize(h->side);
     free_all(h);
     delete h;
     return CPALS_OK;

@@ -91,9 +91,17 @@ struct Handle {
     // TTM intermediates (ping-pong), in the Multi-TTM's arithmetic type
     void* tbuf[2] = {nullptr, nullptr};
     int64_t tbuf_elems = 0;
-    // generic FP64 scratch for split reductions and TSQR
+    // FP64 scratch for split-K partials, reductions and pre-split tensor-core
+    // tiles (main stream), and a separate workspace for the TSQR levels, so a QR
+    // on the side stream never shares memory with the Multi-TTM
     double* scratch = nullptr;
     int64_t scratch_elems = 0;
+    double* qr_ws = nullptr;
+    int64_t qr_ws_elems = 0;
+    // side stream (higher priority) for the QR of V_n, which overlaps the
+    // Multi-TTM; fork/join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // device scalars
     int* d_status = nullptr;

@@ -598,7 +598,7 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
                                             (int)(sizeof(double) * (kQrSmemLimitDoubles + 64 + 32))));
         attr_set = true;
     }
-    return tsqr(h, A, m, n, Q, R, h->scratch, h->scratch_elems);
+    return tsqr(h, A, m, n, Q, R, h->qr_ws, h->qr_ws_elems);
 }
 
 // QR of V_n = F_1 (.) F_2 (.) ... (.) F_{N-1} (the R_m of every mode m != n, highest
