@@ -145,7 +145,7 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol)
         h->krp_mode = n;
         CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-        CPALS_CUDA_TRY(cpals::gemm_nn(h, h->Yn, h->Q0, h->W, In, h->RN1, h->R));
+        CPALS_CUDA_TRY(cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W));
         if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
         else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol));
     }
@@ -467,7 +467,7 @@ int cpals_multi_ttm(cpals_handle* hh, int mode, double* Y, double* W, int mem)
     CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, mode), "refresh QR");
     CUDA_OR_FAIL(h, cpals::multi_ttm(h, mode, h->Q), "Multi-TTM");
     const int64_t In = h->dims[mode];
-    if (W) CUDA_OR_FAIL(h, cpals::gemm_nn(h, h->Yn, h->Q0, h->W, In, h->RN1, h->R), "apply Q0");
+    if (W) CUDA_OR_FAIL(h, cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W), "apply Q0");
     if (Y) CUDA_OR_FAIL(h, cudaMemcpyAsync(Y, h->Yn, sizeof(double) * In * h->RN1, kind_out(mem), h->stream), "copy Y");
     if (W) CUDA_OR_FAIL(h, cudaMemcpyAsync(W, h->W, sizeof(double) * In * h->R, kind_out(mem), h->stream), "copy W");
     if (mem == CPALS_MEM_HOST) return take_status(h);

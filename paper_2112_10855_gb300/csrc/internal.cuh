@@ -154,8 +154,9 @@ cudaError_t residual_direct(Handle* h, double* d_out);
 cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R);
 // QR of V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->Q0, h->R0 (structured, V_n not formed).
 cudaError_t krp_qr(Handle* h, int n);
-// C (m x n) = A (m x k) * B (k x n), FP64, column-major.
-cudaError_t gemm_nn(Handle* h, const double* A, const double* B, double* C, int64_t m, int64_t k, int64_t n);
+// C (m x n) = A (m x k) B (k x n), FP64, column-major, on the TTM kernel (one thread per output row, R-wide
+// register tile, split-K): used for W = Y_(n) Q0 and W T.
+cudaError_t gemm_rows(Handle* h, const double* A, int64_t m, int64_t k, const double* B, int n, double* C);
 // Solve Ahat R0^T = W (QR) or Ahat = W U pinv(S) V^T (SVD) into h->Ahat.
 cudaError_t solve_qr(Handle* h, int64_t In);
 cudaError_t solve_svd(Handle* h, int64_t In, double rtol);

@@ -509,6 +509,14 @@ cudaError_t multi_ttm(Handle* h, int n, const double* const* Q)
     return multi_ttm_impl<float>(h, n, Q);
 }
 
+// C (m x n) = A (m x k) B (k x n), column-major FP64: a TTM with L = m,
+// K = k, T = 1 (rows of A are the output rows), with the same split-K.
+cudaError_t gemm_rows(Handle* h, const double* A, int64_t m, int64_t k, const double* B, int n, double* C)
+{
+    TtmShape s{m, k, 1};
+    return launch_ttm<double>(h, A, B, k, C, s, n);
+}
+
 cudaError_t ttm_first(Handle* h, int n)
 {
     int order[kMaxN];
