@@ -31,16 +31,6 @@ __device__ __forceinline__ double warp_sum(double v)
 // and R_b (written to rows [b*n, (b+1)*n) of Rout, ldr).  Reflectors follow
 // LAPACK's dlarfg form H = I - tau v v^T with v(0) = 1; the diagonal of R is
 // made non-negative by flipping the matching row of R and column of Q.
-//
-// Parallel layout (FP64 runs at 2 lanes/clk/SM, so work, not latency, is what
-// the layout must spread): for reflector j the trailing columns k > j are
-// dotted with v in one pass where thread t owns column c = t % nc and row slice
-// s = t / nc (S = 256 / nc slices).  The S partial sums of each column are then
-// added in slice order by one thread per column (no shuffle trees), and the
-// same (slice, column) threads apply the rank-one update.  The squared norm
-// of the next column is summed during the update.  The working matrix and Q
-// live in shared memory with an odd leading dimension, so lanes that walk
-// different columns of one row hit different banks.
 __global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
     const double* __restrict__ A, int64_t lda, int64_t m, int n, int nb, double* __restrict__ Qout,
     int64_t ldq, double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
@@ -50,152 +40,101 @@ __global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
     const int b = blockIdx.x;
     const int64_t off = (int64_t)b * m / nb, end = (int64_t)(b + 1) * m / nb;
     const int mb = (int)(end - off);
-    const int ld = mb | 1;                // odd leading dimension
-    double* W = sm;                       // ld x n (reflectors below the diagonal, R above)
-    double* Qs = W + (size_t)ld * n;      // ld x n
-    double* tau = Qs + (size_t)ld * n;    // n
-    double* vb = tau + n;                 // mb: scaled reflector of the current step
-    double* part = vb + mb;               // kQrThreads partial sums
-    double* part2 = part + kQrThreads;    // kQrThreads partial norms / Q-phase coefficients
-    double* coefb = part2 + kQrThreads;   // kMaxRank column coefficients
-    __shared__ double sc_scale, sc_norm2;
-    const int tid = threadIdx.x;
+    double* W = sm;                       // mb x n (reflectors below the diagonal, R above)
+    double* Qs = sm + (size_t)mb * n;     // mb x n
+    double* tau = Qs + (size_t)mb * n;    // n
+    double* red = tau + n;                // 32 scratch
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kQrThreads / 32;
 
     for (int64_t e = tid; e < (int64_t)mb * n; e += kQrThreads) {
         const int j = (int)(e / mb), i = (int)(e - (int64_t)j * mb);
-        W[i + (int64_t)ld * j] = A[(off + i) + lda * j];
-    }
-    __syncthreads();
-    if (tid == 0) {                        // norm^2 of W(1:mb, 0)
-        double s2 = 0.0;
-        for (int i = 1; i < mb; ++i) s2 = fma(W[i], W[i], s2);
-        sc_norm2 = s2;
+        W[e] = A[(off + i) + lda * j];
     }
     __syncthreads();
 
     const int kmax = min(mb, n);
     for (int j = 0; j < kmax; ++j) {
-        const int nc = n - j - 1;                       // trailing columns
-        const int ncc = nc > 0 ? nc : 1;
-        const int S = kQrThreads / ncc;                 // row slices
-        const int c = tid % ncc, sl = tid / ncc;
-        const bool worker = sl < S;
-        // (a) reflector scalars (dlarfg): one division
-        if (tid == 0) {
-            const double alpha = W[j + (int64_t)ld * j];
-            const double s2 = sc_norm2;
-            double t = 0.0, scale = 0.0, beta = alpha;
-            if (s2 > 0.0) {
-                const double nrm = sqrt(fma(alpha, alpha, s2));
-                beta = (alpha >= 0.0) ? -nrm : nrm;
-                const double d = beta - alpha;          // tau = d / beta, scale = -1 / d
-                const double r = 1.0 / (beta * d);
-                t = d * d * r;
-                scale = -beta * r;
-            }
-            tau[j] = t;
-            sc_scale = scale;
-            W[j + (int64_t)ld * j] = beta;
-        }
-        __syncthreads();
-        const double tj = tau[j], scale = sc_scale;
-        if (tj == 0.0) {                                 // H_j = I
-            if (tid == 0) {
-                double s2 = 0.0;
-                if (j + 1 < n)
-                    for (int i = j + 2; i < mb; ++i) s2 = fma(W[i + (int64_t)ld * (j + 1)], W[i + (int64_t)ld * (j + 1)], s2);
-                sc_norm2 = s2;
-            }
-            __syncthreads();
-            continue;
-        }
-        // (b) scaled reflector into vb; partial dots of the trailing columns
-        for (int i = j + 1 + tid; i < mb; i += kQrThreads) vb[i] = W[i + (int64_t)ld * j] * scale;
-        if (tid == 0) vb[j] = 1.0;
-        __syncthreads();
-        if (worker && c < nc) {
-            const double* wk = W + (int64_t)ld * (j + 1 + c);
-            double acc = 0.0;
-            for (int i = j + sl; i < mb; i += S) acc = fma(vb[i], wk[i], acc);
-            part[sl * ncc + c] = acc;
-        }
-        __syncthreads();
-        // (c) per column: tau * sum of the slice partials, in slice order
-        if (tid < nc) {
-            double acc = 0.0;
-            for (int q = 0; q < S; ++q) acc += part[q * ncc + tid];
-            coefb[tid] = tj * acc;                       // coefficient of column j+1+tid
-        }
-        __syncthreads();
-        // (d) rank-one update; norm^2 of the next column below its diagonal
-        double nrm_part = 0.0;
-        if (worker && c < nc) {
-            const double coef = coefb[c];
-            double* wk = W + (int64_t)ld * (j + 1 + c);
-            for (int i = j + sl; i < mb; i += S) {
-                const double v = fma(-coef, vb[i], wk[i]);
-                wk[i] = v;
-                if (c == 0 && i > j + 1) nrm_part = fma(v, v, nrm_part);
+        // norm of W(j+1:mb, j) -- warp 0
+        if (warp == 0) {
+            double s = 0.0;
+            for (int i = j + 1 + lane; i < mb; i += 32) s = fma(W[i + mb * j], W[i + mb * j], s);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double alpha = W[j + mb * j];
+                double t = 0.0, scale = 0.0, beta = alpha;
+                if (s > 0.0) {
+                    const double nrm = sqrt(fma(alpha, alpha, s));
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    const double d = beta - alpha;      // tau = d / beta, scale = -1 / d: one division
+                    const double r = 1.0 / (beta * d);
+                    t = d * d * r;
+                    scale = -beta * r;
+                }
+                tau[j] = t;
+                red[0] = scale;
+                W[j + mb * j] = beta;
             }
         }
-        for (int i = j + 1 + tid; i < mb; i += kQrThreads) W[i + (int64_t)ld * j] = vb[i];   // keep v below R
-        if (c == 0 && worker) part2[sl] = nrm_part;
         __syncthreads();
-        if (tid == 0) {
-            double s2 = 0.0;
-            for (int q = 0; q < S; ++q) s2 += part2[q];
-            sc_norm2 = s2;
+        const double scale = red[0];
+        if (tau[j] != 0.0)
+            for (int i = j + 1 + tid; i < mb; i += kQrThreads) W[i + mb * j] *= scale;
+        __syncthreads();
+        // apply H_j to columns j+1..n-1 (one warp per column)
+        const double tj = tau[j];
+        if (tj != 0.0) {
+            for (int k = j + 1 + warp; k < n; k += nwarps) {
+                double s = 0.0;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    s = fma(v, W[i + mb * k], s);
+                }
+                s = warp_sum(s) * tj;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    W[i + mb * k] = fma(-s, v, W[i + mb * k]);
+                }
+            }
         }
         __syncthreads();
     }
-    for (int j = kmax; j < n; ++j)
-        if (tid == 0) tau[j] = 0.0;
-    // explicit Q = H_0 ... H_{k-1} [I; 0], backward accumulation, same layout
+    for (int j = kmax; j < n; ++j) if (tid == 0) tau[j] = 0.0;
+    // explicit Q = H_0 ... H_{k-1} [I; 0], backward accumulation
     for (int64_t e = tid; e < (int64_t)mb * n; e += kQrThreads) {
         const int j = (int)(e / mb), i = (int)(e - (int64_t)j * mb);
-        Qs[i + (int64_t)ld * j] = (i == j) ? 1.0 : 0.0;
+        Qs[e] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int j = kmax - 1; j >= 0; --j) {
         const double tj = tau[j];
-        if (tj == 0.0) continue;
-        const int nc = n - j;                            // columns j..n-1
-        const int S = kQrThreads / nc;
-        const int c = tid % nc, sl = tid / nc;
-        const bool worker = sl < S;
-        const double* vj = W + (int64_t)ld * j;          // v(j) = 1, v(i > j) below the diagonal
-        if (worker) {
-            const double* qk = Qs + (int64_t)ld * (j + c);
-            double acc = 0.0;
-            for (int i = j + sl; i < mb; i += S) acc = fma((i == j) ? 1.0 : vj[i], qk[i], acc);
-            part[sl * nc + c] = acc;
-        }
-        __syncthreads();
-        if (tid < nc) {
-            double acc = 0.0;
-            for (int q = 0; q < S; ++q) acc += part[q * nc + tid];
-            part2[tid] = tj * acc;
-        }
-        __syncthreads();
-        if (worker) {
-            const double coef = part2[c];
-            double* qk = Qs + (int64_t)ld * (j + c);
-            for (int i = j + sl; i < mb; i += S) qk[i] = fma(-coef, (i == j) ? 1.0 : vj[i], qk[i]);
+        if (tj != 0.0) {
+            for (int k = j + warp; k < n; k += nwarps) {
+                double s = 0.0;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    s = fma(v, Qs[i + mb * k], s);
+                }
+                s = warp_sum(s) * tj;
+                for (int i = j + lane; i < mb; i += 32) {
+                    const double v = (i == j) ? 1.0 : W[i + mb * j];
+                    Qs[i + mb * k] = fma(-s, v, Qs[i + mb * k]);
+                }
+            }
         }
         __syncthreads();
     }
     // sign convention diag(R) >= 0, write out
     for (int64_t e = tid; e < (int64_t)mb * n; e += kQrThreads) {
         const int j = (int)(e / mb), i = (int)(e - (int64_t)j * mb);
-        const double sgn = (j < kmax && W[j + (int64_t)ld * j] < 0.0) ? -1.0 : 1.0;
-        Qout[(off + i) + ldq * j] = sgn * Qs[i + (int64_t)ld * j];
+        const double sgn = (j < kmax && W[j + mb * j] < 0.0) ? -1.0 : 1.0;
+        Qout[(off + i) + ldq * j] = sgn * Qs[e];
     }
     for (int e = tid; e < n * n; e += kQrThreads) {
         const int j = e / n, i = e - j * n;     // R(i, j)
         double v = 0.0;
         if (i <= j && i < kmax) {
-            const double sgn = (W[i + (int64_t)ld * i] < 0.0) ? -1.0 : 1.0;
-            v = sgn * W[i + (int64_t)ld * j];
+            const double sgn = (W[i + mb * i] < 0.0) ? -1.0 : 1.0;
+            v = sgn * W[i + mb * j];
         }
         Rout[((int64_t)b * n + i) + ldr * j] = v;
     }
@@ -222,11 +161,10 @@ __global__ void tsqr_combine_kernel(const double* __restrict__ Qi, int64_t m, in
     }
 }
 
-// W and Q (odd leading dimension), tau, the scaled reflector, 2 x 256 partials
-// and the column coefficients
+// W and Q (mb x n each), tau (n) and 32 scratch values
 inline size_t qr_smem_bytes(int64_t mb, int n)
 {
-    return sizeof(double) * ((size_t)2 * (size_t)(mb | 1) * n + n + (size_t)mb + 2 * kQrThreads + kMaxRank);
+    return sizeof(double) * ((size_t)2 * (size_t)mb * n + n + 32);
 }
 
 constexpr size_t kQrSmemMaxBytes = 200 * 1024;   // one leaf CTA's shared memory
