@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the SVD/NORMAL/FP32 side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--workload", choices=["c2", "c3", "c5b"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c5b", "c4"], default="c2",
                     help="c2: the headline 400^3 rank-10 FP64 workload; c3: 4-way 120^4 rank 20 and c5b: 5-way "
                          "40^5 rank 8, both comparing FP64, FP32 and 3xBF16 passes over X")
     ap.add_argument("--fit-sweeps", type=int, default=300,
@@ -349,11 +349,105 @@ def run_mixed(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_batch(args, world, rank):
+    """512 independent 3-way problems (dims ~ U{16..128}, ranks ~ U{2..16}, planted
+    rank plus 1% noise): the batched path (one persistent kernel per mode
+    update, one graph per sweep) against one handle per problem (one graph
+    launch per problem per sweep), both FP32 passes over X and FP64 factors."""
+    import torch
+    from paper_2112_10855_gb300 import _build, cpals, inputs
+    torch.cuda.set_device(0)
+    _build.build()
+    cpals.load()
+    count = 512
+    dims, ranks = inputs.batch_shapes(count, seed=2112 + rank)
+    probs = [inputs.planted(tuple(int(x) for x in dims[p]), int(ranks[p]), seed=2112 + 7919 * rank + p,
+                            init_seed=10855 + 7919 * rank + p, noise=0.01) for p in range(count)]
+    X32 = [pr.X.astype(np.float32) for pr in probs]
+    total_elems = int(sum(x.size for x in X32))
+    stream = torch.cuda.Stream()
+    b = cpals.CPALSBatch([pr.dims for pr in probs], [pr.rank for pr in probs])
+    b.set_stream(stream)
+    b.set_tensors(X32)
+    b.set_factors([pr.init_factors for pr in probs])
+    b.iterate(args.warmup)                      # includes the launch-shape tuning and the graph capture
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = b.launch_count()
+    e0.record(stream)
+    fits_b, st_b = b.iterate(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1)
+    launches_b = b.launch_count() - l0
+    grid, threads = b.launch_shape()
+    del b
+    # one problem per launch: a single-problem handle each, one graph launch per sweep
+    Xd = [torch.from_numpy(x).to("cuda") for x in X32]
+    hs = []
+    for p, pr in enumerate(probs):
+        h = cpals.CPALS(pr.dims, pr.rank, "f32")
+        h.set_stream(stream)
+        h.set_tensor(Xd[p])
+        h.set_factors([np.asfortranarray(a) for a in pr.init_factors])
+        h.iterate(1, want_fits=False)
+        hs.append(h)
+    torch.cuda.synchronize()
+    ksingle = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(ksingle):
+        for h in hs:
+            h.iterate(1, want_fits=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_1 = e0.elapsed_time(e1)
+    wall_1 = time.perf_counter() - t0
+    # agreement: the same sweeps from the same start on both paths (first 32 problems)
+    sub = list(range(32))
+    bb = cpals.CPALSBatch([probs[p].dims for p in sub], [probs[p].rank for p in sub])
+    bb.set_tensors([X32[p] for p in sub])
+    bb.set_factors([probs[p].init_factors for p in sub])
+    fb, _ = bb.iterate(3)
+    diffs = []
+    for i, p in enumerate(sub):
+        h = cpals.CPALS(probs[p].dims, probs[p].rank, "f32")
+        h.set_tensor(Xd[p])
+        h.set_factors([np.asfortranarray(a) for a in probs[p].init_factors])
+        f = h.iterate(3)
+        diffs.append(abs(float(f[-1]) - float(fb[i])))
+    v_b = args.steps / (ms_b * 1e-3)
+    v_1 = ksingle / (ms_1 * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": v_b, "unit": UNIT + " (every problem of the batch advances one sweep)",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32 passes over X, fp64 factors",
+            "data": "synthetic",
+            "config": {"workload": f"{count} independent 3-way tensors, dims ~ U{{16..128}}, ranks ~ U{{2..16}}, "
+                                   "planted rank + 1% noise; CP-ALS-QR (QR solve)",
+                       "elements": total_elems, "x_bytes_fp32": 4 * total_elems},
+            "batched": {"iters_per_s": v_b, "problem_sweeps_per_s": v_b * count, "ms_per_sweep": ms_b / args.steps,
+                        "launches_per_sweep": launches_b / args.steps, "grid": grid, "threads": threads,
+                        "x_stream_gbs": 3 * 4 * total_elems / (ms_b / args.steps * 1e-3) / 1e9,
+                        "statuses_ok": int((st_b == 0).sum())},
+            "one_problem_per_launch": {"iters_per_s": v_1, "ms_per_sweep": ms_1 / ksingle, "sweeps": ksingle,
+                                       "host_wall_s": wall_1},
+            "speedup_batched_vs_per_problem": v_b / v_1,
+            "fit_agreement_max_abs_diff_3_sweeps": max(diffs),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "c4":
+        run_batch(args, world, rank)
         return
     if args.workload != "c2":
         run_mixed(args, world, rank)

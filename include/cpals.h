@@ -228,6 +228,54 @@ int64_t cpals_launch_count(const cpals_handle* h);
 int cpals_multi_ttm_static(const int64_t* dims, int N, int rank, int mode, const double* X,
                            const double* const* Q, double* Y, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Batched problems: many independent 3-way CP-ALS-QR problems of uneven dims
+ * and ranks advance together (one persistent kernel per mode update; each
+ * CTA runs the whole mode-loop body of Alg. cp-als-qr for one problem at a
+ * time: QR of V_n = R_hi (.) R_lo, the FP32 Multi-TTM, W = Y_(n) Q0, the R0
+ * substitution, normalisation and the factor QR in FP64, then the efficient
+ * fit of Sec. 3.3.1 after the last mode).  The passes over X run in FP32;
+ * every small factor is FP64.
+ * --------------------------------------------------------------------- */
+typedef struct cpals_batch cpals_batch;
+
+/* count problems; dims is count x 3 (row p = I_0, I_1, I_2 of problem p),
+ * ranks has count entries.  Requires 1 <= rank <= 16 and rank <= every dim
+ * <= 4096, and the largest problem's working set (Q0, R0, W and the factor QR in
+ * FP64) within one CTA's shared memory.  Allocates all device buffers. */
+int cpals_batch_create(int count, const int64_t* dims, const int* ranks, cpals_batch** out);
+int cpals_batch_destroy(cpals_batch* b);
+int cpals_batch_set_stream(cpals_batch* b, void* stream);
+
+/* X: count pointers to FP32 tensors (prod(dims_p) values, mode 0 fastest),
+ * copied into the batch; ||X_p||^2 is computed in FP64. */
+int cpals_batch_set_tensors(cpals_batch* b, const float* const* X, int mem);
+
+/* A: 3*count pointers (A[3p+m] = factor m of problem p, I_m x R_p column-major
+ * FP64), copied; lambda = 1; the QR of every factor is taken (Alg. cp-als-qr
+ * initialisation); per-problem status words are cleared. */
+int cpals_batch_set_factors(cpals_batch* b, const double* const* A, int mem);
+
+/* Copy out factors (A as for set; entries may be NULL) and lambda (count
+ * pointers of R_p values; entries may be NULL). */
+int cpals_batch_get_factors(cpals_batch* b, double* const* A, double* const* lambda, int mem);
+
+/* `iters` sweeps over the three modes for every problem.  The sweep is a
+ * captured CUDA graph of three launches.  The first call picks the launch
+ * shape by timing one sweep per candidate on a saved copy of the factors.
+ * fits_host (count values, may be NULL) receives each problem's efficient fit
+ * after the last sweep; status_host (count values, may be NULL) receives each
+ * problem's status: CPALS_ERR_SINGULAR for a problem whose R0 became
+ * numerically singular (its factors stay as they were, and it is skipped
+ * after that).  Synchronises. */
+int cpals_batch_iterate(cpals_batch* b, int iters, double* fits_host, int* status_host);
+
+/* Kernel launches issued so far (a graph replay counts its three kernels). */
+int64_t cpals_batch_launch_count(const cpals_batch* b);
+
+/* The launch shape the first iterate picked (0 before it). */
+int cpals_batch_launch_shape(const cpals_batch* b, int* grid, int* threads);
+
 /* Measured FMA throughput probe (not part of the method): runs dependent
  * FMA chains on every SM for `ms_target` ms and writes the achieved
  * TFLOP/s for FP64 and FP32.  Used to state the ALU roofline.  Synchronises. */

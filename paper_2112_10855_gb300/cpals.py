@@ -76,6 +76,16 @@ def load(path: str | None = None):
     L.cpals_launch_count.argtypes = [_vp]
     L.cpals_launch_count.restype = C.c_int64
     L.cpals_multi_ttm_static.argtypes = [i64p, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp), _vp, _vp]
+    L.cpals_batch_create.argtypes = [C.c_int, i64p, C.POINTER(C.c_int), C.POINTER(_vp)]
+    L.cpals_batch_destroy.argtypes = [_vp]
+    L.cpals_batch_set_stream.argtypes = [_vp, _vp]
+    L.cpals_batch_set_tensors.argtypes = [_vp, C.POINTER(_vp), C.c_int]
+    L.cpals_batch_set_factors.argtypes = [_vp, C.POINTER(_vp), C.c_int]
+    L.cpals_batch_get_factors.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_vp), C.c_int]
+    L.cpals_batch_iterate.argtypes = [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.cpals_batch_launch_count.argtypes = [_vp]
+    L.cpals_batch_launch_count.restype = C.c_int64
+    L.cpals_batch_launch_shape.argtypes = [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.cpals_probe_fma_peak.argtypes = [C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     _lib = L
     return L
@@ -276,6 +286,79 @@ class CPALS:
         f = C.c_double()
         _check(self._h, load().cpals_fit(self._h, 1 if direct else 0, C.byref(f)))
         return f.value
+
+
+class CPALSBatch:
+    """Many independent 3-way problems: cpals_batch_create and the cpals_batch_* calls."""
+
+    def __init__(self, dims, ranks):
+        L = load()
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        self.ranks = [int(r) for r in ranks]
+        self.count = len(self.dims)
+        flat = (C.c_int64 * (3 * self.count))(*[x for d in self.dims for x in d])
+        rk = (C.c_int * self.count)(*self.ranks)
+        h = _vp()
+        rc = L.cpals_batch_create(self.count, flat, rk, C.byref(h))
+        if rc != OK:
+            raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cpals_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _rc(self, rc):
+        if rc != OK:
+            raise CPALSError(rc, load().cpals_last_error(None).decode(errors="replace"))
+
+    def set_stream(self, stream):
+        raw = getattr(stream, "cuda_stream", stream)
+        self._rc(load().cpals_batch_set_stream(self._h, C.c_void_p(raw or 0)))
+
+    def set_tensors(self, Xs):
+        """Xs: count flat FP32 arrays (numpy: host; torch CUDA: device)."""
+        arrs = [np.ascontiguousarray(x, dtype=np.float32) if isinstance(x, np.ndarray) else x for x in Xs]
+        ptrs = [_ptr(a) for a in arrs]
+        mem = ptrs[0][1]
+        self._keepX = arrs
+        self._rc(load().cpals_batch_set_tensors(self._h, (_vp * self.count)(*[p for p, _ in ptrs]), mem))
+
+    def set_factors(self, A):
+        """A: count lists of 3 column-major FP64 I_m x R_p arrays (numpy)."""
+        mats = [np.asfortranarray(a, dtype=np.float64) for fs in A for a in fs]
+        self._keepA = mats
+        ptrs = (_vp * len(mats))(*[C.c_void_p(m.ctypes.data) for m in mats])
+        self._rc(load().cpals_batch_set_factors(self._h, ptrs, MEM_HOST))
+
+    def get_factors(self):
+        outs = [[np.zeros((d[m], r), order="F") for m in range(3)] for d, r in zip(self.dims, self.ranks)]
+        lams = [np.zeros(r) for r in self.ranks]
+        aptr = (_vp * (3 * self.count))(*[C.c_void_p(o.ctypes.data) for fs in outs for o in fs])
+        lptr = (_vp * self.count)(*[C.c_void_p(l.ctypes.data) for l in lams])
+        self._rc(load().cpals_batch_get_factors(self._h, aptr, lptr, MEM_HOST))
+        return outs, lams
+
+    def iterate(self, iters):
+        fits = (C.c_double * self.count)()
+        st = (C.c_int * self.count)()
+        self._rc(load().cpals_batch_iterate(self._h, int(iters), fits, st))
+        return np.array(fits[:]), np.array(st[:])
+
+    def launch_count(self):
+        return load().cpals_batch_launch_count(self._h)
+
+    def launch_shape(self):
+        g, t = C.c_int(), C.c_int()
+        load().cpals_batch_launch_shape(self._h, C.byref(g), C.byref(t))
+        return g.value, t.value
 
 
 def multi_ttm_static(X, Q, mode, rank, dims, Y, stream=None):

@@ -643,6 +643,101 @@ int cpals_multi_ttm_static(const int64_t* dims, int N, int rank, int mode, const
     return CPALS_OK;
 }
 
+// ---------------------------------------------------------------- batched problems
+int cpals_batch_create(int count, const int64_t* dims, const int* ranks, cpals_batch** out)
+{
+    if (!out) return fail(nullptr, CPALS_ERR_ARG, "%s", "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !dims || !ranks) return fail(nullptr, CPALS_ERR_ARG, "%s", "count >= 1 with dims and ranks");
+    int maxR = 0, maxI = 0;
+    for (int p = 0; p < count; ++p) {
+        const int R = ranks[p];
+        if (R < 1 || R > 16) return fail(nullptr, CPALS_ERR_ARG, "%s", "batched ranks must be in [1, 16]");
+        for (int m = 0; m < 3; ++m) {
+            const int64_t d = dims[3 * p + m];
+            if (d < R || d > 4096)
+                return fail(nullptr, CPALS_ERR_ARG, "%s", "batched dims must be in [rank, 4096]");
+            maxI = std::max<int>(maxI, (int)d);
+        }
+        maxR = std::max(maxR, R);
+    }
+    if (cpals::batch_smem_bytes(maxR, maxI) > 220 * 1024)
+        return fail(nullptr, CPALS_ERR_ARG, "%s", "batched problem too large for one CTA's shared memory");
+    cpals::Batch* b = cpals::batch_new();
+    if (!b) return fail(nullptr, CPALS_ERR_NOMEM, "%s", "host allocation failed");
+    cudaError_t e = cpals::batch_build(b, count, dims, ranks);
+    if (e != cudaSuccess) {
+        cpals::batch_delete(b);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? fail(nullptr, CPALS_ERR_NOMEM, "%s", "device allocation failed")
+                                              : cuda_fail(nullptr, e, "batch create");
+    }
+    *out = reinterpret_cast<cpals_batch*>(b);
+    return CPALS_OK;
+}
+
+int cpals_batch_destroy(cpals_batch* bb)
+{
+    cpals::batch_delete(reinterpret_cast<cpals::Batch*>(bb));
+    return CPALS_OK;
+}
+
+int cpals_batch_set_stream(cpals_batch* bb, void* stream)
+{
+    auto* b = reinterpret_cast<cpals::Batch*>(bb);
+    if (!b) return fail(nullptr, CPALS_ERR_ARG, "%s", "null batch");
+    cpals::batch_set_stream(b, reinterpret_cast<cudaStream_t>(stream));
+    return CPALS_OK;
+}
+
+int cpals_batch_set_tensors(cpals_batch* bb, const float* const* X, int mem)
+{
+    auto* b = reinterpret_cast<cpals::Batch*>(bb);
+    if (!b || !X || !mem_ok(mem)) return fail(nullptr, CPALS_ERR_ARG, "%s", "bad batch, tensors or mem flag");
+    cudaError_t e = cpals::batch_set_tensors(b, X, mem == CPALS_MEM_HOST);
+    return e == cudaSuccess ? CPALS_OK : cuda_fail(nullptr, e, "batch set tensors");
+}
+
+int cpals_batch_set_factors(cpals_batch* bb, const double* const* A, int mem)
+{
+    auto* b = reinterpret_cast<cpals::Batch*>(bb);
+    if (!b || !A || !mem_ok(mem)) return fail(nullptr, CPALS_ERR_ARG, "%s", "bad batch, factors or mem flag");
+    cudaError_t e = cpals::batch_set_factors(b, A, mem == CPALS_MEM_HOST);
+    return e == cudaSuccess ? CPALS_OK : cuda_fail(nullptr, e, "batch set factors");
+}
+
+int cpals_batch_get_factors(cpals_batch* bb, double* const* A, double* const* lambda, int mem)
+{
+    auto* b = reinterpret_cast<cpals::Batch*>(bb);
+    if (!b || !mem_ok(mem)) return fail(nullptr, CPALS_ERR_ARG, "%s", "bad batch or mem flag");
+    cudaError_t e = cpals::batch_get_factors(b, A, lambda, mem == CPALS_MEM_HOST);
+    return e == cudaSuccess ? CPALS_OK : cuda_fail(nullptr, e, "batch get factors");
+}
+
+int cpals_batch_iterate(cpals_batch* bb, int iters, double* fits_host, int* status_host)
+{
+    auto* b = reinterpret_cast<cpals::Batch*>(bb);
+    if (!b || iters < 0) return fail(nullptr, CPALS_ERR_ARG, "%s", "bad batch or iteration count");
+    if (!cpals::batch_ready(b)) return fail(nullptr, CPALS_ERR_STATE, "%s", "tensors and factors must be set");
+    cudaError_t e = cpals::batch_iterate(b, iters, fits_host, status_host);
+    return e == cudaSuccess ? CPALS_OK : cuda_fail(nullptr, e, "batch iterate");
+}
+
+int64_t cpals_batch_launch_count(const cpals_batch* bb)
+{
+    const auto* b = reinterpret_cast<const cpals::Batch*>(bb);
+    return b ? cpals::batch_launches(b) : -1;
+}
+
+int cpals_batch_launch_shape(const cpals_batch* bb, int* grid, int* threads)
+{
+    const auto* b = reinterpret_cast<const cpals::Batch*>(bb);
+    if (!b) return CPALS_ERR_ARG;
+    if (grid) *grid = cpals::batch_tuned_grid(b);
+    if (threads) *threads = cpals::batch_tuned_threads(b);
+    return CPALS_OK;
+}
+
 int cpals_probe_fma_peak(double ms_target, double* fp64_tflops, double* fp32_tflops)
 {
     int dev = 0, sms = 0;

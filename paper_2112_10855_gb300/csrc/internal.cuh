@@ -169,6 +169,23 @@ cudaError_t gram(Handle* h, const double* A, int64_t I, double* G);
 // Efficient fit after the last mode of a sweep; appends to the fit ring.
 cudaError_t fit_efficient(Handle* h, int solve);
 
+// ---------------------------------------------------------------- batched problems
+struct Batch;
+Batch* batch_new();
+void batch_delete(Batch* b);
+cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ranks);
+size_t batch_smem_bytes(int maxR, int maxI);
+cudaError_t batch_set_stream(Batch* b, cudaStream_t s);
+cudaError_t batch_set_tensors(Batch* b, const float* const* X, bool host);
+cudaError_t batch_set_factors(Batch* b, const double* const* A, bool host);
+cudaError_t batch_get_factors(Batch* b, double* const* A, double* const* lambda, bool host);
+cudaError_t batch_iterate(Batch* b, int iters, double* fits_host, int* status_host);
+int64_t batch_launches(const Batch* b);
+bool batch_ready(const Batch* b);
+int batch_tuned_grid(const Batch* b);
+int batch_tuned_threads(const Batch* b);
+char* batch_err(Batch* b);
+
 }  // namespace cpals
 
 #define CPALS_CUDA_TRY(expr)                                  \
