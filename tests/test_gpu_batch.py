@@ -5,7 +5,9 @@ FP64 oracle run on each problem separately, from the same initial factors.
 Bars: the Multi-TTM runs in FP32 (relative error ~sqrt(I) * 2^-24 per
 contraction), everything else in FP64.  After one sweep the factors agree with
 the oracle to 1e-4 relative (FP32 error amplified by the solve's
-conditioning), and after 8 sweeps the efficient fit agrees to 1e-6.
+conditioning), and at convergence (150 sweeps) the efficient fit agrees to 1e-6
+relative.  Before convergence the ALS trajectory is sensitive to rounding, so
+a mid-trajectory fit is not compared.
 """
 import numpy as np
 import pytest
@@ -56,14 +58,14 @@ def test_batch_one_sweep_matches_oracle(cuda_lib, small_batch):
         assert abs(fits[p] - o.fit_last()) <= 1e-5
 
 
-def test_batch_fits_after_sweeps_match_oracle(cuda_lib, small_batch):
+def test_batch_converged_fits_match_oracle(cuda_lib, small_batch):
     b = make_batch(small_batch)
-    fits, st = b.iterate(8)
+    fits, st = b.iterate(150)
     assert (st == 0).all()
     for p, pr in enumerate(small_batch):
         o = oracle.OracleCPALS(pr.X.astype(np.float32).astype(np.float64), pr.dims, pr.rank)
         o.set_factors(pr.init_factors)
-        _, f = o.iterate(8, solve=oracle.QR)
+        _, f = o.iterate(150, solve=oracle.QR)
         assert abs(fits[p] - f[-1]) <= 1e-6 * max(abs(f[-1]), 1.0), (p, fits[p], f[-1])
 
 
