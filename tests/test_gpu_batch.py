@@ -5,9 +5,13 @@ FP64 oracle run on each problem separately, from the same initial factors.
 Bars: the Multi-TTM runs in FP32 (relative error ~sqrt(I) * 2^-24 per
 contraction), everything else in FP64.  After one sweep the factors agree with
 the oracle to 1e-4 relative (FP32 error amplified by the solve's
-conditioning), and at convergence (150 sweeps) the efficient fit agrees to 1e-6
-relative.  Before convergence the ALS trajectory is sensitive to rounding, so
-a mid-trajectory fit is not compared.
+conditioning).  At convergence (150 sweeps) the direct fit of the factors the
+batch found (FP64 residual against the tensor) agrees with the oracle's to
+1e-6 relative.  The batch's own efficient fit is computed from FP32 data.
+At fit 0.99 the residual identity of Sec. 3.3.1 cancels ~1e-4 of ||X||^2,
+so that value carries ~5e-6 absolute error and is checked to 2e-5 only.
+Before convergence the ALS trajectory is sensitive to rounding, so a
+mid-trajectory fit is not compared.
 """
 import numpy as np
 import pytest
@@ -62,11 +66,16 @@ def test_batch_converged_fits_match_oracle(cuda_lib, small_batch):
     b = make_batch(small_batch)
     fits, st = b.iterate(150)
     assert (st == 0).all()
+    A, lam = b.get_factors()
     for p, pr in enumerate(small_batch):
-        o = oracle.OracleCPALS(pr.X.astype(np.float32).astype(np.float64), pr.dims, pr.rank)
+        X = pr.X.astype(np.float32).astype(np.float64)
+        o = oracle.OracleCPALS(X, pr.dims, pr.rank)
         o.set_factors(pr.init_factors)
         _, f = o.iterate(150, solve=oracle.QR)
-        assert abs(fits[p] - f[-1]) <= 1e-6 * max(abs(f[-1]), 1.0), (p, fits[p], f[-1])
+        fit_b = 1.0 - oracle.residual_direct(X, pr.dims, lam[p], A[p]) / np.linalg.norm(X)
+        fit_o = o.fit_direct()
+        assert abs(fit_b - fit_o) <= 1e-6 * abs(fit_o), (p, fit_b, fit_o)
+        assert abs(fits[p] - f[-1]) <= 2e-5, (p, fits[p], f[-1])
 
 
 def test_batch_matches_single_problem_f32_path(cuda_lib, small_batch):
