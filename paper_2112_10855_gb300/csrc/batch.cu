@@ -126,6 +126,7 @@ __device__ void cta_householder(double* W, int m, int n, double* Q, double* Rout
 }
 
 // One CTA: Out(l, r, t) = sum_k In(l, k, t) * qs[k*R + r] over the [L, K, T] view.
+// Loads are issued eight k at a time so that each thread keeps eight in flight.
 __device__ void cta_ttm_f32(const float* __restrict__ in, int64_t L, int K, int64_t T, const float* qs, int R,
                             float* __restrict__ out)
 {
@@ -136,8 +137,21 @@ __device__ void cta_ttm_f32(const float* __restrict__ in, int64_t L, int K, int6
         float acc[kBMaxR];
 #pragma unroll
         for (int r = 0; r < kBMaxR; ++r) acc[r] = 0.0f;
-        for (int k = 0; k < K; ++k) {
-            const float x = p[L * k];
+        int k = 0;
+        for (; k + 8 <= K; k += 8) {
+            float x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = __ldg(p + L * (k + u));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float* q = qs + (k + u) * R;
+#pragma unroll
+                for (int r = 0; r < kBMaxR; ++r)
+                    if (r < R) acc[r] = fmaf(x[u], q[r], acc[r]);
+            }
+        }
+        for (; k < K; ++k) {
+            const float x = __ldg(p + L * k);
             const float* q = qs + k * R;
 #pragma unroll
             for (int r = 0; r < kBMaxR; ++r)
@@ -252,16 +266,34 @@ __global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restri
             __syncthreads();
         }
         // ---- 3. W = Y_(n) Q0 (FP64); Y element (col, i) at a + Rn*(i + In*c), col = a + Rn*c
+        // one thread per row i with all R accumulators; Q0 rows are shared-memory broadcasts
         const float* Y = Yall + pr.y;
         const int Rn = (n == 0) ? 1 : (n == 1 ? R : RR);
-        for (int e = tid; e < In * R; e += blockDim.x) {
-            const int r = e / In, i = e - r * In;
-            double acc = 0.0;
-            for (int col = 0; col < RR; ++col) {
-                const int a = col % Rn, c = col / Rn;
-                acc = fma((double)Y[a + (int64_t)Rn * (i + (int64_t)In * c)], regB[col + RR * r], acc);
+        for (int i = tid; i < In; i += blockDim.x) {
+            double acc[kBMaxR];
+#pragma unroll
+            for (int r = 0; r < kBMaxR; ++r) acc[r] = 0.0;
+            for (int c0 = 0; c0 < RR; c0 += 8) {
+                float y[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int col = c0 + u;
+                    const int a = col % Rn, c = col / Rn;
+                    y[u] = (col < RR) ? __ldg(Y + a + (int64_t)Rn * (i + (int64_t)In * c)) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int col = c0 + u;
+                    if (col < RR) {
+#pragma unroll
+                        for (int r = 0; r < kBMaxR; ++r)
+                            if (r < R) acc[r] = fma((double)y[u], regB[col + RR * r], acc[r]);
+                    }
+                }
             }
-            Ws[e] = acc;
+#pragma unroll
+            for (int r = 0; r < kBMaxR; ++r)
+                if (r < R) Ws[i + In * r] = acc[r];
         }
         __syncthreads();
         // ---- 4. Ahat R0^T = W by substitution, one row per thread (Ahat into regA)
