@@ -560,6 +560,21 @@ def main():
             torch.cuda.synchronize()
             variants[f"f64_{solve}"] = 5 / (e0.elapsed_time(e1) * 1e-3)
             del hv
+        hn = cpals.CPALS(p.dims, R, "f64")
+        hn.set_stream(stream)
+        hn.set_tensor(Xd)
+        hn.set_factors([np.asfortranarray(a) for a in p.init_factors])
+        hn.set_dimtree(False)
+        hn.iterate(2, solve=args.solve, svd_rtol=1e-10, want_fits=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hn.iterate(10, solve=args.solve, svd_rtol=1e-10, want_fits=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        variants[f"f64_{args.solve}_per_mode_multi_ttm"] = 10 / (e0.elapsed_time(e1) * 1e-3)
+        del hn
         hf = cpals.CPALS(p.dims, R, "f32")
         hf.set_stream(stream)
         hf.set_tensor(Xd)

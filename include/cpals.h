@@ -186,6 +186,17 @@ int cpals_fit(cpals_handle* h, int direct, double* fit_host);
 /* Synchronise the handle's stream and report (then clear) the device status word. */
 int cpals_sync(cpals_handle* h);
 
+/* Options of a handle.
+ *  CPALS_OPT_DIMTREE (default 1): sweeps of cpals_iterate with the QR or SVD
+ *    solve on an N >= 3 tensor share Multi-TTM work across modes by a
+ *    dimension tree (Sec. 3.3.3).  X is contracted once over the modes of the
+ *    second half for the Multi-TTMs of the first half, and once over the first
+ *    half (with its updated Q_m) for the second half.  That is two passes over
+ *    X per sweep instead of N.  0 runs a full Multi-TTM from X per mode.  The
+ *    results differ only by rounding (Sec. 2.2: TTMs commute). */
+typedef enum { CPALS_OPT_DIMTREE = 0 } cpals_option;
+int cpals_set_option(cpals_handle* h, int option, int64_t value);
+
 /* Number of kernel launches the handle has issued so far (graph replays count
  * each kernel node once per replay). */
 int64_t cpals_launch_count(const cpals_handle* h);

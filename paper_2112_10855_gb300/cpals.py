@@ -73,6 +73,7 @@ def load(path: str | None = None):
                                 C.POINTER(C.c_double)]
     L.cpals_fit.argtypes = [_vp, C.c_int, C.POINTER(C.c_double)]
     L.cpals_sync.argtypes = [_vp]
+    L.cpals_set_option.argtypes = [_vp, C.c_int, C.c_int64]
     L.cpals_launch_count.argtypes = [_vp]
     L.cpals_launch_count.restype = C.c_int64
     L.cpals_multi_ttm_static.argtypes = [i64p, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp), _vp, _vp]
@@ -174,6 +175,10 @@ class CPALS:
 
     def launch_count(self):
         return load().cpals_launch_count(self._h)
+
+    def set_dimtree(self, on: bool):
+        """CPALS_OPT_DIMTREE: share Multi-TTM passes over X across modes in sweeps."""
+        _check(self._h, load().cpals_set_option(self._h, 0, 1 if on else 0))
 
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))

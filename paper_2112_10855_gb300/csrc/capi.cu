@@ -50,7 +50,7 @@ void free_all(Handle* h)
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->A[m]); f(h->Q[m]); f(h->Rf[m]); f(h->G[m]); }
     f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
-    f(h->tbuf[0]); f(h->tbuf[1]); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
+    f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -124,7 +124,7 @@ cudaError_t refresh_derived(Handle* h, int solve, int skip)
 }
 
 // One mode update (Alg. cp-als-qr mode-loop body, or Alg. cp-als for NORMAL).
-cudaError_t mode_update(Handle* h, int n, int solve, double rtol)
+cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_partial = false)
 {
     CPALS_CUDA_TRY(refresh_derived(h, solve, n));
     const int64_t In = h->dims[n];
@@ -143,7 +143,8 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol)
         CPALS_CUDA_TRY(e);
         CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
         h->krp_mode = n;
-        CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
+        if (from_partial) CPALS_CUDA_TRY(cpals::multi_ttm_from_partial(h, n));
+        else CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
         CPALS_CUDA_TRY(cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W));
         if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
@@ -162,9 +163,30 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol)
     return cudaSuccess;
 }
 
+// One sweep over the modes.  For the QR/SVD solves of an N >= 3 tensor the
+// Multi-TTMs follow a dimension tree (Sec. 3.3.3): the modes split into halves
+// H1 = {0..h-1} and H2 = {h..N-1}.  X is contracted once over H2 (whose Q_m do
+// not change while H1 is updated), and each H1 mode contracts the rest of H1
+// from that partial with the current Q_m.  Then X is contracted once over H1
+// with the updated Q_m for the H2 modes.  That makes two passes over X per
+// sweep instead of N.  The TTMs of a Multi-TTM can run in any order
+// (Sec. 2.2), so only rounding differs from the per-mode Multi-TTM.
 cudaError_t sweep(Handle* h, int solve, double rtol)
 {
-    for (int n = 0; n < h->N; ++n) CPALS_CUDA_TRY(mode_update(h, n, solve, rtol));
+    if (solve == CPALS_SOLVE_NORMAL || h->N < 3 || !h->dimtree || !h->tA) {
+        for (int n = 0; n < h->N; ++n) CPALS_CUDA_TRY(mode_update(h, n, solve, rtol));
+        return cpals::fit_efficient(h, solve);
+    }
+    const int N = h->N, h1 = (N + 1) / 2;
+    int H1[cpals::kMaxN], H2[cpals::kMaxN], n1 = 0, n2 = 0;
+    for (int m = 0; m < N; ++m) {
+        if (m < h1) H1[n1++] = m;
+        else H2[n2++] = m;
+    }
+    CPALS_CUDA_TRY(cpals::dimtree_pass(h, H2, n2));
+    for (int k = 0; k < n1; ++k) CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true));
+    CPALS_CUDA_TRY(cpals::dimtree_pass(h, H1, n1));
+    for (int k = 0; k < n2; ++k) CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true));
     return cpals::fit_efficient(h, solve);
 }
 
@@ -248,6 +270,19 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
              cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi) == cudaSuccess &&
              cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (ok && N >= 3) {
+        const int h1 = (N + 1) / 2;
+        int64_t a = 1, b = 1;
+        for (int m = 0; m < N; ++m) {
+            a *= (m < h1) ? dims[m] : (int64_t)rank;
+            b *= (m < h1) ? (int64_t)rank : dims[m];
+        }
+        h->tA_elems = std::max(a, b);
+        void* pa = nullptr;
+        ok = cudaMalloc(&pa, tsz * h->tA_elems) == cudaSuccess;
+        h->tA = pa;
+        if (ok) h->owned_bytes += tsz * h->tA_elems;
     }
     if (ok) {
         void* p0 = nullptr; void* p1 = nullptr;
@@ -611,6 +646,21 @@ int cpals_sync(cpals_handle* hh)
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
     return take_status(h);
+}
+
+int cpals_set_option(cpals_handle* hh, int option, int64_t value)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (option != CPALS_OPT_DIMTREE || (value != 0 && value != 1))
+        return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
+    const bool v = value != 0;
+    if (v != h->dimtree) {
+        h->dimtree = v;
+        for (int s = 0; s < 3; ++s)             // captured sweeps follow the old schedule
+            if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
+    }
+    return CPALS_OK;
 }
 
 int64_t cpals_launch_count(const cpals_handle* hh)

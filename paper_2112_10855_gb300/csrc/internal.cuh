@@ -91,6 +91,13 @@ struct Handle {
     // TTM intermediates (ping-pong), in the Multi-TTM's arithmetic type
     void* tbuf[2] = {nullptr, nullptr};
     int64_t tbuf_elems = 0;
+    // dimension tree (Sec. 3.3.3): X contracted over one half of the modes,
+    // shared by the Multi-TTMs of the other half within a sweep
+    void* tA = nullptr;
+    int64_t tA_elems = 0;
+    int64_t tA_dims[kMaxN] = {0};
+    int tA_contracted[kMaxN] = {0};
+    bool dimtree = true;
     // FP64 scratch for split-K partials, reductions and pre-split tensor-core
     // tiles (main stream), and a separate workspace for the TSQR levels, so a QR
     // on the side stream never shares memory with the Multi-TTM
@@ -128,6 +135,10 @@ struct Handle {
 // Multi-TTM (Alg. cp-als-qr Multi-TTM step): writes the FP64 unfolding Y_(n)
 // into h->Yn using Q_m = h->Q[m] (or the given override array).
 cudaError_t multi_ttm(Handle* h, int n, const double* const* Q);
+// Dimension tree: X contracted over `modes` into h->tA; then Y_(n) for a mode of
+// the other half from h->tA (the remaining modes other than n).
+cudaError_t dimtree_pass(Handle* h, const int* modes, int nm);
+cudaError_t multi_ttm_from_partial(Handle* h, int n);
 // Only the first TTM of the Multi-TTM of mode n (the pass over X).
 cudaError_t ttm_first(Handle* h, int n);
 // Multi-TTM with all scratch in a fixed file-scope device array (no allocation).

@@ -352,21 +352,29 @@ bool first_on_tensor_cores(const Handle* h)
     return sizeof(T) == 4 && (h->prec == CPALS_BF16X3 || h->prec == CPALS_TF32X3) && tc_supported(h->R);
 }
 
+// Contract the listed modes of `in` (current dims d, updated in place) with
+// Q_m^T, largest original dim first (ties: higher mode), ping-ponging through
+// the two TTM buffers.  The last TTM writes to final_out when given.  With
+// from_x the first TTM reads X and may run on the tensor cores.  *result
+// receives the tensor that holds the contraction (in itself if nm == 0).
 template <typename T>
-cudaError_t multi_ttm_impl(Handle* h, int n, const double* const* Q)
+cudaError_t ttm_chain(Handle* h, const T* in, int64_t* d, const int* modes_in, int nm, const double* const* Q,
+                      bool from_x, T* final_out, const T** result)
 {
     const int N = h->N, R = h->R;
-    int order[kMaxN];
-    ttm_order(N, h->dims, n, order);
-    int64_t d[kMaxN];
-    for (int m = 0; m < N; ++m) d[m] = h->dims[m];
-    const T* in = x_ptr<T>(h);
+    int modes[kMaxN];
+    for (int k = 0; k < nm; ++k) modes[k] = modes_in[k];
+    for (int a = 0; a < nm; ++a)
+        for (int b = a + 1; b < nm; ++b) {
+            const int x = modes[a], y = modes[b];
+            if (h->dims[y] > h->dims[x] || (h->dims[y] == h->dims[x] && y > x)) { modes[a] = y; modes[b] = x; }
+        }
     int cur = 0;
-    for (int k = 0; k < N - 1; ++k) {
-        const int m = order[k];
+    for (int k = 0; k < nm; ++k) {
+        const int m = modes[k];
         const TtmShape s = ttm_shape(N, d, m);
-        T* out = (T*)h->tbuf[cur];
-        if (k == 0 && first_on_tensor_cores<T>(h))
+        T* out = (k == nm - 1 && final_out) ? final_out : (T*)h->tbuf[cur];
+        if (k == 0 && from_x && first_on_tensor_cores<T>(h))
             CPALS_CUDA_TRY(ttm_split_tc(h, (const float*)in, Q[m], h->dims[m], (float*)out, s, R,
                                         h->prec == CPALS_TF32X3));
         else
@@ -375,13 +383,59 @@ cudaError_t multi_ttm_impl(Handle* h, int n, const double* const* Q)
         in = out;
         cur ^= 1;
     }
+    *result = in;
+    return cudaSuccess;
+}
+
+// Final Multi-TTM tensor of mode n (R in every other mode) to the FP64 unfolding Y_(n).
+template <typename T>
+cudaError_t unfold_yn(Handle* h, const T* in, int n)
+{
     int64_t Rn = 1;
-    for (int m = 0; m < n; ++m) Rn *= R;
+    for (int m = 0; m < n; ++m) Rn *= h->R;
     const int64_t total = h->dims[n] * h->RN1;
     unfold_kernel<T><<<grid_for(total, 256, h->num_sms), 256, 0, h->stream>>>(in, h->Yn, Rn, h->dims[n], total,
                                                                                h->d_status);
     h->launches++;
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t multi_ttm_impl(Handle* h, int n, const double* const* Q)
+{
+    int modes[kMaxN], nm = 0;
+    for (int m = 0; m < h->N; ++m)
+        if (m != n) modes[nm++] = m;
+    int64_t d[kMaxN];
+    for (int m = 0; m < h->N; ++m) d[m] = h->dims[m];
+    const T* res = nullptr;
+    CPALS_CUDA_TRY(ttm_chain<T>(h, x_ptr<T>(h), d, modes, nm, Q, true, nullptr, &res));
+    return unfold_yn<T>(h, res, n);
+}
+
+// Dimension tree (Sec. 3.3.3): X contracted over `modes` into h->tA.
+template <typename T>
+cudaError_t dimtree_pass_impl(Handle* h, const int* modes, int nm)
+{
+    for (int m = 0; m < h->N; ++m) h->tA_dims[m] = h->dims[m];
+    const T* res = nullptr;
+    return ttm_chain<T>(h, x_ptr<T>(h), h->tA_dims, modes, nm, h->Q, true, (T*)h->tA, &res);
+}
+
+// Y_(n) from the shared partial h->tA: contract the modes that the pass left
+// uncontracted, other than n, with their current Q_m.
+template <typename T>
+cudaError_t multi_ttm_from_partial_impl(Handle* h, int n)
+{
+    int modes[kMaxN], nm = 0;
+    int64_t d[kMaxN];
+    for (int m = 0; m < h->N; ++m) {
+        d[m] = h->tA_dims[m];
+        if (m != n && !h->tA_contracted[m]) modes[nm++] = m;
+    }
+    const T* res = nullptr;
+    CPALS_CUDA_TRY(ttm_chain<T>(h, (const T*)h->tA, d, modes, nm, h->Q, false, nullptr, &res));
+    return unfold_yn<T>(h, res, n);
 }
 
 template <typename T>
@@ -502,6 +556,20 @@ __global__ void cast_kernel(const double* __restrict__ src, float* __restrict__ 
 }
 
 }  // namespace
+
+cudaError_t dimtree_pass(Handle* h, const int* modes, int nm)
+{
+    for (int m = 0; m < h->N; ++m) h->tA_contracted[m] = 0;
+    for (int k = 0; k < nm; ++k) h->tA_contracted[modes[k]] = 1;
+    if (h->prec == CPALS_F64) return dimtree_pass_impl<double>(h, modes, nm);
+    return dimtree_pass_impl<float>(h, modes, nm);
+}
+
+cudaError_t multi_ttm_from_partial(Handle* h, int n)
+{
+    if (h->prec == CPALS_F64) return multi_ttm_from_partial_impl<double>(h, n);
+    return multi_ttm_from_partial_impl<float>(h, n);
+}
 
 cudaError_t multi_ttm(Handle* h, int n, const double* const* Q)
 {

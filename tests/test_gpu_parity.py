@@ -164,6 +164,30 @@ def test_sweeps_match_oracle_c1_shape(cuda_lib, solve):
     assert abs(h.fit(direct=True) - o.fit_direct()) <= 1e-10
 
 
+@pytest.mark.parametrize("dims,R", [((24, 22, 20), 4), ((14, 13, 12, 11), 3), ((9, 8, 8, 7, 6), 2),
+                                    ((30, 30, 30), 6)])
+@pytest.mark.parametrize("solve", ["qr", "svd"])
+def test_dimension_tree_sweeps_match_oracle(cuda_lib, dims, R, solve):
+    # sweeps with the dimension tree (two passes over X per sweep) against the
+    # oracle's per-mode Multi-TTMs: only rounding differs
+    p = inputs.planted(dims, R, seed=31, init_seed=32, noise=0.02)
+    osolve = oracle.QR if solve == "qr" else oracle.SVD
+    o = oracle.OracleCPALS(p.X, p.dims, R)
+    o.set_factors(p.init_factors)
+    _, fits_o = o.iterate(6, solve=osolve, rtol=1e-12)
+    h = gpu_handle(p.dims, R, p.X, p.init_factors)
+    fits = h.iterate(6, solve=solve, svd_rtol=1e-12)
+    assert np.abs(fits - fits_o).max() <= 1e-10
+    A, lam = h.get_factors()
+    for m in range(len(dims)):
+        assert rel(A[m], o.factor(m)) <= 1e-8
+    # and against the same library without the tree
+    h2 = gpu_handle(p.dims, R, p.X, p.init_factors)
+    h2.set_dimtree(False)
+    fits2 = h2.iterate(6, solve=solve, svd_rtol=1e-12)
+    assert np.abs(fits - fits2).max() <= 1e-11
+
+
 def test_direct_fit_and_resume(cuda_lib):
     # 10 + 10 sweeps equal 20 sweeps bit for bit (checkpoint = get/set factors)
     p = inputs.workload_c1(size=24, rank=4)
