@@ -222,14 +222,14 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     int64_t ks = 1;
     const int64_t want = (int64_t)h->num_sms * (2048 / tpb);   // about 2048 threads per SM
     const int64_t outn = rows * R;
-    if (gx * gy < want && s.K >= 2 * kKC && part != nullptr) {
+    constexpr int64_t kMinSplitK = 8;    // contracted indices per split at least
+    if (gx * gy < want && s.K >= 2 * kMinSplitK && part != nullptr) {
         ks = (want + gx * gy - 1) / (gx * gy);
-        ks = std::min<int64_t>(ks, s.K / kKC);
+        ks = std::min<int64_t>(ks, s.K / kMinSplitK);
         ks = std::min<int64_t>(ks, part_elems / std::max<int64_t>(outn, 1));
         if (ks < 2) ks = 1;
     }
-    int64_t kchunk = (s.K + ks - 1) / ks;
-    kchunk = ((kchunk + kKC - 1) / kKC) * kKC;     // whole k-chunks per split
+    const int64_t kchunk = (s.K + ks - 1) / ks;
     ks = (s.K + kchunk - 1) / kchunk;
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
     T* dst = (ks > 1) ? part : out;
