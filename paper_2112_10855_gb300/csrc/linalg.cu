@@ -212,9 +212,11 @@ __global__ void trsm_qr_kernel(const double* __restrict__ W, const double* __res
 {
     if (*status != kStatusOk) return;
     __shared__ double r0[kMaxRank * kMaxRank];
+    __shared__ double rinv[kMaxRank];
     __shared__ int singular;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) r0[e] = R0[e];
     __syncthreads();
+    for (int k = threadIdx.x; k < R; k += blockDim.x) rinv[k] = 1.0 / r0[k + R * k];
     if (threadIdx.x == 0) {
         double dmax = 0.0;
         for (int k = 0; k < R; ++k) dmax = fmax(dmax, fabs(r0[k + R * k]));
@@ -227,11 +229,18 @@ __global__ void trsm_qr_kernel(const double* __restrict__ W, const double* __res
     __syncthreads();
     if (singular) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
+        // back substitution R0 x = w with the reciprocals of diag(R0); the
+        // inner sums run as two independent chains
         double x[kMaxRank];
         for (int k = R - 1; k >= 0; --k) {
-            double s = W[i + I * k];
-            for (int j = k + 1; j < R; ++j) s = fma(-r0[k + R * j], x[j], s);
-            x[k] = s / r0[k + R * k];
+            double s0 = W[i + I * k], s1 = 0.0;
+            int j = k + 1;
+            for (; j + 1 < R; j += 2) {
+                s0 = fma(-r0[k + R * j], x[j], s0);
+                s1 = fma(-r0[k + R * (j + 1)], x[j + 1], s1);
+            }
+            if (j < R) s0 = fma(-r0[k + R * j], x[j], s0);
+            x[k] = (s0 + s1) * rinv[k];
         }
         for (int k = 0; k < R; ++k) Ahat[i + I * k] = x[k];
     }

@@ -167,15 +167,22 @@ __global__ void __launch_bounds__(TPB) ttm_rows4_kernel(
     }
 }
 
+// out[g*n + e] = sum of part[q*n + e] over the splits q of group g (groups of
+// `group` consecutive splits, added in split order).  With one group this is
+// the final sum; with several, a second call adds the group sums in order.
 template <typename T>
-__global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int64_t n, T* __restrict__ out,
+__global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int group, int64_t n, T* __restrict__ out,
                                      const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        T s = part[e];
-        for (int q = 1; q < ks; ++q) s += part[(int64_t)q * n + e];
-        out[e] = s;
+    const int ng = (ks + group - 1) / group;
+    const int64_t total = n * ng;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = w / n, e = w - g * n;
+        const int q0 = (int)g * group, q1 = min(ks, q0 + group);
+        T s = part[(int64_t)q0 * n + e];
+        for (int q = q0 + 1; q < q1; ++q) s += part[(int64_t)q * n + e];
+        out[g * n + e] = s;
     }
 }
 
@@ -226,7 +233,8 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     if (gx * gy < want && s.K >= 2 * kMinSplitK && part != nullptr) {
         ks = (want + gx * gy - 1) / (gx * gy);
         ks = std::min<int64_t>(ks, s.K / kMinSplitK);
-        ks = std::min<int64_t>(ks, part_elems / std::max<int64_t>(outn, 1));
+        // room for the ks partials and the ks/16 group sums of the two-level reduction
+        ks = std::min<int64_t>(ks, (part_elems * 16 / 17) / std::max<int64_t>(outn, 1));
         if (ks < 2) ks = 1;
     }
     const int64_t kchunk = (s.K + ks - 1) / ks;
@@ -259,10 +267,24 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
     if (ks > 1) {
-        int64_t g = (outn + 255) / 256;
-        if (g > 16LL * h->num_sms) g = 16LL * h->num_sms;
-        reduce_splits_kernel<T><<<(unsigned)g, 256, 0, h->stream>>>(part, (int)ks, outn, out, h->d_status);
-        h->launches++;
+        constexpr int kGroup = 16;
+        const int64_t ng = (ks + kGroup - 1) / kGroup;
+        auto grid_of = [&](int64_t work) {
+            int64_t g = (work + 255) / 256;
+            return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 16LL * h->num_sms));
+        };
+        if (ng == 1) {
+            reduce_splits_kernel<T><<<grid_of(outn), 256, 0, h->stream>>>(part, (int)ks, kGroup, outn, out,
+                                                                          h->d_status);
+            h->launches++;
+        } else {
+            T* gsum = part + ks * outn;     // group sums after the partials
+            reduce_splits_kernel<T><<<grid_of(outn * ng), 256, 0, h->stream>>>(part, (int)ks, kGroup, outn, gsum,
+                                                                               h->d_status);
+            reduce_splits_kernel<T><<<grid_of(outn), 256, 0, h->stream>>>(gsum, (int)ng, (int)ng, outn, out,
+                                                                          h->d_status);
+            h->launches += 2;
+        }
         CPALS_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
