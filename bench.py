@@ -86,7 +86,8 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -543,7 +544,7 @@ def main():
 
     variants = {}
     if not args.no_variants:
-        for solve in ("svd", "normal"):
+        for solve in ("svd", "normal", "normal_pinv"):
             if solve == args.solve:
                 continue
             hv = cpals.CPALS(p.dims, R, "f64")

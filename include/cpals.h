@@ -70,7 +70,9 @@ typedef enum {
 typedef enum {
     CPALS_SOLVE_QR = 0,     /* CP-ALS-QR: substitution with R0 (Eq. ls-qr-q0-step) */
     CPALS_SOLVE_SVD = 1,    /* CP-ALS-QR-SVD: Ahat = W U pinv(Sigma) V^T with R0 = U Sigma V^T (Sec. 3.1) */
-    CPALS_SOLVE_NORMAL = 2  /* CP-ALS: MTTKRP and Cholesky of the Hadamard product of Grams (Alg. cp-als) */
+    CPALS_SOLVE_NORMAL = 2, /* CP-ALS: MTTKRP and Cholesky of the Hadamard product of Grams (Alg. cp-als) */
+    CPALS_SOLVE_NORMAL_PINV = 3 /* CP-ALS-PINV: the same normal equations solved with the pseudo-inverse of S
+                                   (Sec. 2.3), Ahat = M pinv(S) keeping sigma_i > svd_rtol * sigma_1 */
 } cpals_solve;
 
 typedef enum { CPALS_MEM_DEVICE = 0, CPALS_MEM_HOST = 1 } cpals_mem;
@@ -157,9 +159,10 @@ int cpals_mttkrp(cpals_handle* h, int mode, double* M, int mem);
  *    apply Q0, solve by substitution or by the truncated SVD of R0 keeping
  *    sigma_i > svd_rtol * sigma_1, normalise columns with the 2-norm into A_n
  *    and lambda, re-QR A_n = Q_n R_n).
- *  NORMAL: the mode-loop body of Alg. cp-als (Hadamard product of Grams S_n,
- *    MTTKRP, Cholesky solve, normalise, re-Gram); Q_n and R_n are refreshed
- *    too, so that solves can be mixed.
+ *  NORMAL / NORMAL_PINV: the mode-loop body of Alg. cp-als (Hadamard product
+ *    of Grams S_n, MTTKRP, Cholesky or pseudo-inverse solve, normalise,
+ *    re-Gram).  The QR of a factor is refreshed only when a later QR/SVD solve
+ *    needs it.
  * svd_rtol <= 0 selects R * eps.  Asynchronous; a singular solve is recorded
  * in the device status word and leaves the factor unchanged. */
 int cpals_solve_mode(cpals_handle* h, int mode, int solve, double svd_rtol);

@@ -11,5 +11,5 @@ from .oracle import (  # noqa: F401
     build, lib, qr, krp, unfold, ttm, ttm_order, multi_ttm, trsm_qr, jacobi_svd, svd_solve,
     normalize, mttkrp, cholesky_solve, residual_direct, fit_efficient_qr, score, OracleCPALS,
     use_library, compile_variant, source_text,
-    QR, SVD, NORMAL,
+    QR, SVD, NORMAL, NORMAL_PINV,
 )

@@ -514,7 +514,7 @@ double orc_fit_efficient_normal(double normX2, int64_t IN, int64_t R, const doub
 /* ------------------------------------------------------------------ */
 /* Driver state: Alg. cp-als-qr and Alg. cp-als                        */
 /* ------------------------------------------------------------------ */
-enum { ORC_QR = 0, ORC_SVD = 1, ORC_NORMAL = 2 };
+enum { ORC_QR = 0, ORC_SVD = 1, ORC_NORMAL = 2, ORC_NORMAL_PINV = 3 };
 
 typedef struct {
     int N;
@@ -600,7 +600,7 @@ void orc_krp_qr(orc_state* st, int n)
 }
 
 /* One CP-ALS-QR mode update (Alg. cp-als-qr mode loop) or one CP-ALS mode update
- * (Alg. cp-als mode loop).  Returns 0 on success, 1 if the solve was singular
+ * (Alg. cp-als mode loop, Cholesky or pseudo-inverse solve).  Returns 0 on success, 1 if the solve was singular
  * (factor left unchanged). */
 int orc_update_mode(orc_state* st, int n, int solve, double rtol)
 {
@@ -609,14 +609,20 @@ int orc_update_mode(orc_state* st, int n, int solve, double rtol)
     int64_t RN1 = 1;
     for (int k = 0; k < N - 1; ++k) RN1 *= R;
     st->last_mode = n;
-    if (solve == ORC_NORMAL) {
+    if (solve == ORC_NORMAL || solve == ORC_NORMAL_PINV) {
         /* S_n = Hadamard product of the other Grams */
         for (int64_t k = 0; k < R * R; ++k) st->S[k] = 1.0;
         for (int m = 0; m < N; ++m)
             if (m != n)
                 for (int64_t k = 0; k < R * R; ++k) st->S[k] *= st->G[m][k];
         orc_mttkrp(N, st->dims, st->X, n, R, (const double* const*)st->A, st->M);
-        if (orc_cholesky_solve(In, R, st->M, st->S, st->Ahat)) { st->last_status = 1; return 1; }
+        if (solve == ORC_NORMAL) {
+            if (orc_cholesky_solve(In, R, st->M, st->S, st->Ahat)) { st->last_status = 1; return 1; }
+        } else {
+            /* CP-ALS-PINV (Sec. 2.3): Ahat = M pinv(S); S symmetric, so pinv(S^T) = pinv(S)
+               and the SVD solve of Sec. 2.1 applies with S in place of R0 */
+            orc_svd_solve(In, R, st->M, st->S, rtol, st->Ahat);
+        }
     } else {
         orc_krp_qr(st, n);
         orc_multi_ttm(N, st->dims, st->X, n, R, (const double* const*)st->Q, NULL, st->Y);
@@ -638,7 +644,7 @@ int orc_update_mode(orc_state* st, int n, int solve, double rtol)
 double orc_fit_last(orc_state* st, int solve)
 {
     const int n = st->N - 1;
-    if (solve == ORC_NORMAL)
+    if (solve == ORC_NORMAL || solve == ORC_NORMAL_PINV)
         return orc_fit_efficient_normal(st->normX2, st->dims[n], st->R, st->M, st->Ahat, st->S,
                                         st->G[n], st->lambda);
     return orc_fit_efficient_qr(st->normX2, st->dims[n], st->R, st->W, st->Ahat, st->R0,

@@ -19,7 +19,7 @@ _SO = os.path.join(_OUT_DIR, "libcpals_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-QR, SVD, NORMAL = 0, 1, 2
+QR, SVD, NORMAL, NORMAL_PINV = 0, 1, 2, 3
 
 _dp = C.POINTER(C.c_double)
 _i64p = C.POINTER(C.c_int64)

@@ -21,12 +21,12 @@ from . import _build
 
 OK, ERR_ARG, ERR_NOMEM, ERR_CUDA, ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE = range(7)
 F64, F32, BF16X3, TF32X3 = 0, 1, 2, 3
-SOLVE_QR, SOLVE_SVD, SOLVE_NORMAL = 0, 1, 2
+SOLVE_QR, SOLVE_SVD, SOLVE_NORMAL, SOLVE_NORMAL_PINV = 0, 1, 2, 3
 MEM_DEVICE, MEM_HOST = 0, 1
 ELEM_F64, ELEM_F32 = 0, 1
 
 PRECISIONS = {"f64": F64, "f32": F32, "bf16x3": BF16X3, "tf32x3": TF32X3}
-SOLVES = {"qr": SOLVE_QR, "svd": SOLVE_SVD, "normal": SOLVE_NORMAL}
+SOLVES = {"qr": SOLVE_QR, "svd": SOLVE_SVD, "normal": SOLVE_NORMAL, "normal_pinv": SOLVE_NORMAL_PINV}
 
 _vp = C.c_void_p
 _lib = None

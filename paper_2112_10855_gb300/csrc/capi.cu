@@ -55,7 +55,7 @@ void free_all(Handle* h)
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
-    for (int s = 0; s < 3; ++s) if (h->graph[s]) cudaGraphExecDestroy(h->graph[s]);
+    for (int s = 0; s < 4; ++s) if (h->graph[s]) cudaGraphExecDestroy(h->graph[s]);
 }
 
 // Largest TTM intermediate over all modes and steps of the Multi-TTM (and MTTKRP).
@@ -102,13 +102,15 @@ int take_status(Handle* h)
     return CPALS_OK;
 }
 
+inline bool is_normal(int solve) { return solve == CPALS_SOLVE_NORMAL || solve == CPALS_SOLVE_NORMAL_PINV; }
+
 // Make the derived data (Q_m, R_m for QR/SVD; G_m for NORMAL) of every mode
 // other than `skip` current.
 cudaError_t refresh_derived(Handle* h, int solve, int skip)
 {
     for (int m = 0; m < h->N; ++m) {
         if (m == skip) continue;
-        if (solve == CPALS_SOLVE_NORMAL) {
+        if (is_normal(solve)) {
             if (!h->gram_valid[m]) {
                 CPALS_CUDA_TRY(cpals::gram(h, h->A[m], h->dims[m], h->G[m]));
                 h->gram_valid[m] = true;
@@ -128,9 +130,10 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
 {
     CPALS_CUDA_TRY(refresh_derived(h, solve, n));
     const int64_t In = h->dims[n];
-    if (solve == CPALS_SOLVE_NORMAL) {
+    if (is_normal(solve)) {
         CPALS_CUDA_TRY(cpals::mttkrp(h, n));
-        CPALS_CUDA_TRY(cpals::solve_normal(h, n));
+        if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n));
+        else CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol));
     } else {
         // The QR of V_n needs only the R_m and the Multi-TTM only the Q_m: run the
         // QR on the side stream meanwhile and join before W = Y_(n) Q0.
@@ -151,7 +154,7 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol));
     }
     CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
-    if (solve == CPALS_SOLVE_NORMAL) {
+    if (is_normal(solve)) {
         CPALS_CUDA_TRY(cpals::gram(h, h->A[n], In, h->G[n]));
         h->gram_valid[n] = true;
         h->qr_valid[n] = false;
@@ -173,7 +176,7 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
 // (Sec. 2.2), so only rounding differs from the per-mode Multi-TTM.
 cudaError_t sweep(Handle* h, int solve, double rtol)
 {
-    if (solve == CPALS_SOLVE_NORMAL || h->N < 3 || !h->dimtree || !h->tA) {
+    if (is_normal(solve) || h->N < 3 || !h->dimtree || !h->tA) {
         for (int n = 0; n < h->N; ++n) CPALS_CUDA_TRY(mode_update(h, n, solve, rtol));
         return cpals::fit_efficient(h, solve);
     }
@@ -538,7 +541,7 @@ int cpals_solve_mode(cpals_handle* hh, int mode, int solve, double svd_rtol)
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
     if (mode < 0 || mode >= h->N) return fail(h, CPALS_ERR_ARG, "%s", "bad mode");
-    if (solve < CPALS_SOLVE_QR || solve > CPALS_SOLVE_NORMAL) return fail(h, CPALS_ERR_ARG, "%s", "bad solve kind");
+    if (solve < CPALS_SOLVE_QR || solve > CPALS_SOLVE_NORMAL_PINV) return fail(h, CPALS_ERR_ARG, "%s", "bad solve kind");
     if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
     CUDA_OR_FAIL(h, mode_update(h, mode, solve, svd_rtol), "mode update");
     h->last_sweep_solve = -1;
@@ -551,7 +554,7 @@ int cpals_iterate(cpals_handle* hh, int iters, double tol, int solve, double svd
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
     if (done) *done = 0;
     if (iters < 0 || tol < 0.0) return fail(h, CPALS_ERR_ARG, "%s", "iters and tol must be >= 0");
-    if (solve < CPALS_SOLVE_QR || solve > CPALS_SOLVE_NORMAL) return fail(h, CPALS_ERR_ARG, "%s", "bad solve kind");
+    if (solve < CPALS_SOLVE_QR || solve > CPALS_SOLVE_NORMAL_PINV) return fail(h, CPALS_ERR_ARG, "%s", "bad solve kind");
     if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
     if (iters == 0) return CPALS_OK;
     // derived data valid for every mode, so that one captured sweep fits all
@@ -657,7 +660,7 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
     const bool v = value != 0;
     if (v != h->dimtree) {
         h->dimtree = v;
-        for (int s = 0; s < 3; ++s)             // captured sweeps follow the old schedule
+        for (int s = 0; s < 4; ++s)             // captured sweeps follow the old schedule
             if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
     }
     return CPALS_OK;

@@ -119,9 +119,9 @@ struct Handle {
     int last_sweep_solve = -1;      // solve kind of the last finished sweep
 
     // graphs, one per solve kind
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-    double graph_rtol[3] = {0, 0, 0};
-    int64_t graph_nodes[3] = {0, 0, 0};
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    double graph_rtol[4] = {0, 0, 0, 0};
+    int64_t graph_nodes[4] = {0, 0, 0, 0};
 
     int64_t launches = 0;
     size_t owned_bytes = 0;
@@ -173,6 +173,8 @@ cudaError_t solve_qr(Handle* h, int64_t In);
 cudaError_t solve_svd(Handle* h, int64_t In, double rtol);
 // S_n = Hadamard product of the other Grams, then Cholesky solve Ahat S = M.
 cudaError_t solve_normal(Handle* h, int n);
+// S_n as above, then Ahat = M pinv(S_n) with the truncated Jacobi SVD (CP-ALS-PINV).
+cudaError_t solve_normal_pinv(Handle* h, int n, double rtol);
 // Normalise columns of h->Ahat into A_n and lambda; then QR and Gram of A_n.
 cudaError_t normalize_and_refactor(Handle* h, int n);
 // Gram G = A^T A for an I x R factor.

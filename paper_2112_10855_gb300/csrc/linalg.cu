@@ -332,7 +332,7 @@ struct GPtrs {
 };
 
 __global__ void hadamard_cholesky_kernel(GPtrs gp, int N, int n, int R, double* __restrict__ S,
-                                         double* __restrict__ Lout, int* __restrict__ status)
+                                         double* __restrict__ Lout, int* __restrict__ status, int chol)
 {
     if (*status != kStatusOk) return;
     __shared__ double L[kMaxRank * kMaxRank];
@@ -347,6 +347,7 @@ __global__ void hadamard_cholesky_kernel(GPtrs gp, int N, int n, int R, double* 
     }
     if (tid == 0) bad = 0;
     __syncthreads();
+    if (!chol) return;
     for (int j = 0; j < R; ++j) {
         if (tid == 0) {
             double d = L[j + R * j];
@@ -644,11 +645,33 @@ cudaError_t solve_normal(Handle* h, int n)
 {
     GPtrs gp;
     for (int m = 0; m < h->N; ++m) gp.G[m] = h->G[m];
-    hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status);
+    hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status, 1);
     chol_rows_kernel<<<grid_for(h->dims[n], 128, h->num_sms), 128, 0, h->stream>>>(h->M, h->T, h->dims[n], h->R,
                                                                                    h->Ahat, h->d_status);
     h->launches += 2;
     return cudaGetLastError();
+}
+
+cudaError_t solve_normal_pinv(Handle* h, int n, double rtol)
+{
+    if (!(rtol > 0.0)) rtol = (double)h->R * kEps;
+    GPtrs gp;
+    for (int m = 0; m < h->N; ++m) gp.G[m] = h->G[m];
+    hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status, 0);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    // S is symmetric, so pinv(S) = pinv(S^T): the same operator as the SVD solve with R0 -> S
+    constexpr size_t smem = sizeof(double) * (2 * kMaxRank * kMaxRank + kMaxRank);
+    static bool attr_set = false;
+    if (!attr_set) {
+        CPALS_CUDA_TRY(cudaFuncSetAttribute(jacobi_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        attr_set = true;
+    }
+    jacobi_pinv_kernel<<<1, 256, smem, h->stream>>>(h->S, h->R, rtol, h->T, h->d_status);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    return gemm_rows(h, h->M, h->dims[n], h->R, h->T, h->R, h->Ahat);
 }
 
 cudaError_t gram(Handle* h, const double* A, int64_t I, double* G)
@@ -670,7 +693,7 @@ cudaError_t fit_efficient(Handle* h, int solve)
 {
     const int n = h->N - 1;
     const int64_t I = h->dims[n];
-    const int qr = (solve != CPALS_SOLVE_NORMAL);
+    const int qr = (solve != CPALS_SOLVE_NORMAL && solve != CPALS_SOLVE_NORMAL_PINV);
     const unsigned nb = (unsigned)((I + 31) / 32);
     fit_inner_kernel<<<nb, 256, 0, h->stream>>>(qr ? h->W : h->M, h->Ahat, h->R0, I, h->R, qr, h->scratch,
                                                 h->d_status);

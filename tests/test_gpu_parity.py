@@ -117,11 +117,14 @@ def test_apply_q0_matches_oracle(cuda_lib, dims, R):
         assert rel(W, ref["W"]) <= 1e-12
 
 
-@pytest.mark.parametrize("solve", ["qr", "svd", "normal"])
+OSOLVE = {"qr": oracle.QR, "svd": oracle.SVD, "normal": oracle.NORMAL, "normal_pinv": oracle.NORMAL_PINV}
+
+
+@pytest.mark.parametrize("solve", ["qr", "svd", "normal", "normal_pinv"])
 @pytest.mark.parametrize("dims,R", [((37, 29, 41), 5), ((12, 11, 10, 9), 3), ((60, 50, 40), 10)])
 def test_mode_update_matches_oracle(cuda_lib, solve, dims, R):
     X, A = gaussian_problem(dims, R, seed=11)
-    osolve = {"qr": oracle.QR, "svd": oracle.SVD, "normal": oracle.NORMAL}[solve]
+    osolve = OSOLVE[solve]
     for n in range(len(dims)):
         o = oracle.OracleCPALS(X, dims, R)
         o.set_factors(A)
@@ -145,11 +148,11 @@ def test_mttkrp_matches_oracle(cuda_lib, mode):
     assert rel(M, oracle.mttkrp(X, dims, mode, A)) <= 1e-12
 
 
-@pytest.mark.parametrize("solve", ["qr", "svd", "normal"])
+@pytest.mark.parametrize("solve", ["qr", "svd", "normal", "normal_pinv"])
 def test_sweeps_match_oracle_c1_shape(cuda_lib, solve):
     # 50^3, rank 5, N(0,1) factors, unit weights, 1% noise, 20 sweeps
     p = inputs.workload_c1()
-    osolve = {"qr": oracle.QR, "svd": oracle.SVD, "normal": oracle.NORMAL}[solve]
+    osolve = OSOLVE[solve]
     o = oracle.OracleCPALS(p.X, p.dims, p.rank)
     o.set_factors(p.init_factors)
     k, fits_o = o.iterate(20, solve=osolve, rtol=1e-10)

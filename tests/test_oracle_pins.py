@@ -238,6 +238,20 @@ def test_normal_update_equals_qr_update_well_conditioned():
         assert rel(S, F.Z(A, n).T @ F.Z(A, n)) < 1e-13
 
 
+def test_normal_pinv_update_equals_normal_and_solve():
+    # CP-ALS-PINV (Sec. 2.3): Ahat = M pinv(S); for a well-conditioned S it is
+    # the Cholesky solution and numpy's solve of Ahat S = M
+    dims, R = (8, 7, 6), 3
+    X, A = _problem(dims, R, seed=4)
+    for n in range(3):
+        a = oracle.OracleCPALS(X, dims, R); a.set_factors(A); a.update_mode(n, oracle.NORMAL)
+        b = oracle.OracleCPALS(X, dims, R); b.set_factors(A); b.update_mode(n, oracle.NORMAL_PINV, 1e-12)
+        assert rel(a.factor(n), b.factor(n)) < 1e-10
+        M, S = b.last_mttkrp(n)
+        ref = np.linalg.solve(S.T, M.T).T
+        assert rel(b.last(n)["Ahat"], ref) < 1e-10
+
+
 def test_trsm_against_solve():
     R0 = np.triu(RNG.standard_normal((6, 6))) + 4 * np.eye(6)
     W = RNG.standard_normal((11, 6))
