@@ -232,6 +232,15 @@ def test_singular_qr_solve_is_reported_and_factor_kept(cuda_lib):
     o.set_factors(A)
     o.update_mode(0, oracle.SVD, 1e-10)
     assert rel(Ag[0] * lam[None, :], o.factor(0) * o.lam()[None, :]) <= 1e-8
+    # CP-ALS-PINV on the exactly rank-deficient Hadamard Gram: M pinv(S)
+    h = gpu_handle(dims, R, X, A)
+    h.solve_mode(0, "normal_pinv", 1e-10)
+    h.sync()
+    Ag, lam = h.get_factors()
+    o = oracle.OracleCPALS(X, dims, R)
+    o.set_factors(A)
+    o.update_mode(0, oracle.NORMAL_PINV, 1e-10)
+    assert rel(Ag[0] * lam[None, :], o.factor(0) * o.lam()[None, :]) <= 1e-8
 
 
 def test_host_tensor_path_and_edge_shapes(cuda_lib):

@@ -252,6 +252,26 @@ def test_normal_pinv_update_equals_normal_and_solve():
         assert rel(b.last(n)["Ahat"], ref) < 1e-10
 
 
+def test_normal_pinv_on_singular_gram_matches_numpy_pinv():
+    # columns 0 and 1 equal in every factor but mode n make the Hadamard Gram S
+    # exactly rank-deficient; CP-ALS-PINV (Sec. 2.3) then gives M pinv(S) with
+    # the relative cut, where the Cholesky form (Alg. cp-als) fails
+    dims, R = (7, 6, 5), 3
+    X, A = _problem(dims, R, seed=9)
+    for n in range(3):
+        B = [a.copy() for a in A]
+        for m in range(3):
+            if m != n:
+                B[m][:, 1] = B[m][:, 0]
+        o = oracle.OracleCPALS(X, dims, R); o.set_factors(B)
+        o.update_mode(n, oracle.NORMAL_PINV, 1e-10)
+        M, S = o.last_mttkrp(n)
+        assert np.linalg.matrix_rank(S) == R - 1
+        ref = M @ np.linalg.pinv(S, rcond=1e-10)
+        assert rel(o.last(n)["Ahat"], ref) < 1e-9
+        assert np.abs(o.last(n)["Ahat"][:, 0] - o.last(n)["Ahat"][:, 1]).max() < 1e-9 * np.abs(ref).max()
+
+
 def test_trsm_against_solve():
     R0 = np.triu(RNG.standard_normal((6, 6))) + 4 * np.eye(6)
     W = RNG.standard_normal((11, 6))
