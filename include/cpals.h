@@ -196,8 +196,15 @@ int cpals_sync(cpals_handle* h);
  *    second half for the Multi-TTMs of the first half, and once over the first
  *    half (with its updated Q_m) for the second half.  That is two passes over
  *    X per sweep instead of N.  0 runs a full Multi-TTM from X per mode.  The
- *    results differ only by rounding (Sec. 2.2: TTMs commute). */
-typedef enum { CPALS_OPT_DIMTREE = 0 } cpals_option;
+ *    results differ only by rounding (Sec. 2.2: TTMs commute).
+ *  CPALS_OPT_TC_PIPELINE (default 1): with CPALS_BF16X3 / CPALS_TF32X3, the
+ *    first TTM of a Multi-TTM (the pass over X, Eq. multittm) runs in one
+ *    persistent tensor-core kernel per launch that streams X through the
+ *    Tensor Memory Accelerator, whenever the product of the dims before the
+ *    contracted mode is a multiple of 4.  0 always uses one CTA per 128-row
+ *    tile.  Both compute the same split products; the sums differ only in the
+ *    order of two FP32 additions per output. */
+typedef enum { CPALS_OPT_DIMTREE = 0, CPALS_OPT_TC_PIPELINE = 1 } cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
 
 /* Number of kernel launches the handle has issued so far (graph replays count

@@ -180,6 +180,10 @@ class CPALS:
         """CPALS_OPT_DIMTREE: share Multi-TTM passes over X across modes in sweeps."""
         _check(self._h, load().cpals_set_option(self._h, 0, 1 if on else 0))
 
+    def set_tc_pipeline(self, on: bool):
+        """CPALS_OPT_TC_PIPELINE: persistent TMA-fed tensor-core kernel for the pass over X."""
+        _check(self._h, load().cpals_set_option(self._h, 1, 1 if on else 0))
+
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
 

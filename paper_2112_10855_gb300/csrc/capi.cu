@@ -655,9 +655,17 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
 {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
-    if (option != CPALS_OPT_DIMTREE || (value != 0 && value != 1))
+    if ((option != CPALS_OPT_DIMTREE && option != CPALS_OPT_TC_PIPELINE) || (value != 0 && value != 1))
         return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
     const bool v = value != 0;
+    if (option == CPALS_OPT_TC_PIPELINE) {
+        if (v != h->tc_pipe) {
+            h->tc_pipe = v;
+            for (int s = 0; s < 4; ++s)         // captured sweeps hold the old kernels
+                if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
+        }
+        return CPALS_OK;
+    }
     if (v != h->dimtree) {
         h->dimtree = v;
         for (int s = 0; s < 4; ++s)             // captured sweeps follow the old schedule

@@ -98,6 +98,9 @@ struct Handle {
     int64_t tA_dims[kMaxN] = {0};
     int tA_contracted[kMaxN] = {0};
     bool dimtree = true;
+    // first TTM on the tensor cores through the persistent TMA pipeline when
+    // the shape allows it (else one CTA per 128-row tile)
+    bool tc_pipe = true;
     // FP64 scratch for split-K partials, reductions and pre-split tensor-core
     // tiles (main stream), and a separate workspace for the TSQR levels, so a QR
     // on the side stream never shares memory with the Multi-TTM

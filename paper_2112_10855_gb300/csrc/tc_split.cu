@@ -27,9 +27,22 @@
 //
 // Every wait is bounded.  On timeout the kernel records CPALS_ERR_TIMEOUT in
 // the status word, frees its tensor memory and returns.
+//
+// A second, persistent kernel (ttm_split_tc_pipe_kernel, below) serves the
+// shapes whose row stride L is a multiple of 4 floats: one CTA per SM walks a
+// list of row tiles; a producer warp streams X in [rows x K-chunk] boxes with
+// the Tensor Memory Accelerator (cp.async.bulk.tensor) and the pre-split Q
+// tiles with cp.async.bulk into a ring of shared-memory stages; eight split
+// warps turn each staged box into hi/lo A operands written straight to tensor
+// memory (tcgen05.st); one thread issues the MMAs with A read from tensor
+// memory; four epilogue warps drain a double-buffered accumulator while the
+// next tile accumulates.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -284,7 +297,10 @@ __global__ void __launch_bounds__(kTcThreads) ttm_split_tc_kernel(
 {
     using E = Elem<TF32>;
     using Cfg = TcCfg<N>;
-    if (*status != kStatusOk) return;
+    __shared__ int skip;   // one read of the status word, so every thread takes the same branch
+    if (threadIdx.x == 0) skip = *(volatile int*)status != kStatusOk;
+    __syncthreads();
+    if (skip) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* mbar = (uint64_t*)(smem + 2 * Cfg::kStage);
@@ -430,6 +446,384 @@ __global__ void __launch_bounds__(kTcThreads) ttm_split_tc_kernel(
     if (warp == 0) tmem_dealloc<Cfg::kNcols>(tmem);
 }
 
+// ---------------------------------------------------------------- persistent pipeline
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `parity` on mbar; false when the CTA's abort flag is
+// raised or after ~1 s (which raises the flag).
+__device__ __forceinline__ bool pipe_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if ((it & 15) == 15) {
+            if (*abort_flag) return false;
+            const uint64_t t = global_ns();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > 1000000000ull) { *abort_flag = 1; return false; }
+        }
+    }
+}
+
+// Drain wait used on the way out: ignores the abort flag, gives up after ~1 s.
+__device__ __forceinline__ void pipe_drain(uint64_t* mbar, uint32_t parity)
+{
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(mbar, parity))
+        if (global_ns() - t0 > 1000000000ull) return;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" : : "r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" : : "r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: a 3-D box of the tensor map at (x, y, z) into shared memory.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];"
+        :
+        : "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :
+        : "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// 16 consecutive 32-bit tensor-memory columns of this thread's lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        :
+        : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+          "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D (tensor memory) += A (tensor memory) x B (shared memory descriptor).
+template <bool TF32>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    if constexpr (TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
+            :
+            : "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+            :
+            : "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+// Persistent pipeline configuration.  A stage holds one fp32 box of X
+// (128 rows x one 128-byte operand K-chunk) and the hi|lo Q tiles of that
+// chunk (2N rows).  Tensor memory (512 columns) holds two accumulators of 2N
+// columns (A_hi*B_hi + A_lo*B_hi in the first N, A_hi*B_lo in the second N)
+// and one A slot of 64 columns per stage (hi in the first 32, lo in the next
+// 32; bf16 packs two K values per column, tf32 one).
+template <int N, bool TF32>
+struct PipeCfg {
+    using E = Elem<TF32>;
+    static constexpr int kc = E::kChunk;                              // K per stage
+    static constexpr uint32_t kXBytes = kTcRows * kc * 4;             // fp32 box
+    static constexpr uint32_t kBBytes = 2u * N * 128u;                // hi + lo Q tiles
+    static constexpr uint32_t kStageBytes = kXBytes + kBBytes;
+    static constexpr int kAccCols = 2 * N;
+    static constexpr int kACols = 64;
+    static constexpr int kByTmem = (512 - 2 * kAccCols) / kACols;
+    static constexpr int kBySmem = (200 * 1024) / (int)kStageBytes;
+    static constexpr int kStages = kByTmem < kBySmem ? (kByTmem < 8 ? kByTmem : 8) : (kBySmem < 8 ? kBySmem : 8);
+    static constexpr int kThreads = 14 * 32;   // 4 epilogue, 8 split, 1 producer, 1 MMA warp
+    static constexpr uint32_t kSmem = kStages * kStageBytes + 1024 + 256;
+    static_assert(kStages >= 2, "pipeline needs two stages");
+    static_assert(kStages * kStageBytes > 114 * 1024, "one CTA per SM owns all 512 TMEM columns");
+};
+
+// Out(l, r, t) = sum_k X(l, k, t) Q(k, r) for the tiles blockIdx.x, +gridDim.x, ...
+// A tile is BL consecutive l times BT consecutive t (BL*BT <= 128 rows).
+template <int N, bool TF32>
+__global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pipe_kernel(
+    const __grid_constant__ CUtensorMap xmap, const uint8_t* __restrict__ btiles, float* __restrict__ out,
+    int64_t L, int64_t Tn, int R, int BL, int BT, int64_t ntl, int64_t ntiles, int nchunks,
+    int* __restrict__ status)
+{
+    using Cfg = PipeCfg<N, TF32>;
+    using E = Elem<TF32>;
+    constexpr int S = Cfg::kStages;
+    __shared__ int skip;   // one read of the status word, so every thread takes the same branch
+    if (threadIdx.x == 0) skip = *(volatile int*)status != kStatusOk;
+    __syncthreads();
+    if (skip) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = (uint64_t*)(smem + S * Cfg::kStageBytes);
+    uint64_t* ready = full + S;
+    uint64_t* empty = ready + S;
+    uint64_t* accfull = empty + S;
+    uint64_t* accempty = accfull + 2;
+    uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int kMmaWarp = 13, kProducerWarp = 12;
+    if (warp == kMmaWarp) tmem_alloc<512>(tmem_slot);
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&ready[s], 8);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&accfull[a], 1);
+            mbar_init(&accempty[a], 4);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const int64_t items = my_tiles * nchunks;
+    const int rows_used = BL * BT;
+    auto acol = [&](int s) { return (uint32_t)(2 * Cfg::kAccCols + s * Cfg::kACols); };
+
+    if (warp == kProducerWarp) {
+        if (lane == 0) {
+            const uint32_t tx = (uint32_t)rows_used * Cfg::kc * 4u + Cfg::kBBytes;
+            int64_t it = 0;
+            for (; it < items; ++it) {
+                const int s = (int)(it % S);
+                if (!pipe_wait(&empty[s], (uint32_t)((it / S) & 1) ^ 1u, abort_flag)) break;
+                const int64_t tile = blockIdx.x + (it / nchunks) * (int64_t)gridDim.x;
+                const int c = (int)(it % nchunks);
+                const int64_t tt = tile / ntl, tl = tile - tt * ntl;
+                uint8_t* st = smem + (size_t)s * Cfg::kStageBytes;
+                mbar_expect_tx(&full[s], tx);
+                tma_load_3d(st, &xmap, (int)(tl * BL), c * Cfg::kc, (int)(tt * BT), &full[s]);
+                bulk_load(st + Cfg::kXBytes, btiles + (size_t)c * Cfg::kBBytes, Cfg::kBBytes, &full[s]);
+            }
+            // every issued copy lands before the CTA may exit
+            for (int s = 0; s < S; ++s) {
+                const int64_t last = it - 1 - ((it - 1 - s) % S + S) % S;   // last issued item on stage s
+                if (last >= 0 && last < it) pipe_drain(&full[s], (uint32_t)((last / S) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            constexpr uint32_t idesc2 = make_idesc_e<TF32>(kTcRows, 2 * N);
+            constexpr uint32_t idesc1 = make_idesc_e<TF32>(kTcRows, N);
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t j = 0; j < my_tiles && ok; ++j) {
+                const int a = (int)(j & 1);
+                if (!pipe_wait(&accempty[a], (uint32_t)((j >> 1) & 1) ^ 1u, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * Cfg::kAccCols);
+                for (int c = 0; c < nchunks; ++c, ++it) {
+                    const int s = (int)(it % S);
+                    const uint32_t ph = (uint32_t)((it / S) & 1);
+                    if (!pipe_wait(&full[s], ph, abort_flag) || !pipe_wait(&ready[s], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ahi = tmem + acol(s), alo = ahi + 32u;
+                    const uint32_t bh = smem_u32(smem + (size_t)s * Cfg::kStageBytes + Cfg::kXBytes);
+#pragma unroll
+                    for (int ks = 0; ks < E::kChunk / E::kStep; ++ks) {
+                        const uint64_t bd = make_desc(bh + (uint32_t)ks * 2u * kLbo);
+                        mma_ts<TF32>(d, ahi + 8u * ks, bd, idesc2, (c | ks) ? 1u : 0u);   // [hi*hi | hi*lo]
+                        mma_ts<TF32>(d, alo + 8u * ks, bd, idesc1, 1u);                    // += lo*hi
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&accfull[a]);
+            }
+            // the MMAs read tensor memory and shared memory: drain before exit
+            if (it > 0) {
+                const int64_t last = it - 1;
+                pipe_drain(&empty[last % S], (uint32_t)((last / S) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (warp >= 4) {
+        // split warps: lane quadrant q = warp % 4, K half h
+        const int q = warp & 3, h = (warp - 4) >> 2;
+        const int m = 32 * q + lane;
+        const bool mok = m < rows_used;
+        const int bt = mok ? m / BL : 0, bl = mok ? m - bt * BL : 0;
+        const int xoff = bt * Cfg::kc * BL + bl;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+        constexpr int kHalf = Cfg::kc / 2;   // K values per split thread per stage
+        for (int64_t it = 0; it < items; ++it) {
+            const int s = (int)(it % S);
+            // warp-uniform outcome: tcgen05.st below is warp-collective
+            if (!__all_sync(0xffffffffu, pipe_wait(&full[s], (uint32_t)((it / S) & 1), abort_flag))) break;
+            const float* xs = reinterpret_cast<const float*>(smem + (size_t)s * Cfg::kStageBytes) + xoff;
+            uint32_t hi[16], lo[16];
+            if constexpr (TF32) {
+#pragma unroll
+                for (int p = 0; p < 16; ++p) {
+                    const float x = mok ? xs[(h * kHalf + p) * BL] : 0.0f;
+                    hi[p] = to_tf32(x);
+                    lo[p] = to_tf32(x - __uint_as_float(hi[p]));
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < 16; ++p) {
+                    const int k = h * kHalf + 2 * p;
+                    const float x0 = mok ? xs[k * BL] : 0.0f;
+                    const float x1 = mok ? xs[(k + 1) * BL] : 0.0f;
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                    hi[p] = pack2(h0, h1);
+                    lo[p] = pack2(__float2bfloat16_rn(x0 - __bfloat162float(h0)),
+                                  __float2bfloat16_rn(x1 - __bfloat162float(h1)));
+                }
+            }
+            const uint32_t col = tmem + acol(s) + (uint32_t)(h * 16);
+            tmem_st16(lane_base + col, hi);
+            tmem_st16(lane_base + col + 32u, lo);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ready[s]);
+        }
+    } else {
+        // epilogue warps 0..3: lane quadrant = warp
+        const int m = 32 * warp + lane;
+        const bool mok = m < rows_used;
+        const int bt = mok ? m / BL : 0, bl = mok ? m - bt * BL : 0;
+        const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        for (int64_t j = 0; j < my_tiles; ++j) {
+            const int a = (int)(j & 1);
+            // warp-uniform outcome: tcgen05.ld below is warp-collective
+            if (!__all_sync(0xffffffffu, pipe_wait(&accfull[a], (uint32_t)((j >> 1) & 1), abort_flag))) break;
+            tc_fence_after();
+            const int64_t tile = blockIdx.x + j * (int64_t)gridDim.x;
+            const int64_t tt = tile / ntl, tl = tile - tt * ntl;
+            const int64_t l = tl * BL + bl, t = tt * BT + bt;
+            const bool ok = mok && l < L && t < Tn;
+            float* o = out + l + L * (int64_t)R * t;
+#pragma unroll
+            for (int c0 = 0; c0 < N; c0 += 16) {
+                float v[16], w[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)(a * Cfg::kAccCols + c0), v);
+                tmem_ld16(tmem + lane_base + (uint32_t)(a * Cfg::kAccCols + N + c0), w);
+                if (ok) {
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj)
+                        if (c0 + jj < R) o[L * (int64_t)(c0 + jj)] = v[jj] + w[jj];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty[a]);
+        }
+    }
+
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_TIMEOUT);
+    tc_fence_after();
+    if (warp == kMmaWarp) tmem_dealloc<512>(tmem);
+}
+
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeTiledFn encode_tiled_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// The pipeline serves a shape when the TMA strides are 16-byte multiples
+// (L % 4 == 0, 16-byte aligned X) and every coordinate fits in int32.
+bool pipe_shape_ok(const float* in, TtmShape s)
+{
+    const int64_t lim = (int64_t)1 << 30;
+    return s.L % 4 == 0 && (((uintptr_t)in) & 15) == 0 && s.L < lim && s.K < lim && s.T < lim &&
+           encode_tiled_fn() != nullptr;
+}
+
+template <int N, bool TF32>
+cudaError_t launch_pipe(Handle* h, const float* in, const uint8_t* tiles, float* out, TtmShape s, int R,
+                        int nchunks)
+{
+    using Cfg = PipeCfg<N, TF32>;
+    static std::once_flag attr_once;
+    cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [&] {
+        attr_err = cudaFuncSetAttribute(ttm_split_tc_pipe_kernel<N, TF32>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+    });
+    CPALS_CUDA_TRY(attr_err);
+    const int BL = s.L >= kTcRows ? kTcRows : (int)s.L;
+    const int BT = kTcRows / BL;
+    CUtensorMap map;
+    const cuuint64_t gdim[3] = {(cuuint64_t)s.L, (cuuint64_t)s.K, (cuuint64_t)s.T};
+    const cuuint64_t gstride[2] = {(cuuint64_t)s.L * 4u, (cuuint64_t)s.L * (cuuint64_t)s.K * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)BL, (cuuint32_t)Cfg::kc, (cuuint32_t)BT};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult cr = encode_tiled_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(in), gdim,
+                                          gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const int64_t ntl = (s.L + BL - 1) / BL;
+    const int64_t ntiles = ntl * ((s.T + BT - 1) / BT);
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
+    ttm_split_tc_pipe_kernel<N, TF32><<<grid, Cfg::kThreads, Cfg::kSmem, h->stream>>>(
+        map, tiles, out, s.L, s.T, R, BL, BT, ntl, ntiles, nchunks, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
 template <int N, bool TF32>
 cudaError_t launch_tc(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R)
 {
@@ -450,6 +844,7 @@ cudaError_t launch_tc(Handle* h, const float* in, const double* Q, int64_t ldq, 
         Q, ldq, s.K, R, tiles, nchunks, h->d_status);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
+    if (h->tc_pipe && pipe_shape_ok(in, s)) return launch_pipe<N, TF32>(h, in, tiles, out, s, R, nchunks);
     const int64_t rows = s.L * s.T;
     const int64_t grid = (rows + kTcRows - 1) / kTcRows;
     ttm_split_tc_kernel<N, TF32><<<(unsigned)grid, kTcThreads, Cfg::kSmem, h->stream>>>(

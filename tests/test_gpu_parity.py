@@ -303,17 +303,24 @@ def test_full_size_sweep_c2(cuda_lib):
 # ---------------------------------------------------------------- tensor cores (BF16X3, TF32X3)
 # shapes cover the 128-bit load path (L % 4 == 0: (40,30,20) mode 0, (64,48,40),
 # (36,36,36,36)) and the scalar path (L = 1 fibers, odd L such as (70,45,33))
+# The persistent TMA pipeline takes every first TTM whose row stride L (the
+# product of the dims before the contracted mode) is a multiple of 4: here
+# L = 40, 64 (row tiles of several t slices), 300, 46656, 1296 (ragged
+# 128-row tiles, more tiles than SMs), 2400 with K = 150 (several ragged
+# K-chunks at R = 48), and the increasing dims (16, 20, 24, 28) (every mode).
 TC_SHAPES = [((40, 30, 20), 16), ((300, 20), 16), ((20, 18, 17, 16), 16), ((70, 45, 33), 20), ((129, 64, 40), 32),
-             ((64, 48, 40), 32), ((36, 36, 36, 36), 16), ((66, 65, 64), 64)]
+             ((64, 48, 40), 32), ((36, 36, 36, 36), 16), ((66, 65, 64), 64), ((48, 50, 150), 48),
+             ((16, 20, 24, 28), 16)]
 # relative error per split product: ~2^-16 with bf16 parts, ~2^-21 with tf32 parts;
 # over a contraction of length K the relative Frobenius error stays below
 # 2 * u * sqrt(K_max) (K_max = the largest contracted dim)
 TC_U = {"bf16x3": 2.0 ** -16, "tf32x3": 2.0 ** -21}
 
 
+@pytest.mark.parametrize("pipeline", [True, False])
 @pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("dims,R", TC_SHAPES)
-def test_split_tc_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision):
+def test_split_tc_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision, pipeline):
     # integers |x| <= 48 are exact in bf16 and tf32 (lo parts are zero) and 0/1
     # factors keep every product and partial sum exact in FP32, so the
     # tensor-core path must agree bit for bit with the oracle; a wrong operand
@@ -324,22 +331,45 @@ def test_split_tc_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision):
     Q = [np.asfortranarray((rng.random((d, R)) < 0.5).astype(np.float64)) for d in dims]
     Rm = [np.asfortranarray(np.triu(np.ones((R, R)))) for _ in dims]
     h = gpu_handle(dims, R, X, precision=precision)
+    h.set_tc_pipeline(pipeline)
     h.set_factor_qr(Q, Rm)
     for n in range(len(dims)):
         Y, _ = h.multi_ttm(n)
         np.testing.assert_array_equal(Y, oracle.multi_ttm(X, dims, n, Q))
 
 
+@pytest.mark.parametrize("pipeline", [True, False])
 @pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("dims,R", TC_SHAPES)
-def test_split_tc_multi_ttm_error_bound(cuda_lib, dims, R, precision):
+def test_split_tc_multi_ttm_error_bound(cuda_lib, dims, R, precision, pipeline):
     # hi*hi + hi*lo + lo*hi drops lo*lo and rounds the lo parts
     X, A = gaussian_problem(dims, R, seed=23)
     QR = [oracle.qr(a) for a in A]
     h = gpu_handle(dims, R, X, precision=precision)
+    h.set_tc_pipeline(pipeline)
     h.set_factor_qr([q for q, _ in QR], [r for _, r in QR])
     tol = 2.0 * TC_U[precision] * np.sqrt(max(dims))
     for n in range(len(dims)):
         Y, _ = h.multi_ttm(n)
         err = rel(Y, oracle.multi_ttm(X, dims, n, [q for q, _ in QR]))
         assert err <= tol, (n, err, tol)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
+def test_split_tc_sweeps_track_oracle(cuda_lib, precision):
+    # dimension-tree sweeps whose passes over X run on the tensor cores: the
+    # first pass contracts mode 3 (L = 48*52*56), the second mode 1 (L = 48,
+    # two t slices per row tile); fit per sweep against the FP64 oracle, and
+    # the persistent pipeline against the per-tile kernel
+    p = inputs.planted((48, 52, 56, 60), 16, seed=5, init_seed=6, noise=0.01)
+    o = oracle.OracleCPALS(p.X, p.dims, p.rank)
+    o.set_factors(p.init_factors)
+    _, ofits = o.iterate(4, solve=oracle.QR)
+    fits = {}
+    for pipeline in (True, False):
+        h = gpu_handle(p.dims, p.rank, p.X, p.init_factors, precision=precision)
+        h.set_tc_pipeline(pipeline)
+        fits[pipeline] = np.asarray(h.iterate(4, solve="qr"))
+    tol = 1e-4 if precision == "bf16x3" else 1e-5
+    assert np.abs(fits[True] - np.asarray(ofits)).max() <= tol, (fits[True], ofits)
+    assert np.abs(fits[True] - fits[False]).max() <= tol / 10
