@@ -30,13 +30,14 @@
 //
 // A second, persistent kernel (ttm_split_tc_pipe_kernel, below) serves the
 // shapes whose row stride L is a multiple of 4 floats: one CTA per SM walks a
-// list of row tiles; a producer warp streams X in [rows x K-chunk] boxes with
-// the Tensor Memory Accelerator (cp.async.bulk.tensor) and the pre-split Q
-// tiles with cp.async.bulk into a ring of shared-memory stages; eight split
-// warps turn each staged box into hi/lo A operands written straight to tensor
-// memory (tcgen05.st); one thread issues the MMAs with A read from tensor
-// memory; four epilogue warps drain a double-buffered accumulator while the
-// next tile accumulates.
+// list of row tiles.  A producer warp streams X in [rows x K-chunk] boxes with
+// the Tensor Memory Accelerator (cp.async.bulk.tensor) into a deep ring of
+// shared-memory stages; eight split warps turn each box into hi/lo A operands
+// written straight to tensor memory (tcgen05.st) and free the box at once; a
+// second producer warp brings the pre-split Q tiles of each item
+// (cp.async.bulk) into a short ring of operand slots; one thread issues the
+// MMAs with A read from tensor memory; four epilogue warps drain a
+// double-buffered accumulator while the next tile accumulates.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -191,6 +192,12 @@ __device__ __forceinline__ uint32_t to_tf32(float x)
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
+
+// The same rounding on the bit pattern: add half a unit in the last tf32 place
+// to the magnitude bits and clear the 13 dropped bits (round to nearest, ties
+// away from zero; a carry into the exponent is the correct rounding up).
+// Equal to cvt.rna.tf32.f32 for finite inputs below the largest finite float.
+__device__ __forceinline__ uint32_t tf32_rna_bits(uint32_t xb) { return (xb + 0x1000u) & 0xFFFFE000u; }
 
 template <bool TF32>
 __device__ __forceinline__ void split_group(const float* x, uint4& hi, uint4& lo)
@@ -455,19 +462,31 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about `ns` nanoseconds pass, without issuing instructions.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t parity, uint32_t ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase of `parity` on mbar; false when the CTA's abort flag is
 // raised or after ~1 s (which raises the flag).
 __device__ __forceinline__ bool pipe_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag)
 {
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(mbar, parity)) return true;
-        if ((it & 15) == 15) {
-            if (*abort_flag) return false;
-            const uint64_t t = global_ns();
-            if (t0 == 0) t0 = t;
-            else if (t - t0 > 1000000000ull) { *abort_flag = 1; return false; }
-        }
+    if (mbar_try_wait(mbar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait_sleep(mbar, parity, 100000u)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > 1000000000ull) { *abort_flag = 1; return false; }
     }
 }
 
@@ -475,7 +494,7 @@ __device__ __forceinline__ bool pipe_wait(uint64_t* mbar, uint32_t parity, volat
 __device__ __forceinline__ void pipe_drain(uint64_t* mbar, uint32_t parity)
 {
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(mbar, parity))
+    while (!mbar_try_wait_sleep(mbar, parity, 100000u))
         if (global_ns() - t0 > 1000000000ull) return;
 }
 
@@ -549,67 +568,96 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
     }
 }
 
-// Persistent pipeline configuration.  A stage holds one fp32 box of X
-// (128 rows x one 128-byte operand K-chunk) and the hi|lo Q tiles of that
-// chunk (2N rows).  Tensor memory (512 columns) holds two accumulators of 2N
-// columns (A_hi*B_hi + A_lo*B_hi in the first N, A_hi*B_lo in the second N)
-// and one A slot of 64 columns per stage (hi in the first 32, lo in the next
-// 32; bf16 packs two K values per column, tf32 one).
+// Persistent pipeline configuration.  Two rings:
+//  - X ring (SX stages, sized at launch): one fp32 box of X per item (128 rows
+//    x one 128-byte operand K-chunk), filled by the TMA producer warp and
+//    released as soon as the split warps have read it;
+//  - A/B slots (kASlots): the hi|lo A operands of an item in tensor memory (64
+//    columns: hi in the first 32, lo in the next 32; bf16 packs two K values
+//    per column, tf32 one) and the hi|lo Q tiles of its chunk in shared memory
+//    (2N rows), filled by the split warps and the Q producer warp and released
+//    by the MMA commit.  When the Q tiles of all K-chunks fit in kBResident
+//    bytes they are loaded once and stay resident (every row tile uses the
+//    same Q_m), and the slots hold only the A operands.
+// Tensor memory (512 columns) also holds two accumulators of 2N columns
+// (A_hi*B_hi + A_lo*B_hi in the first N, A_hi*B_lo in the second N).
 template <int N, bool TF32>
 struct PipeCfg {
     using E = Elem<TF32>;
-    static constexpr int kc = E::kChunk;                              // K per stage
+    static constexpr int kc = E::kChunk;                              // K per item
     static constexpr uint32_t kXBytes = kTcRows * kc * 4;             // fp32 box
     static constexpr uint32_t kBBytes = 2u * N * 128u;                // hi + lo Q tiles
-    static constexpr uint32_t kStageBytes = kXBytes + kBBytes;
     static constexpr int kAccCols = 2 * N;
     static constexpr int kACols = 64;
-    static constexpr int kByTmem = (512 - 2 * kAccCols) / kACols;
-    static constexpr int kBySmem = (200 * 1024) / (int)kStageBytes;
-    static constexpr int kStages = kByTmem < kBySmem ? (kByTmem < 8 ? kByTmem : 8) : (kBySmem < 8 ? kBySmem : 8);
-    static constexpr int kThreads = 14 * 32;   // 4 epilogue, 8 split, 1 producer, 1 MMA warp
-    static constexpr uint32_t kSmem = kStages * kStageBytes + 1024 + 256;
-    static_assert(kStages >= 2, "pipeline needs two stages");
-    static_assert(kStages * kStageBytes > 114 * 1024, "one CTA per SM owns all 512 TMEM columns");
+    static constexpr int kASlots = N <= 32 ? 4 : 3;
+    static constexpr uint32_t kBResident = 64u * 1024u;
+    static constexpr uint32_t kRingBudget = 220u * 1024u;           // X ring + Q tiles
+    static constexpr int kMaxX = 16;
+    static constexpr int kEpiWarps = 4, kSplitWarps = 8;
+    static constexpr int kXProducerWarp = kEpiWarps + kSplitWarps, kMmaWarp = kXProducerWarp + 1,
+                         kBProducerWarp = kMmaWarp + 1;
+    static constexpr int kThreads = (kBProducerWarp + 1) * 32;
+    static constexpr uint32_t kSmemMax = kRingBudget + 1024 + 512;   // + alignment + barriers
+    static_assert(2 * kAccCols + kASlots * kACols <= 512, "tensor memory budget");
+    static_assert(kASlots * kBBytes <= kBResident, "the Q region holds the ring slots");
+    static_assert((kRingBudget - kBResident) / kXBytes * kXBytes > 114 * 1024,
+                  "one CTA per SM owns all 512 TMEM columns");
+    static_assert(kSmemMax + 16 <= 232448, "shared memory per CTA");
+    // X stages and Q-region bytes for a launch
+    static int x_stages(uint32_t bregion)
+    {
+        const int n = (int)((kRingBudget - bregion) / kXBytes);
+        return n < kMaxX ? n : kMaxX;
+    }
 };
 
 // Out(l, r, t) = sum_k X(l, k, t) Q(k, r) for the tiles blockIdx.x, +gridDim.x, ...
 // A tile is BL consecutive l times BT consecutive t (BL*BT <= 128 rows).
+// Every split warp waits on every item and every ring has a single in-order
+// consumer per barrier, so each parity wait refers to an unambiguous phase.
 template <int N, bool TF32>
 __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pipe_kernel(
     const __grid_constant__ CUtensorMap xmap, const uint8_t* __restrict__ btiles, float* __restrict__ out,
-    int64_t L, int64_t Tn, int R, int BL, int BT, int64_t ntl, int64_t ntiles, int nchunks,
+    int64_t L, int64_t Tn, int R, int BL, int BT, int64_t ntl, int64_t ntiles, int nchunks, int SX, int bres,
     int* __restrict__ status)
 {
     using Cfg = PipeCfg<N, TF32>;
     using E = Elem<TF32>;
-    constexpr int S = Cfg::kStages;
+    constexpr int SA = Cfg::kASlots;
     __shared__ int skip;   // one read of the status word, so every thread takes the same branch
     if (threadIdx.x == 0) skip = *(volatile int*)status != kStatusOk;
     __syncthreads();
     if (skip) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = (uint64_t*)(smem + S * Cfg::kStageBytes);
-    uint64_t* ready = full + S;
-    uint64_t* empty = ready + S;
-    uint64_t* accfull = empty + S;
+    uint8_t* xring = smem;
+    uint8_t* bslots = smem + (size_t)SX * Cfg::kXBytes;
+    const uint32_t bregion = bres ? (uint32_t)nchunks * Cfg::kBBytes : (uint32_t)SA * Cfg::kBBytes;
+    uint64_t* xfull = (uint64_t*)(bslots + bregion);
+    uint64_t* xempty = xfull + Cfg::kMaxX;
+    uint64_t* bfull = xempty + Cfg::kMaxX;
+    uint64_t* ready = bfull + SA;
+    uint64_t* aempty = ready + SA;
+    uint64_t* accfull = aempty + SA;
     uint64_t* accempty = accfull + 2;
     uint32_t* tmem_slot = (uint32_t*)(accempty + 2);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int kMmaWarp = 13, kProducerWarp = 12;
-    if (warp == kMmaWarp) tmem_alloc<512>(tmem_slot);
+    if (warp == Cfg::kMmaWarp) tmem_alloc<512>(tmem_slot);
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&ready[s], 8);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < SX; ++s) {
+            mbar_init(&xfull[s], 1);
+            mbar_init(&xempty[s], Cfg::kSplitWarps);
+        }
+        for (int j = 0; j < SA; ++j) {
+            mbar_init(&bfull[j], 1);
+            mbar_init(&ready[j], Cfg::kSplitWarps);
+            mbar_init(&aempty[j], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&accfull[a], 1);
-            mbar_init(&accempty[a], 4);
+            mbar_init(&accempty[a], Cfg::kEpiWarps);
         }
         *abort_flag = 0;
         fence_mbar_init();
@@ -622,109 +670,137 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
     const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
     const int64_t items = my_tiles * nchunks;
     const int rows_used = BL * BT;
-    auto acol = [&](int s) { return (uint32_t)(2 * Cfg::kAccCols + s * Cfg::kACols); };
+    auto acol = [&](int j) { return (uint32_t)(2 * Cfg::kAccCols + j * Cfg::kACols); };
+    // last item issued on slot `s` of a ring of `n` slots when `it` items were issued
+    auto last_on = [](int64_t it, int s, int n) { return it - 1 - ((it - 1 - s) % n + n) % n; };
 
-    if (warp == kProducerWarp) {
+    if (warp == Cfg::kXProducerWarp) {
         if (lane == 0) {
-            const uint32_t tx = (uint32_t)rows_used * Cfg::kc * 4u + Cfg::kBBytes;
+            const uint32_t tx = (uint32_t)rows_used * Cfg::kc * 4u;
             int64_t it = 0;
             for (; it < items; ++it) {
-                const int s = (int)(it % S);
-                if (!pipe_wait(&empty[s], (uint32_t)((it / S) & 1) ^ 1u, abort_flag)) break;
+                const int s = (int)(it % SX);
+                if (!pipe_wait(&xempty[s], (uint32_t)((it / SX) & 1) ^ 1u, abort_flag)) break;
                 const int64_t tile = blockIdx.x + (it / nchunks) * (int64_t)gridDim.x;
                 const int c = (int)(it % nchunks);
                 const int64_t tt = tile / ntl, tl = tile - tt * ntl;
-                uint8_t* st = smem + (size_t)s * Cfg::kStageBytes;
-                mbar_expect_tx(&full[s], tx);
-                tma_load_3d(st, &xmap, (int)(tl * BL), c * Cfg::kc, (int)(tt * BT), &full[s]);
-                bulk_load(st + Cfg::kXBytes, btiles + (size_t)c * Cfg::kBBytes, Cfg::kBBytes, &full[s]);
+                mbar_expect_tx(&xfull[s], tx);
+                tma_load_3d(xring + (size_t)s * Cfg::kXBytes, &xmap, (int)(tl * BL), c * Cfg::kc, (int)(tt * BT),
+                            &xfull[s]);
             }
-            // every issued copy lands before the CTA may exit
-            for (int s = 0; s < S; ++s) {
-                const int64_t last = it - 1 - ((it - 1 - s) % S + S) % S;   // last issued item on stage s
-                if (last >= 0 && last < it) pipe_drain(&full[s], (uint32_t)((last / S) & 1));
+            for (int s = 0; s < SX; ++s) {   // every issued copy lands before the CTA may exit
+                const int64_t last = last_on(it, s, SX);
+                if (last >= 0) pipe_drain(&xfull[s], (uint32_t)((last / SX) & 1));
             }
         }
         __syncwarp();
-    } else if (warp == kMmaWarp) {
+    } else if (warp == Cfg::kBProducerWarp) {
+        if (lane == 0 && bres) {
+            // Q tiles of every chunk, once
+            mbar_expect_tx(&bfull[0], bregion);
+            bulk_load(bslots, btiles, bregion, &bfull[0]);
+            pipe_drain(&bfull[0], 0u);
+        } else if (lane == 0) {
+            int64_t it = 0;
+            for (; it < items; ++it) {
+                const int j = (int)(it % SA);
+                if (!pipe_wait(&aempty[j], (uint32_t)((it / SA) & 1) ^ 1u, abort_flag)) break;
+                const int c = (int)(it % nchunks);
+                mbar_expect_tx(&bfull[j], Cfg::kBBytes);
+                bulk_load(bslots + (size_t)j * Cfg::kBBytes, btiles + (size_t)c * Cfg::kBBytes, Cfg::kBBytes,
+                          &bfull[j]);
+            }
+            for (int j = 0; j < SA; ++j) {
+                const int64_t last = last_on(it, j, SA);
+                if (last >= 0) pipe_drain(&bfull[j], (uint32_t)((last / SA) & 1));
+            }
+        }
+        __syncwarp();
+    } else if (warp == Cfg::kMmaWarp) {
         if (lane == 0) {
             constexpr uint32_t idesc2 = make_idesc_e<TF32>(kTcRows, 2 * N);
             constexpr uint32_t idesc1 = make_idesc_e<TF32>(kTcRows, N);
             int64_t it = 0;
-            bool ok = true;
-            for (int64_t j = 0; j < my_tiles && ok; ++j) {
-                const int a = (int)(j & 1);
-                if (!pipe_wait(&accempty[a], (uint32_t)((j >> 1) & 1) ^ 1u, abort_flag)) break;
+            bool ok = !bres || pipe_wait(&bfull[0], 0u, abort_flag);
+            for (int64_t t = 0; t < my_tiles && ok; ++t) {
+                const int a = (int)(t & 1);
+                if (!pipe_wait(&accempty[a], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(a * Cfg::kAccCols);
                 for (int c = 0; c < nchunks; ++c, ++it) {
-                    const int s = (int)(it % S);
-                    const uint32_t ph = (uint32_t)((it / S) & 1);
-                    if (!pipe_wait(&full[s], ph, abort_flag) || !pipe_wait(&ready[s], ph, abort_flag)) {
+                    const int j = (int)(it % SA);
+                    const uint32_t ph = (uint32_t)((it / SA) & 1);
+                    if ((!bres && !pipe_wait(&bfull[j], ph, abort_flag)) || !pipe_wait(&ready[j], ph, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t ahi = tmem + acol(s), alo = ahi + 32u;
-                    const uint32_t bh = smem_u32(smem + (size_t)s * Cfg::kStageBytes + Cfg::kXBytes);
+                    const uint32_t ahi = tmem + acol(j), alo = ahi + 32u;
+                    const uint32_t bh = smem_u32(bslots + (size_t)(bres ? c : j) * Cfg::kBBytes);
 #pragma unroll
                     for (int ks = 0; ks < E::kChunk / E::kStep; ++ks) {
                         const uint64_t bd = make_desc(bh + (uint32_t)ks * 2u * kLbo);
                         mma_ts<TF32>(d, ahi + 8u * ks, bd, idesc2, (c | ks) ? 1u : 0u);   // [hi*hi | hi*lo]
                         mma_ts<TF32>(d, alo + 8u * ks, bd, idesc1, 1u);                    // += lo*hi
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit(&aempty[j]);
                 }
                 if (ok) mma_commit(&accfull[a]);
             }
             // the MMAs read tensor memory and shared memory: drain before exit
             if (it > 0) {
                 const int64_t last = it - 1;
-                pipe_drain(&empty[last % S], (uint32_t)((last / S) & 1));
+                pipe_drain(&aempty[last % SA], (uint32_t)((last / SA) & 1));
             }
         }
         __syncwarp();
-    } else if (warp >= 4) {
+    } else if (warp >= Cfg::kEpiWarps) {
         // split warps: lane quadrant q = warp % 4, K half h
-        const int q = warp & 3, h = (warp - 4) >> 2;
+        const int q = warp & 3, h = (warp - Cfg::kEpiWarps) >> 2;
         const int m = 32 * q + lane;
         const bool mok = m < rows_used;
         const int bt = mok ? m / BL : 0, bl = mok ? m - bt * BL : 0;
         const int xoff = bt * Cfg::kc * BL + bl;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        constexpr int kHalf = Cfg::kc / 2;   // K values per split thread per stage
+        constexpr int kHalf = Cfg::kc / 2;   // K values per split thread per item
         for (int64_t it = 0; it < items; ++it) {
-            const int s = (int)(it % S);
+            const int s = (int)(it % SX), j = (int)(it % SA);
             // warp-uniform outcome: tcgen05.st below is warp-collective
-            if (!__all_sync(0xffffffffu, pipe_wait(&full[s], (uint32_t)((it / S) & 1), abort_flag))) break;
-            const float* xs = reinterpret_cast<const float*>(smem + (size_t)s * Cfg::kStageBytes) + xoff;
+            const bool got = pipe_wait(&xfull[s], (uint32_t)((it / SX) & 1), abort_flag) &&
+                             pipe_wait(&aempty[j], (uint32_t)((it / SA) & 1) ^ 1u, abort_flag);
+            if (!__all_sync(0xffffffffu, got)) break;
+            // rows past the tile's last valid row split row 0's values: their
+            // accumulator rows are never stored
+            const float* xk = reinterpret_cast<const float*>(xring + (size_t)s * Cfg::kXBytes) + xoff + h * kHalf * BL;
             uint32_t hi[16], lo[16];
             if constexpr (TF32) {
 #pragma unroll
                 for (int p = 0; p < 16; ++p) {
-                    const float x = mok ? xs[(h * kHalf + p) * BL] : 0.0f;
-                    hi[p] = to_tf32(x);
-                    lo[p] = to_tf32(x - __uint_as_float(hi[p]));
+                    const uint32_t xb = __float_as_uint(xk[p * BL]);
+                    hi[p] = tf32_rna_bits(xb);
+                    lo[p] = tf32_rna_bits(__float_as_uint(__uint_as_float(xb) - __uint_as_float(hi[p])));
                 }
             } else {
 #pragma unroll
                 for (int p = 0; p < 16; ++p) {
-                    const int k = h * kHalf + 2 * p;
-                    const float x0 = mok ? xs[k * BL] : 0.0f;
-                    const float x1 = mok ? xs[(k + 1) * BL] : 0.0f;
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-                    hi[p] = pack2(h0, h1);
-                    lo[p] = pack2(__float2bfloat16_rn(x0 - __bfloat162float(h0)),
-                                  __float2bfloat16_rn(x1 - __bfloat162float(h1)));
+                    const float x0 = xk[(2 * p) * BL], x1 = xk[(2 * p + 1) * BL];
+                    const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
+                    const float2 hf = __bfloat1622float2(hh);
+                    const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                    hi[p] = *reinterpret_cast<const uint32_t*>(&hh);
+                    lo[p] = *reinterpret_cast<const uint32_t*>(&ll);
                 }
             }
-            const uint32_t col = tmem + acol(s) + (uint32_t)(h * 16);
+            // the box has been read (the values above are in registers)
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&xempty[s]);
+            const uint32_t col = tmem + acol(j) + (uint32_t)(h * 16);
             tmem_st16(lane_base + col, hi);
             tmem_st16(lane_base + col + 32u, lo);
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&ready[s]);
+            if (lane == 0) mbar_arrive(&ready[j]);
         }
     } else {
         // epilogue warps 0..3: lane quadrant = warp
@@ -732,16 +808,16 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
         const bool mok = m < rows_used;
         const int bt = mok ? m / BL : 0, bl = mok ? m - bt * BL : 0;
         const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-        for (int64_t j = 0; j < my_tiles; ++j) {
-            const int a = (int)(j & 1);
+        for (int64_t t = 0; t < my_tiles; ++t) {
+            const int a = (int)(t & 1);
             // warp-uniform outcome: tcgen05.ld below is warp-collective
-            if (!__all_sync(0xffffffffu, pipe_wait(&accfull[a], (uint32_t)((j >> 1) & 1), abort_flag))) break;
+            if (!__all_sync(0xffffffffu, pipe_wait(&accfull[a], (uint32_t)((t >> 1) & 1), abort_flag))) break;
             tc_fence_after();
-            const int64_t tile = blockIdx.x + j * (int64_t)gridDim.x;
+            const int64_t tile = blockIdx.x + t * (int64_t)gridDim.x;
             const int64_t tt = tile / ntl, tl = tile - tt * ntl;
-            const int64_t l = tl * BL + bl, t = tt * BT + bt;
-            const bool ok = mok && l < L && t < Tn;
-            float* o = out + l + L * (int64_t)R * t;
+            const int64_t l = tl * BL + bl, tq = tt * BT + bt;
+            const bool ok = mok && l < L && tq < Tn;
+            float* o = out + l + L * (int64_t)R * tq;
 #pragma unroll
             for (int c0 = 0; c0 < N; c0 += 16) {
                 float v[16], w[16];
@@ -762,7 +838,7 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
     __syncthreads();
     if (*abort_flag && tid == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_TIMEOUT);
     tc_fence_after();
-    if (warp == kMmaWarp) tmem_dealloc<512>(tmem);
+    if (warp == Cfg::kMmaWarp) tmem_dealloc<512>(tmem);
 }
 
 using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -800,7 +876,7 @@ cudaError_t launch_pipe(Handle* h, const float* in, const uint8_t* tiles, float*
     cudaError_t attr_err = cudaSuccess;
     std::call_once(attr_once, [&] {
         attr_err = cudaFuncSetAttribute(ttm_split_tc_pipe_kernel<N, TF32>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmem);
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::kSmemMax);
     });
     CPALS_CUDA_TRY(attr_err);
     const int BL = s.L >= kTcRows ? kTcRows : (int)s.L;
@@ -818,8 +894,12 @@ cudaError_t launch_pipe(Handle* h, const float* in, const uint8_t* tiles, float*
     const int64_t ntl = (s.L + BL - 1) / BL;
     const int64_t ntiles = ntl * ((s.T + BT - 1) / BT);
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-    ttm_split_tc_pipe_kernel<N, TF32><<<grid, Cfg::kThreads, Cfg::kSmem, h->stream>>>(
-        map, tiles, out, s.L, s.T, R, BL, BT, ntl, ntiles, nchunks, h->d_status);
+    const bool bres = (uint64_t)nchunks * Cfg::kBBytes <= Cfg::kBResident;
+    const uint32_t bregion = bres ? (uint32_t)nchunks * Cfg::kBBytes : (uint32_t)Cfg::kASlots * Cfg::kBBytes;
+    const int SX = Cfg::x_stages(bregion);
+    const uint32_t smem = (uint32_t)SX * Cfg::kXBytes + bregion + 1024 + 512;
+    ttm_split_tc_pipe_kernel<N, TF32><<<grid, Cfg::kThreads, smem, h->stream>>>(
+        map, tiles, out, s.L, s.T, R, BL, BT, ntl, ntiles, nchunks, SX, bres ? 1 : 0, h->d_status);
     h->launches++;
     return cudaGetLastError();
 }

@@ -307,10 +307,12 @@ def test_full_size_sweep_c2(cuda_lib):
 # product of the dims before the contracted mode) is a multiple of 4: here
 # L = 40, 64 (row tiles of several t slices), 300, 46656, 1296 (ragged
 # 128-row tiles, more tiles than SMs), 2400 with K = 150 (several ragged
-# K-chunks at R = 48), and the increasing dims (16, 20, 24, 28) (every mode).
+# K-chunks at R = 48), the increasing dims (16, 20, 24, 28) (every mode), and
+# L = 4096 with K = 300 at R = 64, whose Q tiles (80 KB in bf16, 160 KB in
+# tf32) stream through the operand slots instead of staying resident.
 TC_SHAPES = [((40, 30, 20), 16), ((300, 20), 16), ((20, 18, 17, 16), 16), ((70, 45, 33), 20), ((129, 64, 40), 32),
              ((64, 48, 40), 32), ((36, 36, 36, 36), 16), ((66, 65, 64), 64), ((48, 50, 150), 48),
-             ((16, 20, 24, 28), 16)]
+             ((16, 20, 24, 28), 16), ((64, 64, 300), 64)]
 # relative error per split product: ~2^-16 with bf16 parts, ~2^-21 with tf32 parts;
 # over a contraction of length K the relative Frobenius error stays below
 # 2 * u * sqrt(K_max) (K_max = the largest contracted dim)
