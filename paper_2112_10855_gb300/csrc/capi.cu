@@ -265,7 +265,9 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
          dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
          dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
          dalloc(h, &h->d_fit_count, 1) == cudaSuccess;
-    h->qr_ws_elems = std::max<int64_t>(4 * big * R + 64 * R * R, 4096);
+    // TSQR: leaf Q (m x R), stacked leaf R factors and their Q (2 m x R at most), the
+    // tree levels above (4 m x R at most in total)
+    h->qr_ws_elems = std::max<int64_t>(8 * big * R + 64 * R * R, 4096);
     ok = ok && dalloc(h, &h->qr_ws, h->qr_ws_elems) == cudaSuccess;
     if (ok) {
         int lo = 0, hi = 0;

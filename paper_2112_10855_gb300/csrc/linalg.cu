@@ -161,6 +161,156 @@ __global__ void tsqr_combine_kernel(const double* __restrict__ Qi, int64_t m, in
     }
 }
 
+// QR of pairs of stacked upper-triangular n x n blocks (the TSQR tree above
+// the leaves).  CTA b takes triangles 2b and 2b+1 of the K stacked in A (rows
+// [2bn, 2bn+2n)); when K is odd the last CTA's second triangle is zero.  The
+// Householder reflector of column j has its unit entry in row j of the upper
+// block and its other non-zeros in rows 0..j of the lower block (the rest of
+// the column is already zero), and applying it keeps both blocks upper
+// triangular, so a pair costs about (2/3) n^3 flops for R and as much for the
+// explicit Q, against 8 n^3 each for a dense 2n x n Householder QR.  Same
+// reflector form and sign convention as hh_qr_blocks_kernel.  Output: Q of
+// the pair (2n x n) in rows [2bn, 2bn+2n) of Qout, R in rows [bn, bn+n) of Rout.
+//
+// Thread (c, g) = (tid % 64, tid / 64) owns column c and the rows i = g mod 4
+// of every update, so each FP64 instruction works on 32 columns at once; the
+// four partial dot products of a column are added in a fixed order.
+constexpr int kTriThreads = 256;
+
+__global__ void __launch_bounds__(kTriThreads) hh_qr_tri_kernel(
+    const double* __restrict__ A, int64_t lda, int K, int n, double* __restrict__ Qout, int64_t ldq,
+    double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    extern __shared__ double sm[];
+    const int ld = n + 1;             // odd leading dimension: lanes on consecutive columns hit distinct banks
+    double* U = sm;                   // upper block
+    double* Lo = U + n * ld;          // lower block; rows 0..j of column j: reflector j
+    double* Qt = Lo + n * ld;         // explicit Q, upper half
+    double* Qb = Qt + n * ld;         // explicit Q, lower half
+    double* tau = Qb + n * ld;        // n
+    double* part = tau + n;           // 4 x 64 partial sums
+    double* sv = part + 256;          // 64
+    double* red = sv + 64;            // 2
+    const int b = blockIdx.x;
+    const bool second = 2 * b + 1 < K;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c = tid & 63, g = tid >> 6;
+    const double* A1 = A + (int64_t)2 * b * n;
+    const double* A2 = A1 + n;
+    for (int e = tid; e < n * n; e += kTriThreads) {
+        const int j = e / n, i = e - j * n;
+        U[i + ld * j] = (i <= j) ? A1[i + lda * j] : 0.0;
+        Lo[i + ld * j] = (second && i <= j) ? A2[i + lda * j] : 0.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        if (warp == 0) {
+            double s = 0.0;
+            for (int i = lane; i <= j; i += 32) s = fma(Lo[i + ld * j], Lo[i + ld * j], s);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double alpha = U[j + ld * j];
+                double t = 0.0, scale = 0.0, beta = alpha;
+                if (s > 0.0) {
+                    const double nrm = sqrt(fma(alpha, alpha, s));
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    const double d = beta - alpha;
+                    const double r = 1.0 / (beta * d);
+                    t = d * d * r;
+                    scale = -beta * r;
+                }
+                tau[j] = t;
+                red[0] = scale;
+                U[j + ld * j] = beta;
+            }
+        }
+        __syncthreads();
+        const double tj = tau[j];
+        if (tj == 0.0) continue;   // uniform: nothing below the diagonal to eliminate
+        if (tid <= j) Lo[tid + ld * j] *= red[0];
+        __syncthreads();
+        const bool col = c > j && c < n;
+        if (col) {
+            double p = 0.0;
+            for (int i = g; i <= j; i += 4) p = fma(Lo[i + ld * j], Lo[i + ld * c], p);
+            part[g * 64 + c] = p;
+        }
+        __syncthreads();
+        if (col && g == 0) {
+            const double sc = (((part[c] + part[64 + c]) + part[128 + c]) + part[192 + c] + U[j + ld * c]) * tj;
+            sv[c] = sc;
+            U[j + ld * c] -= sc;
+        }
+        __syncthreads();
+        if (col) {
+            const double sc = sv[c];
+            for (int i = g; i <= j; i += 4) Lo[i + ld * c] = fma(-sc, Lo[i + ld * j], Lo[i + ld * c]);
+        }
+        __syncthreads();
+    }
+    // explicit Q = H_0 ... H_{n-1} [I; 0], backward accumulation (H_j touches columns >= j)
+    for (int e = tid; e < n * n; e += kTriThreads) {
+        const int j = e / n, i = e - j * n;
+        Qt[i + ld * j] = (i == j) ? 1.0 : 0.0;
+        Qb[i + ld * j] = 0.0;
+    }
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        if (tj == 0.0) continue;
+        const bool col = c >= j && c < n;
+        if (col) {
+            double p = 0.0;
+            for (int i = g; i <= j; i += 4) p = fma(Lo[i + ld * j], Qb[i + ld * c], p);
+            part[g * 64 + c] = p;
+        }
+        __syncthreads();
+        if (col && g == 0) {
+            const double sc = (((part[c] + part[64 + c]) + part[128 + c]) + part[192 + c] + Qt[j + ld * c]) * tj;
+            sv[c] = sc;
+            Qt[j + ld * c] -= sc;
+        }
+        __syncthreads();
+        if (col) {
+            const double sc = sv[c];
+            for (int i = g; i <= j; i += 4) Qb[i + ld * c] = fma(-sc, Lo[i + ld * j], Qb[i + ld * c]);
+        }
+        __syncthreads();
+    }
+    double* Q1 = Qout + (int64_t)2 * b * n;
+    for (int e = tid; e < n * n; e += kTriThreads) {
+        const int j = e / n, i = e - j * n;
+        const double sgn = (U[j + ld * j] < 0.0) ? -1.0 : 1.0;
+        Q1[i + ldq * j] = sgn * Qt[i + ld * j];
+        Q1[n + i + ldq * j] = sgn * Qb[i + ld * j];
+        double v = 0.0;
+        if (i <= j) v = ((U[i + ld * i] < 0.0) ? -1.0 : 1.0) * U[i + ld * j];
+        Rout[((int64_t)b * n + i) + ldr * j] = v;
+    }
+}
+
+// Qout(r, :) = Qi(r, :) * Qt(p n : p n + n, :) for the rows r < rows of pair
+// p = r / (2n) (the TSQR tree's combine of a level with the level above).
+__global__ void tri_combine_kernel(const double* __restrict__ Qi, int64_t ldqi, int64_t rows, int n,
+                                   const double* __restrict__ Qt, int64_t ldt, double* __restrict__ Qout,
+                                   int64_t ldo, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t total = rows * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / rows, r = e - c * rows;
+        const int64_t p = r / (2 * n);
+        const double* t = Qt + p * n + ldt * c;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s = fma(Qi[r + ldqi * k], t[k], s);
+        Qout[r + ldo * c] = s;
+    }
+}
+
+inline size_t tri_smem_bytes(int n) { return sizeof(double) * ((size_t)4 * n * (n + 1) + n + 256 + 64 + 2); }
+
 // W and Q (mb x n each), tau (n) and 32 scratch values
 inline size_t qr_smem_bytes(int64_t mb, int n)
 {
@@ -248,79 +398,123 @@ __global__ void trsm_qr_kernel(const double* __restrict__ W, const double* __res
 
 // One-sided Jacobi SVD of R0 (Hestenes), then T = U pinv(Sigma) V^T keeping
 // sigma_j > rtol * sigma_max.  Pairs are visited in round-robin order so that
-// the R/2 rotations of a round are independent (one warp per pair).
-__global__ void __launch_bounds__(256) jacobi_pinv_kernel(const double* __restrict__ R0, int R, double rtol,
-                                                          double* __restrict__ T, const int* __restrict__ status)
+// the R/2 rotations of a round are independent.  Lane l of every warp works
+// on pair l, warp w on rows [w RW, (w+1) RW): the three dot products of a
+// pair are summed over the warps in a fixed order, warp 0 forms all rotations
+// of the round at once, and every warp rotates its rows of B and V.  A pair is
+// rotated while the cosine of the angle between its columns exceeds R * eps
+// (the rounding level of their length-R dot product); a sweep with no
+// rotation ends the iteration.
+constexpr int kJacobiWarps = 8;
+constexpr int kJacobiThreads = 32 * kJacobiWarps;
+
+__host__ __device__ constexpr size_t jacobi_smem_doubles()
+{
+    return (size_t)2 * kMaxRank * (kMaxRank + 1) + (size_t)kJacobiWarps * 32 * 3 + 32 * 3 + 2 * kMaxRank;
+}
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_pinv_kernel(const double* __restrict__ R0, int R,
+                                                                    double rtol, double* __restrict__ T,
+                                                                    const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     extern __shared__ double jsm[];
-    double* B = jsm;                          // R x Rp, leading dimension R
-    double* V = jsm + kMaxRank * kMaxRank;    // R x Rp
-    double* sig = V + kMaxRank * kMaxRank;    // R
+    const int ld = R + 1;                     // odd: lanes on different columns hit different banks
+    double* B = jsm;                          // R x Rp
+    double* V = B + (size_t)kMaxRank * (kMaxRank + 1);
+    double* part = V + (size_t)kMaxRank * (kMaxRank + 1);   // [warp][pair][3]
+    double* rot = part + kJacobiWarps * 32 * 3;             // [pair][c, s, flag]
+    double* sig = rot + 32 * 3;                             // R
+    double* isq = sig + kMaxRank;                           // R: 1 / sigma_j^2 or 0 (truncated)
     __shared__ int rotated;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Rp = (R + 1) & ~1;   // padded to even; column R (if any) is a zero dummy
-    for (int e = tid; e < Rp * R; e += blockDim.x) {
+    const int np = Rp / 2;
+    const int RW = (R + kJacobiWarps - 1) / kJacobiWarps;
+    const int i0 = warp * RW, i1 = min(R, i0 + RW);
+    const double tol = (double)R * kEps;
+    for (int e = tid; e < Rp * R; e += kJacobiThreads) {
         const int j = e / R, i = e - j * R;
-        B[i + R * j] = (j < R) ? R0[i + R * j] : 0.0;
-    }
-    for (int e = tid; e < Rp * Rp; e += blockDim.x) {
-        const int j = e / Rp, i = e - j * Rp;
-        if (i < R && j < Rp) V[i + R * j] = (i == j) ? 1.0 : 0.0;
+        B[i + ld * j] = (j < R) ? R0[i + R * j] : 0.0;
+        V[i + ld * j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
     for (int sweep = 0; sweep < 80; ++sweep) {
         if (tid == 0) rotated = 0;
-        __syncthreads();
         for (int round = 0; round < Rp - 1; ++round) {
-            for (int pi = warp; pi < Rp / 2; pi += nwarps) {
-                // round-robin pairing: position 0 fixed, others rotate
-                int a = (pi == 0) ? 0 : 1 + (pi - 1 + round) % (Rp - 1);
-                int b = 1 + (Rp - 2 - pi + round) % (Rp - 1);
-                int p = min(a, b), q = max(a, b);
-                if (q >= R) continue;   // dummy column
+            // round-robin pairing: position 0 fixed, others rotate
+            const int pi = lane;
+            int p = 0, q = 0;
+            if (pi < np) {
+                const int a = (pi == 0) ? 0 : 1 + (pi - 1 + round) % (Rp - 1);
+                const int b = 1 + (Rp - 2 - pi + round) % (Rp - 1);
+                p = min(a, b);
+                q = max(a, b);
+            }
+            const bool live = pi < np && q < R;   // q == R: the dummy column
+            if (live) {
                 double sa = 0.0, sb = 0.0, sg = 0.0;
-                for (int i = lane; i < R; i += 32) {
-                    const double bp = B[i + R * p], bq = B[i + R * q];
+                for (int i = i0; i < i1; ++i) {
+                    const double bp = B[i + ld * p], bq = B[i + ld * q];
                     sa = fma(bp, bp, sa);
                     sb = fma(bq, bq, sb);
                     sg = fma(bp, bq, sg);
                 }
-                sa = warp_sum(sa); sb = warp_sum(sb); sg = warp_sum(sg);
-                if (sg == 0.0 || fabs(sg) <= kEps * sqrt(sa * sb)) continue;
-                const double zeta = (sb - sa) / (2.0 * sg);
-                const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                for (int i = lane; i < R; i += 32) {
-                    const double bp = B[i + R * p], bq = B[i + R * q];
-                    B[i + R * p] = c * bp - s * bq;
-                    B[i + R * q] = s * bp + c * bq;
-                    const double vp = V[i + R * p], vq = V[i + R * q];
-                    V[i + R * p] = c * vp - s * vq;
-                    V[i + R * q] = s * vp + c * vq;
+                double* pp = part + (warp * 32 + pi) * 3;
+                pp[0] = sa; pp[1] = sb; pp[2] = sg;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                double c = 1.0, sn = 0.0, flag = 0.0;
+                if (live) {
+                    double sa = 0.0, sb = 0.0, sg = 0.0;
+                    for (int w = 0; w < kJacobiWarps; ++w) {
+                        const double* pp = part + (w * 32 + pi) * 3;
+                        if (w * RW < R) { sa += pp[0]; sb += pp[1]; sg += pp[2]; }
+                    }
+                    if (sg != 0.0 && fabs(sg) > tol * sqrt(sa * sb)) {
+                        const double zeta = (sb - sa) / (2.0 * sg);
+                        const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        sn = c * t;
+                        flag = 1.0;
+                    }
                 }
-                if (lane == 0) rotated = 1;
+                if (pi < 32) { rot[3 * pi] = c; rot[3 * pi + 1] = sn; rot[3 * pi + 2] = flag; }
+                if (__any_sync(0xffffffffu, flag != 0.0) && lane == 0) rotated = 1;
+            }
+            __syncthreads();
+            if (live && rot[3 * pi + 2] != 0.0) {
+                const double c = rot[3 * pi], sn = rot[3 * pi + 1];
+                for (int i = i0; i < i1; ++i) {
+                    const double bp = B[i + ld * p], bq = B[i + ld * q];
+                    B[i + ld * p] = c * bp - sn * bq;
+                    B[i + ld * q] = sn * bp + c * bq;
+                    const double vp = V[i + ld * p], vq = V[i + ld * q];
+                    V[i + ld * p] = c * vp - sn * vq;
+                    V[i + ld * q] = sn * vp + c * vq;
+                }
             }
             __syncthreads();
         }
-        const int any = rotated;
-        __syncthreads();
-        if (!any) break;
+        if (!rotated) break;   // uniform: read after the round's last barrier
+        __syncthreads();       // nobody clears `rotated` before everyone has read it
     }
-    for (int j = warp; j < R; j += nwarps) {
+    for (int j = tid; j < R; j += kJacobiThreads) {
         double s = 0.0;
-        for (int i = lane; i < R; i += 32) s = fma(B[i + R * j], B[i + R * j], s);
-        s = warp_sum(s);
-        if (lane == 0) sig[j] = sqrt(s);
+        for (int i = 0; i < R; ++i) s = fma(B[i + ld * j], B[i + ld * j], s);
+        sig[j] = sqrt(s);
     }
     __syncthreads();
     double smax = 0.0;
     for (int j = 0; j < R; ++j) smax = fmax(smax, sig[j]);
-    for (int e = tid; e < R * R; e += blockDim.x) {
+    for (int j = tid; j < R; j += kJacobiThreads)
+        isq[j] = (sig[j] > rtol * smax && sig[j] > 0.0) ? 1.0 / (sig[j] * sig[j]) : 0.0;
+    __syncthreads();
+    for (int e = tid; e < R * R; e += kJacobiThreads) {
         const int bcol = e / R, a = e - bcol * R;   // T(a, bcol) = sum_j B(a,j) V(bcol,j) / sig_j^2
         double s = 0.0;
-        for (int j = 0; j < R; ++j)
-            if (sig[j] > rtol * smax && sig[j] > 0.0) s = fma(B[a + R * j] / (sig[j] * sig[j]), V[bcol + R * j], s);
+        for (int j = 0; j < R; ++j) s = fma(B[a + ld * j] * isq[j], V[bcol + ld * j], s);
         T[a + R * bcol] = s;
     }
 }
@@ -526,20 +720,59 @@ inline unsigned grid_for(int64_t n, int threads, int num_sms)
 // A leaf QR is latency-bound (n sequential reflector steps), so a matrix that
 // fits one CTA's shared memory is factored by a single leaf; taller ones are
 // split into blocks of max(2n, 32, m / #SMs) rows.
+// Q (K n x n) and R (n x n) of K >= 2 stacked upper-triangular blocks, by a
+// binary tree of pair QRs.
+cudaError_t tsqr_tri(Handle* h, const double* Rs, int K, int n, double* Q, double* R, double* ws, int64_t ws_elems)
+{
+    const int P = (K + 1) / 2;
+    const size_t smem = tri_smem_bytes(n);
+    if (P == 1) {   // K == 2: the pair's Q is the result
+        hh_qr_tri_kernel<<<1, kTriThreads, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Q, (int64_t)K * n, R, n,
+                                                            h->d_status);
+        h->launches++;
+        return cudaGetLastError();
+    }
+    const int64_t nn = (int64_t)n * n;
+    double* Qi = ws;                        // 2P n x n
+    double* Rs2 = Qi + 2 * P * nn;          // P n x n
+    double* Qt = Rs2 + P * nn;              // P n x n
+    const int64_t used = 4 * P * nn;
+    if (used > ws_elems) return cudaErrorInvalidValue;
+    hh_qr_tri_kernel<<<P, kTriThreads, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Qi, 2 * (int64_t)P * n, Rs2,
+                                                         (int64_t)P * n, h->d_status);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    CPALS_CUDA_TRY(tsqr_tri(h, Rs2, P, n, Qt, R, ws + used, ws_elems - used));
+    const int64_t rows = (int64_t)K * n;
+    tri_combine_kernel<<<grid_for(rows * n, 256, h->num_sms), 256, 0, h->stream>>>(
+        Qi, 2 * (int64_t)P * n, rows, n, Qt, (int64_t)P * n, Q, rows, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+// Tall-skinny QR: one CTA when the matrix is small (about 1 MFLOP or less),
+// else dense Householder leaves of at least n rows spread over the SMs, the
+// tree of triangle pairs, and one combine back to the leaves.
 cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, double* ws, int64_t ws_elems)
 {
-    if (qr_leaf_fits(m, n)) {
+    if (qr_leaf_fits(m, n) && m * n * n <= ((int64_t)1 << 18)) {
         const size_t smem = qr_smem_bytes((int)m, n);
         hh_qr_blocks_kernel<<<1, kQrThreads, smem, h->stream>>>(A, m, m, n, 1, Q, m, R, n, h->d_status);
         h->launches++;
         return cudaGetLastError();
     }
-    const int64_t leaf_rows = std::max<int64_t>({2 * (int64_t)n, 32, (m + h->num_sms - 1) / h->num_sms});
+    const int64_t leaf_rows = std::max<int64_t>({(int64_t)n, 32, (m + h->num_sms - 1) / h->num_sms});
     int64_t nb = (m + leaf_rows - 1) / leaf_rows;
     // each block must keep >= n rows: balanced blocks have floor(m/nb) rows
     while (nb > 1 && m / nb < n) --nb;
     const int64_t mbmax = (m + nb - 1) / nb;
     if (!qr_leaf_fits(mbmax, n)) return cudaErrorInvalidValue;
+    if (nb == 1) {
+        hh_qr_blocks_kernel<<<1, kQrThreads, qr_smem_bytes((int)m, n), h->stream>>>(A, m, m, n, 1, Q, m, R, n,
+                                                                                      h->d_status);
+        h->launches++;
+        return cudaGetLastError();
+    }
     double* Qi = ws;                        // m x n
     double* Rs = Qi + m * n;                // (nb*n) x n
     double* Qt = Rs + nb * n * n;           // (nb*n) x n
@@ -550,7 +783,7 @@ cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double
         A, m, m, n, (int)nb, Qi, m, Rs, nb * n, h->d_status);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
-    CPALS_CUDA_TRY(tsqr(h, Rs, nb * n, n, Qt, R, rest, ws_elems - used));
+    CPALS_CUDA_TRY(tsqr_tri(h, Rs, (int)nb, n, Qt, R, rest, ws_elems - used));
     tsqr_combine_kernel<<<grid_for(m * n, 256, h->num_sms), 256, 0, h->stream>>>(Qi, m, n, (int)nb, Qt, nb * n, Q,
                                                                                   h->d_status);
     h->launches++;
@@ -565,6 +798,8 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
     if (!attr_set) {
         CPALS_CUDA_TRY(cudaFuncSetAttribute(hh_qr_blocks_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)kQrSmemMaxBytes));
+        CPALS_CUDA_TRY(cudaFuncSetAttribute(hh_qr_tri_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)tri_smem_bytes(kMaxRank)));
         attr_set = true;
     }
     return tsqr(h, A, m, n, Q, R, h->qr_ws, h->qr_ws_elems);
@@ -628,14 +863,14 @@ cudaError_t solve_qr(Handle* h, int64_t In)
 cudaError_t solve_svd(Handle* h, int64_t In, double rtol)
 {
     if (!(rtol > 0.0)) rtol = (double)h->R * kEps;
-    constexpr size_t smem = sizeof(double) * (2 * kMaxRank * kMaxRank + kMaxRank);
+    constexpr size_t smem = sizeof(double) * jacobi_smem_doubles();
     static bool attr_set = false;
     if (!attr_set) {
         CPALS_CUDA_TRY(cudaFuncSetAttribute(jacobi_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
         attr_set = true;
     }
-    jacobi_pinv_kernel<<<1, 256, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status);
+    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
     return gemm_rows(h, h->W, In, h->R, h->T, h->R, h->Ahat);
@@ -661,14 +896,14 @@ cudaError_t solve_normal_pinv(Handle* h, int n, double rtol)
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
     // S is symmetric, so pinv(S) = pinv(S^T): the same operator as the SVD solve with R0 -> S
-    constexpr size_t smem = sizeof(double) * (2 * kMaxRank * kMaxRank + kMaxRank);
+    constexpr size_t smem = sizeof(double) * jacobi_smem_doubles();
     static bool attr_set = false;
     if (!attr_set) {
         CPALS_CUDA_TRY(cudaFuncSetAttribute(jacobi_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
         attr_set = true;
     }
-    jacobi_pinv_kernel<<<1, 256, smem, h->stream>>>(h->S, h->R, rtol, h->T, h->d_status);
+    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->S, h->R, rtol, h->T, h->d_status);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
     return gemm_rows(h, h->M, h->dims[n], h->R, h->T, h->R, h->Ahat);

@@ -181,6 +181,12 @@ def workload_c3(seed=2112, init_seed=10855, size=120, rank=20):
                    noise=0.01)
 
 
+def workload_c5a(seed=2112, init_seed=10855, size=1000, rank=64, noise=1e-3):
+    """3-way size^3, rank 64, congruence 0.999, weights logspace 1..1e-6, 0.1% noise."""
+    return planted((size,) * 3, rank, seed=seed, init_seed=init_seed, congruence=0.999,
+                   weights=logspace_weights(rank, 1e-6), noise=noise)
+
+
 def batch_shapes(count=512, seed=2112, lo=16, hi=128, rlo=2, rhi=16, order=3):
     """Per-problem dims ~ U{lo..hi} and ranks ~ U{rlo..rhi} for the batched workload."""
     dims = randint(seed, 11, count * order, lo, hi).reshape(count, order)

@@ -121,8 +121,11 @@ OSOLVE = {"qr": oracle.QR, "svd": oracle.SVD, "normal": oracle.NORMAL, "normal_p
 
 
 @pytest.mark.parametrize("solve", ["qr", "svd", "normal", "normal_pinv"])
-@pytest.mark.parametrize("dims,R", [((37, 29, 41), 5), ((12, 11, 10, 9), 3), ((60, 50, 40), 10)])
+@pytest.mark.parametrize("dims,R", [((37, 29, 41), 5), ((12, 11, 10, 9), 3), ((60, 50, 40), 10),
+                                    ((70, 66, 64), 64)])
 def test_mode_update_matches_oracle(cuda_lib, solve, dims, R):
+    # rank 64: V_n (4096 x 64) goes through the TSQR tree of triangle pairs,
+    # the SVD and pseudo-inverse solves through the 64 x 64 Jacobi SVD
     X, A = gaussian_problem(dims, R, seed=11)
     osolve = OSOLVE[solve]
     for n in range(len(dims)):
