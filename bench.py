@@ -53,10 +53,11 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the SVD/NORMAL/FP32 side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--workload", choices=["c2", "c3", "c5a", "c5b", "c4"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c5a", "c5b", "c4", "sine"], default="c2",
                     help="c2: the headline 400^3 rank-10 FP64 workload; c3: 4-way 120^4 rank 20, c5a: 3-way "
                          "1000^3 rank 64 (SVD solve) and c5b: 5-way 40^5 rank 8, each comparing FP64, FP32, 3xBF16 "
-                         "and 3xTF32 passes over X; c4: 512 independent small problems, batched")
+                         "and 3xTF32 passes over X; c4: 512 independent small problems, batched; sine: sine-of-sums "
+                         "tensors in Kruskal form (Sec. 4.3)")
     ap.add_argument("--fit-sweeps", type=int, default=300,
                     help="at most this many sweeps (stop at |fit change| < 1e-10) for the equal-fit comparison")
     return ap.parse_args()
@@ -449,6 +450,76 @@ def run_batch(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_sine(args, world, rank):
+    """Sec. 4.3 sine of sums, given in Kruskal form (Sec. 3.3.2): sweeps/s of
+    the Kruskal-input path against the dense path on the same tensor where the
+    dense tensor fits, the order-10 case that only the Kruskal path can hold,
+    and the direct relative error after 40 sweeps of CP-ALS-QR, CP-ALS-QR-SVD,
+    CP-ALS and CP-ALS-PINV from the same start (the comparison of Sec. 4.3)."""
+    import torch
+    from paper_2112_10855_gb300 import _build, cpals, inputs
+    torch.cuda.set_device(0)
+    _build.build()
+    cpals.load()
+    rng = np.random.default_rng(2112 + rank)
+
+    def timed(h, solve, steps, warmup):
+        h.iterate(warmup, solve=solve, svd_rtol=1e-12, want_fits=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.iterate(steps, solve=solve, svd_rtol=1e-12, want_fits=False)
+        e1.record()
+        torch.cuda.synchronize()
+        return steps / (e0.elapsed_time(e1) * 1e-3)
+
+    cases = []
+    for N, n, rep, dense in [(4, 128, "expanded", True), (5, 64, "expanded", True), (10, 12, "rank_n", False)]:
+        mu, V = (inputs.sine_of_sums_expanded(N, n) if rep == "expanded" else inputs.sine_of_sums_rank_n(N, n))
+        dims, R = (n,) * N, N
+        A = [np.asfortranarray(rng.standard_normal((n, R))) for _ in range(N)]
+        hk = cpals.CPALS(dims, R, kruskal_rank=len(mu))
+        hk.set_tensor_kruskal(mu, V)
+        hk.set_factors(A)
+        entry = {"N": N, "n": n, "input": f"{rep}, Kruskal rank {len(mu)}", "rank": R,
+                 "kruskal_qr_iters_per_s": timed(hk, "qr", args.steps, args.warmup)}
+        del hk
+        if dense:
+            X = torch.from_numpy(inputs.cp_full(dims, V, mu)).cuda()
+            hd = cpals.CPALS(dims, R)
+            hd.set_tensor(X)
+            hd.set_factors(A)
+            entry["dense_qr_iters_per_s"] = timed(hd, "qr", max(2, args.steps // 10), args.warmup)
+            entry["kruskal_speedup_vs_dense"] = entry["kruskal_qr_iters_per_s"] / entry["dense_qr_iters_per_s"]
+            del hd, X
+        cases.append(entry)
+    # accuracy after 40 sweeps, Sec. 4.3's 4-way case at n = 64
+    N, n = 4, 64
+    mu, V = inputs.sine_of_sums_expanded(N, n)
+    dims = (n,) * N
+    A = [np.asfortranarray(rng.standard_normal((n, N))) for _ in range(N)]
+    errs = {}
+    for solve in ["qr", "svd", "normal", "normal_pinv"]:
+        h = cpals.CPALS(dims, N, kruskal_rank=len(mu))
+        h.set_tensor_kruskal(mu, V)
+        h.set_factors(A)
+        h.iterate(40, solve=solve, svd_rtol=1e-12, want_fits=False)
+        errs[solve] = 1.0 - h.fit(direct=True)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": cases[-1]["kruskal_qr_iters_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "sine of sums sin(x_1 + ... + x_N) on the grid 2 pi k / n, given in Kruskal "
+                                   "form; value: N = 10, n = 12, rank-10 input (Eq. sinsum_rkd), CP rank 10, "
+                                   "CP-ALS-QR"},
+            "cases": cases,
+            "relative_error_after_40_sweeps_4way_n64": errs,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -457,6 +528,9 @@ def main():
         return
     if args.workload == "c4":
         run_batch(args, world, rank)
+        return
+    if args.workload == "sine":
+        run_sine(args, world, rank)
         return
     if args.workload != "c2":
         run_mixed(args, world, rank)

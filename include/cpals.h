@@ -79,8 +79,8 @@ typedef enum { CPALS_MEM_DEVICE = 0, CPALS_MEM_HOST = 1 } cpals_mem;
 typedef enum { CPALS_ELEM_F64 = 0, CPALS_ELEM_F32 = 1 } cpals_elem;
 
 /* Create a rank-`rank` CP-ALS problem for an N-way tensor of the given dims
- * (Sec. 3.1).  Requires 2 <= N <= 8, 1 <= rank <= 64 and rank <= dims[m]
- * for every m.  The compact QR A_m = Q_m R_m with Q_m of size I_m x R
+ * (Sec. 3.1).  Requires 2 <= N <= 12, 1 <= rank <= 64, rank <= dims[m]
+ * for every m, and rank^N <= 2^36 (Q0 and Y_(n) are held densely).  The compact QR A_m = Q_m R_m with Q_m of size I_m x R
  * (Sec. 3.1) needs I_m >= R, and that also keeps every Z_n from being wide.
  * Allocates every device workspace buffer now (cudaMalloc), on the current
  * device.  On success, *out receives the handle.
@@ -111,6 +111,36 @@ int cpals_workspace_bytes(const cpals_handle* h, size_t* bytes);
  *    borrowed (DEVICE) or copied (HOST).
  * Also computes ||X||_F^2 in FP64 (Sec. 3.3.1: it is pre-computed once). */
 int cpals_set_tensor(cpals_handle* h, const void* X, int elem, int mem);
+
+/* Kruskal-tensor input (Sec. 3.3.2).  The data tensor is given in Kruskal
+ * form X = sum_{s<S} mu_s v_s^(1) o ... o v_s^(N) and is never formed: the
+ * Multi-TTM Y = X x_{m != n} Q_m^T is again a Kruskal tensor with factors
+ * Q_m^T V_m (m != n) and V_n, so W_n = Y_(n) Q0 is an MTTKRP of Q0 followed
+ * by a small product (Sec. 3.3.2).  Q0 itself stays in the factored form of
+ * its structured QR (Eq. kr-id), which makes a mode update O(N S R^3 +
+ * sum_m I_m R S) and allows orders and ranks whose R^{N-1} x R matrix Q0
+ * could not be stored.  The MTTKRP of the normal equations is
+ * V_n diag(mu) (*_{m != n} V_m^T A_m); ||X||^2 = mu^T (*_m V_m^T V_m) mu.
+ *
+ * cpals_create_kruskal: dims, N, rank as for cpals_create (2 <= N <= 12,
+ *   1 <= rank <= 64, rank <= dims[m]; no bound on rank^N); S = the Kruskal
+ *   rank of X, 1 <= S <= 4096.  FP64 throughout.  Allocates every buffer now.
+ *   Errors: CPALS_ERR_ARG, CPALS_ERR_NOMEM, CPALS_ERR_CUDA.
+ * The handle accepts every call below except cpals_set_tensor and
+ * cpals_ttm_first (CPALS_ERR_STATE: there is no dense tensor), with these
+ * differences: cpals_krp_qr returns R0 only (Q0 != NULL -> CPALS_ERR_ARG);
+ * cpals_multi_ttm returns Y_(n) only while I_max * R^{N-1} <= 2^24
+ * (CPALS_ERR_ARG otherwise); cpals_fit(direct = 1) evaluates both tensors
+ * entry by entry (prod(dims) entries, (S + R) N products each);
+ * CPALS_OPT_DIMTREE has no effect. */
+int cpals_create_kruskal(const int64_t* dims, int N, int rank, int S, cpals_handle** out);
+
+/* Set the Kruskal tensor of a handle from cpals_create_kruskal: N pointers
+ * V[m] (I_m x S, column-major, FP64) and the S weights mu (NULL for ones).
+ * The data is copied; ||X||^2 is computed.  Synchronises.
+ * Errors: CPALS_ERR_ARG (NULL pointers, bad mem flag), CPALS_ERR_STATE (a
+ * dense-tensor handle), CPALS_ERR_CUDA. */
+int cpals_set_tensor_kruskal(cpals_handle* h, const double* mu, const double* const* V, int mem);
 
 /* Set the factors A_m (N pointers, I_m x R, FP64) and weights lambda (R values,
  * or NULL for ones).  Alg. cp-als-qr initialisation: the compact QR
@@ -225,7 +255,7 @@ int64_t cpals_launch_count(const cpals_handle* h);
  * array of 2^21 doubles (16 MiB).  Every GPU that loads the library holds
  * that array until the process exits.
  *
- *  dims, N, rank: as for cpals_create (2 <= N <= 8, 1 <= rank <= 64,
+ *  dims, N, rank: as for cpals_create (2 <= N <= 12, 1 <= rank <= 64,
  *    rank <= every dim).
  *  mode: the kept mode n (0-based).
  *  X: device pointer to prod(dims) FP64 values (mode 0 fastest), read only.

@@ -60,6 +60,8 @@ def load(path: str | None = None):
     L.cpals_set_stream.argtypes = [_vp, _vp]
     L.cpals_workspace_bytes.argtypes = [_vp, C.POINTER(C.c_size_t)]
     L.cpals_set_tensor.argtypes = [_vp, _vp, C.c_int, C.c_int]
+    L.cpals_create_kruskal.argtypes = [i64p, C.c_int, C.c_int, C.c_int, C.POINTER(_vp)]
+    L.cpals_set_tensor_kruskal.argtypes = [_vp, _vp, C.POINTER(_vp), C.c_int]
     L.cpals_set_factors.argtypes = [_vp, C.POINTER(_vp), _vp, C.c_int]
     L.cpals_get_factors.argtypes = [_vp, C.POINTER(_vp), _vp, C.c_int]
     L.cpals_get_factor_qr.argtypes = [_vp, C.c_int, _vp, _vp, C.c_int]
@@ -136,16 +138,24 @@ def _colmajor_ok(x, rows, cols):
 class CPALS:
     """One CP-ALS(-QR) problem: cpals_create / cpals_destroy and the calls of include/cpals.h."""
 
-    def __init__(self, dims, rank, precision="f64"):
+    def __init__(self, dims, rank, precision="f64", kruskal_rank=None):
+        """kruskal_rank=S: a handle for a tensor given in Kruskal form
+        (cpals_create_kruskal, Sec. 3.3.2); set it with set_tensor_kruskal."""
         import torch  # noqa: F401  (the library shares the device and context with torch)
         L = load()
         self.dims = tuple(int(d) for d in dims)
         self.N = len(self.dims)
         self.R = int(rank)
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.S = None if kruskal_rank is None else int(kruskal_rank)
         d = (C.c_int64 * self.N)(*self.dims)
         h = _vp()
-        rc = L.cpals_create(d, self.N, self.R, self.precision, C.byref(h))
+        if self.S is None:
+            rc = L.cpals_create(d, self.N, self.R, self.precision, C.byref(h))
+        else:
+            if self.precision != PRECISIONS["f64"]:
+                raise ValueError("Kruskal input runs in FP64")
+            rc = L.cpals_create_kruskal(d, self.N, self.R, self.S, C.byref(h))
         if rc != OK:
             raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
         self._h = h
@@ -204,11 +214,12 @@ class CPALS:
         self._X = X   # a borrowed device pointer must stay alive
         _check(self._h, load().cpals_set_tensor(self._h, p, elem, mem))
 
-    def _mats_in(self, mats, rows):
+    def _mats_in(self, mats, rows, cols=None):
+        cols = self.R if cols is None else cols
         ptrs, mem = [], None
         for m, A in enumerate(mats):
-            if not _colmajor_ok(A, rows[m], self.R):
-                raise ValueError(f"matrix {m} must be a column-major float64 {rows[m]} x {self.R} array")
+            if not _colmajor_ok(A, rows[m], cols):
+                raise ValueError(f"matrix {m} must be a column-major float64 {rows[m]} x {cols} array")
             p, mm = _ptr(A)
             if mem is not None and mm != mem:
                 raise ValueError("mix of host and device matrices")
@@ -224,6 +235,16 @@ class CPALS:
             if lm != mem:
                 raise ValueError("lambda must live where the factors live")
         _check(self._h, load().cpals_set_factors(self._h, arr, lp, mem))
+
+    def set_tensor_kruskal(self, mu, V):
+        """V: N column-major FP64 I_m x S arrays (numpy or CUDA torch); mu: S weights or None."""
+        arr, mem = self._mats_in(V, self.dims, cols=self.S)
+        mp = None
+        if mu is not None:
+            mp, mm = _ptr(mu)
+            if mm != mem:
+                raise ValueError("mu must live where the factors live")
+        _check(self._h, load().cpals_set_tensor_kruskal(self._h, mp, arr, mem))
 
     def set_factor_qr(self, Q, R):
         qa, mem = self._mats_in(Q, self.dims)
@@ -256,7 +277,7 @@ class CPALS:
     # -- the hot path
     def krp_qr(self, mode, device=False):
         RN1 = self.R ** (self.N - 1)
-        Q0 = self._out(RN1, self.R, device)
+        Q0 = None if self.S is not None else self._out(RN1, self.R, device)
         R0 = self._out(self.R, self.R, device)
         _check(self._h, load().cpals_krp_qr(self._h, mode, _ptr(Q0)[0], _ptr(R0)[0],
                                             MEM_DEVICE if device else MEM_HOST))

@@ -52,6 +52,8 @@ void free_all(Handle* h)
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
     f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
+    for (int m = 0; m < cpals::kMaxN; ++m) { f(h->KV[m]); f(h->KC[m]); f(h->KE[m]); }
+    f(h->Kmu); f(h->KGV); f(h->KP); f(h->KMw[0]); f(h->KMw[1]);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -115,14 +117,29 @@ cudaError_t refresh_derived(Handle* h, int solve, int skip)
                 CPALS_CUDA_TRY(cpals::gram(h, h->A[m], h->dims[m], h->G[m]));
                 h->gram_valid[m] = true;
             }
+            if (h->kruskal && h->have_X && !h->ke_valid[m]) {
+                CPALS_CUDA_TRY(cpals::kr_refresh_e(h, m));
+                h->ke_valid[m] = true;
+            }
         } else {
             if (!h->qr_valid[m]) {
                 CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], h->dims[m], h->R, h->Q[m], h->Rf[m]));
                 h->qr_valid[m] = true;
+                h->kc_valid[m] = false;
+            }
+            if (h->kruskal && h->have_X && !h->kc_valid[m]) {
+                CPALS_CUDA_TRY(cpals::kr_refresh_c(h, m));
+                h->kc_valid[m] = true;
             }
         }
     }
     return cudaSuccess;
+}
+
+// Invalidate everything derived from the factors (after new factors or Q/R).
+void factors_changed(Handle* h)
+{
+    for (int m = 0; m < h->N; ++m) { h->kc_valid[m] = false; h->ke_valid[m] = false; }
 }
 
 // One mode update (Alg. cp-als-qr mode-loop body, or Alg. cp-als for NORMAL).
@@ -130,6 +147,37 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
 {
     CPALS_CUDA_TRY(refresh_derived(h, solve, n));
     const int64_t In = h->dims[n];
+    if (h->kruskal) {
+        // Kruskal input (Sec. 3.3.2): no pass over a dense tensor
+        if (is_normal(solve)) {
+            CPALS_CUDA_TRY(cpals::kr_mttkrp(h, n));
+            if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n));
+            else CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol));
+        } else {
+            CPALS_CUDA_TRY(cpals::krp_qr(h, n, true));
+            h->krp_mode = n;
+            CPALS_CUDA_TRY(cpals::kr_apply_q0(h, n));
+            if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
+            else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol));
+        }
+        CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
+        if (is_normal(solve)) {
+            CPALS_CUDA_TRY(cpals::gram(h, h->A[n], In, h->G[n]));
+            CPALS_CUDA_TRY(cpals::kr_refresh_e(h, n));
+            h->gram_valid[n] = true;
+            h->ke_valid[n] = true;
+            h->qr_valid[n] = false;
+            h->kc_valid[n] = false;
+        } else {
+            CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n]));
+            CPALS_CUDA_TRY(cpals::kr_refresh_c(h, n));
+            h->qr_valid[n] = true;
+            h->kc_valid[n] = true;
+            h->gram_valid[n] = false;
+            h->ke_valid[n] = false;
+        }
+        return cudaSuccess;
+    }
     if (is_normal(solve)) {
         CPALS_CUDA_TRY(cpals::mttkrp(h, n));
         if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n));
@@ -219,8 +267,15 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
     if (!out) return fail(nullptr, CPALS_ERR_ARG, "%s", "out is NULL");
     *out = nullptr;
     if (!dims) return fail(nullptr, CPALS_ERR_ARG, "%s", "dims is NULL");
-    if (N < 2 || N > cpals::kMaxN) return fail(nullptr, CPALS_ERR_ARG, "%s", "N must be in [2, 8]");
+    if (N < 2 || N > cpals::kMaxN) return fail(nullptr, CPALS_ERR_ARG, "%s", "N must be in [2, 12]");
     if (rank < 1 || rank > cpals::kMaxRank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must be in [1, 64]");
+    {
+        // the dense path holds Q0 (R^{N-1} x R) and Y_(n) (I_n x R^{N-1})
+        double rn1 = 1.0;
+        for (int m = 0; m < N - 1; ++m) rn1 *= rank;
+        if (rn1 * rank > (double)(1LL << 36))
+            return fail(nullptr, CPALS_ERR_ARG, "%s", "R^N too large for a dense tensor handle (use Kruskal input)");
+    }
     if (precision != CPALS_F64 && precision != CPALS_F32 && precision != CPALS_BF16X3 && precision != CPALS_TF32X3)
         return fail(nullptr, CPALS_ERR_ARG, "%s", "unknown precision");
     for (int m = 0; m < N; ++m)
@@ -320,6 +375,114 @@ int cpals_destroy(cpals_handle* hh)
     return CPALS_OK;
 }
 
+int cpals_create_kruskal(const int64_t* dims, int N, int rank, int S, cpals_handle** out)
+{
+    if (!out) return fail(nullptr, CPALS_ERR_ARG, "%s", "out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(nullptr, CPALS_ERR_ARG, "%s", "dims is NULL");
+    if (N < 2 || N > cpals::kMaxN) return fail(nullptr, CPALS_ERR_ARG, "%s", "N must be in [2, 12]");
+    if (rank < 1 || rank > cpals::kMaxRank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must be in [1, 64]");
+    if (S < 1 || S > 4096) return fail(nullptr, CPALS_ERR_ARG, "%s", "the Kruskal rank S must be in [1, 4096]");
+    for (int m = 0; m < N; ++m)
+        if (dims[m] < rank)
+            return fail(nullptr, CPALS_ERR_ARG, "%s",
+                        "rank must not exceed any dim (the compact QR of each I_m x R factor needs I_m >= R)");
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return fail(nullptr, CPALS_ERR_NOMEM, "%s", "host allocation failed");
+    h->N = N; h->R = rank; h->prec = CPALS_F64; h->kruskal = true; h->KS = S;
+    h->P = 1; h->RN1 = 1; h->Imax = 0;
+    double pd = 1.0, rd = 1.0;
+    for (int m = 0; m < N; ++m) {
+        h->dims[m] = dims[m];
+        pd *= (double)dims[m];
+        h->Imax = std::max(h->Imax, dims[m]);
+    }
+    for (int m = 0; m < N - 1; ++m) rd *= rank;
+    // P and R^{N-1} are only used when they fit (direct fit, Y_(n) for small cases)
+    h->P = pd < 9.0e18 ? (int64_t)pd : -1;
+    h->RN1 = rd < 9.0e18 ? (int64_t)rd : -1;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) { int rc = cuda_fail(nullptr, e, "device query"); delete h; return rc; }
+    const int R = rank;
+    const int64_t big = std::max<int64_t>(h->Imax, (int64_t)R * R);
+    const size_t R2 = (size_t)R * R, R3 = R2 * R;
+    h->scratch_elems = std::max<int64_t>({4 * big * R + 64 * R * R, 4096, (int64_t)h->num_sms * 2 * h->Imax * R});
+    h->fit_cap = 4096;
+    bool ok = true;
+    for (int m = 0; m < N && ok; ++m) {
+        ok = dalloc(h, &h->A[m], dims[m] * R) == cudaSuccess && dalloc(h, &h->Q[m], dims[m] * R) == cudaSuccess &&
+             dalloc(h, &h->Rf[m], R2) == cudaSuccess && dalloc(h, &h->G[m], R2) == cudaSuccess &&
+             dalloc(h, &h->KV[m], dims[m] * S) == cudaSuccess && dalloc(h, &h->KC[m], (size_t)R * S) == cudaSuccess &&
+             dalloc(h, &h->KE[m], (size_t)S * R) == cudaSuccess;
+    }
+    ok = ok && dalloc(h, &h->lambda, R) == cudaSuccess && dalloc(h, &h->R0, R2) == cudaSuccess &&
+         dalloc(h, &h->W, h->Imax * R) == cudaSuccess && dalloc(h, &h->Ahat, h->Imax * R) == cudaSuccess &&
+         dalloc(h, &h->M, h->Imax * R) == cudaSuccess && dalloc(h, &h->S, R2) == cudaSuccess &&
+         dalloc(h, &h->T, R2) == cudaSuccess && dalloc(h, &h->KM, R3) == cudaSuccess &&
+         dalloc(h, &h->KQ, R3) == cudaSuccess && dalloc(h, &h->KR[0], R2) == cudaSuccess &&
+         dalloc(h, &h->KR[1], R2) == cudaSuccess && dalloc(h, &h->KP, std::max(1, N - 2) * R3) == cudaSuccess &&
+         dalloc(h, &h->Kmu, S) == cudaSuccess && dalloc(h, &h->KGV, (size_t)N * S * S) == cudaSuccess &&
+         dalloc(h, &h->KMw[0], (size_t)S * R) == cudaSuccess && dalloc(h, &h->KMw[1], (size_t)S * R) == cudaSuccess &&
+         dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
+         dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
+         dalloc(h, &h->d_fit_count, 1) == cudaSuccess;
+    // Y_(n) is formed (for cpals_multi_ttm) only when it is small
+    if (ok && h->RN1 > 0 && (double)h->Imax * (double)h->RN1 <= (double)(1 << 24))
+        ok = dalloc(h, &h->Yn, h->Imax * h->RN1) == cudaSuccess;
+    h->qr_ws_elems = std::max<int64_t>(8 * big * R + 64 * R * R, 4096);
+    ok = ok && dalloc(h, &h->qr_ws, h->qr_ws_elems) == cudaSuccess;
+    if (ok) {
+        int lo = 0, hi = 0;
+        ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+             cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        free_all(h);
+        delete h;
+        cudaGetLastError();
+        return fail(nullptr, CPALS_ERR_NOMEM, "%s", "device allocation failed");
+    }
+    h->dimtree = false;
+    e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_fit_count, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->lambda, 0, sizeof(double) * R);
+    if (e != cudaSuccess) { int rc = cuda_fail(nullptr, e, "memset"); free_all(h); delete h; return rc; }
+    *out = reinterpret_cast<cpals_handle*>(h);
+    return CPALS_OK;
+}
+
+int cpals_set_tensor_kruskal(cpals_handle* hh, const double* mu, const double* const* V, int mem)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (!h->kruskal) return fail(h, CPALS_ERR_STATE, "%s", "the handle was not made by cpals_create_kruskal");
+    if (!V || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad factor pointers or mem flag");
+    for (int m = 0; m < h->N; ++m)
+        if (!V[m]) return fail(h, CPALS_ERR_ARG, "%s", "a factor pointer is NULL");
+    const int S = h->KS;
+    for (int m = 0; m < h->N; ++m)
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->KV[m], V[m], sizeof(double) * h->dims[m] * S, kind_in(mem), h->stream),
+                     "copy Kruskal factor");
+    std::vector<double> ones(S, 1.0);   // lives until the synchronisation below
+    if (mu) {
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->Kmu, mu, sizeof(double) * S, kind_in(mem), h->stream), "copy weights");
+    } else {
+        CUDA_OR_FAIL(h, cudaMemcpyAsync(h->Kmu, ones.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->stream),
+                     "copy weights");
+    }
+    CUDA_OR_FAIL(h, cpals::kr_norm2(h), "norm of X");
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->normX2_host, h->d_normX2, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+                 "norm read");
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "set_tensor sync");
+    h->have_X = true;
+    h->last_sweep_solve = -1;
+    factors_changed(h);
+    return take_status(h);
+}
+
 const char* cpals_last_error(const cpals_handle* hh)
 {
     const Handle* h = reinterpret_cast<const Handle*>(hh);
@@ -351,6 +514,7 @@ int cpals_set_tensor(cpals_handle* hh, const void* X, int elem, int mem)
         return fail(h, CPALS_ERR_ARG, "%s", "bad elem or mem flag");
     if (elem == CPALS_ELEM_F32 && h->prec == CPALS_F64)
         return fail(h, CPALS_ERR_ARG, "%s", "an FP32 tensor needs precision F32, BF16X3 or TF32X3");
+    if (h->kruskal) return fail(h, CPALS_ERR_STATE, "%s", "a Kruskal-input handle takes cpals_set_tensor_kruskal");
     h->X64 = nullptr; h->X32 = nullptr; h->have_X = false;
     if (h->prec == CPALS_F64) {
         if (mem == CPALS_MEM_DEVICE) {
@@ -426,6 +590,7 @@ int cpals_set_factors(cpals_handle* hh, const double* const* A, const double* la
     h->have_factors = true;
     h->krp_mode = -1;
     h->last_sweep_solve = -1;
+    factors_changed(h);
     return CPALS_OK;
 }
 
@@ -476,6 +641,7 @@ int cpals_set_factor_qr(cpals_handle* hh, const double* const* Q, const double* 
     if (mem == CPALS_MEM_HOST) CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "sync");
     h->have_factors = true;
     h->krp_mode = -1;
+    factors_changed(h);
     return CPALS_OK;
 }
 
@@ -485,8 +651,9 @@ int cpals_krp_qr(cpals_handle* hh, int mode, double* Q0, double* R0, int mem)
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
     if (mode < 0 || mode >= h->N || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad mode or mem flag");
     if (!h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "no factors set");
+    if (Q0 && h->kruskal) return fail(h, CPALS_ERR_ARG, "%s", "a Kruskal-input handle keeps Q0 in factored form");
     CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, mode), "refresh QR");
-    CUDA_OR_FAIL(h, cpals::krp_qr(h, mode), "KRP QR");
+    CUDA_OR_FAIL(h, cpals::krp_qr(h, mode, h->kruskal), "KRP QR");
     h->krp_mode = mode;
     if (Q0) CUDA_OR_FAIL(h, cudaMemcpyAsync(Q0, h->Q0, sizeof(double) * h->RN1 * h->R, kind_out(mem), h->stream),
                          "copy Q0");
@@ -505,8 +672,19 @@ int cpals_multi_ttm(cpals_handle* hh, int mode, double* Y, double* W, int mem)
     if (!h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "no factors set");
     if (W && h->krp_mode != mode) return fail(h, CPALS_ERR_STATE, "%s", "W needs cpals_krp_qr on this mode first");
     CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, mode), "refresh QR");
-    CUDA_OR_FAIL(h, cpals::multi_ttm(h, mode, h->Q), "Multi-TTM");
     const int64_t In = h->dims[mode];
+    if (h->kruskal) {
+        if (Y && !h->Yn) return fail(h, CPALS_ERR_ARG, "%s", "Y_(n) of this size is not formed for Kruskal input");
+        if (Y) CUDA_OR_FAIL(h, cpals::kr_unfold(h, mode, h->Yn), "Kruskal Y");
+        if (W) CUDA_OR_FAIL(h, cpals::kr_apply_q0(h, mode), "Kruskal W");
+        if (Y) CUDA_OR_FAIL(h, cudaMemcpyAsync(Y, h->Yn, sizeof(double) * In * h->RN1, kind_out(mem), h->stream),
+                            "copy Y");
+        if (W) CUDA_OR_FAIL(h, cudaMemcpyAsync(W, h->W, sizeof(double) * In * h->R, kind_out(mem), h->stream),
+                            "copy W");
+        if (mem == CPALS_MEM_HOST) return take_status(h);
+        return CPALS_OK;
+    }
+    CUDA_OR_FAIL(h, cpals::multi_ttm(h, mode, h->Q), "Multi-TTM");
     if (W) CUDA_OR_FAIL(h, cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W), "apply Q0");
     if (Y) CUDA_OR_FAIL(h, cudaMemcpyAsync(Y, h->Yn, sizeof(double) * In * h->RN1, kind_out(mem), h->stream), "copy Y");
     if (W) CUDA_OR_FAIL(h, cudaMemcpyAsync(W, h->W, sizeof(double) * In * h->R, kind_out(mem), h->stream), "copy W");
@@ -520,6 +698,7 @@ int cpals_ttm_first(cpals_handle* hh, int mode)
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
     if (mode < 0 || mode >= h->N) return fail(h, CPALS_ERR_ARG, "%s", "bad mode");
     if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
+    if (h->kruskal) return fail(h, CPALS_ERR_STATE, "%s", "no pass over a dense tensor with Kruskal input");
     CUDA_OR_FAIL(h, refresh_derived(h, CPALS_SOLVE_QR, mode), "refresh QR");
     CUDA_OR_FAIL(h, cpals::ttm_first(h, mode), "first TTM");
     return CPALS_OK;
@@ -531,7 +710,16 @@ int cpals_mttkrp(cpals_handle* hh, int mode, double* M, int mem)
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
     if (mode < 0 || mode >= h->N || !mem_ok(mem)) return fail(h, CPALS_ERR_ARG, "%s", "bad mode or mem flag");
     if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
-    CUDA_OR_FAIL(h, cpals::mttkrp(h, mode), "MTTKRP");
+    if (h->kruskal) {
+        for (int m = 0; m < h->N; ++m)
+            if (m != mode && !h->ke_valid[m]) {
+                CUDA_OR_FAIL(h, cpals::kr_refresh_e(h, m), "V^T A");
+                h->ke_valid[m] = true;
+            }
+        CUDA_OR_FAIL(h, cpals::kr_mttkrp(h, mode), "Kruskal MTTKRP");
+    } else {
+        CUDA_OR_FAIL(h, cpals::mttkrp(h, mode), "MTTKRP");
+    }
     if (M) CUDA_OR_FAIL(h, cudaMemcpyAsync(M, h->M, sizeof(double) * h->dims[mode] * h->R, kind_out(mem), h->stream),
                         "copy M");
     if (mem == CPALS_MEM_HOST) return take_status(h);
@@ -633,7 +821,8 @@ int cpals_fit(cpals_handle* hh, int direct, double* fit_host)
     if (direct) {
         double* d_res = h->d_fit + h->fit_cap;   // reuse the "last fit" slot for the residual
         double res2 = 0.0;
-        CUDA_OR_FAIL(h, cpals::residual_direct(h, d_res), "direct residual");
+        if (h->kruskal) CUDA_OR_FAIL(h, cpals::kr_residual(h, d_res), "direct residual");
+        else CUDA_OR_FAIL(h, cpals::residual_direct(h, d_res), "direct residual");
         CUDA_OR_FAIL(h, cudaMemcpyAsync(&res2, d_res, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "read");
         int st = take_status(h);
         if (st != CPALS_OK) return st;

@@ -10,7 +10,7 @@
 
 namespace cpals {
 
-constexpr int kMaxN = 8;
+constexpr int kMaxN = 12;
 constexpr int kMaxRank = 64;
 
 // Device status word values (a subset of cpals_status).
@@ -127,6 +127,23 @@ struct Handle {
     int64_t graph_nodes[4] = {0, 0, 0, 0};
 
     int64_t launches = 0;
+    // Kruskal-tensor input (Sec. 3.3.2): X = sum_s mu_s v_s^(1) o ... o v_s^(N),
+    // V_m = KV[m] (I_m x S); C_m = Q_m^T V_m (R x S) for the QR solves, E_m =
+    // V_m^T A_m (S x R) for the normal equations; the Gram V_m^T V_m of each
+    // mode (S x S, for ||X||^2); the fold factors of the QR of V_n (KP: up to
+    // N-2 matrices of R^2 x R) and two S x R work matrices.
+    bool kruskal = false;
+    int KS = 0;
+    double* KV[kMaxN] = {nullptr};
+    double* KC[kMaxN] = {nullptr};
+    double* KE[kMaxN] = {nullptr};
+    bool kc_valid[kMaxN] = {false};
+    bool ke_valid[kMaxN] = {false};
+    double* Kmu = nullptr;
+    double* KGV = nullptr;
+    double* KP = nullptr;
+    double* KMw[2] = {nullptr, nullptr};
+
     size_t owned_bytes = 0;
     char err[512] = {0};
 };
@@ -167,7 +184,9 @@ cudaError_t residual_direct(Handle* h, double* d_out);
 // (lda = m), Q is m x n, R is n x n.  A may alias Q.
 cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R);
 // QR of V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->Q0, h->R0 (structured, V_n not formed).
-cudaError_t krp_qr(Handle* h, int n);
+// With implicit = true Q0 is not formed either: the Q factors of the fold steps
+// go to h->KP (for the Kruskal-input path) and only R0 is written.
+cudaError_t krp_qr(Handle* h, int n, bool implicit = false);
 // C (m x n) = A (m x k) B (k x n), FP64, column-major, on the TTM kernel (one thread per output row, R-wide
 // register tile, split-K): used for W = Y_(n) Q0 and W T.
 cudaError_t gemm_rows(Handle* h, const double* A, int64_t m, int64_t k, const double* B, int n, double* C);
@@ -184,6 +203,23 @@ cudaError_t normalize_and_refactor(Handle* h, int n);
 cudaError_t gram(Handle* h, const double* A, int64_t I, double* G);
 // Efficient fit after the last mode of a sweep; appends to the fit ring.
 cudaError_t fit_efficient(Handle* h, int solve);
+
+// ---------------------------------------------------------------- Kruskal-tensor input (kruskal.cu)
+// out (na x nb) = A^T B for column-major A (I x na), B (I x nb).
+cudaError_t kr_atb(Handle* h, const double* A, const double* B, int64_t I, int na, int nb, double* out);
+// ||X||^2 of the Kruskal tensor into h->d_normX2.
+cudaError_t kr_norm2(Handle* h);
+// C_m = Q_m^T V_m and E_m = V_m^T A_m.
+cudaError_t kr_refresh_c(Handle* h, int m);
+cudaError_t kr_refresh_e(Handle* h, int m);
+// W_n = Y_(n) Q0 into h->W from the fold factors in h->KP (krp_qr implicit).
+cudaError_t kr_apply_q0(Handle* h, int n);
+// MTTKRP of the normal equations into h->M.
+cudaError_t kr_mttkrp(Handle* h, int n);
+// The unfolding Y_(n) (I_n x R^{N-1}) into Y (device).
+cudaError_t kr_unfold(Handle* h, int n, double* Y);
+// Direct residual ||X - Xhat||^2 into *out (device), entry by entry.
+cudaError_t kr_residual(Handle* h, double* out);
 
 // ---------------------------------------------------------------- batched problems
 struct Batch;

@@ -815,14 +815,15 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
 // step to build the explicit Q0 (R^{N-1} x R).  The thin QR with diag(R0) >= 0
 // is unique, so this equals the Householder QR of the explicit V_n up to
 // rounding.
-cudaError_t krp_qr(Handle* h, int n)
+cudaError_t krp_qr(Handle* h, int n, bool implicit)
 {
     const int R = h->R;
+    const size_t R3 = (size_t)R * R * R;
     int modes[kMaxN];
     int cnt = 0;
     for (int m = 0; m < h->N; ++m)
         if (m != n) modes[cnt++] = m;   // ascending: modes[0] is the fastest (rightmost) factor
-    if (cnt == 1) return householder_qr(h, h->Rf[modes[0]], R, R, h->Q0, h->R0);
+    if (cnt == 1) return householder_qr(h, h->Rf[modes[0]], R, R, implicit ? h->KP : h->Q0, h->R0);
     const double* curR = h->Rf[modes[0]];
     int64_t S = 0;                       // rows of the current Q_B (0: Q_B = I)
     for (int k = 1; k < cnt; ++k) {
@@ -832,7 +833,10 @@ cudaError_t krp_qr(Handle* h, int n)
         h->launches++;
         CPALS_CUDA_TRY(cudaGetLastError());
         double* Rout = last ? h->R0 : h->KR[k & 1];
-        if (S == 0) {
+        if (implicit) {
+            // keep the step's Q factor: Q0 = (I (x) Q_{k-1}) P_k is applied later in factored form
+            CPALS_CUDA_TRY(householder_qr(h, h->KM, (int64_t)R * R, R, h->KP + (size_t)(k - 1) * R3, Rout));
+        } else if (S == 0) {
             // Q_B = I: the QR of F (.) R_B is already Q0 (or the next Q_B)
             double* Qout = last ? h->Q0 : h->KQb[k & 1];
             CPALS_CUDA_TRY(householder_qr(h, h->KM, (int64_t)R * R, R, Qout, Rout));

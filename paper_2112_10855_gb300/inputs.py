@@ -187,6 +187,56 @@ def workload_c5a(seed=2112, init_seed=10855, size=1000, rank=64, noise=1e-3):
                    weights=logspace_weights(rank, 1e-6), noise=noise)
 
 
+def sine_grid(n: int) -> np.ndarray:
+    """n points 2 pi k / n, k = 0..n-1, on [0, 2 pi) (the discretisation of Sec. 4.3)."""
+    return 2.0 * math.pi * np.arange(n) / n
+
+
+def sine_of_sums_expanded(N: int, n: int):
+    """sin(x_1 + ... + x_N) on the grid as a Kruskal tensor of rank 2^{N-1}.
+
+    Expanding with sin(a + b) = sin a cos b + cos a sin b mode by mode leaves
+    one term per subset T of the modes with |T| odd: prod_{j in T} sin(x_j)
+    prod_{j not in T} cos(x_j), with sign (-1)^{(|T|-1)/2}.  Returns (mu, V):
+    weights (2^{N-1},) and N factor matrices (n x 2^{N-1}, column-major).
+    """
+    x = sine_grid(n)
+    terms = [t for t in range(1 << N) if bin(t).count("1") % 2 == 1]
+    S = len(terms)
+    mu = np.array([(-1.0) ** ((bin(t).count("1") - 1) // 2) for t in terms])
+    V = []
+    for j in range(N):
+        Vj = np.empty((n, S), order="F")
+        for c, t in enumerate(terms):
+            Vj[:, c] = np.sin(x) if (t >> j) & 1 else np.cos(x)
+        V.append(Vj)
+    return mu, V
+
+
+def sine_of_sums_rank_n(N: int, n: int, alpha=None):
+    """sin(x_1 + ... + x_N) on the grid as the rank-N Kruskal tensor of Eq.
+    sinsum_rkd: term j has sin(x_j) in mode j and
+    sin(x_k + alpha_k - alpha_j) / sin(alpha_k - alpha_j) in every mode k != j.
+    alpha defaults to alpha_j = j pi / N (every difference a non-multiple of pi).
+    Returns (mu = ones, V)."""
+    x = sine_grid(n)
+    a = np.arange(N) * math.pi / N if alpha is None else np.asarray(alpha, dtype=np.float64)
+    V = []
+    for k in range(N):
+        Vk = np.empty((n, N), order="F")
+        for j in range(N):
+            Vk[:, j] = np.sin(x) if k == j else np.sin(x + a[k] - a[j]) / math.sin(a[k] - a[j])
+        V.append(Vk)
+    return np.ones(N), V
+
+
+def random_kruskal(dims, S, seed=2112, stream=300):
+    """A Kruskal tensor with N(0,1) factors (I_m x S) and weights U(0.5, 1.5)."""
+    V = [gaussian_matrix(seed, stream + m, d, S) for m, d in enumerate(dims)]
+    mu = 0.5 + uniform(seed, stream + 99, S)
+    return mu, [np.asfortranarray(v) for v in V]
+
+
 def batch_shapes(count=512, seed=2112, lo=16, hi=128, rlo=2, rhi=16, order=3):
     """Per-problem dims ~ U{lo..hi} and ranks ~ U{rlo..rhi} for the batched workload."""
     dims = randint(seed, 11, count * order, lo, hi).reshape(count, order)

@@ -44,7 +44,8 @@ def test_exports_are_c_symbols():
     ((10, 0, 10), 3, 2, 0),         # empty mode
     ((10, 4, 10), 3, 5, 0),         # rank above a dim
     ((10, 10, 10), 3, 3, 7),        # unknown precision
-    ((3,) * 9, 9, 2, 0),            # N above the maximum
+    ((3,) * 13, 13, 2, 0),          # N above the maximum
+    ((64,) * 8, 8, 64, 0),          # R^N above what a dense handle holds
 ])
 def test_create_rejects_bad_arguments_on_the_host(lib, dims, N, rank, prec):
     d = (C.c_int64 * len(dims))(*dims)
@@ -53,6 +54,20 @@ def test_create_rejects_bad_arguments_on_the_host(lib, dims, N, rank, prec):
     assert rc == cpals.ERR_ARG
     assert not h.value
     assert lib.cpals_last_error(None)
+
+
+@pytest.mark.parametrize("dims,N,rank,S", [
+    ((10, 10, 10), 3, 3, 0),        # Kruskal rank 0
+    ((10, 10, 10), 3, 3, 5000),     # Kruskal rank above the maximum
+    ((10, 4, 10), 3, 5, 3),         # rank above a dim
+    ((3,) * 13, 13, 2, 2),          # N above the maximum
+])
+def test_create_kruskal_rejects_bad_arguments_on_the_host(lib, dims, N, rank, S):
+    d = (C.c_int64 * len(dims))(*dims)
+    h = C.c_void_p()
+    rc = lib.cpals_create_kruskal(d, N, rank, S, C.byref(h))
+    assert rc == cpals.ERR_ARG
+    assert not h.value
 
 
 def test_null_handle_calls_fail_cleanly(lib):

@@ -381,3 +381,22 @@ def test_score_invariances():
     C = [RNG.standard_normal((d, R)) for d in dims]
     assert oracle.score(dims, lam, A, lam, C) < 0.5
     assert abs(oracle.score(dims, lam, A, 2 * lam, A) - 0.5) < 1e-14
+
+
+@pytest.mark.parametrize("N,n", [(2, 9), (3, 8), (4, 7), (5, 6), (6, 5), (10, 3)])
+def test_sine_of_sums_representations(N, n):
+    # Sec. 4.3: the 2^{N-1}-term expansion and the rank-N representation of
+    # Eq. sinsum_rkd both reproduce sin(x_1 + ... + x_N) on the grid
+    # 2 pi k / n; this pins the Kruskal inputs of the sine-of-sums workload
+    # (and cp_full, which expands them for the oracle)
+    from paper_2112_10855_gb300 import inputs
+    x = inputs.sine_grid(n)
+    grids = np.meshgrid(*([x] * N), indexing="ij")
+    ref = np.sin(sum(grids)).reshape(-1, order="F")
+    dims = (n,) * N
+    mu, V = inputs.sine_of_sums_expanded(N, n)
+    assert len(mu) == 2 ** (N - 1)
+    assert np.abs(inputs.cp_full(dims, V, mu) - ref).max() <= 1e-14 * N
+    mu, V = inputs.sine_of_sums_rank_n(N, n)
+    assert len(mu) == N
+    assert np.abs(inputs.cp_full(dims, V, mu) - ref).max() <= 1e-13 * N
