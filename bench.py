@@ -58,6 +58,9 @@ def parse():
                          "1000^3 rank 64 (SVD solve) and c5b: 5-way 40^5 rank 8, each comparing FP64, FP32, 3xBF16 "
                          "and 3xTF32 passes over X; c4: 512 independent small problems, batched; sine: sine-of-sums "
                          "tensors in Kruskal form (Sec. 4.3)")
+    ap.add_argument("--recovery-seeds", type=int, default=5,
+                    help="c3: planted problems (seeds) on which every precision runs to convergence and is scored "
+                         "against the planted factors (factor-match score, Sec. 4.2); 0 skips")
     ap.add_argument("--fit-sweeps", type=int, default=300,
                     help="at most this many sweeps (stop at |fit change| < 1e-10) for the equal-fit comparison")
     return ap.parse_args()
@@ -345,6 +348,9 @@ def run_mixed(args, world, rank):
                 float(np.linalg.norm(A1[m] - ref["A"][m]) / np.linalg.norm(ref["A"][m])) for m in range(len(A1)))
             entry["fit_rel_diff_vs_f64"] = abs(fit_final - ref["fit"]) / abs(ref["fit"])
         out[prec] = entry
+    recovery = None
+    if args.workload == "c3" and args.recovery_seeds > 0:
+        recovery = recovery_rates(args, p.dims, R, fit_sweeps, solve, rtol, stream)
     if rank == 0:
         line = {
             "metric": METRIC, "value": out["bf16x3"]["iters_per_s"], "unit": UNIT, "n_gpus": world,
@@ -356,7 +362,39 @@ def run_mixed(args, world, rank):
             "precisions": out,
             "speedup_vs_f64": {k: out[k]["iters_per_s"] / out["f64"]["iters_per_s"] for k in out},
         }
+        if recovery is not None:
+            line["planted_recovery"] = recovery
         print(json.dumps(line), flush=True)
+
+
+def recovery_rates(args, dims, R, fit_sweeps, solve, rtol, stream):
+    """Every precision from the same start on --recovery-seeds planted 120^4
+    problems, run to convergence (|fit change| < 1e-10, at most fit_sweeps),
+    then scored against the planted factors and weights (factor-match score,
+    Sec. 4.2).  "Recovered" = score >= 0.99."""
+    import torch
+    from paper_2112_10855_gb300 import cpals, inputs
+    from paper_2112_10855_gb300.score import factor_match_score
+    scores = {k: [] for k in ["f64", "f32", "bf16x3", "tf32x3"]}
+    for s in range(args.recovery_seeds):
+        p = inputs.workload_c3(seed=3000 + s, init_seed=4000 + s)
+        Xd = torch.from_numpy(p.X).cuda()
+        for prec in scores:
+            h = cpals.CPALS(p.dims, R, prec)
+            h.set_stream(stream)
+            h.set_tensor(Xd)
+            h.set_factors([np.asfortranarray(a) for a in p.init_factors])
+            h.iterate(fit_sweeps, tol=1e-10, solve=solve, svd_rtol=rtol, want_fits=False)
+            A, lam = h.get_factors()
+            scores[prec].append(factor_match_score(lam, A, p.true_weights, p.true_factors))
+            del h
+        del Xd
+    f64 = np.asarray(scores["f64"])
+    return {"seeds": args.recovery_seeds,
+            "recovered_fraction_at_0.99": {k: float(np.mean(np.asarray(v) >= 0.99)) for k, v in scores.items()},
+            "recovered_fraction_at_0.95": {k: float(np.mean(np.asarray(v) >= 0.95)) for k, v in scores.items()},
+            "max_abs_score_diff_vs_f64": {k: float(np.abs(np.asarray(v) - f64).max()) for k, v in scores.items()},
+            "scores": {k: [round(x, 6) for x in v] for k, v in scores.items()}}
 
 
 def run_batch(args, world, rank):

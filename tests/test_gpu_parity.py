@@ -378,3 +378,23 @@ def test_split_tc_sweeps_track_oracle(cuda_lib, precision):
     tol = 1e-4 if precision == "bf16x3" else 1e-5
     assert np.abs(fits[True] - np.asarray(ofits)).max() <= tol, (fits[True], ofits)
     assert np.abs(fits[True] - fits[False]).max() <= tol / 10
+
+
+def test_mixed_precisions_recover_planted_factors_like_fp64(cuda_lib):
+    # the mixed precisions (FP32, and 3 x bf16 / 3 x tf32 on the tensor cores at
+    # rank 16) recover the planted model as FP64 does: factor-match score
+    # (Sec. 4.2) against the planted factors within 1e-3 of FP64's
+    from paper_2112_10855_gb300.score import factor_match_score
+    p = inputs.planted((64, 60, 56), 16, seed=41, init_seed=42, congruence=0.5, noise=0.01)
+    Xd = torch.from_numpy(p.X).cuda()
+    scores = {}
+    for prec in ["f64", "f32", "bf16x3", "tf32x3"]:
+        h = cpals.CPALS(p.dims, p.rank, prec)
+        h.set_tensor(Xd)
+        h.set_factors([np.asfortranarray(a) for a in p.init_factors])
+        h.iterate(150, tol=1e-10, solve="qr")
+        A, lam = h.get_factors()
+        scores[prec] = factor_match_score(lam, A, p.true_weights, p.true_factors)
+    assert scores["f64"] >= 0.95, scores
+    for prec in ["f32", "bf16x3", "tf32x3"]:
+        assert abs(scores[prec] - scores["f64"]) <= 1e-3, scores

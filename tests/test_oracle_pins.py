@@ -400,3 +400,21 @@ def test_sine_of_sums_representations(N, n):
     mu, V = inputs.sine_of_sums_rank_n(N, n)
     assert len(mu) == N
     assert np.abs(inputs.cp_full(dims, V, mu) - ref).max() <= 1e-13 * N
+
+
+def test_package_score_equals_oracle_brute_force():
+    # the package's factor-match score (linear assignment) against the
+    # oracle's brute force over permutations, on random and on permuted,
+    # sign-flipped and rescaled copies of a model
+    from paper_2112_10855_gb300.score import factor_match_score
+    rng = np.random.default_rng(5)
+    for R in (1, 2, 4, 6):
+        dims = (7, 6, 5)
+        A1 = [rng.standard_normal((d, R)) for d in dims]
+        A2 = [rng.standard_normal((d, R)) for d in dims]
+        l1, l2 = rng.random(R) + 0.5, rng.random(R) + 0.5
+        assert abs(factor_match_score(l1, A1, l2, A2) - oracle.score(dims, l1, A1, l2, A2)) < 1e-13
+        perm = rng.permutation(R)
+        A3 = [(-a[:, perm]) * 3.0 for a in A1]
+        assert abs(factor_match_score(l1, A1, l1[perm], A3) - 1.0) < 1e-13
+        assert abs(oracle.score(dims, l1, A1, l1[perm], A3) - 1.0) < 1e-13
