@@ -584,12 +584,19 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
 template <int N, bool TF32>
 struct PipeCfg {
     using E = Elem<TF32>;
-    static constexpr int kc = E::kChunk;                              // K per item
+    // an item is IC operand chunks of 128 bytes per row: 64 K values for bf16
+    // (one chunk) and for tf32 (two), i.e. a 32 KB box of X either way
+    static constexpr int IC = TF32 ? 2 : 1;
+    static constexpr int kc = E::kChunk * IC;                         // K per item
+    static constexpr int kSteps = kc / E::kStep;                      // MMA K steps per item
     static constexpr uint32_t kXBytes = kTcRows * kc * 4;             // fp32 box
-    static constexpr uint32_t kBBytes = 2u * N * 128u;                // hi + lo Q tiles
+    static constexpr uint32_t kChunkB = 2u * N * 128u;                // hi + lo Q tiles of one chunk
+    static constexpr uint32_t kBBytes = IC * kChunkB;                 // Q tiles of one item
     static constexpr int kAccCols = 2 * N;
-    static constexpr int kACols = 64;
-    static constexpr int kASlots = N <= 32 ? 4 : 3;
+    static constexpr int kHalfCols = 32 * IC;                         // TMEM columns of A_hi (or A_lo) per item
+    static constexpr int kACols = 2 * kHalfCols;
+    static constexpr int kASlotsFit = (512 - 2 * kAccCols) / kACols;
+    static constexpr int kASlots = kASlotsFit < 4 ? kASlotsFit : 4;
     static constexpr uint32_t kBResident = 64u * 1024u;
     static constexpr uint32_t kRingBudget = 220u * 1024u;           // X ring + Q tiles
     static constexpr int kMaxX = 16;
@@ -599,6 +606,7 @@ struct PipeCfg {
     static constexpr int kThreads = (kBProducerWarp + 1) * 32;
     static constexpr uint32_t kSmemMax = kRingBudget + 1024 + 512;   // + alignment + barriers
     static_assert(2 * kAccCols + kASlots * kACols <= 512, "tensor memory budget");
+    static_assert(kASlots >= 2, "two operand slots at least");
     static_assert(kASlots * kBBytes <= kBResident, "the Q region holds the ring slots");
     static_assert((kRingBudget - kBResident) / kXBytes * kXBytes > 114 * 1024,
                   "one CTA per SM owns all 512 TMEM columns");
@@ -612,13 +620,14 @@ struct PipeCfg {
 };
 
 // Out(l, r, t) = sum_k X(l, k, t) Q(k, r) for the tiles blockIdx.x, +gridDim.x, ...
-// A tile is BL consecutive l times BT consecutive t (BL*BT <= 128 rows).
-// Every split warp waits on every item and every ring has a single in-order
-// consumer per barrier, so each parity wait refers to an unambiguous phase.
+// A tile is BL consecutive l times BT consecutive t (BL*BT <= 128 rows) and
+// nitems items of K.  Every split warp waits on every item and every ring
+// has a single in-order consumer per barrier, so each parity wait refers to
+// an unambiguous phase.
 template <int N, bool TF32>
 __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pipe_kernel(
     const __grid_constant__ CUtensorMap xmap, const uint8_t* __restrict__ btiles, float* __restrict__ out,
-    int64_t L, int64_t Tn, int R, int BL, int BT, int64_t ntl, int64_t ntiles, int nchunks, int SX, int bres,
+    int64_t L, int64_t Tn, int R, int BL, int BT, int64_t ntl, int64_t ntiles, int nitems, int SX, int bres,
     int* __restrict__ status)
 {
     using Cfg = PipeCfg<N, TF32>;
@@ -632,7 +641,7 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* xring = smem;
     uint8_t* bslots = smem + (size_t)SX * Cfg::kXBytes;
-    const uint32_t bregion = bres ? (uint32_t)nchunks * Cfg::kBBytes : (uint32_t)SA * Cfg::kBBytes;
+    const uint32_t bregion = bres ? (uint32_t)nitems * Cfg::kBBytes : (uint32_t)SA * Cfg::kBBytes;
     uint64_t* xfull = (uint64_t*)(bslots + bregion);
     uint64_t* xempty = xfull + Cfg::kMaxX;
     uint64_t* bfull = xempty + Cfg::kMaxX;
@@ -668,9 +677,10 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
     const uint32_t tmem = *tmem_slot;
 
     const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
-    const int64_t items = my_tiles * nchunks;
+    const int64_t items = my_tiles * nitems;
     const int rows_used = BL * BT;
     auto acol = [&](int j) { return (uint32_t)(2 * Cfg::kAccCols + j * Cfg::kACols); };
+    (void)sizeof(E);
     // last item issued on slot `s` of a ring of `n` slots when `it` items were issued
     auto last_on = [](int64_t it, int s, int n) { return it - 1 - ((it - 1 - s) % n + n) % n; };
 
@@ -681,8 +691,8 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
             for (; it < items; ++it) {
                 const int s = (int)(it % SX);
                 if (!pipe_wait(&xempty[s], (uint32_t)((it / SX) & 1) ^ 1u, abort_flag)) break;
-                const int64_t tile = blockIdx.x + (it / nchunks) * (int64_t)gridDim.x;
-                const int c = (int)(it % nchunks);
+                const int64_t tile = blockIdx.x + (it / nitems) * (int64_t)gridDim.x;
+                const int c = (int)(it % nitems);
                 const int64_t tt = tile / ntl, tl = tile - tt * ntl;
                 mbar_expect_tx(&xfull[s], tx);
                 tma_load_3d(xring + (size_t)s * Cfg::kXBytes, &xmap, (int)(tl * BL), c * Cfg::kc, (int)(tt * BT),
@@ -705,7 +715,7 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
             for (; it < items; ++it) {
                 const int j = (int)(it % SA);
                 if (!pipe_wait(&aempty[j], (uint32_t)((it / SA) & 1) ^ 1u, abort_flag)) break;
-                const int c = (int)(it % nchunks);
+                const int c = (int)(it % nitems);
                 mbar_expect_tx(&bfull[j], Cfg::kBBytes);
                 bulk_load(bslots + (size_t)j * Cfg::kBBytes, btiles + (size_t)c * Cfg::kBBytes, Cfg::kBBytes,
                           &bfull[j]);
@@ -727,7 +737,7 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
                 if (!pipe_wait(&accempty[a], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(a * Cfg::kAccCols);
-                for (int c = 0; c < nchunks; ++c, ++it) {
+                for (int c = 0; c < nitems; ++c, ++it) {
                     const int j = (int)(it % SA);
                     const uint32_t ph = (uint32_t)((it / SA) & 1);
                     if ((!bres && !pipe_wait(&bfull[j], ph, abort_flag)) || !pipe_wait(&ready[j], ph, abort_flag)) {
@@ -735,11 +745,13 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t ahi = tmem + acol(j), alo = ahi + 32u;
+                    const uint32_t ahi = tmem + acol(j), alo = ahi + (uint32_t)Cfg::kHalfCols;
                     const uint32_t bh = smem_u32(bslots + (size_t)(bres ? c : j) * Cfg::kBBytes);
 #pragma unroll
-                    for (int ks = 0; ks < E::kChunk / E::kStep; ++ks) {
-                        const uint64_t bd = make_desc(bh + (uint32_t)ks * 2u * kLbo);
+                    for (int ks = 0; ks < Cfg::kSteps; ++ks) {
+                        // K step ks sits in 128-byte chunk ks / 4 of the item, 32 bytes per step
+                        const uint64_t bd =
+                            make_desc(bh + (uint32_t)(ks >> 2) * Cfg::kChunkB + (uint32_t)(ks & 3) * 2u * kLbo);
                         mma_ts<TF32>(d, ahi + 8u * ks, bd, idesc2, (c | ks) ? 1u : 0u);   // [hi*hi | hi*lo]
                         mma_ts<TF32>(d, alo + 8u * ks, bd, idesc1, 1u);                    // += lo*hi
                     }
@@ -762,7 +774,8 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
         const int bt = mok ? m / BL : 0, bl = mok ? m - bt * BL : 0;
         const int xoff = bt * Cfg::kc * BL + bl;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        constexpr int kHalf = Cfg::kc / 2;   // K values per split thread per item
+        constexpr int kHalf = Cfg::kc / 2;                      // K values per split thread per item
+        constexpr int kCols = TF32 ? kHalf : kHalf / 2;        // TMEM columns of them (hi, and again lo)
         for (int64_t it = 0; it < items; ++it) {
             const int s = (int)(it % SX), j = (int)(it % SA);
             // warp-uniform outcome: tcgen05.st below is warp-collective
@@ -772,31 +785,34 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
             // rows past the tile's last valid row split row 0's values: their
             // accumulator rows are never stored
             const float* xk = reinterpret_cast<const float*>(xring + (size_t)s * Cfg::kXBytes) + xoff + h * kHalf * BL;
-            uint32_t hi[16], lo[16];
-            if constexpr (TF32) {
+            const uint32_t col = tmem + acol(j) + (uint32_t)(h * kCols);
 #pragma unroll
-                for (int p = 0; p < 16; ++p) {
-                    const uint32_t xb = __float_as_uint(xk[p * BL]);
-                    hi[p] = tf32_rna_bits(xb);
-                    lo[p] = tf32_rna_bits(__float_as_uint(__uint_as_float(xb) - __uint_as_float(hi[p])));
-                }
-            } else {
+            for (int g = 0; g < kCols / 16; ++g) {
+                uint32_t hi[16], lo[16];
+                if constexpr (TF32) {
 #pragma unroll
-                for (int p = 0; p < 16; ++p) {
-                    const float x0 = xk[(2 * p) * BL], x1 = xk[(2 * p + 1) * BL];
-                    const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
-                    const float2 hf = __bfloat1622float2(hh);
-                    const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-                    hi[p] = *reinterpret_cast<const uint32_t*>(&hh);
-                    lo[p] = *reinterpret_cast<const uint32_t*>(&ll);
+                    for (int p = 0; p < 16; ++p) {
+                        const uint32_t xb = __float_as_uint(xk[(16 * g + p) * BL]);
+                        hi[p] = tf32_rna_bits(xb);
+                        lo[p] = tf32_rna_bits(__float_as_uint(__uint_as_float(xb) - __uint_as_float(hi[p])));
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 16; ++p) {
+                        const float x0 = xk[(32 * g + 2 * p) * BL], x1 = xk[(32 * g + 2 * p + 1) * BL];
+                        const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
+                        const float2 hf = __bfloat1622float2(hh);
+                        const __nv_bfloat162 ll = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+                        hi[p] = *reinterpret_cast<const uint32_t*>(&hh);
+                        lo[p] = *reinterpret_cast<const uint32_t*>(&ll);
+                    }
                 }
+                tmem_st16(lane_base + col + (uint32_t)(16 * g), hi);
+                tmem_st16(lane_base + col + (uint32_t)(Cfg::kHalfCols + 16 * g), lo);
             }
-            // the box has been read (the values above are in registers)
+            // the box has been read (its values went through registers above)
             __syncwarp();
             if (lane == 0) mbar_arrive(&xempty[s]);
-            const uint32_t col = tmem + acol(j) + (uint32_t)(h * 16);
-            tmem_st16(lane_base + col, hi);
-            tmem_st16(lane_base + col + 32u, lo);
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
@@ -869,7 +885,7 @@ bool pipe_shape_ok(const float* in, TtmShape s)
 
 template <int N, bool TF32>
 cudaError_t launch_pipe(Handle* h, const float* in, const uint8_t* tiles, float* out, TtmShape s, int R,
-                        int nchunks)
+                        int nitems)
 {
     using Cfg = PipeCfg<N, TF32>;
     static std::once_flag attr_once;
@@ -894,12 +910,12 @@ cudaError_t launch_pipe(Handle* h, const float* in, const uint8_t* tiles, float*
     const int64_t ntl = (s.L + BL - 1) / BL;
     const int64_t ntiles = ntl * ((s.T + BT - 1) / BT);
     const int grid = (int)std::min<int64_t>(ntiles, (int64_t)h->num_sms);
-    const bool bres = (uint64_t)nchunks * Cfg::kBBytes <= Cfg::kBResident;
-    const uint32_t bregion = bres ? (uint32_t)nchunks * Cfg::kBBytes : (uint32_t)Cfg::kASlots * Cfg::kBBytes;
+    const bool bres = (uint64_t)nitems * Cfg::kBBytes <= Cfg::kBResident;
+    const uint32_t bregion = bres ? (uint32_t)nitems * Cfg::kBBytes : (uint32_t)Cfg::kASlots * Cfg::kBBytes;
     const int SX = Cfg::x_stages(bregion);
     const uint32_t smem = (uint32_t)SX * Cfg::kXBytes + bregion + 1024 + 512;
     ttm_split_tc_pipe_kernel<N, TF32><<<grid, Cfg::kThreads, smem, h->stream>>>(
-        map, tiles, out, s.L, s.T, R, BL, BT, ntl, ntiles, nchunks, SX, bres ? 1 : 0, h->d_status);
+        map, tiles, out, s.L, s.T, R, BL, BT, ntl, ntiles, nitems, SX, bres ? 1 : 0, h->d_status);
     h->launches++;
     return cudaGetLastError();
 }
@@ -915,7 +931,12 @@ cudaError_t launch_tc(Handle* h, const float* in, const double* Q, int64_t ldq, 
                                             (int)Cfg::kSmem));
         attr = true;
     }
-    const int nchunks = (int)((s.K + E::kChunk - 1) / E::kChunk);
+    const bool pipe = h->tc_pipe && pipe_shape_ok(in, s);
+    // 128-byte K chunks of the pre-split Q tiles: whole items for the pipeline
+    constexpr int IC = PipeCfg<N, TF32>::IC;
+    int nchunks = (int)((s.K + E::kChunk - 1) / E::kChunk);
+    const int nitems = (nchunks + IC - 1) / IC;
+    if (pipe) nchunks = nitems * IC;
     const size_t tile_bytes = (size_t)nchunks * 2 * Cfg::kBBytes;
     if (tile_bytes > (size_t)h->scratch_elems * sizeof(double)) return cudaErrorInvalidValue;
     uint8_t* tiles = reinterpret_cast<uint8_t*>(h->scratch);
@@ -924,7 +945,7 @@ cudaError_t launch_tc(Handle* h, const float* in, const double* Q, int64_t ldq, 
         Q, ldq, s.K, R, tiles, nchunks, h->d_status);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
-    if (h->tc_pipe && pipe_shape_ok(in, s)) return launch_pipe<N, TF32>(h, in, tiles, out, s, R, nchunks);
+    if (pipe) return launch_pipe<N, TF32>(h, in, tiles, out, s, R, nitems);
     const int64_t rows = s.L * s.T;
     const int64_t grid = (rows + kTcRows - 1) / kTcRows;
     ttm_split_tc_kernel<N, TF32><<<(unsigned)grid, kTcThreads, Cfg::kSmem, h->stream>>>(
