@@ -220,9 +220,9 @@ int cpals_fit(cpals_handle* h, int direct, double* fit_host);
 int cpals_sync(cpals_handle* h);
 
 /* Options of a handle.
- *  CPALS_OPT_DIMTREE (default 1): sweeps of cpals_iterate with the QR or SVD
- *    solve on an N >= 3 tensor share Multi-TTM work across modes by a
- *    dimension tree (Sec. 3.3.3).  X is contracted once over the modes of the
+ *  CPALS_OPT_DIMTREE (default 1): sweeps of cpals_iterate on an N >= 3
+ *    dense tensor share Multi-TTM work (and, for the NORMAL / NORMAL_PINV
+ *    solves, MTTKRP work) across modes by a dimension tree (Sec. 3.3.3).  X is contracted once over the modes of the
  *    second half for the Multi-TTMs of the first half, and once over the first
  *    half (with its updated Q_m) for the second half.  That is two passes over
  *    X per sweep instead of N.  0 runs a full Multi-TTM from X per mode.  The

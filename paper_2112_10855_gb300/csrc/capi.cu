@@ -179,7 +179,8 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         return cudaSuccess;
     }
     if (is_normal(solve)) {
-        CPALS_CUDA_TRY(cpals::mttkrp(h, n));
+        if (from_partial) CPALS_CUDA_TRY(cpals::mttkrp_from_partial(h, n));
+        else CPALS_CUDA_TRY(cpals::mttkrp(h, n));
         if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n));
         else CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol));
     } else {
@@ -214,17 +215,19 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
     return cudaSuccess;
 }
 
-// One sweep over the modes.  For the QR/SVD solves of an N >= 3 tensor the
-// Multi-TTMs follow a dimension tree (Sec. 3.3.3): the modes split into halves
+// One sweep over the modes.  For an N >= 3 dense tensor the Multi-TTMs
+// follow a dimension tree (Sec. 3.3.3): the modes split into halves
 // H1 = {0..h-1} and H2 = {h..N-1}.  X is contracted once over H2 (whose Q_m do
 // not change while H1 is updated), and each H1 mode contracts the rest of H1
 // from that partial with the current Q_m.  Then X is contracted once over H1
 // with the updated Q_m for the H2 modes.  That makes two passes over X per
 // sweep instead of N.  The TTMs of a Multi-TTM can run in any order
-// (Sec. 2.2), so only rounding differs from the per-mode Multi-TTM.
+// (Sec. 2.2), so only rounding differs from the per-mode Multi-TTM.  The
+// normal equations share the same tree for their MTTKRPs (A_m instead of
+// Q_m, diagonal contractions after the first).
 cudaError_t sweep(Handle* h, int solve, double rtol)
 {
-    if (is_normal(solve) || h->N < 3 || !h->dimtree || !h->tA) {
+    if (h->N < 3 || !h->dimtree || !h->tA || h->kruskal) {
         for (int n = 0; n < h->N; ++n) CPALS_CUDA_TRY(mode_update(h, n, solve, rtol));
         return cpals::fit_efficient(h, solve);
     }
@@ -234,9 +237,13 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
         if (m < h1) H1[n1++] = m;
         else H2[n2++] = m;
     }
-    CPALS_CUDA_TRY(cpals::dimtree_pass(h, H2, n2));
+    // the normal equations use the same halves with the MTTKRP's contractions
+    auto pass = [&](const int* modes, int nm) {
+        return is_normal(solve) ? cpals::mttkrp_tree_pass(h, modes, nm) : cpals::dimtree_pass(h, modes, nm);
+    };
+    CPALS_CUDA_TRY(pass(H2, n2));
     for (int k = 0; k < n1; ++k) CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true));
-    CPALS_CUDA_TRY(cpals::dimtree_pass(h, H1, n1));
+    CPALS_CUDA_TRY(pass(H1, n1));
     for (int k = 0; k < n2; ++k) CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true));
     return cpals::fit_efficient(h, solve);
 }

@@ -97,6 +97,7 @@ struct Handle {
     int64_t tA_elems = 0;
     int64_t tA_dims[kMaxN] = {0};
     int tA_contracted[kMaxN] = {0};
+    int tA_rank = -1;        // normal-equations partial: position of the rank index
     bool dimtree = true;
     // first TTM on the tensor cores through the persistent TMA pipeline when
     // the shape allows it (else one CTA per 128-row tile)
@@ -173,6 +174,10 @@ cudaError_t ttm_split_tc(Handle* h, const float* in, const double* Q, int64_t ld
                          bool tf32);
 // MTTKRP M_n = X_(n) Z_n (Alg. cp-als) into h->M.
 cudaError_t mttkrp(Handle* h, int n);
+// Dimension tree for the MTTKRP: X contracted over `modes` (full TTM with the
+// first A_m, then diagonal contractions) into h->tA; then M_n from h->tA.
+cudaError_t mttkrp_tree_pass(Handle* h, const int* modes, int nm);
+cudaError_t mttkrp_from_partial(Handle* h, int n);
 // Squared Frobenius norm of X into h->d_normX2.
 cudaError_t norm2(Handle* h);
 // FP64 -> FP32 copy with round-to-nearest-even.

@@ -460,47 +460,113 @@ cudaError_t multi_ttm_from_partial_impl(Handle* h, int n)
     return unfold_yn<T>(h, res, n);
 }
 
+// MTTKRP contractions (Alg. cp-als): the first contraction of X over a mode c
+// is a full TTM with A_c (cost 2 P R), after which the rank index r sits in
+// the place of mode c; every later mode m is contracted diagonally with
+// A_m(:, r) and leaves a dimension of 1.  `rank_pos` is -1 before the first
+// contraction.  The modes go largest first (ties: higher mode), like the
+// TTMs of the Multi-TTM.  The last contraction writes to final_out when given.
 template <typename T>
-cudaError_t mttkrp_impl(Handle* h, int n)
+cudaError_t mttkrp_chain(Handle* h, const T* in, int64_t* d, const int* modes_in, int nm, int* rank_pos, bool from_x,
+                         T* final_out, const T** result)
 {
     const int N = h->N, R = h->R;
-    int order[kMaxN];
-    ttm_order(N, h->dims, n, order);
-    int64_t d[kMaxN];
-    for (int m = 0; m < N; ++m) d[m] = h->dims[m];
-    // first contraction: a full TTM with A_c (cost 2 P R, as the MTTKRP of Alg. cp-als)
-    const int c = order[0];
-    TtmShape s = ttm_shape(N, d, c);
-    T* buf = (T*)h->tbuf[0];
-    CPALS_CUDA_TRY(launch_ttm<T>(h, x_ptr<T>(h), h->A[c], h->dims[c], buf, s, R));
-    d[c] = R;
-    const T* in = buf;
-    int cur = 1;
-    for (int k = 1; k < N - 1; ++k) {
-        const int m = order[k];
-        s = ttm_shape(N, d, m);
-        int64_t div = 1;
-        int r_in_l;
-        if (c < m) { r_in_l = 1; for (int q = 0; q < c; ++q) div *= d[q]; }
-        else { r_in_l = 0; for (int q = m + 1; q < c; ++q) div *= d[q]; }
-        T* out = (T*)h->tbuf[cur];
-        const int64_t rows = s.L * s.T;
-        diag_contract_kernel<T><<<grid_for(rows, 256, h->num_sms), 256, 0, h->stream>>>(
-            in, h->A[m], h->dims[m], out, s.L, s.K, s.T, r_in_l, div, R, h->d_status);
-        h->launches++;
-        CPALS_CUDA_TRY(cudaGetLastError());
-        d[m] = 1;
+    int modes[kMaxN];
+    for (int k = 0; k < nm; ++k) modes[k] = modes_in[k];
+    for (int a = 0; a < nm; ++a)
+        for (int b = a + 1; b < nm; ++b) {
+            const int x = modes[a], y = modes[b];
+            if (h->dims[y] > h->dims[x] || (h->dims[y] == h->dims[x] && y > x)) { modes[a] = y; modes[b] = x; }
+        }
+    int cur = 0;
+    for (int k = 0; k < nm; ++k) {
+        const int m = modes[k];
+        const TtmShape s = ttm_shape(N, d, m);
+        T* out = (k == nm - 1 && final_out) ? final_out : (T*)h->tbuf[cur];
+        if (*rank_pos < 0) {
+            if (from_x && first_on_tensor_cores<T>(h))
+                CPALS_CUDA_TRY(ttm_split_tc(h, (const float*)in, h->A[m], h->dims[m], (float*)out, s, R,
+                                            h->prec == CPALS_TF32X3));
+            else
+                CPALS_CUDA_TRY(launch_ttm<T>(h, in, h->A[m], h->dims[m], out, s, R));
+            d[m] = R;
+            *rank_pos = m;
+        } else {
+            const int c = *rank_pos;
+            int64_t div = 1;
+            int r_in_l;
+            if (c < m) { r_in_l = 1; for (int q = 0; q < c; ++q) div *= d[q]; }
+            else { r_in_l = 0; for (int q = m + 1; q < c; ++q) div *= d[q]; }
+            const int64_t rows = s.L * s.T;
+            diag_contract_kernel<T><<<grid_for(rows, 256, h->num_sms), 256, 0, h->stream>>>(
+                in, h->A[m], h->dims[m], out, s.L, s.K, s.T, r_in_l, div, R, h->d_status);
+            h->launches++;
+            CPALS_CUDA_TRY(cudaGetLastError());
+            d[m] = 1;
+        }
         in = out;
         cur ^= 1;
     }
-    // remaining dims: I_n at n, R at c, ones elsewhere
+    *result = in;
+    return cudaSuccess;
+}
+
+// M_n(i, r) from a tensor whose dims are I_n at n, R at the rank position c
+// and 1 elsewhere.
+template <typename T>
+cudaError_t mttkrp_gather(Handle* h, const T* in, const int64_t* d, int n, int c)
+{
     int64_t sn = 1, sc = 1;
     for (int q = 0; q < n; ++q) sn *= d[q];
     for (int q = 0; q < c; ++q) sc *= d[q];
-    gather2d_kernel<T><<<grid_for(h->dims[n] * R, 256, h->num_sms), 256, 0, h->stream>>>(
-        in, h->M, h->dims[n], R, sn, sc, h->d_status);
+    gather2d_kernel<T><<<grid_for(h->dims[n] * h->R, 256, h->num_sms), 256, 0, h->stream>>>(
+        in, h->M, h->dims[n], h->R, sn, sc, h->d_status);
     h->launches++;
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t mttkrp_impl(Handle* h, int n)
+{
+    int modes[kMaxN], nm = 0;
+    int64_t d[kMaxN];
+    for (int m = 0; m < h->N; ++m) {
+        d[m] = h->dims[m];
+        if (m != n) modes[nm++] = m;
+    }
+    int c = -1;
+    const T* res = nullptr;
+    CPALS_CUDA_TRY(mttkrp_chain<T>(h, x_ptr<T>(h), d, modes, nm, &c, true, nullptr, &res));
+    return mttkrp_gather<T>(h, res, d, n, c);
+}
+
+// Dimension tree for the normal equations: X contracted over `modes` (one
+// half) into h->tA, the rank index at h->tA_rank.
+template <typename T>
+cudaError_t mttkrp_tree_pass_impl(Handle* h, const int* modes, int nm)
+{
+    for (int m = 0; m < h->N; ++m) h->tA_dims[m] = h->dims[m];
+    int c = -1;
+    const T* res = nullptr;
+    CPALS_CUDA_TRY(mttkrp_chain<T>(h, x_ptr<T>(h), h->tA_dims, modes, nm, &c, true, (T*)h->tA, &res));
+    h->tA_rank = c;
+    return cudaSuccess;
+}
+
+// M_n from the partial: the uncontracted modes other than n, with their current A_m.
+template <typename T>
+cudaError_t mttkrp_from_partial_impl(Handle* h, int n)
+{
+    int modes[kMaxN], nm = 0;
+    int64_t d[kMaxN];
+    for (int m = 0; m < h->N; ++m) {
+        d[m] = h->tA_dims[m];
+        if (m != n && !h->tA_contracted[m]) modes[nm++] = m;
+    }
+    int c = h->tA_rank;
+    const T* res = (const T*)h->tA;
+    CPALS_CUDA_TRY(mttkrp_chain<T>(h, (const T*)h->tA, d, modes, nm, &c, false, nullptr, &res));
+    return mttkrp_gather<T>(h, res, d, n, c);
 }
 
 // ---------------------------------------------------------------- reductions
@@ -624,6 +690,20 @@ cudaError_t mttkrp(Handle* h, int n)
 {
     if (h->prec == CPALS_F64) return mttkrp_impl<double>(h, n);
     return mttkrp_impl<float>(h, n);
+}
+
+cudaError_t mttkrp_tree_pass(Handle* h, const int* modes, int nm)
+{
+    for (int m = 0; m < h->N; ++m) h->tA_contracted[m] = 0;
+    for (int k = 0; k < nm; ++k) h->tA_contracted[modes[k]] = 1;
+    if (h->prec == CPALS_F64) return mttkrp_tree_pass_impl<double>(h, modes, nm);
+    return mttkrp_tree_pass_impl<float>(h, modes, nm);
+}
+
+cudaError_t mttkrp_from_partial(Handle* h, int n)
+{
+    if (h->prec == CPALS_F64) return mttkrp_from_partial_impl<double>(h, n);
+    return mttkrp_from_partial_impl<float>(h, n);
 }
 
 cudaError_t norm2(Handle* h)

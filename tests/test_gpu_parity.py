@@ -172,12 +172,12 @@ def test_sweeps_match_oracle_c1_shape(cuda_lib, solve):
 
 @pytest.mark.parametrize("dims,R", [((24, 22, 20), 4), ((14, 13, 12, 11), 3), ((9, 8, 8, 7, 6), 2),
                                     ((30, 30, 30), 6)])
-@pytest.mark.parametrize("solve", ["qr", "svd"])
+@pytest.mark.parametrize("solve", ["qr", "svd", "normal", "normal_pinv"])
 def test_dimension_tree_sweeps_match_oracle(cuda_lib, dims, R, solve):
     # sweeps with the dimension tree (two passes over X per sweep) against the
     # oracle's per-mode Multi-TTMs: only rounding differs
     p = inputs.planted(dims, R, seed=31, init_seed=32, noise=0.02)
-    osolve = oracle.QR if solve == "qr" else oracle.SVD
+    osolve = OSOLVE[solve]
     o = oracle.OracleCPALS(p.X, p.dims, R)
     o.set_factors(p.init_factors)
     _, fits_o = o.iterate(6, solve=osolve, rtol=1e-12)
@@ -398,3 +398,17 @@ def test_mixed_precisions_recover_planted_factors_like_fp64(cuda_lib):
     assert scores["f64"] >= 0.95, scores
     for prec in ["f32", "bf16x3", "tf32x3"]:
         assert abs(scores[prec] - scores["f64"]) <= 1e-3, scores
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16x3", "tf32x3"])
+def test_mixed_mttkrp_error_bound(cuda_lib, precision):
+    # the MTTKRP of the normal equations with FP32 passes over X; at rank 16
+    # its first contraction runs on the tensor cores (split products)
+    dims, R = (40, 36, 32), 16
+    X, A = gaussian_problem(dims, R, seed=19)
+    h = gpu_handle(dims, R, X, A, precision=precision)
+    u = {"f32": 2.0 ** -24, **TC_U}[precision]
+    tol = 2.0 * u * np.sqrt(max(dims)) + 4.0 * 2.0 ** -24 * np.sqrt(max(dims))
+    for n in range(len(dims)):
+        err = rel(h.mttkrp(n), oracle.mttkrp(X, dims, n, A))
+        assert err <= tol, (n, err, tol)
