@@ -89,8 +89,11 @@ def test_factor_qr_matches_oracle(cuda_lib, m, R):
     assert (np.diag(Rm) >= 0).all()
 
 
+# R <= 32 goes through the staircase QR of each Khatri-Rao step (rows ordered
+# by max(i, j)); R = 1 and R = 32 are its edges; R = 48 the dense TSQR
 @pytest.mark.parametrize("dims,R", [((6, 5, 7), 3), ((20, 20, 20), 10), ((12, 11, 10, 9), 5), ((30, 30, 30), 16),
-                                    ((7, 6, 5, 4, 3), 3), ((20, 20, 20, 20), 20)])
+                                    ((7, 6, 5, 4, 3), 3), ((20, 20, 20, 20), 20), ((5, 4, 3), 1),
+                                    ((40, 36, 34), 32), ((10, 9, 8, 7), 7), ((50, 49, 48), 48)])
 def test_krp_qr_matches_oracle(cuda_lib, dims, R):
     X, A = gaussian_problem(dims, R, seed=3)
     o = oracle.OracleCPALS(X, dims, R)
