@@ -16,7 +16,7 @@ namespace cpals {
 
 namespace {
 
-constexpr int kQrThreads = 256;
+constexpr int kQrThreads = 512;
 constexpr double kEps = 2.220446049250313e-16;
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -53,12 +53,18 @@ __global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
     __syncthreads();
 
     const int kmax = min(mb, n);
+    // warp 0 updates column j+1 first in step j and then already holds the norm
+    // of W(j+2:mb, j+1) that step j+1's reflector needs
+    double s_next = 0.0;
     for (int j = 0; j < kmax; ++j) {
         // norm of W(j+1:mb, j) -- warp 0
         if (warp == 0) {
-            double s = 0.0;
-            for (int i = j + 1 + lane; i < mb; i += 32) s = fma(W[i + mb * j], W[i + mb * j], s);
-            s = warp_sum(s);
+            double s = s_next;
+            if (j == 0 || tau[j - 1] == 0.0) {
+                s = 0.0;
+                for (int i = j + 1 + lane; i < mb; i += 32) s = fma(W[i + mb * j], W[i + mb * j], s);
+                s = warp_sum(s);
+            }
             if (lane == 0) {
                 const double alpha = W[j + mb * j];
                 double t = 0.0, scale = 0.0, beta = alpha;
@@ -90,10 +96,14 @@ __global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
                     s = fma(v, W[i + mb * k], s);
                 }
                 s = warp_sum(s) * tj;
+                double s2 = 0.0;
                 for (int i = j + lane; i < mb; i += 32) {
                     const double v = (i == j) ? 1.0 : W[i + mb * j];
-                    W[i + mb * k] = fma(-s, v, W[i + mb * k]);
+                    const double w = fma(-s, v, W[i + mb * k]);
+                    W[i + mb * k] = w;
+                    if (i > k) s2 = fma(w, w, s2);
                 }
+                if (k == j + 1) s_next = warp_sum(s2);   // warp 0: next reflector's norm
             }
         }
         __syncthreads();
