@@ -415,3 +415,47 @@ def test_mixed_mttkrp_error_bound(cuda_lib, precision):
     for n in range(len(dims)):
         err = rel(h.mttkrp(n), oracle.mttkrp(X, dims, n, A))
         assert err <= tol, (n, err, tol)
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "tf32x3"])
+def test_full_size_tensor_core_multi_ttm_sampled_rows(cuda_lib, precision):
+    # the 1000^3 rank-64 workload's size and launch configuration: the
+    # persistent TMA pipeline over 7813 row tiles with Q tiles streamed
+    # through the operand ring (K = 1000); rows of Y_(0) (1000 x 4096) against
+    # Q_1^T X_i Q_2 in FP64 from the sampled slices of X, under the split
+    # products' error bound
+    n = 1000
+    R = 64
+    g = torch.Generator(device="cuda").manual_seed(7)
+    X = torch.randn(n * n * n, dtype=torch.float64, device="cuda", generator=g)
+    rng = np.random.default_rng(8)
+    A = [np.asfortranarray(rng.standard_normal((n, R))) for _ in range(3)]
+    h = cpals.CPALS((n, n, n), R, precision)
+    h.set_tensor(X)
+    h.set_factors(A)
+    Y, _ = h.multi_ttm(0)
+    Q = [h.get_factor_qr(m)[0] for m in range(3)]
+    X3 = X.view(n, n, n)                  # [i2][i1][i0]: mode 0 fastest
+    tol = 2.0 * TC_U[precision] * np.sqrt(n) + 4.0 * 2.0 ** -24 * np.sqrt(n)
+    for i in (0, 1, 517, 998, 999):
+        Xi = X3[:, :, i].cpu().numpy().T  # (i1, i2)
+        ref = Q[1].T @ Xi @ Q[2]          # (r1, r2); Y_(0) column r1 + R r2
+        got = Y[i].reshape((R, R), order="F")
+        assert rel(got, ref) <= tol, (i, rel(got, ref), tol)
+    del X, X3
+
+
+@pytest.mark.parametrize("precision", ["bf16x3", "f32"])
+def test_full_size_mixed_multi_ttm_c3(cuda_lib, precision):
+    # the 4-way 120^4 rank-20 workload at full size: one Multi-TTM per mode
+    # against the FP64 oracle with the same Q_m
+    p = inputs.workload_c3()
+    Q = [oracle.qr(a)[0] for a in p.init_factors]
+    h = gpu_handle(p.dims, p.rank, p.X, precision=precision)
+    h.set_factor_qr(Q, [oracle.qr(a)[1] for a in p.init_factors])
+    u = {"f32": 2.0 ** -24, **TC_U}[precision]
+    tol = 2.0 * u * np.sqrt(120) + 4.0 * 2.0 ** -24 * np.sqrt(120)
+    for n in (0, 3):
+        Y, _ = h.multi_ttm(n)
+        err = rel(Y, oracle.multi_ttm(p.X, p.dims, n, Q))
+        assert err <= tol, (n, err, tol)
