@@ -543,45 +543,42 @@ __global__ void trsm_qr_kernel(const double* __restrict__ W, const double* __res
 // on pair l, warp w on rows [w RW, (w+1) RW): the three dot products of a
 // pair are summed over the warps in a fixed order, warp 0 forms all rotations
 // of the round at once, and every warp rotates its rows of B and V.  A pair is
-// rotated while the cosine of the angle between its columns exceeds R * eps
-// (the rounding level of their length-R dot product); a sweep with no
-// rotation ends the iteration.
+// rotated while the cosine of the angle between its columns exceeds R times
+// the unit roundoff of the arithmetic (the rounding level of their length-R
+// dot product); a sweep with no rotation ends the iteration.
+//
+// At R >= 32 the sweeps start from an FP32 preconditioner: one-sided Jacobi
+// of R0 in FP32 (whose pipe issues 64 times faster than FP64 here) gives an
+// orthogonal-to-FP32 V32 (sweeps stop below 8 R u_32 or after 20); one
+// Newton-Schulz step V <- V (3 I - V^T V) / 2 in FP64 squares its distance
+// from orthogonality (about 1e-6 -> 1e-12); then the
+// FP64 sweeps run on B = R0 V, which is already nearly column-orthogonal, and
+// converge in a few sweeps instead of about twelve.  The result is the SVD of
+// R0 to FP64 accuracy either way.
 constexpr int kJacobiWarps = 8;
 constexpr int kJacobiThreads = 32 * kJacobiWarps;
+constexpr int kJacobiMixedMinR = 32;
 
 __host__ __device__ constexpr size_t jacobi_smem_doubles()
 {
-    return (size_t)2 * kMaxRank * (kMaxRank + 1) + (size_t)kJacobiWarps * 32 * 3 + 32 * 3 + 2 * kMaxRank;
+    // B, V (FP64), B32, V32 (FP32, half the space), G (FP64 R x R), partial sums, rotations, sigma, 1/sigma^2
+    return (size_t)2 * kMaxRank * (kMaxRank + 1) + (size_t)kMaxRank * (kMaxRank + 1) +
+           (size_t)kMaxRank * kMaxRank + (size_t)kJacobiWarps * 32 * 3 + 32 * 3 + 2 * kMaxRank;
 }
 
-__global__ void __launch_bounds__(kJacobiThreads) jacobi_pinv_kernel(const double* __restrict__ R0, int R,
-                                                                    double rtol, double* __restrict__ T,
-                                                                    const int* __restrict__ status)
+// Sweeps of one-sided Jacobi on the columns of B (R x Rp, leading dimension
+// ld), accumulating the rotations into V.  Block-wide; returns the sweep count.
+template <typename T>
+__device__ int jacobi_sweeps(T* B, T* V, int ld, int R, T tol, int max_sweeps, T* part, T* rot, int* rotated)
 {
-    if (*status != kStatusOk) return;
-    extern __shared__ double jsm[];
-    const int ld = R + 1;                     // odd: lanes on different columns hit different banks
-    double* B = jsm;                          // R x Rp
-    double* V = B + (size_t)kMaxRank * (kMaxRank + 1);
-    double* part = V + (size_t)kMaxRank * (kMaxRank + 1);   // [warp][pair][3]
-    double* rot = part + kJacobiWarps * 32 * 3;             // [pair][c, s, flag]
-    double* sig = rot + 32 * 3;                             // R
-    double* isq = sig + kMaxRank;                           // R: 1 / sigma_j^2 or 0 (truncated)
-    __shared__ int rotated;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Rp = (R + 1) & ~1;   // padded to even; column R (if any) is a zero dummy
     const int np = Rp / 2;
     const int RW = (R + kJacobiWarps - 1) / kJacobiWarps;
     const int i0 = warp * RW, i1 = min(R, i0 + RW);
-    const double tol = (double)R * kEps;
-    for (int e = tid; e < Rp * R; e += kJacobiThreads) {
-        const int j = e / R, i = e - j * R;
-        B[i + ld * j] = (j < R) ? R0[i + R * j] : 0.0;
-        V[i + ld * j] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    for (int sweep = 0; sweep < 80; ++sweep) {
-        if (tid == 0) rotated = 0;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) *rotated = 0;
         for (int round = 0; round < Rp - 1; ++round) {
             // round-robin pairing: position 0 fixed, others rotate
             const int pi = lane;
@@ -594,53 +591,123 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_pinv_kernel(const doubl
             }
             const bool live = pi < np && q < R;   // q == R: the dummy column
             if (live) {
-                double sa = 0.0, sb = 0.0, sg = 0.0;
+                T sa = 0, sb = 0, sg = 0;
                 for (int i = i0; i < i1; ++i) {
-                    const double bp = B[i + ld * p], bq = B[i + ld * q];
+                    const T bp = B[i + ld * p], bq = B[i + ld * q];
                     sa = fma(bp, bp, sa);
                     sb = fma(bq, bq, sb);
                     sg = fma(bp, bq, sg);
                 }
-                double* pp = part + (warp * 32 + pi) * 3;
+                T* pp = part + (warp * 32 + pi) * 3;
                 pp[0] = sa; pp[1] = sb; pp[2] = sg;
             }
             __syncthreads();
             if (warp == 0) {
-                double c = 1.0, sn = 0.0, flag = 0.0;
+                T c = 1, sn = 0, flag = 0;
                 if (live) {
-                    double sa = 0.0, sb = 0.0, sg = 0.0;
+                    T sa = 0, sb = 0, sg = 0;
                     for (int w = 0; w < kJacobiWarps; ++w) {
-                        const double* pp = part + (w * 32 + pi) * 3;
+                        const T* pp = part + (w * 32 + pi) * 3;
                         if (w * RW < R) { sa += pp[0]; sb += pp[1]; sg += pp[2]; }
                     }
-                    if (sg != 0.0 && fabs(sg) > tol * sqrt(sa * sb)) {
-                        const double zeta = (sb - sa) / (2.0 * sg);
-                        const double t = ((zeta >= 0.0) ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                    if (sg != T(0) && fabs(sg) > tol * sqrt(sa * sb)) {
+                        const T zeta = (sb - sa) / (T(2) * sg);
+                        const T t = ((zeta >= T(0)) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        c = T(1) / sqrt(T(1) + t * t);
                         sn = c * t;
-                        flag = 1.0;
+                        flag = 1;
                     }
                 }
                 if (pi < 32) { rot[3 * pi] = c; rot[3 * pi + 1] = sn; rot[3 * pi + 2] = flag; }
-                if (__any_sync(0xffffffffu, flag != 0.0) && lane == 0) rotated = 1;
+                if (__any_sync(0xffffffffu, flag != T(0)) && lane == 0) *rotated = 1;
             }
             __syncthreads();
-            if (live && rot[3 * pi + 2] != 0.0) {
-                const double c = rot[3 * pi], sn = rot[3 * pi + 1];
+            if (live && rot[3 * pi + 2] != T(0)) {
+                const T c = rot[3 * pi], sn = rot[3 * pi + 1];
                 for (int i = i0; i < i1; ++i) {
-                    const double bp = B[i + ld * p], bq = B[i + ld * q];
+                    const T bp = B[i + ld * p], bq = B[i + ld * q];
                     B[i + ld * p] = c * bp - sn * bq;
                     B[i + ld * q] = sn * bp + c * bq;
-                    const double vp = V[i + ld * p], vq = V[i + ld * q];
+                    const T vp = V[i + ld * p], vq = V[i + ld * q];
                     V[i + ld * p] = c * vp - sn * vq;
                     V[i + ld * q] = sn * vp + c * vq;
                 }
             }
             __syncthreads();
         }
-        if (!rotated) break;   // uniform: read after the round's last barrier
-        __syncthreads();       // nobody clears `rotated` before everyone has read it
+        if (!*rotated) break;   // uniform: read after the round's last barrier
+        __syncthreads();        // nobody clears the flag before everyone has read it
     }
+    return sweep;
+}
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_pinv_kernel(const double* __restrict__ R0, int R,
+                                                                    double rtol, double* __restrict__ T,
+                                                                    const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    extern __shared__ double jsm[];
+    const int ld = R + 1;                     // odd: lanes on different columns hit different banks
+    const int Rp = (R + 1) & ~1;
+    double* B = jsm;                          // R x Rp
+    double* V = B + (size_t)kMaxRank * (kMaxRank + 1);
+    float* B32 = reinterpret_cast<float*>(V + (size_t)kMaxRank * (kMaxRank + 1));
+    float* V32 = B32 + (size_t)kMaxRank * (kMaxRank + 1);
+    double* G = reinterpret_cast<double*>(V32 + (size_t)kMaxRank * (kMaxRank + 1));   // R x R
+    double* part = G + (size_t)kMaxRank * kMaxRank;          // [warp][pair][3]
+    double* rot = part + kJacobiWarps * 32 * 3;             // [pair][c, s, flag]
+    double* sig = rot + 32 * 3;                             // R
+    double* isq = sig + kMaxRank;                           // R: 1 / sigma_j^2 or 0 (truncated)
+    __shared__ int rotated;
+    const int tid = threadIdx.x;
+    if (R >= kJacobiMixedMinR) {
+        // FP32 preconditioner
+        for (int e = tid; e < Rp * R; e += kJacobiThreads) {
+            const int j = e / R, i = e - j * R;
+            B32[i + ld * j] = (j < R) ? (float)R0[i + R * j] : 0.0f;
+            V32[i + ld * j] = (i == j) ? 1.0f : 0.0f;
+        }
+        __syncthreads();
+        // stop at 8 R u_32 (clear of the FP32 rounding level of the dot products);
+        // the FP64 sweeps converge quadratically from there
+        jacobi_sweeps<float>(B32, V32, ld, R, 8.0f * (float)R * 5.9604645e-8f, 20, reinterpret_cast<float*>(part),
+                             reinterpret_cast<float*>(rot), &rotated);
+        // G = V32^T V32 in FP64; V = V32 (3 I - G) / 2
+        for (int e = tid; e < R * R; e += kJacobiThreads) {
+            const int b = e / R, a = e - b * R;
+            double s = 0.0;
+            for (int i = 0; i < R; ++i) s = fma((double)V32[i + ld * a], (double)V32[i + ld * b], s);
+            G[a + R * b] = s;
+        }
+        __syncthreads();
+        for (int e = tid; e < Rp * R; e += kJacobiThreads) {
+            const int j = e / R, i = e - j * R;
+            double s = 0.0;
+            if (j < R) {
+                for (int k = 0; k < R; ++k) s = fma((double)V32[i + ld * k], (k == j ? 3.0 : 0.0) - G[k + R * j], s);
+                s *= 0.5;
+            }
+            V[i + ld * j] = s;
+        }
+        __syncthreads();
+        // B = R0 V (the input is a full matrix: R0, or S for the pseudo-inverse solve)
+        for (int e = tid; e < Rp * R; e += kJacobiThreads) {
+            const int j = e / R, i = e - j * R;
+            double s = 0.0;
+            if (j < R)
+                for (int k = 0; k < R; ++k) s = fma(R0[i + R * k], V[k + ld * j], s);
+            B[i + ld * j] = s;
+        }
+        __syncthreads();
+    } else {
+        for (int e = tid; e < Rp * R; e += kJacobiThreads) {
+            const int j = e / R, i = e - j * R;
+            B[i + ld * j] = (j < R) ? R0[i + R * j] : 0.0;
+            V[i + ld * j] = (i == j) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+    }
+    jacobi_sweeps<double>(B, V, ld, R, (double)R * kEps, 80, part, rot, &rotated);
     for (int j = tid; j < R; j += kJacobiThreads) {
         double s = 0.0;
         for (int i = 0; i < R; ++i) s = fma(B[i + ld * j], B[i + ld * j], s);

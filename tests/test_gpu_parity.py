@@ -459,3 +459,22 @@ def test_full_size_mixed_multi_ttm_c3(cuda_lib, precision):
         Y, _ = h.multi_ttm(n)
         err = rel(Y, oracle.multi_ttm(p.X, p.dims, n, Q))
         assert err <= tol, (n, err, tol)
+
+
+@pytest.mark.parametrize("solve", ["svd", "normal_pinv"])
+def test_truncated_solves_at_rank_40_match_oracle(cuda_lib, solve):
+    # rank >= 32 takes the FP32-preconditioned Jacobi SVD; with columns 38
+    # and 39 equal in every factor, R0 (and S) lose one rank exactly and the
+    # truncated solve must match the oracle's minimum-norm update
+    dims, R = (45, 44, 43), 40
+    X, A = gaussian_problem(dims, R, seed=29)
+    for m in range(3):
+        A[m][:, 39] = A[m][:, 38]
+    h = gpu_handle(dims, R, X, A)
+    h.solve_mode(0, solve, 1e-10)
+    h.sync()
+    Ag, lam = h.get_factors()
+    o = oracle.OracleCPALS(X, dims, R)
+    o.set_factors(A)
+    o.update_mode(0, OSOLVE[solve], 1e-10)
+    assert rel(Ag[0] * lam[None, :], o.factor(0) * o.lam()[None, :]) <= 1e-8
