@@ -233,8 +233,15 @@ int cpals_sync(cpals_handle* h);
  *    Tensor Memory Accelerator, whenever the product of the dims before the
  *    contracted mode is a multiple of 4.  0 always uses one CTA per 128-row
  *    tile.  Both compute the same split products; the sums differ only in the
- *    order of two FP32 additions per output. */
-typedef enum { CPALS_OPT_DIMTREE = 0, CPALS_OPT_TC_PIPELINE = 1 } cpals_option;
+ *    order of two FP32 additions per output.
+ *  CPALS_OPT_KRP_TREE (default 1): in a dimension-tree sweep with the QR or
+ *    SVD solve, the QR of V_n follows the same halves.  The QR of the
+ *    Khatri-Rao product of each half's R_m is taken once per sweep, on a side
+ *    stream while X is contracted, and each mode folds only the R_m of its own
+ *    half onto the other half's R and applies that half's Q as a Kronecker
+ *    factor (Eq. kr-id).  0 folds all N-1 factors for every mode.  The Q0, R0
+ *    differ only by rounding. */
+typedef enum { CPALS_OPT_DIMTREE = 0, CPALS_OPT_TC_PIPELINE = 1, CPALS_OPT_KRP_TREE = 2 } cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
 
 /* Number of kernel launches the handle has issued so far (graph replays count

@@ -194,6 +194,10 @@ class CPALS:
         """CPALS_OPT_TC_PIPELINE: persistent TMA-fed tensor-core kernel for the pass over X."""
         _check(self._h, load().cpals_set_option(self._h, 1, 1 if on else 0))
 
+    def set_krp_tree(self, on: bool):
+        """CPALS_OPT_KRP_TREE: per-half QR of the Khatri-Rao products in dimension-tree sweeps."""
+        _check(self._h, load().cpals_set_option(self._h, 2, 1 if on else 0))
+
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
 

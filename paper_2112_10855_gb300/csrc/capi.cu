@@ -50,6 +50,7 @@ void free_all(Handle* h)
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->A[m]); f(h->Q[m]); f(h->Rf[m]); f(h->G[m]); }
     f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
+    f(h->HQ[0]); f(h->HQ[1]); f(h->HR[0]); f(h->HR[1]); f(h->Qin);
     f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->KV[m]); f(h->KC[m]); f(h->KE[m]); }
@@ -142,8 +143,18 @@ void factors_changed(Handle* h)
     for (int m = 0; m < h->N; ++m) { h->kc_valid[m] = false; h->ke_valid[m] = false; }
 }
 
+// Where the QR of V_n comes from in a dimension-tree sweep: the QR of the
+// other half's Khatri-Rao product (slot) and the own half's other modes.
+struct TreeQR {
+    int slot;
+    bool other_left;
+    const int* own;
+    int nown;
+};
+
 // One mode update (Alg. cp-als-qr mode-loop body, or Alg. cp-als for NORMAL).
-cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_partial = false)
+cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_partial = false,
+                        const TreeQR* tq = nullptr)
 {
     CPALS_CUDA_TRY(refresh_derived(h, solve, n));
     const int64_t In = h->dims[n];
@@ -190,7 +201,8 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         cudaStream_t main = h->stream;
         h->stream = h->side;
-        cudaError_t e = cpals::krp_qr(h, n);
+        cudaError_t e = tq ? cpals::krp_qr_tree(h, n, tq->slot, tq->other_left, tq->own, tq->nown)
+                           : cpals::krp_qr(h, n);
         h->stream = main;
         CPALS_CUDA_TRY(e);
         CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
@@ -241,10 +253,48 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
     auto pass = [&](const int* modes, int nm) {
         return is_normal(solve) ? cpals::mttkrp_tree_pass(h, modes, nm) : cpals::dimtree_pass(h, modes, nm);
     };
+    if (is_normal(solve) || !h->krp_tree) {
+        CPALS_CUDA_TRY(pass(H2, n2));
+        for (int k = 0; k < n1; ++k) CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true));
+        CPALS_CUDA_TRY(pass(H1, n1));
+        for (int k = 0; k < n2; ++k) CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true));
+        return cpals::fit_efficient(h, solve);
+    }
+    // The QR of V_n follows the same tree: V_n of an H1 mode is (Khatri-Rao of
+    // H2) (.) (the other H1 modes), and the H2 factors do not change while H1
+    // is updated, so the QR of the H2 half is taken once, on the side stream
+    // under the pass over X for H1's partial; the QR of the H1 half likewise
+    // under the second pass.  Each mode then folds only its own half's other
+    // R_m onto that half's R and applies the half's Q as a Kronecker factor
+    // (Eq. kr-id), which leaves the same Q0, R0 up to rounding.
+    auto half_qr = [&](const int* modes, int nm, int slot) -> cudaError_t {
+        CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+        CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        cudaStream_t main = h->stream;
+        h->stream = h->side;
+        cudaError_t e = cpals::krp_qr_half(h, modes, nm, slot);
+        h->stream = main;
+        return e;
+    };
+    int own[cpals::kMaxN];
+    auto own_of = [&](const int* modes, int nm, int n) {
+        int c = 0;
+        for (int k = 0; k < nm; ++k)
+            if (modes[k] != n) own[c++] = modes[k];
+        return c;
+    };
+    CPALS_CUDA_TRY(half_qr(H2, n2, 1));
     CPALS_CUDA_TRY(pass(H2, n2));
-    for (int k = 0; k < n1; ++k) CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true));
+    for (int k = 0; k < n1; ++k) {
+        const TreeQR tq{1, true, own, own_of(H1, n1, H1[k])};
+        CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true, &tq));
+    }
+    CPALS_CUDA_TRY(half_qr(H1, n1, 0));
     CPALS_CUDA_TRY(pass(H1, n1));
-    for (int k = 0; k < n2; ++k) CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true));
+    for (int k = 0; k < n2; ++k) {
+        const TreeQR tq{0, false, own, own_of(H2, n2, H2[k])};
+        CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true, &tq));
+    }
     return cpals::fit_efficient(h, solve);
 }
 
@@ -350,6 +400,13 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
         ok = cudaMalloc(&pa, tsz * h->tA_elems) == cudaSuccess;
         h->tA = pa;
         if (ok) h->owned_bytes += tsz * h->tA_elems;
+        // per-half QR of the Khatri-Rao products: R^|H1| and R^|H2| rows; the
+        // inner fold of a mode has R^|H1| rows at most (|H1| >= |H2|)
+        int64_t r1 = 1, r2 = 1;
+        for (int m = 0; m < N; ++m) (m < h1 ? r1 : r2) *= rank;
+        ok = ok && dalloc(h, &h->HQ[0], r1 * R) == cudaSuccess && dalloc(h, &h->HQ[1], r2 * R) == cudaSuccess &&
+             dalloc(h, &h->HR[0], (size_t)R * R) == cudaSuccess && dalloc(h, &h->HR[1], (size_t)R * R) == cudaSuccess &&
+             dalloc(h, &h->Qin, r1 * R) == cudaSuccess;
     }
     if (ok) {
         void* p0 = nullptr; void* p1 = nullptr;
@@ -853,9 +910,18 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
 {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
-    if ((option != CPALS_OPT_DIMTREE && option != CPALS_OPT_TC_PIPELINE) || (value != 0 && value != 1))
+    if ((option != CPALS_OPT_DIMTREE && option != CPALS_OPT_TC_PIPELINE && option != CPALS_OPT_KRP_TREE) ||
+        (value != 0 && value != 1))
         return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
     const bool v = value != 0;
+    if (option == CPALS_OPT_KRP_TREE) {
+        if (v != h->krp_tree) {
+            h->krp_tree = v;
+            for (int s = 0; s < 4; ++s)         // captured sweeps follow the old schedule
+                if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
+        }
+        return CPALS_OK;
+    }
     if (option == CPALS_OPT_TC_PIPELINE) {
         if (v != h->tc_pipe) {
             h->tc_pipe = v;

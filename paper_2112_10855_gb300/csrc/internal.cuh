@@ -87,6 +87,17 @@ struct Handle {
     double* KR[2] = {nullptr, nullptr};
     double* KQb[2] = {nullptr, nullptr};
     int krp_mode = -1;       // mode whose Q0/R0 are current
+    // tree-structured QR of V_n in a dimension-tree sweep: the QR of the
+    // Khatri-Rao product of each half's R_m (HQ[s] rows x R, HR[s]), computed
+    // once per sweep; a half of one mode keeps Q = I and R = its own R_m.
+    // Qin holds the inner fold (R x own factors) before the Kronecker apply.
+    bool krp_tree = true;
+    double* HQ[2] = {nullptr, nullptr};
+    double* HR[2] = {nullptr, nullptr};
+    const double* hr_ptr[2] = {nullptr, nullptr};
+    bool hq_single[2] = {false, false};
+    int64_t hq_rows[2] = {0, 0};
+    double* Qin = nullptr;
 
     // TTM intermediates (ping-pong), in the Multi-TTM's arithmetic type
     void* tbuf[2] = {nullptr, nullptr};
@@ -192,6 +203,17 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
 // With implicit = true Q0 is not formed either: the Q factors of the fold steps
 // go to h->KP (for the Kruskal-input path) and only R0 is written.
 cudaError_t krp_qr(Handle* h, int n, bool implicit = false);
+// QR of the Khatri-Rao product of the upper-triangular factors Rl[cnt-1] (.)
+// ... (.) Rl[0] (Rl[0] fastest), cnt >= 2, by the Kronecker fold; explicit Q
+// to Qout (R^cnt x R) and R to Rout, or the step Q's to h->KP (implicit).
+cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, double* Rout, bool implicit);
+// QR of the Khatri-Rao product of the R_m of one half of the modes (ascending
+// list) into h->HQ[slot], h->HR[slot] (a single mode: Q = I, R = its R_m).
+cudaError_t krp_qr_half(Handle* h, const int* modes, int cnt, int slot);
+// Q0, R0 of V_n from the QR of the other half (slot) and the R_m of the own
+// half's other modes (ascending list own[0..nown)): other_left = true when the
+// other half holds the higher (slower) modes.
+cudaError_t krp_qr_tree(Handle* h, int n, int slot, bool other_left, const int* own, int nown);
 // C (m x n) = A (m x k) B (k x n), FP64, column-major, on the TTM kernel (one thread per output row, R-wide
 // register tile, split-K): used for W = Y_(n) Q0 and W T.
 cudaError_t gemm_rows(Handle* h, const double* A, int64_t m, int64_t k, const double* B, int n, double* C);

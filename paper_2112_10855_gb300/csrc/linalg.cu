@@ -477,20 +477,41 @@ __global__ void krp2_kernel(const double* __restrict__ F, const double* __restri
     }
 }
 
-// out = (I_R (x) Qb) Qp: out(i*S + j, c) = sum_c' Qb(j, c') Qp(i*R + c', c),
-// with Qb of size S x R and Qp of size R^2 x R (Kronecker index rule, Sec. 2.2).
+// out = (I_outer (x) Qb) Qp: out(i*S + j, c) = sum_c' Qb(j, c') Qp(i*R + c', c),
+// with Qb of size S x R and Qp of size (outer R) x R (Kronecker index rule,
+// Sec. 2.2).
 __global__ void kron_left_apply_kernel(const double* __restrict__ Qb, int64_t S, const double* __restrict__ Qp,
-                                       int R, double* __restrict__ out, const int* __restrict__ status)
+                                       int R, int64_t outer, double* __restrict__ out, const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
-    const int64_t rows = (int64_t)R * S, total = rows * R;
+    const int64_t rows = outer * S, total = rows * R;
+    const int64_t ldp = outer * R;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / rows, row = e - c * rows;
         const int64_t i = row / S, j = row - i * S;
-        const double* qp = Qp + i * R + (int64_t)R * R * c;
+        const double* qp = Qp + i * R + ldp * c;
         double acc = 0.0;
         for (int cp = 0; cp < R; ++cp) acc = fma(Qb[j + S * cp], qp[cp], acc);
+        out[e] = acc;
+    }
+}
+
+// out = (Qa (x) I_S) Qp: out(a*S + j, c) = sum_c' Qa(a, c') Qp(c'*S + j, c),
+// with Qa of size Sa x R and Qp of size (R S) x R.
+__global__ void kron_right_apply_kernel(const double* __restrict__ Qa, int64_t Sa, const double* __restrict__ Qp,
+                                        int R, int64_t S, double* __restrict__ out, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t rows = Sa * S, total = rows * R;
+    const int64_t ldp = (int64_t)R * S;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / rows, row = e - c * rows;
+        const int64_t a = row / S, j = row - a * S;
+        const double* qp = Qp + j + ldp * c;
+        double acc = 0.0;
+        for (int cp = 0; cp < R; ++cp) acc = fma(Qa[a + Sa * cp], qp[(int64_t)cp * S], acc);
         out[e] = acc;
     }
 }
@@ -1033,56 +1054,127 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
 // step to build the explicit Q0 (R^{N-1} x R).  The thin QR with diag(R0) >= 0
 // is unique, so this equals the Householder QR of the explicit V_n up to
 // rounding.
-cudaError_t krp_qr(Handle* h, int n, bool implicit)
+// QR of the Khatri-Rao product Rl[cnt-1] (.) ... (.) Rl[0] of upper-triangular
+// R x R factors (Rl[0] rightmost: its row index runs fastest), cnt >= 2, by
+// the Kronecker fold: if B = Q_B R_B then F (.) B = (I (x) Q_B)(F (.) R_B)
+// (Eq. kr-id), so each step is the QR of a Khatri-Rao product of two
+// triangular factors.  Writes the explicit Q (R^cnt x R) to Qout and R to
+// Rout; with implicit = true the Q factor of every step goes to h->KP instead
+// (the Kruskal-input path applies Q0 in that factored form).
+cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, double* Rout, bool implicit)
 {
+    if (cnt < 2) return cudaErrorInvalidValue;
     CPALS_CUDA_TRY(qr_kernel_attrs());
     const int R = h->R;
     const size_t R3 = (size_t)R * R * R;
-    int modes[kMaxN];
-    int cnt = 0;
-    for (int m = 0; m < h->N; ++m)
-        if (m != n) modes[cnt++] = m;   // ascending: modes[0] is the fastest (rightmost) factor
-    if (cnt == 1) return householder_qr(h, h->Rf[modes[0]], R, R, implicit ? h->KP : h->Q0, h->R0);
-    const double* curR = h->Rf[modes[0]];
+    const double* curR = Rl[0];
     int64_t S = 0;                       // rows of the current Q_B (0: Q_B = I)
     for (int k = 1; k < cnt; ++k) {
         const bool last = (k == cnt - 1);
-        double* Rout = last ? h->R0 : h->KR[k & 1];
-        // QR of F (.) R_B, F = R_{m_k}: both factors are upper triangular
-        auto step_qr = [&](double* Qout) -> cudaError_t {
+        double* Ro = last ? Rout : h->KR[k & 1];
+        // QR of F (.) R_B, F = Rl[k]: both factors are upper triangular
+        auto step_qr = [&](double* Qo) -> cudaError_t {
             if (R <= kStairMaxN) {
-                krp_stair_qr_kernel<<<1, kQrThreads, stair_smem_bytes(R), h->stream>>>(h->Rf[modes[k]], curR, R,
-                                                                                       Qout, Rout, h->d_status);
+                krp_stair_qr_kernel<<<1, kQrThreads, stair_smem_bytes(R), h->stream>>>(Rl[k], curR, R, Qo, Ro,
+                                                                                       h->d_status);
                 h->launches++;
                 return cudaGetLastError();
             }
-            krp2_kernel<<<grid_for((int64_t)R * R * R, 256, h->num_sms), 256, 0, h->stream>>>(
-                h->Rf[modes[k]], curR, R, h->KM, h->d_status);
+            krp2_kernel<<<grid_for((int64_t)R * R * R, 256, h->num_sms), 256, 0, h->stream>>>(Rl[k], curR, R, h->KM,
+                                                                                              h->d_status);
             h->launches++;
             CPALS_CUDA_TRY(cudaGetLastError());
-            return householder_qr(h, h->KM, (int64_t)R * R, R, Qout, Rout);
+            return householder_qr(h, h->KM, (int64_t)R * R, R, Qo, Ro);
         };
         if (implicit) {
-            // keep the step's Q factor: Q0 = (I (x) Q_{k-1}) P_k is applied later in factored form
             CPALS_CUDA_TRY(step_qr(h->KP + (size_t)(k - 1) * R3));
         } else if (S == 0) {
-            // Q_B = I: the QR of F (.) R_B is already Q0 (or the next Q_B)
-            double* Qout = last ? h->Q0 : h->KQb[k & 1];
-            CPALS_CUDA_TRY(step_qr(Qout));
+            // Q_B = I: the QR of F (.) R_B is already the result (or the next Q_B)
+            CPALS_CUDA_TRY(step_qr(last ? Qout : h->KQb[k & 1]));
             S = (int64_t)R * R;
         } else {
             CPALS_CUDA_TRY(step_qr(h->KQ));
             const double* Qb = h->KQb[(k - 1) & 1];
-            double* Qout = last ? h->Q0 : h->KQb[k & 1];
+            double* Qo = last ? Qout : h->KQb[k & 1];
             kron_left_apply_kernel<<<grid_for((int64_t)R * S * R, 256, h->num_sms), 256, 0, h->stream>>>(
-                Qb, S, h->KQ, R, Qout, h->d_status);
+                Qb, S, h->KQ, R, (int64_t)R, Qo, h->d_status);
             h->launches++;
             CPALS_CUDA_TRY(cudaGetLastError());
             S *= R;
         }
-        curR = Rout;
+        curR = Ro;
     }
     return cudaSuccess;
+}
+
+cudaError_t krp_qr(Handle* h, int n, bool implicit)
+{
+    CPALS_CUDA_TRY(qr_kernel_attrs());
+    const int R = h->R;
+    const double* Rl[kMaxN];
+    int cnt = 0;
+    for (int m = 0; m < h->N; ++m)
+        if (m != n) Rl[cnt++] = h->Rf[m];   // ascending: Rl[0] is the fastest (rightmost) factor
+    if (cnt == 1) return householder_qr(h, Rl[0], R, R, implicit ? h->KP : h->Q0, h->R0);
+    return fold_qr(h, Rl, cnt, implicit ? nullptr : h->Q0, h->R0, implicit);
+}
+
+cudaError_t krp_qr_half(Handle* h, const int* modes, int cnt, int slot)
+{
+    h->hq_single[slot] = (cnt == 1);
+    if (cnt == 1) {                       // one factor: its own R, Q = I
+        h->hr_ptr[slot] = h->Rf[modes[0]];
+        h->hq_rows[slot] = h->R;
+        return cudaSuccess;
+    }
+    const double* Rl[kMaxN];
+    int64_t rows = 1;
+    for (int k = 0; k < cnt; ++k) {
+        Rl[k] = h->Rf[modes[k]];
+        rows *= h->R;
+    }
+    h->hr_ptr[slot] = h->HR[slot];
+    h->hq_rows[slot] = rows;
+    return fold_qr(h, Rl, cnt, h->HQ[slot], h->HR[slot], false);
+}
+
+cudaError_t krp_qr_tree(Handle* h, int n, int slot, bool other_left, const int* own, int nown)
+{
+    const int R = h->R;
+    const double* Rl[kMaxN];
+    int cnt = 0;
+    int64_t S = 1;                        // rows of the Khatri-Rao product of the own factors
+    for (int k = 0; k < nown; ++k) S *= R;
+    (void)n;
+    if (other_left) {
+        // V_n = L (.) Own = (Q_L (x) I_S)(R_L (.) Own)
+        for (int k = 0; k < nown; ++k) Rl[cnt++] = h->Rf[own[k]];
+        Rl[cnt++] = h->hr_ptr[slot];
+        if (h->hq_single[slot]) return fold_qr(h, Rl, cnt, h->Q0, h->R0, false);
+        CPALS_CUDA_TRY(fold_qr(h, Rl, cnt, h->Qin, h->R0, false));
+        const int64_t Sa = h->hq_rows[slot];
+        kron_right_apply_kernel<<<grid_for(Sa * S * R, 256, h->num_sms), 256, 0, h->stream>>>(
+            h->HQ[slot], Sa, h->Qin, R, S, h->Q0, h->d_status);
+        h->launches++;
+        return cudaGetLastError();
+    }
+    // V_n = Own (.) M = (I_S (x) Q_M)(Own (.) R_M)
+    if (nown == 0) {
+        const int64_t rows = h->hq_rows[slot];
+        if (h->hq_single[slot]) return householder_qr(h, h->hr_ptr[slot], R, R, h->Q0, h->R0);
+        CPALS_CUDA_TRY(cudaMemcpyAsync(h->Q0, h->HQ[slot], sizeof(double) * rows * R, cudaMemcpyDeviceToDevice,
+                                       h->stream));
+        return cudaMemcpyAsync(h->R0, h->hr_ptr[slot], sizeof(double) * R * R, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    Rl[cnt++] = h->hr_ptr[slot];
+    for (int k = 0; k < nown; ++k) Rl[cnt++] = h->Rf[own[k]];
+    if (h->hq_single[slot]) return fold_qr(h, Rl, cnt, h->Q0, h->R0, false);
+    CPALS_CUDA_TRY(fold_qr(h, Rl, cnt, h->Qin, h->R0, false));
+    const int64_t Sm = h->hq_rows[slot];
+    kron_left_apply_kernel<<<grid_for(S * Sm * R, 256, h->num_sms), 256, 0, h->stream>>>(
+        h->HQ[slot], Sm, h->Qin, R, S, h->Q0, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
 }
 
 cudaError_t solve_qr(Handle* h, int64_t In)

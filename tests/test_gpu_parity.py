@@ -197,6 +197,32 @@ def test_dimension_tree_sweeps_match_oracle(cuda_lib, dims, R, solve):
     assert np.abs(fits - fits2).max() <= 1e-11
 
 
+@pytest.mark.parametrize("dims,R", [((30, 30, 30), 6), ((14, 13, 12, 11), 3), ((9, 8, 8, 7, 6), 2),
+                                    ((6, 6, 5, 5, 4, 4), 2), ((36, 35, 34, 33), 33)])
+@pytest.mark.parametrize("solve", ["qr", "svd"])
+def test_tree_qr_of_vn_sweeps_match_oracle(cuda_lib, dims, R, solve):
+    # the QR of V_n from per-half QRs (Kronecker apply of the other half's Q)
+    # against the oracle's QR of the formed V_n and against the same library
+    # folding all N-1 factors per mode; R = 33 takes the Householder step path
+    p = inputs.planted(dims, R, seed=33, init_seed=34, noise=0.02)
+    o = oracle.OracleCPALS(p.X, p.dims, R)
+    o.set_factors(p.init_factors)
+    _, fits_o = o.iterate(3, solve=OSOLVE[solve], rtol=1e-12)
+    h = gpu_handle(p.dims, R, p.X, p.init_factors)
+    fits = h.iterate(3, solve=solve, svd_rtol=1e-12)
+    assert np.abs(fits - fits_o).max() <= 1e-10
+    A, lam = h.get_factors()
+    for m in range(len(dims)):
+        assert rel(A[m], o.factor(m)) <= 1e-8
+    h2 = gpu_handle(p.dims, R, p.X, p.init_factors)
+    h2.set_krp_tree(False)
+    fits2 = h2.iterate(3, solve=solve, svd_rtol=1e-12)
+    assert np.abs(fits - fits2).max() <= 1e-11
+    A2, _ = h2.get_factors()
+    for m in range(len(dims)):
+        assert rel(A[m], A2[m]) <= 1e-9
+
+
 def test_direct_fit_and_resume(cuda_lib):
     # 10 + 10 sweeps equal 20 sweeps bit for bit (checkpoint = get/set factors)
     p = inputs.workload_c1(size=24, rank=4)
