@@ -186,21 +186,51 @@ __global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int gro
     }
 }
 
-// CTA size: FP64 is bound by the FP64 pipe of each SM, so small CTAs (64
-// rows) keep the per-SM row counts within ~3% of each other with every CTA
-// resident in one wave; FP32 is bound by HBM and uses 256-row CTAs.
-template <typename T>
-struct TtmTpb { static constexpr int value = 256; };
+// CTA size: FP32 is bound by HBM and uses 256-row CTAs.  FP64 is bound by
+// the FP64 pipe of each SM, so what counts is the largest number of rows any
+// SM holds: the CTA size (one of kF64Tpb, picked per launch) minimises
+// ceil(CTAs / SMs) x rows per CTA x indices per split, which keeps every SM
+// within a fraction of a percent of the mean at the large passes.
+constexpr int kRowsMaxTpb = 256;
 constexpr int kQuadTpb = 128;   // FP32 row-quad kernel: 512 rows per CTA
-template <>
-struct TtmTpb<double> { static constexpr int value = 64; };
+constexpr int kF64Tpb[] = {64, 96, 128};
 
 template <typename T, int RC>
-void launch_rows(dim3 grid, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s,
-                 int R, int64_t kchunk, const int* status)
+void launch_rows(dim3 grid, int tpb, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out,
+                 TtmShape s, int R, int64_t kchunk, const int* status)
 {
-    constexpr int TPB = TtmTpb<T>::value;
-    ttm_rows_kernel<T, RC, TPB><<<grid, TPB, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
+#define CPALS_TPB(C)                                                                                           \
+    case C: ttm_rows_kernel<T, RC, C><<<grid, C, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status); break;
+    if constexpr (sizeof(T) == 8) {
+        switch (tpb) {
+            CPALS_TPB(96) CPALS_TPB(128)
+            default: ttm_rows_kernel<T, RC, 64><<<grid, 64, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
+        }
+    } else {
+        (void)tpb;
+        ttm_rows_kernel<T, RC, kRowsMaxTpb><<<grid, kRowsMaxTpb, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk,
+                                                                          status);
+    }
+#undef CPALS_TPB
+}
+
+// Split of the contracted index: split K when the row blocks alone cannot
+// fill the SMs with about 2048 threads each, keeping >= 8 indices per split
+// and room for the partials and the group sums of the two-level reduction.
+inline int64_t ttm_ksplit(int64_t ctas_xy, int tpb, int64_t K, int num_sms, int64_t outn, int64_t part_elems,
+                          bool have_part)
+{
+    constexpr int64_t kMinSplitK = 8;
+    const int64_t want = (int64_t)num_sms * (2048 / tpb);
+    int64_t ks = 1;
+    if (ctas_xy < want && K >= 2 * kMinSplitK && have_part) {
+        ks = (want + ctas_xy - 1) / ctas_xy;
+        ks = std::min<int64_t>(ks, K / kMinSplitK);
+        ks = std::min<int64_t>(ks, (part_elems * 16 / 17) / std::max<int64_t>(outn, 1));
+        if (ks < 2) ks = 1;
+    }
+    const int64_t kchunk = (K + ks - 1) / ks;
+    return (K + kchunk - 1) / kchunk;
 }
 
 // Register width per thread: R itself up to 16, then 20, 24, 32 (wider R in chunks of 32).
@@ -218,27 +248,28 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     const int64_t rows = s.L * s.T;
     if (rows == 0) return cudaSuccess;
     const int rc = ttm_width(R);
-    const int tpb = sizeof(T) == 8 ? TtmTpb<double>::value : TtmTpb<float>::value;
     // FP32 with four rows per thread when the rows come in aligned quads
     const bool quad = sizeof(T) == 4 && (s.L % 4) == 0 && rc <= 24 &&
                       (((uintptr_t)in) & 15) == 0 && (((uintptr_t)out) & 15) == 0 && (((uintptr_t)part) & 15) == 0;
-    const int64_t rows_per_cta = quad ? 4 * kQuadTpb : tpb;
-    const int64_t gx = (rows + rows_per_cta - 1) / rows_per_cta;
     const int64_t gy = (R + rc - 1) / rc;
-    // split K when the row blocks alone cannot fill two waves of the SMs
-    int64_t ks = 1;
-    const int64_t want = (int64_t)h->num_sms * (2048 / tpb);   // about 2048 threads per SM
     const int64_t outn = rows * R;
-    constexpr int64_t kMinSplitK = 8;    // contracted indices per split at least
-    if (gx * gy < want && s.K >= 2 * kMinSplitK && part != nullptr) {
-        ks = (want + gx * gy - 1) / (gx * gy);
-        ks = std::min<int64_t>(ks, s.K / kMinSplitK);
-        // room for the ks partials and the ks/16 group sums of the two-level reduction
-        ks = std::min<int64_t>(ks, (part_elems * 16 / 17) / std::max<int64_t>(outn, 1));
-        if (ks < 2) ks = 1;
+    int tpb = quad ? kQuadTpb : kRowsMaxTpb;
+    int64_t rows_per_cta = quad ? 4 * kQuadTpb : tpb;
+    int64_t gx = (rows + rows_per_cta - 1) / rows_per_cta;
+    int64_t ks = ttm_ksplit(gx * gy, tpb, s.K, h->num_sms, outn, part_elems, part != nullptr);
+    if (sizeof(T) == 8) {
+        // FP64: the CTA size with the smallest per-SM share of rows x indices
+        int64_t best = -1;
+        for (int c : kF64Tpb) {
+            const int64_t cx = (rows + c - 1) / c;
+            const int64_t cks = ttm_ksplit(cx * gy, c, s.K, h->num_sms, outn, part_elems, part != nullptr);
+            const int64_t ckc = (s.K + cks - 1) / cks;
+            const int64_t ctas = cx * gy * cks;
+            const int64_t cost = ((ctas + h->num_sms - 1) / h->num_sms) * c * ckc;
+            if (best < 0 || cost < best) { best = cost; tpb = c; gx = cx; ks = cks; }
+        }
     }
     const int64_t kchunk = (s.K + ks - 1) / ks;
-    ks = (s.K + kchunk - 1) / kchunk;
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
     T* dst = (ks > 1) ? part : out;
     if (quad) {
@@ -257,7 +288,7 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
             default: return cudaErrorInvalidValue;
         }
     } else switch (rc) {
-#define CPALS_RC(W) case W: launch_rows<T, W>(grid, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
+#define CPALS_RC(W) case W: launch_rows<T, W>(grid, tpb, h->stream, in, Q, ldq, dst, s, R, kchunk, h->d_status); break;
         CPALS_RC(1) CPALS_RC(2) CPALS_RC(3) CPALS_RC(4) CPALS_RC(5) CPALS_RC(6) CPALS_RC(7) CPALS_RC(8)
         CPALS_RC(9) CPALS_RC(10) CPALS_RC(11) CPALS_RC(12) CPALS_RC(13) CPALS_RC(14) CPALS_RC(15) CPALS_RC(16)
         CPALS_RC(20) CPALS_RC(24) CPALS_RC(32)
