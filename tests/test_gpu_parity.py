@@ -76,17 +76,41 @@ def test_multi_ttm_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision):
         np.testing.assert_array_equal(Y, oracle.multi_ttm(X, dims, n, Q))
 
 
-@pytest.mark.parametrize("m,R", [(10, 10), (50, 5), (400, 10), (1000, 10), (3000, 20), (500, 64), (1, 1), (129, 64)])
+# (m, R): one Householder CTA, and the multi-launch TSQR (leaves of >= R rows
+# and the tree of triangle pairs) for the taller or wider shapes
+@pytest.mark.parametrize("m,R", [(10, 10), (50, 5), (400, 10), (1000, 10), (3000, 20), (500, 64), (1, 1), (129, 64),
+                                 (21, 10), (120, 20), (64, 32), (300, 32), (2000, 32), (2500, 32), (67, 8)])
 def test_factor_qr_matches_oracle(cuda_lib, m, R):
     rng = np.random.default_rng(m + R)
     A = np.asfortranarray(rng.standard_normal((m, R)))
     dims = (m, R, R)
     X = np.zeros(m * R * R)
-    h = gpu_handle(dims, R, X, [A, np.eye(R), np.eye(R)])
+    h = gpu_handle(dims, R, X)
+    h.set_factors([A, np.asfortranarray(np.eye(R)), np.asfortranarray(np.eye(R))])
     Q, Rm = h.get_factor_qr(0)
     Qo, Ro = oracle.qr(A)
     assert rel(Q, Qo) <= 1e-12 and rel(Rm, Ro) <= 1e-12
     assert (np.diag(Rm) >= 0).all()
+
+
+def test_factor_qr_rank_deficient(cuda_lib):
+    # a zero column and a repeated column: the thin QR is not unique there, so
+    # check the factorisation itself (Q R = A, Q^T Q = I, R upper triangular
+    # with diag(R) >= 0) and the R entries the rank fixes
+    m, R = 400, 10
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((m, R))
+    A[:, 3] = 0.0
+    A[:, 7] = A[:, 1]
+    A = np.asfortranarray(A)
+    h = gpu_handle((m, R, R), R, np.zeros(m * R * R))
+    h.set_factors([A, np.asfortranarray(np.eye(R)), np.asfortranarray(np.eye(R))])
+    Q, Rm = h.get_factor_qr(0)
+    assert np.abs(Q @ Rm - A).max() <= 1e-13 * np.abs(A).max() * m
+    assert np.abs(Q.T @ Q - np.eye(R)).max() <= 1e-13
+    assert np.allclose(np.tril(Rm, -1), 0.0) and (np.diag(Rm) >= 0).all()
+    _, Ro = oracle.qr(np.asfortranarray(A[:, :3]))
+    assert rel(Rm[:3, :3], Ro) <= 1e-12
 
 
 # R <= 32 goes through the staircase QR of each Khatri-Rao step (rows ordered
