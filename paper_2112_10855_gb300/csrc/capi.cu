@@ -145,11 +145,14 @@ void factors_changed(Handle* h)
 
 // Where the QR of V_n comes from in a dimension-tree sweep: the QR of the
 // other half's Khatri-Rao product (slot) and the own half's other modes.
+// ready = true: the sweep has already enqueued this mode's QR on the side
+// stream (followed by ev_join), so the mode update only waits for it.
 struct TreeQR {
     int slot;
     bool other_left;
     const int* own;
     int nown;
+    bool ready;
 };
 
 // One mode update (Alg. cp-als-qr mode-loop body, or Alg. cp-als for NORMAL).
@@ -197,15 +200,17 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
     } else {
         // The QR of V_n needs only the R_m and the Multi-TTM only the Q_m: run the
         // QR on the side stream meanwhile and join before W = Y_(n) Q0.
-        CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
-        CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        cudaStream_t main = h->stream;
-        h->stream = h->side;
-        cudaError_t e = tq ? cpals::krp_qr_tree(h, n, tq->slot, tq->other_left, tq->own, tq->nown)
-                           : cpals::krp_qr(h, n);
-        h->stream = main;
-        CPALS_CUDA_TRY(e);
-        CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+        if (!(tq && tq->ready)) {
+            CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+            CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            cudaStream_t main = h->stream;
+            h->stream = h->side;
+            cudaError_t e = tq ? cpals::krp_qr_tree(h, n, tq->slot, tq->other_left, tq->own, tq->nown)
+                               : cpals::krp_qr(h, n);
+            h->stream = main;
+            CPALS_CUDA_TRY(e);
+            CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+        }
         h->krp_mode = n;
         if (from_partial) CPALS_CUDA_TRY(cpals::multi_ttm_from_partial(h, n));
         else CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
@@ -283,16 +288,30 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
             if (modes[k] != n) own[c++] = modes[k];
         return c;
     };
+    // The first mode of each half needs no factor updated in that half, so its
+    // Q0, R0 follow the half's QR on the side stream, also under the pass.
+    auto early_qr = [&](int n, const TreeQR& tq) -> cudaError_t {
+        cudaStream_t main = h->stream;
+        h->stream = h->side;
+        cudaError_t e = cpals::krp_qr_tree(h, n, tq.slot, tq.other_left, tq.own, tq.nown);
+        h->stream = main;
+        CPALS_CUDA_TRY(e);
+        return cudaEventRecord(h->ev_join, h->side);
+    };
     CPALS_CUDA_TRY(half_qr(H2, n2, 1));
+    const TreeQR first1{1, true, own, own_of(H1, n1, H1[0]), true};
+    CPALS_CUDA_TRY(early_qr(H1[0], first1));
     CPALS_CUDA_TRY(pass(H2, n2));
     for (int k = 0; k < n1; ++k) {
-        const TreeQR tq{1, true, own, own_of(H1, n1, H1[k])};
+        const TreeQR tq = (k == 0) ? first1 : TreeQR{1, true, own, own_of(H1, n1, H1[k]), false};
         CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true, &tq));
     }
     CPALS_CUDA_TRY(half_qr(H1, n1, 0));
+    const TreeQR first2{0, false, own, own_of(H2, n2, H2[0]), true};
+    CPALS_CUDA_TRY(early_qr(H2[0], first2));
     CPALS_CUDA_TRY(pass(H1, n1));
     for (int k = 0; k < n2; ++k) {
-        const TreeQR tq{0, false, own, own_of(H2, n2, H2[k])};
+        const TreeQR tq = (k == 0) ? first2 : TreeQR{0, false, own, own_of(H2, n2, H2[k]), false};
         CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true, &tq));
     }
     return cpals::fit_efficient(h, solve);

@@ -517,44 +517,79 @@ __global__ void kron_right_apply_kernel(const double* __restrict__ Qa, int64_t S
 }
 
 // ---------------------------------------------------------------- solves
-// Ahat R0^T = W by substitution, one thread per row.  Singularity test:
-// |R0(k,k)| <= R * eps * max_j |R0(j,j)| sets the status word and writes nothing.
-__global__ void trsm_qr_kernel(const double* __restrict__ W, const double* __restrict__ R0, int64_t I, int R,
-                               double* __restrict__ Ahat, int* __restrict__ status)
+// Triangular solves of the I_n rows of W (Alg. cp-als-qr's substitution, and
+// the Cholesky solves of Alg. cp-als) run one warp per row, the row's R <= 64
+// entries spread over the lanes (entry e in lane e % 32, slot e / 32).  A
+// dependent FP64 operation costs 64 cycles on this part whatever the number
+// of active lanes, so the column-oriented form -- x_k = w_k / d_k, then every
+// lane updates its entries with x_k -- keeps the chain at R steps of one
+// multiply and one FMA, against ~R^2/2 dependent FMAs for one thread per row.
+constexpr int kSolveWarps = 8;
+
+// One substitution on the warp-distributed row w (slots w0, w1):
+//   back = false: L y = w with L(e, k) = A[e + R k] (lower), from k = 0 up;
+//   back = true:  U x = w with U(e, k) = A[e + R k] (upper), from k = R-1 down,
+//                 or with U = A^T (U(e, k) = A[k + R e]) when trans.
+// d0, d1 are the lanes' reciprocals of the diagonal.
+__device__ __forceinline__ void warp_subst(double& w0, double& w1, const double* A, int R, double d0, double d1,
+                                           bool back, bool trans)
+{
+    const int lane = threadIdx.x & 31;
+    for (int t = 0; t < R; ++t) {
+        const int k = back ? R - 1 - t : t;
+        double xk;
+        if (k < 32) {
+            if (lane == k) w0 *= d0;
+            xk = __shfl_sync(0xffffffffu, w0, k);
+        } else {
+            if (lane == k - 32) w1 *= d1;
+            xk = __shfl_sync(0xffffffffu, w1, k - 32);
+        }
+        const int e0 = lane, e1 = lane + 32;
+        if (e0 < R && (back ? e0 < k : e0 > k)) w0 = fma(-(trans ? A[k + R * e0] : A[e0 + R * k]), xk, w0);
+        if (R > 32 && e1 < R && (back ? e1 < k : e1 > k))
+            w1 = fma(-(trans ? A[k + R * e1] : A[e1 + R * k]), xk, w1);
+    }
+}
+
+// Ahat R0^T = W, i.e. R0 x = w for each row w of W (back substitution).
+// Singularity test: |R0(k,k)| <= R * eps * max_j |R0(j,j)| sets the status
+// word and writes nothing.
+__global__ void __launch_bounds__(kSolveWarps * 32) trsm_qr_kernel(
+    const double* __restrict__ W, const double* __restrict__ R0, int64_t I, int R, double* __restrict__ Ahat,
+    int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     __shared__ double r0[kMaxRank * kMaxRank];
-    __shared__ double rinv[kMaxRank];
     __shared__ int singular;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) r0[e] = R0[e];
     __syncthreads();
-    for (int k = threadIdx.x; k < R; k += blockDim.x) rinv[k] = 1.0 / r0[k + R * k];
-    if (threadIdx.x == 0) {
-        double dmax = 0.0;
-        for (int k = 0; k < R; ++k) dmax = fmax(dmax, fabs(r0[k + R * k]));
-        int s = 0;
-        for (int k = 0; k < R; ++k)
-            if (!(fabs(r0[k + R * k]) > (double)R * kEps * dmax)) s = 1;
-        singular = s;
-        if (s && blockIdx.x == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_SINGULAR);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e0 = lane, e1 = lane + 32;
+    const double a0 = e0 < R ? fabs(r0[e0 + R * e0]) : 0.0;
+    const double a1 = e1 < R ? fabs(r0[e1 + R * e1]) : 0.0;
+    if (warp == 0) {
+        double dmax = fmax(a0, a1);
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        const double tol = (double)R * kEps * dmax;
+        const bool bad = (e0 < R && !(a0 > tol)) || (e1 < R && !(a1 > tol));
+        const int s = __any_sync(0xffffffffu, bad) ? 1 : 0;
+        if (lane == 0) {
+            singular = s;
+            if (s && blockIdx.x == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_SINGULAR);
+        }
     }
     __syncthreads();
     if (singular) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
-        // back substitution R0 x = w with the reciprocals of diag(R0); the
-        // inner sums run as two independent chains
-        double x[kMaxRank];
-        for (int k = R - 1; k >= 0; --k) {
-            double s0 = W[i + I * k], s1 = 0.0;
-            int j = k + 1;
-            for (; j + 1 < R; j += 2) {
-                s0 = fma(-r0[k + R * j], x[j], s0);
-                s1 = fma(-r0[k + R * (j + 1)], x[j + 1], s1);
-            }
-            if (j < R) s0 = fma(-r0[k + R * j], x[j], s0);
-            x[k] = (s0 + s1) * rinv[k];
-        }
-        for (int k = 0; k < R; ++k) Ahat[i + I * k] = x[k];
+    const double d0 = e0 < R ? 1.0 / r0[e0 + R * e0] : 0.0;
+    const double d1 = e1 < R ? 1.0 / r0[e1 + R * e1] : 0.0;
+    const int64_t gw = (int64_t)blockIdx.x * kSolveWarps + warp, nw = (int64_t)gridDim.x * kSolveWarps;
+    for (int64_t i = gw; i < I; i += nw) {
+        double w0 = e0 < R ? W[i + I * e0] : 0.0;
+        double w1 = e1 < R ? W[i + I * e1] : 0.0;
+        warp_subst(w0, w1, r0, R, d0, d1, true, false);
+        if (e0 < R) Ahat[i + I * e0] = w0;
+        if (e1 < R) Ahat[i + I * e1] = w1;
     }
 }
 
@@ -797,26 +832,26 @@ __global__ void hadamard_cholesky_kernel(GPtrs gp, int N, int n, int R, double* 
 }
 
 // Ahat S = M with S = L L^T: per row, L y = m, L^T x = y.
-__global__ void chol_rows_kernel(const double* __restrict__ Mm, const double* __restrict__ Lg, int64_t I, int R,
-                                 double* __restrict__ Ahat, const int* __restrict__ status)
+__global__ void __launch_bounds__(kSolveWarps * 32) chol_rows_kernel(
+    const double* __restrict__ Mm, const double* __restrict__ Lg, int64_t I, int R, double* __restrict__ Ahat,
+    const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     __shared__ double L[kMaxRank * kMaxRank];
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) L[e] = Lg[e];
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < I; i += (int64_t)gridDim.x * blockDim.x) {
-        double y[kMaxRank];
-        for (int k = 0; k < R; ++k) {
-            double s = Mm[i + I * k];
-            for (int j = 0; j < k; ++j) s = fma(-L[k + R * j], y[j], s);
-            y[k] = s / L[k + R * k];
-        }
-        for (int k = R - 1; k >= 0; --k) {
-            double s = y[k];
-            for (int j = k + 1; j < R; ++j) s = fma(-L[j + R * k], y[j], s);
-            y[k] = s / L[k + R * k];
-        }
-        for (int k = 0; k < R; ++k) Ahat[i + I * k] = y[k];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e0 = lane, e1 = lane + 32;
+    const double d0 = e0 < R ? 1.0 / L[e0 + R * e0] : 0.0;
+    const double d1 = e1 < R ? 1.0 / L[e1 + R * e1] : 0.0;
+    const int64_t gw = (int64_t)blockIdx.x * kSolveWarps + warp, nw = (int64_t)gridDim.x * kSolveWarps;
+    for (int64_t i = gw; i < I; i += nw) {
+        double w0 = e0 < R ? Mm[i + I * e0] : 0.0;
+        double w1 = e1 < R ? Mm[i + I * e1] : 0.0;
+        warp_subst(w0, w1, L, R, d0, d1, false, false);   // L y = m
+        warp_subst(w0, w1, L, R, d0, d1, true, true);     // L^T x = y
+        if (e0 < R) Ahat[i + I * e0] = w0;
+        if (e1 < R) Ahat[i + I * e1] = w1;
     }
 }
 
@@ -1177,10 +1212,18 @@ cudaError_t krp_qr_tree(Handle* h, int n, int slot, bool other_left, const int* 
     return cudaGetLastError();
 }
 
+// CTAs of kSolveWarps row-warps for the I rows of a solve (grid-stride above
+// four CTAs per SM)
+inline unsigned solve_grid(int64_t I, int num_sms)
+{
+    const int64_t g = (I + kSolveWarps - 1) / kSolveWarps;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 4LL * num_sms));
+}
+
 cudaError_t solve_qr(Handle* h, int64_t In)
 {
-    trsm_qr_kernel<<<grid_for(In, 128, h->num_sms), 128, 0, h->stream>>>(h->W, h->R0, In, h->R, h->Ahat,
-                                                                          h->d_status);
+    trsm_qr_kernel<<<solve_grid(In, h->num_sms), kSolveWarps * 32, 0, h->stream>>>(h->W, h->R0, In, h->R, h->Ahat,
+                                                                                    h->d_status);
     h->launches++;
     return cudaGetLastError();
 }
@@ -1206,8 +1249,8 @@ cudaError_t solve_normal(Handle* h, int n)
     GPtrs gp;
     for (int m = 0; m < h->N; ++m) gp.G[m] = h->G[m];
     hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status, 1);
-    chol_rows_kernel<<<grid_for(h->dims[n], 128, h->num_sms), 128, 0, h->stream>>>(h->M, h->T, h->dims[n], h->R,
-                                                                                   h->Ahat, h->d_status);
+    chol_rows_kernel<<<solve_grid(h->dims[n], h->num_sms), kSolveWarps * 32, 0, h->stream>>>(
+        h->M, h->T, h->dims[n], h->R, h->Ahat, h->d_status);
     h->launches += 2;
     return cudaGetLastError();
 }
