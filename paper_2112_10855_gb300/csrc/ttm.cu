@@ -167,6 +167,62 @@ __global__ void __launch_bounds__(TPB) ttm_rows4_kernel(
     }
 }
 
+// FP32 TTM over the fastest mode (L = 1): row t of the output contracts the
+// contiguous fiber In(:, t).  One thread per fiber reads it four indices at
+// a time (16-byte loads; K % 4 == 0 and a 16-byte aligned tensor), and Q's
+// chunk sits in shared memory as qs[k][r] with r padded to RC4 (a multiple of
+// 4), so four columns of one k come in one broadcast 16-byte read.  With one
+// scalar load per k the row kernel's warp touches 32 lines per instruction
+// and its L1 becomes the bottleneck; here that count falls fourfold.
+template <int RC4>
+__global__ void __launch_bounds__(128) ttm_fiber4_kernel(
+    const float* __restrict__ in, const double* __restrict__ Q, int64_t ldq, float* __restrict__ out, int64_t K,
+    int64_t Tn, int R, int64_t kchunk, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ __align__(16) float qs[kKC][RC4];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r0 = blockIdx.y * RC4;
+    const int rc = min(RC4, R - r0);
+    const bool active = t < Tn;
+    const int64_t kb = (int64_t)blockIdx.z * kchunk;
+    const int64_t ke = (kb + kchunk < K) ? kb + kchunk : K;
+    const float* p = in + K * (active ? t : 0);
+    float acc[RC4];
+#pragma unroll
+    for (int r = 0; r < RC4; ++r) acc[r] = 0.0f;
+    for (int64_t k0 = kb; k0 < ke; k0 += kKC) {
+        const int kc = (int)((ke - k0) < (int64_t)kKC ? (ke - k0) : (int64_t)kKC);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kKC * RC4; i += blockDim.x) {
+            const int kk = i / RC4, rr = i - kk * RC4;
+            qs[kk][rr] = (kk < kc && rr < rc) ? (float)Q[(k0 + kk) + ldq * (int64_t)(r0 + rr)] : 0.0f;
+        }
+        __syncthreads();
+        if (!active) continue;
+        for (int kk = 0; kk < kc; kk += 4) {          // kc % 4 == 0: K and kchunk are multiples of 4
+            const float4 x = __ldg(reinterpret_cast<const float4*>(p + k0 + kk));
+            const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int r = 0; r < RC4; r += 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(&qs[kk + u][r]);
+                    acc[r] = fmaf(xv[u], q.x, acc[r]);
+                    acc[r + 1] = fmaf(xv[u], q.y, acc[r + 1]);
+                    acc[r + 2] = fmaf(xv[u], q.z, acc[r + 2]);
+                    acc[r + 3] = fmaf(xv[u], q.w, acc[r + 3]);
+                }
+        }
+    }
+    if (active) {
+        float* o = out + (int64_t)blockIdx.z * ((int64_t)R * Tn) + (int64_t)R * t;
+#pragma unroll
+        for (int r = 0; r < RC4; ++r)
+            if (r < rc) o[r0 + r] = acc[r];
+    }
+}
+
 // out[g*n + e] = sum of part[q*n + e] over the splits q of group g (groups of
 // `group` consecutive splits, added in split order).  With one group this is
 // the final sum; with several, a second call adds the group sums in order.
@@ -192,8 +248,38 @@ __global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int gro
 // ceil(CTAs / SMs) x rows per CTA x indices per split, which keeps every SM
 // within a fraction of a percent of the mean at the large passes.
 constexpr int kRowsMaxTpb = 256;
-constexpr int kQuadTpb = 128;   // FP32 row-quad kernel: 512 rows per CTA
 constexpr int kF64Tpb[] = {64, 96, 128};
+// FP32 row-quad kernel: 4 rows per thread; its CTA size (64, 96 or 128
+// threads) is picked per launch from the resident CTAs per SM, so that a pass
+// does not end in a ragged second wave (at 135 registers a thread, 128-thread
+// CTAs fit three to an SM).
+constexpr int kQuadTpb[] = {128, 96, 64};
+
+template <int W, int C>
+int quad_occupancy()
+{
+    static const int occ = [] {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, ttm_rows4_kernel<W, C>, C, 0) != cudaSuccess) v = 1;
+        return v > 0 ? v : 1;
+    }();
+    return occ;
+}
+
+template <int W>
+int quad_occupancy(int tpb)
+{
+    return tpb == 64 ? quad_occupancy<W, 64>() : tpb == 96 ? quad_occupancy<W, 96>() : quad_occupancy<W, 128>();
+}
+
+template <int W>
+void launch_rows4(dim3 grid, int tpb, cudaStream_t st, const float* in, const double* Q, int64_t ldq, float* out,
+                  TtmShape s, int R, int64_t kchunk, const int* status)
+{
+    if (tpb == 64) ttm_rows4_kernel<W, 64><<<grid, 64, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
+    else if (tpb == 96) ttm_rows4_kernel<W, 96><<<grid, 96, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
+    else ttm_rows4_kernel<W, 128><<<grid, 128, 0, st>>>(in, Q, ldq, out, s.L, s.K, s.T, R, kchunk, status);
+}
 
 template <typename T, int RC>
 void launch_rows(dim3 grid, int tpb, cudaStream_t st, const T* in, const double* Q, int64_t ldq, T* out,
@@ -241,6 +327,32 @@ inline int ttm_width(int R) {
     return 32;
 }
 
+// Sum the ks K-split partials (part, ks x outn) into out in split order: one
+// pass for up to 16 splits, else groups of 16 and then the group sums.
+template <typename T>
+cudaError_t reduce_ksplit(Handle* h, T* part, int64_t ks, int64_t outn, T* out)
+{
+    if (ks <= 1) return cudaSuccess;
+    constexpr int kGroup = 16;
+    const int64_t ng = (ks + kGroup - 1) / kGroup;
+    auto grid_of = [&](int64_t work) {
+        int64_t g = (work + 255) / 256;
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 16LL * h->num_sms));
+    };
+    if (ng == 1) {
+        reduce_splits_kernel<T><<<grid_of(outn), 256, 0, h->stream>>>(part, (int)ks, kGroup, outn, out, h->d_status);
+        h->launches++;
+    } else {
+        T* gsum = part + ks * outn;     // group sums after the partials
+        reduce_splits_kernel<T><<<grid_of(outn * ng), 256, 0, h->stream>>>(part, (int)ks, kGroup, outn, gsum,
+                                                                           h->d_status);
+        reduce_splits_kernel<T><<<grid_of(outn), 256, 0, h->stream>>>(gsum, (int)ng, (int)ng, outn, out,
+                                                                      h->d_status);
+        h->launches += 2;
+    }
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s, int R,
                              T* part, int64_t part_elems)
@@ -253,10 +365,58 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
                       (((uintptr_t)in) & 15) == 0 && (((uintptr_t)out) & 15) == 0 && (((uintptr_t)part) & 15) == 0;
     const int64_t gy = (R + rc - 1) / rc;
     const int64_t outn = rows * R;
-    int tpb = quad ? kQuadTpb : kRowsMaxTpb;
-    int64_t rows_per_cta = quad ? 4 * kQuadTpb : tpb;
+    // FP32 contraction of the fastest mode: one thread per contiguous fiber
+    const bool fiber = sizeof(T) == 4 && s.L == 1 && (s.K % 4) == 0 && (((uintptr_t)in) & 15) == 0;
+    if (fiber) {
+        const int rc4 = R > 24 ? 32 : (R + 3) / 4 * 4;
+        constexpr int tpbf = 128;
+        const int64_t fgx = (s.T + tpbf - 1) / tpbf, fgy = (R + rc4 - 1) / rc4;
+        int64_t fks = ttm_ksplit(fgx * fgy, tpbf, s.K / 4, h->num_sms, outn, part_elems, part != nullptr);
+        int64_t fkc = ((s.K / 4 + fks - 1) / fks) * 4;    // chunks of whole quads
+        fks = (s.K + fkc - 1) / fkc;
+        const dim3 fgrid((unsigned)fgx, (unsigned)fgy, (unsigned)fks);
+        float* fdst = reinterpret_cast<float*>(fks > 1 ? part : out);
+        const float* fin = reinterpret_cast<const float*>(in);
+        switch (rc4) {
+#define CPALS_RF(W)                                                                                            \
+    case W:                                                                                                    \
+        ttm_fiber4_kernel<W><<<fgrid, tpbf, 0, h->stream>>>(fin, Q, ldq, fdst, s.K, s.T, R, fkc, h->d_status); \
+        break;
+            CPALS_RF(4) CPALS_RF(8) CPALS_RF(12) CPALS_RF(16) CPALS_RF(20) CPALS_RF(24) CPALS_RF(32)
+#undef CPALS_RF
+            default: return cudaErrorInvalidValue;
+        }
+        h->launches++;
+        CPALS_CUDA_TRY(cudaGetLastError());
+        return reduce_ksplit<T>(h, part, fks, outn, out);
+    }
+    int tpb = quad ? 128 : kRowsMaxTpb;
+    int64_t rows_per_cta = quad ? 4 * tpb : tpb;
     int64_t gx = (rows + rows_per_cta - 1) / rows_per_cta;
     int64_t ks = ttm_ksplit(gx * gy, tpb, s.K, h->num_sms, outn, part_elems, part != nullptr);
+    if (quad) {
+        // the CTA size with the smallest per-SM share of rows, a ragged
+        // second wave counted as a quarter more
+        int64_t best = -1;
+        for (int c : kQuadTpb) {
+            int occ = 1;
+            switch (rc) {
+#define CPALS_RO(W) case W: occ = quad_occupancy<W>(c); break;
+                CPALS_RO(1) CPALS_RO(2) CPALS_RO(3) CPALS_RO(4) CPALS_RO(5) CPALS_RO(6) CPALS_RO(7) CPALS_RO(8)
+                CPALS_RO(9) CPALS_RO(10) CPALS_RO(11) CPALS_RO(12) CPALS_RO(13) CPALS_RO(14) CPALS_RO(15) CPALS_RO(16)
+                CPALS_RO(20) CPALS_RO(24)
+#undef CPALS_RO
+                default: break;
+            }
+            const int64_t cx = (rows + 4 * c - 1) / (4 * c);
+            const int64_t cks = ttm_ksplit(cx * gy, c, s.K, h->num_sms, outn, part_elems, part != nullptr);
+            const int64_t ckc = (s.K + cks - 1) / cks;
+            const int64_t per_sm = (cx * gy * cks + h->num_sms - 1) / h->num_sms;
+            int64_t cost = per_sm * 4 * c * ckc;
+            if (per_sm > occ) cost += cost / 4;
+            if (best < 0 || cost < best) { best = cost; tpb = c; gx = cx; ks = cks; }
+        }
+    }
     if (sizeof(T) == 8) {
         // FP64: the CTA size with the smallest per-SM share of rows x indices
         int64_t best = -1;
@@ -276,11 +436,8 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
         const float* fin = reinterpret_cast<const float*>(in);
         float* fdst = reinterpret_cast<float*>(dst);
         switch (rc) {
-#define CPALS_RQ(W)                                                                                            \
-    case W:                                                                                                    \
-        ttm_rows4_kernel<W, kQuadTpb><<<grid, kQuadTpb, 0, h->stream>>>(fin, Q, ldq, fdst, s.L, s.K, s.T, R,   \
-                                                                        kchunk, h->d_status);                  \
-        break;
+#define CPALS_RQ(W) \
+    case W: launch_rows4<W>(grid, tpb, h->stream, fin, Q, ldq, fdst, s, R, kchunk, h->d_status); break;
             CPALS_RQ(1) CPALS_RQ(2) CPALS_RQ(3) CPALS_RQ(4) CPALS_RQ(5) CPALS_RQ(6) CPALS_RQ(7) CPALS_RQ(8)
             CPALS_RQ(9) CPALS_RQ(10) CPALS_RQ(11) CPALS_RQ(12) CPALS_RQ(13) CPALS_RQ(14) CPALS_RQ(15) CPALS_RQ(16)
             CPALS_RQ(20) CPALS_RQ(24)
@@ -297,28 +454,7 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     }
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
-    if (ks > 1) {
-        constexpr int kGroup = 16;
-        const int64_t ng = (ks + kGroup - 1) / kGroup;
-        auto grid_of = [&](int64_t work) {
-            int64_t g = (work + 255) / 256;
-            return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 16LL * h->num_sms));
-        };
-        if (ng == 1) {
-            reduce_splits_kernel<T><<<grid_of(outn), 256, 0, h->stream>>>(part, (int)ks, kGroup, outn, out,
-                                                                          h->d_status);
-            h->launches++;
-        } else {
-            T* gsum = part + ks * outn;     // group sums after the partials
-            reduce_splits_kernel<T><<<grid_of(outn * ng), 256, 0, h->stream>>>(part, (int)ks, kGroup, outn, gsum,
-                                                                               h->d_status);
-            reduce_splits_kernel<T><<<grid_of(outn), 256, 0, h->stream>>>(gsum, (int)ng, (int)ng, outn, out,
-                                                                          h->d_status);
-            h->launches += 2;
-        }
-        CPALS_CUDA_TRY(cudaGetLastError());
-    }
-    return cudaSuccess;
+    return reduce_ksplit<T>(h, part, ks, outn, out);
 }
 
 template <typename T>

@@ -59,7 +59,13 @@ def test_multi_ttm_matches_oracle(cuda_lib, dims, R):
         assert rel(Y, ref) <= 1e-12, (n, rel(Y, ref))
 
 
-@pytest.mark.parametrize("dims,R", [((5, 4, 3), 2), ((3, 4, 3, 3), 3), ((40, 30, 20), 6), ((300, 7), 5)])
+# the later TTMs of the FP32 Multi-TTM run through shared-memory tiles: the
+# last four shapes give them L = 1, L = 3 and L = 6 (staged along k), L >= 16
+# (staged along rows), ragged 128-row tiles, K of 20 to 70 (one to three
+# chunks of 32) and R = 33 (two column blocks)
+@pytest.mark.parametrize("dims,R", [((5, 4, 3), 2), ((3, 4, 3, 3), 3), ((40, 30, 20), 6), ((300, 7), 5),
+                                    ((70, 150, 12), 12), ((45, 40, 70), 3), ((30, 20, 25), 6),
+                                    ((40, 36, 34, 33), 33)])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_multi_ttm_index_bookkeeping_bit_exact(cuda_lib, dims, R, precision):
     # integer X and 0/1 Q: every partial sum is an integer below 2^24, exact in
