@@ -25,6 +25,26 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// dlarfg for a column with leading entry alpha and tail sum of squares s:
+// H = I - tau v v^T with v = [1; scale * tail] maps the column to beta e_1
+// (|beta| = its norm, sign opposite to alpha; tau = 0 when the tail is zero).
+// tau = d / beta and scale = -1 / d with d = beta - alpha take one division.
+__device__ __forceinline__ void hh_reflector(double alpha, double s, double* tau_j, double* scale, double* diag)
+{
+    double t = 0.0, sc = 0.0, beta = alpha;
+    if (s > 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, s));
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        const double d = beta - alpha;
+        const double r = 1.0 / (beta * d);
+        t = d * d * r;
+        sc = -beta * r;
+    }
+    *tau_j = t;
+    *scale = sc;
+    *diag = beta;
+}
+
 // ---------------------------------------------------------------- Householder
 // CTA b factors rows [off_b, off_{b+1}) of the m x n matrix A (lda), with
 // off_b = b*m/nb, into an explicit Q_b (written to the same rows of Qout, ldq)
@@ -53,61 +73,56 @@ __global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
     __syncthreads();
 
     const int kmax = min(mb, n);
-    // warp 0 updates column j+1 first in step j and then already holds the norm
-    // of W(j+2:mb, j+1) that step j+1's reflector needs
-    double s_next = 0.0;
+    // Look-ahead: in step j warp 0 applies H_j to column j+1 first, sums the
+    // squares of its new tail and forms reflector j+1 while the other warps
+    // apply H_j to columns j+2..n-1, so a step needs one block barrier and the
+    // reflector's serial chain (norm, square root, one division) overlaps the
+    // updates.  Reflector tails stay unscaled during the loop (the dlarfg
+    // scale of column j, scl[j], enters each dot product and update once) and
+    // are scaled afterwards.
+    double* scl = red + 32;               // n dlarfg scales
+    if (warp == 0 && kmax > 0) {
+        double s = 0.0;
+        for (int i = 1 + lane; i < mb; i += 32) s = fma(W[i], W[i], s);
+        s = warp_sum(s);
+        if (lane == 0) hh_reflector(W[0], s, &tau[0], &scl[0], &W[0]);
+    }
+    __syncthreads();
     for (int j = 0; j < kmax; ++j) {
-        // norm of W(j+1:mb, j) -- warp 0
-        if (warp == 0) {
-            double s = s_next;
-            if (j == 0 || tau[j - 1] == 0.0) {
-                s = 0.0;
-                for (int i = j + 1 + lane; i < mb; i += 32) s = fma(W[i + mb * j], W[i + mb * j], s);
-                s = warp_sum(s);
-            }
-            if (lane == 0) {
-                const double alpha = W[j + mb * j];
-                double t = 0.0, scale = 0.0, beta = alpha;
-                if (s > 0.0) {
-                    const double nrm = sqrt(fma(alpha, alpha, s));
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    const double d = beta - alpha;      // tau = d / beta, scale = -1 / d: one division
-                    const double r = 1.0 / (beta * d);
-                    t = d * d * r;
-                    scale = -beta * r;
-                }
-                tau[j] = t;
-                red[0] = scale;
-                W[j + mb * j] = beta;
-            }
-        }
-        __syncthreads();
-        const double scale = red[0];
-        if (tau[j] != 0.0)
-            for (int i = j + 1 + tid; i < mb; i += kQrThreads) W[i + mb * j] *= scale;
-        __syncthreads();
-        // apply H_j to columns j+1..n-1 (one warp per column)
-        const double tj = tau[j];
+        const double tj = tau[j], sc = scl[j];
+        const double* wj = W + (size_t)mb * j;
+        double s2 = 0.0;                  // warp 0: squares of the tail of column j+1
         if (tj != 0.0) {
             for (int k = j + 1 + warp; k < n; k += nwarps) {
+                double* wk = W + (size_t)mb * k;
                 double s = 0.0;
-                for (int i = j + lane; i < mb; i += 32) {
-                    const double v = (i == j) ? 1.0 : W[i + mb * j];
-                    s = fma(v, W[i + mb * k], s);
+                for (int i = j + 1 + lane; i < mb; i += 32) s = fma(wj[i], wk[i], s);
+                s = fma(warp_sum(s), sc, wk[j]) * tj;
+                const double ss = s * sc;
+                const bool next = (k == j + 1);
+                for (int i = j + 1 + lane; i < mb; i += 32) {
+                    const double w = fma(-ss, wj[i], wk[i]);
+                    wk[i] = w;
+                    if (next && i > k) s2 = fma(w, w, s2);
                 }
-                s = warp_sum(s) * tj;
-                double s2 = 0.0;
-                for (int i = j + lane; i < mb; i += 32) {
-                    const double v = (i == j) ? 1.0 : W[i + mb * j];
-                    const double w = fma(-s, v, W[i + mb * k]);
-                    W[i + mb * k] = w;
-                    if (i > k) s2 = fma(w, w, s2);
-                }
-                if (k == j + 1) s_next = warp_sum(s2);   // warp 0: next reflector's norm
+                if (lane == 0) wk[j] -= s;
             }
+        } else if (warp == 0 && j + 1 < n) {
+            const double* wk = W + (size_t)mb * (j + 1);
+            for (int i = j + 2 + lane; i < mb; i += 32) s2 = fma(wk[i], wk[i], s2);
+        }
+        if (warp == 0 && j + 1 < kmax) {
+            s2 = warp_sum(s2);
+            double* wn = W + (size_t)mb * (j + 1);
+            if (lane == 0) hh_reflector(wn[j + 1], s2, &tau[j + 1], &scl[j + 1], &wn[j + 1]);
         }
         __syncthreads();
     }
+    for (int64_t e = tid; e < (int64_t)mb * kmax; e += kQrThreads) {
+        const int j = (int)(e / mb), i = (int)(e - (int64_t)j * mb);
+        if (i > j && tau[j] != 0.0) W[e] *= scl[j];
+    }
+    __syncthreads();
     for (int j = kmax; j < n; ++j) if (tid == 0) tau[j] = 0.0;
     // explicit Q = H_0 ... H_{k-1} [I; 0], backward accumulation
     for (int64_t e = tid; e < (int64_t)mb * n; e += kQrThreads) {
@@ -321,10 +336,10 @@ __global__ void tri_combine_kernel(const double* __restrict__ Qi, int64_t ldqi, 
 
 inline size_t tri_smem_bytes(int n) { return sizeof(double) * ((size_t)4 * n * (n + 1) + n + 256 + 64 + 2); }
 
-// W and Q (mb x n each), tau (n) and 32 scratch values
+// W and Q (mb x n each), tau (n), 32 scratch values and the n reflector scales
 inline size_t qr_smem_bytes(int64_t mb, int n)
 {
-    return sizeof(double) * ((size_t)2 * (size_t)mb * n + n + 32);
+    return sizeof(double) * ((size_t)2 * (size_t)mb * n + 2 * (size_t)n + 32);
 }
 
 constexpr size_t kQrSmemMaxBytes = 200 * 1024;   // one leaf CTA's shared memory
