@@ -240,8 +240,20 @@ int cpals_sync(cpals_handle* h);
  *    stream while X is contracted, and each mode folds only the R_m of its own
  *    half onto the other half's R and applies that half's Q as a Kronecker
  *    factor (Eq. kr-id).  0 folds all N-1 factors for every mode.  The Q0, R0
- *    differ only by rounding. */
-typedef enum { CPALS_OPT_DIMTREE = 0, CPALS_OPT_TC_PIPELINE = 1, CPALS_OPT_KRP_TREE = 2 } cpals_option;
+ *    differ only by rounding.
+ *  CPALS_OPT_F32_PIPELINE (default 1): FP32 TTMs (the CPALS_F32 passes over
+ *    X and the FP32 contractions of intermediates in every precision but
+ *    F64) run on the CUDA cores fed by a ring of TMA boxes, whenever the
+ *    product of the dims before the contracted mode is a multiple of 4 and
+ *    9 <= R <= 64.  0 uses the row-per-thread kernels.  Both sum each output in
+ *    order of the contracted index (the row kernels within each K split,
+ *    whose sums they add in a fixed order), so only rounding differs. */
+typedef enum {
+    CPALS_OPT_DIMTREE = 0,
+    CPALS_OPT_TC_PIPELINE = 1,
+    CPALS_OPT_KRP_TREE = 2,
+    CPALS_OPT_F32_PIPELINE = 3
+} cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
 
 /* Number of kernel launches the handle has issued so far (graph replays count

@@ -198,6 +198,10 @@ class CPALS:
         """CPALS_OPT_KRP_TREE: per-half QR of the Khatri-Rao products in dimension-tree sweeps."""
         _check(self._h, load().cpals_set_option(self._h, 2, 1 if on else 0))
 
+    def set_f32_pipeline(self, on: bool):
+        """CPALS_OPT_F32_PIPELINE: TMA-fed CUDA-core kernel for the FP32 TTMs."""
+        _check(self._h, load().cpals_set_option(self._h, 3, 1 if on else 0))
+
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
 

@@ -929,10 +929,19 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
 {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
-    if ((option != CPALS_OPT_DIMTREE && option != CPALS_OPT_TC_PIPELINE && option != CPALS_OPT_KRP_TREE) ||
+    if ((option != CPALS_OPT_DIMTREE && option != CPALS_OPT_TC_PIPELINE && option != CPALS_OPT_KRP_TREE &&
+         option != CPALS_OPT_F32_PIPELINE) ||
         (value != 0 && value != 1))
         return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
     const bool v = value != 0;
+    if (option == CPALS_OPT_F32_PIPELINE) {
+        if (v != h->f32_pipe) {
+            h->f32_pipe = v;
+            for (int s = 0; s < 4; ++s)         // captured sweeps hold the old kernels
+                if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
+        }
+        return CPALS_OK;
+    }
     if (option == CPALS_OPT_KRP_TREE) {
         if (v != h->krp_tree) {
             h->krp_tree = v;

@@ -92,6 +92,7 @@ struct Handle {
     // once per sweep; a half of one mode keeps Q = I and R = its own R_m.
     // Qin holds the inner fold (R x own factors) before the Kronecker apply.
     bool krp_tree = true;
+    bool f32_pipe = true;    // FP32 TTMs through the TMA-fed CUDA-core pipeline where the shape allows
     double* HQ[2] = {nullptr, nullptr};
     double* HR[2] = {nullptr, nullptr};
     const double* hr_ptr[2] = {nullptr, nullptr};
@@ -181,6 +182,10 @@ int64_t multi_ttm_static_need(int N, const int64_t* dims, int R, int n);
 // First TTM on the tcgen05 tensor cores with split products (FP32 X):
 // 3 x bf16 (kind::f16) or, with tf32 = true, 3 x tf32 (kind::tf32).
 bool tc_supported(int R);
+// FP32 TTM on the CUDA cores fed by the TMA ring of the tensor-core pipeline
+// (L % 4 == 0, 16-byte aligned tensors, R <= 64; f32_pipe_ok says when).
+bool f32_pipe_ok(const float* in, const float* out, TtmShape s, int R);
+cudaError_t ttm_f32_pipe(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R);
 cudaError_t ttm_split_tc(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R,
                          bool tf32);
 // MTTKRP M_n = X_(n) Z_n (Alg. cp-als) into h->M.

@@ -857,6 +857,187 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
     if (warp == Cfg::kMmaWarp) tmem_dealloc<512>(tmem);
 }
 
+// ---------------------------------------------------------------- FP32 pipeline (CUDA cores)
+// The same TMA ring feeds FP32 FMAs on the CUDA cores: the FP32 precision's
+// passes over X and the FP32 contractions of intermediates (Eq. multittm).
+// One producer warp streams [rows x 64 K] boxes of In (tensor map [L, K, T])
+// and, unless Q fits whole in shared memory, the matching 64-row chunk of Q
+// into a ring of stages.  Four compute warps own a tile of 128 rows: lane q
+// takes rows 4q..4q+3 (one 16-byte read per k; BL % 4 == 0 keeps the four in
+// one t) and warp g takes columns g TN .. g TN + TN - 1 (TN = RC / 4), whose Q
+// values sit together in the stage ([g][k][TNP], TNP = TN rounded up to 4) so
+// a k costs TNP / 4 broadcast 16-byte reads.  The FMAs run in order of k, and
+// a tile's outputs are written with 16-byte stores along l.  Up to four CTAs
+// share an SM (as registers allow), each with a short ring: with only four
+// compute warps a CTA leaves the FMA pipe idle while its warps wait on shared
+// memory, and more CTAs per SM cover that better than a longer ring.
+constexpr int kF32Kc = 64;              // K per item
+constexpr int kF32ComputeWarps = 4;
+constexpr int kF32Threads = (kF32ComputeWarps + 1) * 32;
+constexpr uint32_t kF32XBytes = kTcRows * kF32Kc * 4;     // 32 KB box at 128 rows
+constexpr uint32_t kF32SmemBudget = 54u * 1024u;          // four CTAs per SM
+constexpr uint32_t kF32SmemBudgetWide = 110u * 1024u;     // RC >= 48: registers allow two
+constexpr int kF32MaxStages = 6;
+constexpr uint32_t kF32QResident = 20u * 1024u;
+
+template <int RC>
+struct F32Cfg {
+    static constexpr int TN = RC / 4;
+    static constexpr int TNP = (TN + 3) / 4 * 4;
+    static constexpr uint32_t kQItemBytes = 4u * kF32Kc * TNP * 4u;      // one item's Q chunk, all groups
+    static constexpr uint32_t kBudget = RC >= 48 ? kF32SmemBudgetWide : kF32SmemBudget;
+};
+
+// Q (K x R, FP64, ldq) to the FP32 item chunks [c][g][k][TNP] (zero padded).
+template <int RC>
+__global__ void f32_q_kernel(const double* __restrict__ Q, int64_t ldq, int64_t K, int R, float* __restrict__ qf,
+                             int nitems, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    using C = F32Cfg<RC>;
+    const int64_t total = (int64_t)nitems * 4 * kF32Kc * C::TNP;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % C::TNP);
+        const int64_t r1 = e / C::TNP;
+        const int k = (int)(r1 % kF32Kc);
+        const int64_t r2 = r1 / kF32Kc;
+        const int g = (int)(r2 % 4);
+        const int64_t c = r2 / 4;
+        const int64_t kk = c * kF32Kc + k;
+        const int col = g * C::TN + j;
+        qf[e] = (j < C::TN && kk < K && col < R) ? (float)Q[kk + ldq * (int64_t)col] : 0.0f;
+    }
+}
+
+template <int RC>
+__global__ void __launch_bounds__(kF32Threads) ttm_f32_pipe_kernel(
+    const __grid_constant__ CUtensorMap xmap, const float* __restrict__ qf, float* __restrict__ out, int64_t L,
+    int64_t Tn, int R, int BL, int BT, int64_t ntl, int64_t ntiles, int nitems, int SX, int qres,
+    int* __restrict__ status)
+{
+    using C = F32Cfg<RC>;
+    __shared__ int skip;
+    if (threadIdx.x == 0) skip = *(volatile int*)status != kStatusOk;
+    __syncthreads();
+    if (skip) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    const uint32_t qbytes = qres ? (uint32_t)nitems * C::kQItemBytes : 0u;
+    const uint32_t stage = kF32XBytes + (qres ? 0u : C::kQItemBytes);
+    uint8_t* qregion = smem;
+    uint8_t* ring = smem + qbytes;
+    uint64_t* full = (uint64_t*)(ring + (size_t)SX * stage);
+    uint64_t* empty = full + kF32MaxStages;
+    uint64_t* qfull = empty + kF32MaxStages;
+    volatile int* abort_flag = (volatile int*)(qfull + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < SX; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kF32ComputeWarps);
+        }
+        mbar_init(qfull, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int64_t my_tiles = (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const int64_t items = my_tiles * nitems;
+    const int rows_used = BL * BT;
+    auto last_on = [](int64_t it, int s, int n) { return it - 1 - ((it - 1 - s) % n + n) % n; };
+
+    if (warp == kF32ComputeWarps) {
+        if (lane == 0) {
+            if (qres) {
+                mbar_expect_tx(qfull, qbytes);
+                bulk_load(qregion, qf, qbytes, qfull);
+            }
+            const uint32_t tx = (uint32_t)rows_used * kF32Kc * 4u + (qres ? 0u : C::kQItemBytes);
+            int64_t it = 0;
+            for (; it < items; ++it) {
+                const int s = (int)(it % SX);
+                if (!pipe_wait(&empty[s], (uint32_t)((it / SX) & 1) ^ 1u, abort_flag)) break;
+                const int64_t tile = blockIdx.x + (it / nitems) * (int64_t)gridDim.x;
+                const int c = (int)(it % nitems);
+                const int64_t tt = tile / ntl, tl = tile - tt * ntl;
+                uint8_t* st = ring + (size_t)s * stage;
+                mbar_expect_tx(&full[s], tx);
+                tma_load_3d(st, &xmap, (int)(tl * BL), c * kF32Kc, (int)(tt * BT), &full[s]);
+                if (!qres)
+                    bulk_load(st + kF32XBytes, qf + (size_t)c * (C::kQItemBytes / 4), C::kQItemBytes, &full[s]);
+            }
+            for (int s = 0; s < SX; ++s) {   // every issued copy lands before the CTA may exit
+                const int64_t last = last_on(it, s, SX);
+                if (last >= 0) pipe_drain(&full[s], (uint32_t)((last / SX) & 1));
+            }
+            if (qres) pipe_drain(qfull, 0u);
+        }
+        __syncwarp();
+    } else {
+        const int g = warp, q = lane;
+        const int m0 = 4 * q;                      // first of this thread's four rows in the tile
+        const bool mok = m0 < rows_used;
+        const int bt = mok ? m0 / BL : 0, bl = mok ? m0 - bt * BL : 0;
+        const int xoff = bt * kF32Kc * BL + bl;    // box layout [bt][k][bl]
+        bool ok = !qres || pipe_wait(qfull, 0u, abort_flag);
+        int64_t it = 0;
+        for (int64_t t = 0; t < my_tiles && ok; ++t) {
+            float acc[4][C::TN];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < C::TN; ++j) acc[i][j] = 0.0f;
+            for (int c = 0; c < nitems; ++c, ++it) {
+                const int s = (int)(it % SX);
+                if (!pipe_wait(&full[s], (uint32_t)((it / SX) & 1), abort_flag)) { ok = false; break; }
+                const uint8_t* st = ring + (size_t)s * stage;
+                const float* xs = reinterpret_cast<const float*>(st) + xoff;
+                const float* qs = qres ? reinterpret_cast<const float*>(qregion) + (size_t)c * (C::kQItemBytes / 4)
+                                       : reinterpret_cast<const float*>(st + kF32XBytes);
+                qs += (size_t)g * kF32Kc * C::TNP;
+#pragma unroll 4
+                for (int k = 0; k < kF32Kc; ++k) {
+                    const float4 x = *reinterpret_cast<const float4*>(xs + k * BL);
+                    float qv[C::TNP];
+#pragma unroll
+                    for (int j = 0; j < C::TNP; j += 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(qs + k * C::TNP + j);
+                        qv[j] = v.x; qv[j + 1] = v.y; qv[j + 2] = v.z; qv[j + 3] = v.w;
+                    }
+#pragma unroll
+                    for (int j = 0; j < C::TN; ++j) {
+                        acc[0][j] = fmaf(x.x, qv[j], acc[0][j]);
+                        acc[1][j] = fmaf(x.y, qv[j], acc[1][j]);
+                        acc[2][j] = fmaf(x.z, qv[j], acc[2][j]);
+                        acc[3][j] = fmaf(x.w, qv[j], acc[3][j]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            if (!ok) break;
+            const int64_t tile = blockIdx.x + t * (int64_t)gridDim.x;
+            const int64_t tt = tile / ntl, tl = tile - tt * ntl;
+            const int64_t l = tl * BL + bl, tq = tt * BT + bt;
+            if (mok && l < L && tq < Tn) {         // L % 4 == 0: the four rows are valid together
+                float* o = out + l + L * (int64_t)R * tq;
+#pragma unroll
+                for (int j = 0; j < C::TN; ++j) {
+                    const int col = g * C::TN + j;
+                    if (col < R)
+                        *reinterpret_cast<float4*>(o + L * (int64_t)col) =
+                            make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicCAS(status, kStatusOk, (int)CPALS_ERR_TIMEOUT);
+}
+
 using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
 
 EncodeTiledFn encode_tiled_fn()
@@ -954,7 +1135,76 @@ cudaError_t launch_tc(Handle* h, const float* in, const double* Q, int64_t ldq, 
     return cudaGetLastError();
 }
 
+template <int RC>
+cudaError_t launch_f32_pipe(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R)
+{
+    using C = F32Cfg<RC>;
+    static std::once_flag attr_once;
+    cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [&] {
+        attr_err = cudaFuncSetAttribute(ttm_f32_pipe_kernel<RC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(C::kBudget + 256));
+    });
+    CPALS_CUDA_TRY(attr_err);
+    const int nitems = (int)((s.K + kF32Kc - 1) / kF32Kc);
+    const size_t qfloats = (size_t)nitems * (C::kQItemBytes / 4);
+    if (qfloats * sizeof(float) > (size_t)h->scratch_elems * sizeof(double)) return cudaErrorInvalidValue;
+    float* qf = reinterpret_cast<float*>(h->scratch);
+    f32_q_kernel<RC><<<(unsigned)std::min<size_t>((qfloats + 255) / 256, 4096), 256, 0, h->stream>>>(
+        Q, ldq, s.K, R, qf, nitems, h->d_status);
+    h->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    const int BL = s.L >= kTcRows ? kTcRows : (int)s.L;
+    const int BT = kTcRows / BL;
+    CUtensorMap map;
+    const cuuint64_t gdim[3] = {(cuuint64_t)s.L, (cuuint64_t)s.K, (cuuint64_t)s.T};
+    const cuuint64_t gstride[2] = {(cuuint64_t)s.L * 4u, (cuuint64_t)s.L * (cuuint64_t)s.K * 4u};
+    const cuuint32_t box[3] = {(cuuint32_t)BL, (cuuint32_t)kF32Kc, (cuuint32_t)BT};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    const CUresult cr = encode_tiled_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(in), gdim,
+                                          gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const int64_t ntl = (s.L + BL - 1) / BL;
+    const int64_t ntiles = ntl * ((s.T + BT - 1) / BT);
+    const bool qres = (uint64_t)nitems * C::kQItemBytes <= kF32QResident;
+    const uint32_t qbytes = qres ? (uint32_t)nitems * C::kQItemBytes : 0u;
+    const uint32_t stage = kF32XBytes + (qres ? 0u : C::kQItemBytes);
+    const int SX = (int)std::min<uint32_t>(kF32MaxStages, (C::kBudget - qbytes) / stage);
+    if (SX < 1) return cudaErrorInvalidValue;
+    const uint32_t smem = qbytes + (uint32_t)SX * stage + 128 + 8 * (2 * kF32MaxStages + 1) + 16;
+    int per_sm = 1;
+    CPALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ttm_f32_pipe_kernel<RC>, kF32Threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)per_sm * h->num_sms);
+    ttm_f32_pipe_kernel<RC><<<grid, kF32Threads, smem, h->stream>>>(map, qf, out, s.L, s.T, R, BL, BT, ntl, ntiles,
+                                                                    nitems, SX, qres ? 1 : 0, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+// Below R = 9 the row-quad kernel streams X faster (at R = 8 the pipeline
+// holds 3.0 TB/s against 4.5 TB/s): the pipeline takes R = 9..64.
+bool f32_pipe_ok(const float* in, const float* out, TtmShape s, int R)
+{
+    return R > 8 && R <= 64 && pipe_shape_ok(in, s) && (((uintptr_t)out) & 15) == 0;
+}
+
+cudaError_t ttm_f32_pipe(Handle* h, const float* in, const double* Q, int64_t ldq, float* out, TtmShape s, int R)
+{
+    if (s.L * s.T == 0) return cudaSuccess;
+    if (R <= 8) return cudaErrorInvalidValue;   // f32_pipe_ok excludes it
+    if (R <= 12) return launch_f32_pipe<12>(h, in, Q, ldq, out, s, R);
+    if (R <= 16) return launch_f32_pipe<16>(h, in, Q, ldq, out, s, R);
+    if (R <= 20) return launch_f32_pipe<20>(h, in, Q, ldq, out, s, R);
+    if (R <= 24) return launch_f32_pipe<24>(h, in, Q, ldq, out, s, R);
+    if (R <= 32) return launch_f32_pipe<32>(h, in, Q, ldq, out, s, R);
+    if (R <= 48) return launch_f32_pipe<48>(h, in, Q, ldq, out, s, R);
+    return launch_f32_pipe<64>(h, in, Q, ldq, out, s, R);
+}
 
 bool tc_supported(int R) { return R >= 16 && R <= 64; }
 

@@ -457,9 +457,14 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     return reduce_ksplit<T>(h, part, ks, outn, out);
 }
 
+// One TTM: FP32 through the TMA-fed pipeline where the shape allows it, else
+// the row kernels.
 template <typename T>
 cudaError_t launch_ttm(Handle* h, const T* in, const double* Q, int64_t ldq, T* out, TtmShape s, int R)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (h->f32_pipe && f32_pipe_ok(in, out, s, R)) return ttm_f32_pipe(h, in, Q, ldq, out, s, R);
+    }
     return launch_ttm_split<T>(h, in, Q, ldq, out, s, R, (T*)h->scratch,
                                h->scratch_elems * (int64_t)(sizeof(double) / sizeof(T)));
 }

@@ -335,6 +335,37 @@ def test_f32_multi_ttm_error_bound(cuda_lib, dims, R):
         assert rel(Y, oracle.multi_ttm(X, dims, n, [q for q, _ in QR])) <= 2e-6
 
 
+# the FP32 TTMs with L % 4 == 0 run through the TMA-fed CUDA-core pipeline:
+# boxes of 128 rows (BL = 128, or BL = L < 128 with 128 / L t slices),
+# ragged row tiles and K chunks of 64, Q resident in shared memory or streamed
+# per chunk (K = 400 at R = 64), and every column width up to 64.  Each output
+# is summed in order of k; the row kernels do the same within a K split and
+# add the splits in a fixed order, so the two paths differ by FP32 rounding
+# only (the integer-valued cases of test_multi_ttm_index_bookkeeping_bit_exact
+# pin both exactly)
+@pytest.mark.parametrize("dims,R", [((64, 40, 36), 20), ((128, 30, 20, 12), 12), ((12, 70, 66), 9),
+                                    ((68, 64, 66), 64), ((36, 400, 44), 33), ((52, 50, 49), 48)])
+def test_f32_pipeline_matches_row_kernels(cuda_lib, dims, R):
+    X, A = gaussian_problem(dims, R, seed=23)
+    QR = [oracle.qr(a) for a in A]
+    hs = []
+    for pipe in (True, False):
+        h = gpu_handle(dims, R, X, precision="f32")
+        h.set_f32_pipeline(pipe)
+        h.set_factor_qr([q for q, _ in QR], [r for _, r in QR])
+        hs.append(h)
+    for n in range(len(dims)):
+        Y1, _ = hs[0].multi_ttm(n)
+        Y0, _ = hs[1].multi_ttm(n)
+        assert rel(Y1, Y0) <= 1e-6
+        assert rel(Y1, oracle.multi_ttm(X, dims, n, [q for q, _ in QR])) <= 2e-6
+    for h in hs:
+        h.set_factors(A)
+    f1 = hs[0].iterate(3, solve="qr")
+    f0 = hs[1].iterate(3, solve="qr")
+    assert np.abs(f1 - f0).max() <= 1e-6
+
+
 def test_full_size_multi_ttm_c2(cuda_lib):
     # 400^3 FP64 rank 10 (the benchmark configuration), same launch path:
     # full parity of Y_(n) for every mode against the oracle
