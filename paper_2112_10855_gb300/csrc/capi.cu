@@ -207,6 +207,8 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
             h->stream = h->side;
             cudaError_t e = tq ? cpals::krp_qr_tree(h, n, tq->slot, tq->other_left, tq->own, tq->nown)
                                : cpals::krp_qr(h, n);
+            // the SVD operator of R0 needs nothing else: it follows on the side stream
+            if (e == cudaSuccess && solve == CPALS_SOLVE_SVD) e = cpals::svd_operator(h, rtol);
             h->stream = main;
             CPALS_CUDA_TRY(e);
             CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
@@ -217,7 +219,7 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
         CPALS_CUDA_TRY(cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W));
         if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
-        else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol));
+        else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol, true));
     }
     CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
     if (is_normal(solve)) {
@@ -294,6 +296,7 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
         cudaStream_t main = h->stream;
         h->stream = h->side;
         cudaError_t e = cpals::krp_qr_tree(h, n, tq.slot, tq.other_left, tq.own, tq.nown);
+        if (e == cudaSuccess && solve == CPALS_SOLVE_SVD) e = cpals::svd_operator(h, rtol);
         h->stream = main;
         CPALS_CUDA_TRY(e);
         return cudaEventRecord(h->ev_join, h->side);

@@ -224,7 +224,11 @@ cudaError_t krp_qr_tree(Handle* h, int n, int slot, bool other_left, const int* 
 cudaError_t gemm_rows(Handle* h, const double* A, int64_t m, int64_t k, const double* B, int n, double* C);
 // Solve Ahat R0^T = W (QR) or Ahat = W U pinv(S) V^T (SVD) into h->Ahat.
 cudaError_t solve_qr(Handle* h, int64_t In);
-cudaError_t solve_svd(Handle* h, int64_t In, double rtol);
+// T = U pinv(Sigma) V^T of R0 (truncated one-sided Jacobi SVD) into h->T; it
+// needs only R0, so a sweep runs it beside the Multi-TTM.
+cudaError_t svd_operator(Handle* h, double rtol);
+// Ahat = W T; the operator T is formed first unless have_operator.
+cudaError_t solve_svd(Handle* h, int64_t In, double rtol, bool have_operator = false);
 // S_n = Hadamard product of the other Grams, then Cholesky solve Ahat S = M.
 cudaError_t solve_normal(Handle* h, int n);
 // S_n as above, then Ahat = M pinv(S_n) with the truncated Jacobi SVD (CP-ALS-PINV).

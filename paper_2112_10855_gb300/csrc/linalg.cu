@@ -1243,7 +1243,7 @@ cudaError_t solve_qr(Handle* h, int64_t In)
     return cudaGetLastError();
 }
 
-cudaError_t solve_svd(Handle* h, int64_t In, double rtol)
+cudaError_t svd_operator(Handle* h, double rtol)
 {
     if (!(rtol > 0.0)) rtol = (double)h->R * kEps;
     constexpr size_t smem = sizeof(double) * jacobi_smem_doubles();
@@ -1255,7 +1255,12 @@ cudaError_t solve_svd(Handle* h, int64_t In, double rtol)
     }
     jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status);
     h->launches++;
-    CPALS_CUDA_TRY(cudaGetLastError());
+    return cudaGetLastError();
+}
+
+cudaError_t solve_svd(Handle* h, int64_t In, double rtol, bool have_operator)
+{
+    if (!have_operator) CPALS_CUDA_TRY(svd_operator(h, rtol));
     return gemm_rows(h, h->W, In, h->R, h->T, h->R, h->Ahat);
 }
 
