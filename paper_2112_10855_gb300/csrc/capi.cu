@@ -193,10 +193,21 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         return cudaSuccess;
     }
     if (is_normal(solve)) {
+        // S_n and its Cholesky factor or pseudo-inverse need only the Grams:
+        // the side stream forms them while the MTTKRP runs
+        CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+        CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+        cudaStream_t main = h->stream;
+        h->stream = h->side;
+        cudaError_t e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
+        h->stream = main;
+        CPALS_CUDA_TRY(e);
+        CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
         if (from_partial) CPALS_CUDA_TRY(cpals::mttkrp_from_partial(h, n));
         else CPALS_CUDA_TRY(cpals::mttkrp(h, n));
-        if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n));
-        else CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol));
+        CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n, true));
+        else CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol, true));
     } else {
         // The QR of V_n needs only the R_m and the Multi-TTM only the Q_m: run the
         // QR on the side stream meanwhile and join before W = Y_(n) Q0.

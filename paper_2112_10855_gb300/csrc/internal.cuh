@@ -229,10 +229,15 @@ cudaError_t solve_qr(Handle* h, int64_t In);
 cudaError_t svd_operator(Handle* h, double rtol);
 // Ahat = W T; the operator T is formed first unless have_operator.
 cudaError_t solve_svd(Handle* h, int64_t In, double rtol, bool have_operator = false);
-// S_n = Hadamard product of the other Grams, then Cholesky solve Ahat S = M.
-cudaError_t solve_normal(Handle* h, int n);
-// S_n as above, then Ahat = M pinv(S_n) with the truncated Jacobi SVD (CP-ALS-PINV).
-cudaError_t solve_normal_pinv(Handle* h, int n, double rtol);
+// S_n = Hadamard product of the other Grams (Alg. cp-als) into h->S, and into
+// h->T its Cholesky factor (pinv = false) or its truncated pseudo-inverse
+// (pinv = true, CP-ALS-PINV).  It needs only the Grams, so a sweep runs it
+// beside the MTTKRP.
+cudaError_t normal_operator(Handle* h, int n, bool pinv, double rtol);
+// Ahat S_n = M by the Cholesky factor, or Ahat = M pinv(S_n); the operator is
+// formed first unless have_operator.
+cudaError_t solve_normal(Handle* h, int n, bool have_operator = false);
+cudaError_t solve_normal_pinv(Handle* h, int n, double rtol, bool have_operator = false);
 // Normalise columns of h->Ahat into A_n and lambda; then QR and Gram of A_n.
 cudaError_t normalize_and_refactor(Handle* h, int n);
 // Gram G = A^T A for an I x R factor.

@@ -1264,26 +1264,16 @@ cudaError_t solve_svd(Handle* h, int64_t In, double rtol, bool have_operator)
     return gemm_rows(h, h->W, In, h->R, h->T, h->R, h->Ahat);
 }
 
-cudaError_t solve_normal(Handle* h, int n)
+cudaError_t normal_operator(Handle* h, int n, bool pinv, double rtol)
 {
     GPtrs gp;
     for (int m = 0; m < h->N; ++m) gp.G[m] = h->G[m];
-    hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status, 1);
-    chol_rows_kernel<<<solve_grid(h->dims[n], h->num_sms), kSolveWarps * 32, 0, h->stream>>>(
-        h->M, h->T, h->dims[n], h->R, h->Ahat, h->d_status);
-    h->launches += 2;
-    return cudaGetLastError();
-}
-
-cudaError_t solve_normal_pinv(Handle* h, int n, double rtol)
-{
-    if (!(rtol > 0.0)) rtol = (double)h->R * kEps;
-    GPtrs gp;
-    for (int m = 0; m < h->N; ++m) gp.G[m] = h->G[m];
-    hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status, 0);
+    hadamard_cholesky_kernel<<<1, 256, 0, h->stream>>>(gp, h->N, n, h->R, h->S, h->T, h->d_status, pinv ? 0 : 1);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
+    if (!pinv) return cudaSuccess;
     // S is symmetric, so pinv(S) = pinv(S^T): the same operator as the SVD solve with R0 -> S
+    if (!(rtol > 0.0)) rtol = (double)h->R * kEps;
     constexpr size_t smem = sizeof(double) * jacobi_smem_doubles();
     static bool attr_set = false;
     if (!attr_set) {
@@ -1293,7 +1283,21 @@ cudaError_t solve_normal_pinv(Handle* h, int n, double rtol)
     }
     jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->S, h->R, rtol, h->T, h->d_status);
     h->launches++;
-    CPALS_CUDA_TRY(cudaGetLastError());
+    return cudaGetLastError();
+}
+
+cudaError_t solve_normal(Handle* h, int n, bool have_operator)
+{
+    if (!have_operator) CPALS_CUDA_TRY(normal_operator(h, n, false, 0.0));
+    chol_rows_kernel<<<solve_grid(h->dims[n], h->num_sms), kSolveWarps * 32, 0, h->stream>>>(
+        h->M, h->T, h->dims[n], h->R, h->Ahat, h->d_status);
+    h->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t solve_normal_pinv(Handle* h, int n, double rtol, bool have_operator)
+{
+    if (!have_operator) CPALS_CUDA_TRY(normal_operator(h, n, true, rtol));
     return gemm_rows(h, h->M, h->dims[n], h->R, h->T, h->R, h->Ahat);
 }
 
