@@ -194,15 +194,18 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
     }
     if (is_normal(solve)) {
         // S_n and its Cholesky factor or pseudo-inverse need only the Grams:
-        // the side stream forms them while the MTTKRP runs
-        CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
-        CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-        cudaStream_t main = h->stream;
-        h->stream = h->side;
-        cudaError_t e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
-        h->stream = main;
-        CPALS_CUDA_TRY(e);
-        CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+        // the side stream forms them while the MTTKRP runs (tq->ready: the
+        // sweep has enqueued them already)
+        if (!(tq && tq->ready)) {
+            CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+            CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            cudaStream_t main = h->stream;
+            h->stream = h->side;
+            cudaError_t e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
+            h->stream = main;
+            CPALS_CUDA_TRY(e);
+            CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
+        }
         if (from_partial) CPALS_CUDA_TRY(cpals::mttkrp_from_partial(h, n));
         else CPALS_CUDA_TRY(cpals::mttkrp(h, n));
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
@@ -271,7 +274,31 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
     auto pass = [&](const int* modes, int nm) {
         return is_normal(solve) ? cpals::mttkrp_tree_pass(h, modes, nm) : cpals::dimtree_pass(h, modes, nm);
     };
-    if (is_normal(solve) || !h->krp_tree) {
+    if (is_normal(solve)) {
+        // the first mode of each half needs only Grams that the pass does not
+        // change: its S_n operator is formed on the side stream under the pass
+        auto early_op = [&](int n) -> cudaError_t {
+            CPALS_CUDA_TRY(cudaEventRecord(h->ev_fork, h->stream));
+            CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+            cudaStream_t main = h->stream;
+            h->stream = h->side;
+            cudaError_t e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
+            h->stream = main;
+            CPALS_CUDA_TRY(e);
+            return cudaEventRecord(h->ev_join, h->side);
+        };
+        const TreeQR ready{0, false, nullptr, 0, true};
+        CPALS_CUDA_TRY(early_op(H1[0]));
+        CPALS_CUDA_TRY(pass(H2, n2));
+        for (int k = 0; k < n1; ++k)
+            CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true, k == 0 ? &ready : nullptr));
+        CPALS_CUDA_TRY(early_op(H2[0]));
+        CPALS_CUDA_TRY(pass(H1, n1));
+        for (int k = 0; k < n2; ++k)
+            CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true, k == 0 ? &ready : nullptr));
+        return cpals::fit_efficient(h, solve);
+    }
+    if (!h->krp_tree) {
         CPALS_CUDA_TRY(pass(H2, n2));
         for (int k = 0; k < n1; ++k) CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true));
         CPALS_CUDA_TRY(pass(H1, n1));
