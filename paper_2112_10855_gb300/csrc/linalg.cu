@@ -912,15 +912,16 @@ __global__ void gram_kernel(const double* __restrict__ A, int64_t I, int R, doub
 //  QR:     sum_{i,k} W(i,k) (Ahat R0^T)(i,k)
 //  NORMAL: sum_{i,k} M(i,k) Ahat(i,k)
 __global__ void fit_inner_kernel(const double* __restrict__ Wm, const double* __restrict__ Ahat,
-                                 const double* __restrict__ R0, int64_t I, int R, int qr,
+                                 const double* __restrict__ R0, int64_t I, int R, int qr, int kchunk,
                                  double* __restrict__ part, const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     __shared__ double sh[32];
     double s = 0.0;
     const int64_t i = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31);
+    const int kb = blockIdx.y * kchunk, ke = min(R, kb + kchunk);
     if (i < I) {
-        for (int k = (threadIdx.x >> 5); k < R; k += (blockDim.x >> 5)) {
+        for (int k = kb + (threadIdx.x >> 5); k < ke; k += (blockDim.x >> 5)) {
             double v;
             if (qr) {
                 v = 0.0;
@@ -937,12 +938,26 @@ __global__ void fit_inner_kernel(const double* __restrict__ Wm, const double* __
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        part[blockIdx.x] = t;
+        part[blockIdx.x + (int64_t)gridDim.x * blockIdx.y] = t;
     }
 }
 
+// Block-wide sum (fixed order: strided per thread, then warps, then thread 0).
+__device__ double block_sum(double v, double* sh)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    __syncthreads();
+    return t;   // valid in thread 0
+}
+
 // Final: inner = sum of partials; model norm
-//  QR:     <R0^T R0, diag(l) R_N^T R_N diag(l)>
+//  QR:     <R0^T R0, diag(l) R_N^T R_N diag(l)> = ||R0 diag(l) R_N^T||_F^2
+//          (R0 and R_N upper triangular: entry (i, j) sums k >= max(i, j))
 //  NORMAL: <S_N, diag(l) G_N diag(l)>
 // fit = 1 - sqrt(max(||X||^2 - 2 inner + nrm, 0)) / ||X||, appended to the ring.
 __global__ void fit_final_kernel(const double* __restrict__ part, int nparts, const double* __restrict__ R0orS,
@@ -954,28 +969,20 @@ __global__ void fit_final_kernel(const double* __restrict__ part, int nparts, co
     __shared__ double sh[32];
     double nrm = 0.0;
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-        const int b = e / R, a = e - b * R;
-        double g0, gN;
+        const int j = e / R, i = e - j * R;
         if (qr) {
-            g0 = 0.0; gN = 0.0;
-            for (int k = 0; k < R; ++k) {
-                g0 = fma(R0orS[k + R * a], R0orS[k + R * b], g0);
-                gN = fma(RNorG[k + R * a], RNorG[k + R * b], gN);
-            }
+            double v = 0.0;
+            for (int k = max(i, j); k < R; ++k) v = fma(R0orS[i + R * k] * lambda[k], RNorG[j + R * k], v);
+            nrm = fma(v, v, nrm);
         } else {
-            g0 = R0orS[e];
-            gN = RNorG[e];
+            nrm = fma(R0orS[e] * lambda[i], RNorG[e] * lambda[j], nrm);
         }
-        nrm = fma(g0 * lambda[a], gN * lambda[b], nrm);
     }
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = nrm;
-    __syncthreads();
+    double in = 0.0;
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x) in += part[p];
+    const double tot = block_sum(nrm, sh);
+    const double inner = block_sum(in, sh);
     if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += sh[w];
-        double inner = 0.0;
-        for (int p = 0; p < nparts; ++p) inner += part[p];
         double res2 = *normX2 - 2.0 * inner + tot;
         if (res2 < 0.0) res2 = 0.0;
         const double f = 1.0 - sqrt(res2) / sqrt(*normX2);
@@ -1322,9 +1329,14 @@ cudaError_t fit_efficient(Handle* h, int solve)
     const int64_t I = h->dims[n];
     const int qr = (solve != CPALS_SOLVE_NORMAL && solve != CPALS_SOLVE_NORMAL_PINV);
     const unsigned nb = (unsigned)((I + 31) / 32);
-    fit_inner_kernel<<<nb, 256, 0, h->stream>>>(qr ? h->W : h->M, h->Ahat, h->R0, I, h->R, qr, h->scratch,
-                                                h->d_status);
-    fit_final_kernel<<<1, 256, 0, h->stream>>>(h->scratch, (int)nb, qr ? h->R0 : h->S, qr ? h->Rf[n] : h->G[n],
+    // split the R columns over CTAs too, so that short modes still fill the SMs
+    const int ks = (int)std::max<int64_t>(1, std::min<int64_t>(h->R, (2LL * h->num_sms + nb - 1) / nb));
+    const int kchunk = (h->R + ks - 1) / ks;
+    const int kgrid = (h->R + kchunk - 1) / kchunk;
+    fit_inner_kernel<<<dim3(nb, (unsigned)kgrid), 256, 0, h->stream>>>(qr ? h->W : h->M, h->Ahat, h->R0, I, h->R, qr,
+                                                                      kchunk, h->scratch, h->d_status);
+    fit_final_kernel<<<1, 256, 0, h->stream>>>(h->scratch, (int)nb * kgrid, qr ? h->R0 : h->S,
+                                               qr ? h->Rf[n] : h->G[n],
                                                h->lambda, h->R, qr, h->d_normX2, h->d_fit, h->fit_cap,
                                                h->d_fit_count, h->d_fit + h->fit_cap, h->d_status);
     h->launches += 2;
