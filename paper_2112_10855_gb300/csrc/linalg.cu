@@ -197,12 +197,19 @@ __global__ void tsqr_combine_kernel(const double* __restrict__ Qi, int64_t m, in
 // reflector form and sign convention as hh_qr_blocks_kernel.  Output: Q of
 // the pair (2n x n) in rows [2bn, 2bn+2n) of Qout, R in rows [bn, bn+n) of Rout.
 //
-// Thread (c, g) = (tid % 64, tid / 64) owns column c and the rows i = g mod 4
-// of every update, so each FP64 instruction works on 32 columns at once; the
-// four partial dot products of a column are added in a fixed order.
-constexpr int kTriThreads = 256;
+// Thread (c, g) = (tid % 64, tid / 64) of the eight compute warps owns column
+// c and the rows i = g mod 4 of every update, so each FP64 instruction works
+// on 32 columns at once; the four partial dot products of a column are added
+// in a fixed order by every thread that needs the sum.  A ninth warp forms
+// the reflectors: step j ends with the threads of column j+1 leaving the
+// partial sums of squares of its updated tail, and while the compute warps
+// form step j+1's partial dot products (which use the unscaled tail) the
+// reflector warp turns those sums into tau, the dlarfg scale and beta.  The
+// tails are scaled once after the loop.  Two block barriers per step.
+constexpr int kTriThreads = 256;                 // compute threads
+constexpr int kTriBlock = kTriThreads + 32;      // + the reflector warp
 
-__global__ void __launch_bounds__(kTriThreads) hh_qr_tri_kernel(
+__global__ void __launch_bounds__(kTriBlock) hh_qr_tri_kernel(
     const double* __restrict__ A, int64_t lda, int K, int n, double* __restrict__ Qout, int64_t ldq,
     double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
 {
@@ -210,101 +217,112 @@ __global__ void __launch_bounds__(kTriThreads) hh_qr_tri_kernel(
     extern __shared__ double sm[];
     const int ld = n + 1;             // odd leading dimension: lanes on consecutive columns hit distinct banks
     double* U = sm;                   // upper block
-    double* Lo = U + n * ld;          // lower block; rows 0..j of column j: reflector j
+    double* Lo = U + n * ld;          // lower block; rows 0..j of column j: reflector j (unscaled in the loop)
     double* Qt = Lo + n * ld;         // explicit Q, upper half
     double* Qb = Qt + n * ld;         // explicit Q, lower half
     double* tau = Qb + n * ld;        // n
-    double* part = tau + n;           // 4 x 64 partial sums
-    double* sv = part + 256;          // 64
-    double* red = sv + 64;            // 2
+    double* scl = tau + n;            // n dlarfg scales
+    double* part = scl + n;           // 4 x 64 partial sums
+    double* part2 = part + 256;       // 4 partial sums of squares (next column)
     const int b = blockIdx.x;
     const bool second = 2 * b + 1 < K;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
+    const bool comp = tid < kTriThreads;
     const int c = tid & 63, g = tid >> 6;
     const double* A1 = A + (int64_t)2 * b * n;
     const double* A2 = A1 + n;
-    for (int e = tid; e < n * n; e += kTriThreads) {
+    for (int e = tid; e < n * n; e += kTriBlock) {
         const int j = e / n, i = e - j * n;
         U[i + ld * j] = (i <= j) ? A1[i + lda * j] : 0.0;
         Lo[i + ld * j] = (second && i <= j) ? A2[i + lda * j] : 0.0;
     }
     __syncthreads();
+    if (tid == kTriThreads) {          // reflector 0: the tail of column 0 is Lo(0, 0)
+        const double v = Lo[0];
+        hh_reflector(U[0], v * v, &tau[0], &scl[0], &U[0]);
+    }
+    __syncthreads();
+    // U(j, c) -= s is held in a register of the group-0 thread of column c and
+    // written during the next step's dot products, which do not read U
+    double upend = 0.0;
+    int ujp = -1;
     for (int j = 0; j < n; ++j) {
-        if (warp == 0) {
-            double s = 0.0;
-            for (int i = lane; i <= j; i += 32) s = fma(Lo[i + ld * j], Lo[i + ld * j], s);
-            s = warp_sum(s);
-            if (lane == 0) {
-                const double alpha = U[j + ld * j];
-                double t = 0.0, scale = 0.0, beta = alpha;
-                if (s > 0.0) {
-                    const double nrm = sqrt(fma(alpha, alpha, s));
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    const double d = beta - alpha;
-                    const double r = 1.0 / (beta * d);
-                    t = d * d * r;
-                    scale = -beta * r;
-                }
-                tau[j] = t;
-                red[0] = scale;
-                U[j + ld * j] = beta;
-            }
-        }
-        __syncthreads();
-        const double tj = tau[j];
-        if (tj == 0.0) continue;   // uniform: nothing below the diagonal to eliminate
-        if (tid <= j) Lo[tid + ld * j] *= red[0];
-        __syncthreads();
-        const bool col = c > j && c < n;
+        const bool col = comp && c > j && c < n;
+        // partial dot products of the unscaled tail of column j with column c
         if (col) {
             double p = 0.0;
             for (int i = g; i <= j; i += 4) p = fma(Lo[i + ld * j], Lo[i + ld * c], p);
             part[g * 64 + c] = p;
         }
+        if (ujp >= 0) { U[ujp + ld * c] -= upend; ujp = -1; }
         __syncthreads();
-        if (col && g == 0) {
-            const double sc = (((part[c] + part[64 + c]) + part[128 + c]) + part[192 + c] + U[j + ld * c]) * tj;
-            sv[c] = sc;
-            U[j + ld * c] -= sc;
+        const double tj = tau[j], sc = scl[j];
+        double q = 0.0;
+        if (col && tj != 0.0) {
+            const double sd = ((part[c] + part[64 + c]) + part[128 + c]) + part[192 + c];
+            const double sj = fma(sd, sc, U[j + ld * c]) * tj;
+            const double ss = sj * sc;
+            for (int i = g; i <= j; i += 4) {
+                const double w = fma(-ss, Lo[i + ld * j], Lo[i + ld * c]);
+                Lo[i + ld * c] = w;
+                if (c == j + 1) q = fma(w, w, q);
+            }
+            if (g == 0) { upend = sj; ujp = j; }
+        } else if (col && c == j + 1) {
+            for (int i = g; i <= j; i += 4) q = fma(Lo[i + ld * c], Lo[i + ld * c], q);
+        }
+        if (comp && c == j + 1 && c < n) {
+            // row j+1 of the lower block joins the tail of column j+1 (untouched so far)
+            if (((j + 1) & 3) == g) q = fma(Lo[(j + 1) + ld * c], Lo[(j + 1) + ld * c], q);
+            part2[g] = q;
         }
         __syncthreads();
-        if (col) {
-            const double sc = sv[c];
-            for (int i = g; i <= j; i += 4) Lo[i + ld * c] = fma(-sc, Lo[i + ld * j], Lo[i + ld * c]);
+        if (tid == kTriThreads && j + 1 < n) {
+            const double s2 = ((part2[0] + part2[1]) + part2[2]) + part2[3];
+            hh_reflector(U[(j + 1) + ld * (j + 1)], s2, &tau[j + 1], &scl[j + 1], &U[(j + 1) + ld * (j + 1)]);
         }
-        __syncthreads();
+        // the next step's partial dots read neither tau, scl nor U: the
+        // reflector warp runs beside them, and the barrier after the dots
+        // orders its writes before their use
+    }
+    if (ujp >= 0) U[ujp + ld * c] -= upend;
+    __syncthreads();
+    for (int e = tid; e < n * n; e += kTriBlock) {
+        const int j = e / n, i = e - j * n;
+        if (i <= j && tau[j] != 0.0) Lo[i + ld * j] *= scl[j];
     }
     // explicit Q = H_0 ... H_{n-1} [I; 0], backward accumulation (H_j touches columns >= j)
-    for (int e = tid; e < n * n; e += kTriThreads) {
+    for (int e = tid; e < n * n; e += kTriBlock) {
         const int j = e / n, i = e - j * n;
         Qt[i + ld * j] = (i == j) ? 1.0 : 0.0;
         Qb[i + ld * j] = 0.0;
     }
     __syncthreads();
+    // Qt(j, c) -= sc likewise waits in the group-0 thread for the next step's
+    // dot products, which read only Qb and the reflectors
+    double qpend = 0.0;
+    int qjp = -1;
     for (int j = n - 1; j >= 0; --j) {
         const double tj = tau[j];
-        if (tj == 0.0) continue;
-        const bool col = c >= j && c < n;
+        const bool col = comp && c >= j && c < n;
         if (col) {
             double p = 0.0;
             for (int i = g; i <= j; i += 4) p = fma(Lo[i + ld * j], Qb[i + ld * c], p);
             part[g * 64 + c] = p;
         }
+        if (qjp >= 0) { Qt[qjp + ld * c] -= qpend; qjp = -1; }
         __syncthreads();
-        if (col && g == 0) {
+        if (col && tj != 0.0) {
             const double sc = (((part[c] + part[64 + c]) + part[128 + c]) + part[192 + c] + Qt[j + ld * c]) * tj;
-            sv[c] = sc;
-            Qt[j + ld * c] -= sc;
-        }
-        __syncthreads();
-        if (col) {
-            const double sc = sv[c];
             for (int i = g; i <= j; i += 4) Qb[i + ld * c] = fma(-sc, Lo[i + ld * j], Qb[i + ld * c]);
+            if (g == 0) { qpend = sc; qjp = j; }
         }
         __syncthreads();
     }
+    if (qjp >= 0) Qt[qjp + ld * c] -= qpend;
+    __syncthreads();
     double* Q1 = Qout + (int64_t)2 * b * n;
-    for (int e = tid; e < n * n; e += kTriThreads) {
+    for (int e = tid; e < n * n; e += kTriBlock) {
         const int j = e / n, i = e - j * n;
         const double sgn = (U[j + ld * j] < 0.0) ? -1.0 : 1.0;
         Q1[i + ldq * j] = sgn * Qt[i + ld * j];
@@ -334,7 +352,7 @@ __global__ void tri_combine_kernel(const double* __restrict__ Qi, int64_t ldqi, 
     }
 }
 
-inline size_t tri_smem_bytes(int n) { return sizeof(double) * ((size_t)4 * n * (n + 1) + n + 256 + 64 + 2); }
+inline size_t tri_smem_bytes(int n) { return sizeof(double) * ((size_t)4 * n * (n + 1) + 2 * (size_t)n + 256 + 4); }
 
 // W and Q (mb x n each), tau (n), 32 scratch values and the n reflector scales
 inline size_t qr_smem_bytes(int64_t mb, int n)
@@ -1013,7 +1031,7 @@ cudaError_t tsqr_tri(Handle* h, const double* Rs, int K, int n, double* Q, doubl
     const int P = (K + 1) / 2;
     const size_t smem = tri_smem_bytes(n);
     if (P == 1) {   // K == 2: the pair's Q is the result
-        hh_qr_tri_kernel<<<1, kTriThreads, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Q, (int64_t)K * n, R, n,
+        hh_qr_tri_kernel<<<1, kTriBlock, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Q, (int64_t)K * n, R, n,
                                                             h->d_status);
         h->launches++;
         return cudaGetLastError();
@@ -1024,7 +1042,7 @@ cudaError_t tsqr_tri(Handle* h, const double* Rs, int K, int n, double* Q, doubl
     double* Qt = Rs2 + P * nn;              // P n x n
     const int64_t used = 4 * P * nn;
     if (used > ws_elems) return cudaErrorInvalidValue;
-    hh_qr_tri_kernel<<<P, kTriThreads, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Qi, 2 * (int64_t)P * n, Rs2,
+    hh_qr_tri_kernel<<<P, kTriBlock, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Qi, 2 * (int64_t)P * n, Rs2,
                                                          (int64_t)P * n, h->d_status);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
