@@ -203,7 +203,9 @@ cudaError_t residual_direct(Handle* h, double* d_out);
 
 // Householder QR with explicit Q and diag(R) >= 0 (Sec. 2.1).  A is m x n
 // (lda = m), Q is m x n, R is n x n.  A may alias Q.
-cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R);
+// dense = false for structured inputs (Khatri-Rao steps, triangular factors),
+// whose leaves keep the kernel that skips identity reflectors.
+cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, bool dense = true);
 // QR of V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->Q0, h->R0 (structured, V_n not formed).
 // With implicit = true Q0 is not formed either: the Q factors of the fold steps
 // go to h->KP (for the Kruskal-input path) and only R0 is written.

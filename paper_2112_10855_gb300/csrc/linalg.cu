@@ -165,6 +165,140 @@ __global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
     }
 }
 
+// Householder QR of dense row blocks with 32 < n <= 64 columns (the TSQR
+// leaves of a rank-33..64 factor).  Same block split, reflector form, sign
+// convention and outputs as hh_qr_blocks_kernel, but thread (c, g) = (tid %
+// 64, tid / 64) of the eight compute warps owns column c and the rows i = g
+// mod 4, as in the triangle-pair kernel: a warp-wide FP64 instruction then
+// serves 32 columns, where a warp per column spends five shuffle-adds per
+// column and step on a block only ~n rows tall.  A ninth warp forms the next
+// reflector beside the compute warps' dot products; tails stay unscaled in
+// the loop; two block barriers per step.
+constexpr int kColsThreads = 256, kColsBlock = kColsThreads + 32;
+
+inline size_t cols_smem_bytes(int64_t mb, int n)
+{
+    const int64_t ldw = mb | 1;
+    return sizeof(double) * ((size_t)2 * ldw * n + 2 * (size_t)n + 256 + 4);
+}
+
+__global__ void __launch_bounds__(kColsBlock) hh_qr_cols_kernel(
+    const double* __restrict__ A, int64_t lda, int64_t m, int n, int nb, double* __restrict__ Qout, int64_t ldq,
+    double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    extern __shared__ double sm[];
+    const int b = blockIdx.x;
+    const int64_t off = (int64_t)b * m / nb, end = (int64_t)(b + 1) * m / nb;
+    const int mb = (int)(end - off);          // >= n (the caller's split keeps it so)
+    const int ldw = mb | 1;                   // odd: lanes on consecutive columns hit distinct banks
+    double* W = sm;                           // mb x n: reflectors below the diagonal, R on and above
+    double* Qs = W + (size_t)ldw * n;         // mb x n explicit Q
+    double* tau = Qs + (size_t)ldw * n;
+    double* scl = tau + n;
+    double* part = scl + n;                   // 4 x 64
+    double* part2 = part + 256;               // 4
+    const int tid = threadIdx.x;
+    const bool comp = tid < kColsThreads;
+    const int c = tid & 63, g = tid >> 6;
+    for (int e = tid; e < mb * n; e += kColsBlock) {
+        const int j = e / mb, i = e - j * mb;
+        W[i + ldw * j] = A[(off + i) + lda * j];
+    }
+    __syncthreads();
+    if (comp && c == 0) {
+        double q = 0.0;
+        for (int i = 1 + g; i < mb; i += 4) q = fma(W[i], W[i], q);
+        part2[g] = q;
+    }
+    __syncthreads();
+    if (tid == kColsThreads) {
+        const double s2 = ((part2[0] + part2[1]) + part2[2]) + part2[3];
+        hh_reflector(W[0], s2, &tau[0], &scl[0], &W[0]);
+    }
+    __syncthreads();
+    // W(j, c) -= s waits in the thread that owns row j of column c and is
+    // written before that thread's next dot product (rows j+2.. of the next
+    // step do not include row j, and nobody else reads it meanwhile)
+    double pend = 0.0;
+    int jp = -1;
+    for (int j = 0; j < n; ++j) {
+        const bool col = comp && c > j && c < n;
+        if (jp >= 0) { W[jp + ldw * c] -= pend; jp = -1; }
+        if (col) {
+            double p = 0.0;
+            for (int i = j + 1 + ((g - (j + 1)) & 3); i < mb; i += 4) p = fma(W[i + ldw * j], W[i + ldw * c], p);
+            part[g * 64 + c] = p;
+        }
+        __syncthreads();
+        const double tj = tau[j], sc = scl[j];
+        double q = 0.0;
+        if (col && tj != 0.0) {
+            const double sd = ((part[c] + part[64 + c]) + part[128 + c]) + part[192 + c];
+            const double sj = fma(sd, sc, W[j + ldw * c]) * tj;
+            const double ss = sj * sc;
+            for (int i = j + 1 + ((g - (j + 1)) & 3); i < mb; i += 4) {
+                const double w = fma(-ss, W[i + ldw * j], W[i + ldw * c]);
+                W[i + ldw * c] = w;
+                if (c == j + 1 && i > j + 1) q = fma(w, w, q);
+            }
+            if (g == (j & 3)) { pend = sj; jp = j; }
+        } else if (col && c == j + 1) {
+            for (int i = j + 2 + ((g - (j + 2)) & 3); i < mb; i += 4) q = fma(W[i + ldw * c], W[i + ldw * c], q);
+        }
+        if (comp && c == j + 1 && c < n) part2[g] = q;
+        __syncthreads();
+        if (tid == kColsThreads && j + 1 < n) {
+            const double s2 = ((part2[0] + part2[1]) + part2[2]) + part2[3];
+            double* d = W + (j + 1) + ldw * (j + 1);
+            hh_reflector(*d, s2, &tau[j + 1], &scl[j + 1], d);
+        }
+    }
+    if (jp >= 0) W[jp + ldw * c] -= pend;
+    __syncthreads();
+    for (int e = tid; e < mb * n; e += kColsBlock) {
+        const int j = e / mb, i = e - j * mb;
+        if (i > j && tau[j] != 0.0) W[i + ldw * j] *= scl[j];
+        Qs[i + ldw * j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // explicit Q = H_0 ... H_{n-1} [I; 0], backward.  Q(j, c) -= s waits in
+    // the thread that owns row j of column c, which writes it before its next
+    // dot product reads the row (step j-1 reads rows j.. of column c)
+    jp = -1;
+    for (int j = n - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        const bool col = comp && c >= j && c < n;
+        if (jp >= 0) { Qs[jp + ldw * c] -= pend; jp = -1; }
+        if (col) {
+            double p = 0.0;
+            for (int i = j + 1 + ((g - (j + 1)) & 3); i < mb; i += 4) p = fma(W[i + ldw * j], Qs[i + ldw * c], p);
+            part[g * 64 + c] = p;
+        }
+        __syncthreads();
+        if (col && tj != 0.0) {
+            const double sc = (((part[c] + part[64 + c]) + part[128 + c]) + part[192 + c] + Qs[j + ldw * c]) * tj;
+            for (int i = j + 1 + ((g - (j + 1)) & 3); i < mb; i += 4)
+                Qs[i + ldw * c] = fma(-sc, W[i + ldw * j], Qs[i + ldw * c]);
+            if (g == (j & 3)) { pend = sc; jp = j; }
+        }
+        __syncthreads();
+    }
+    if (jp >= 0) Qs[jp + ldw * c] -= pend;
+    __syncthreads();
+    for (int e = tid; e < mb * n; e += kColsBlock) {
+        const int j = e / mb, i = e - j * mb;
+        const double sgn = (W[j + ldw * j] < 0.0) ? -1.0 : 1.0;
+        Qout[(off + i) + ldq * j] = sgn * Qs[i + ldw * j];
+    }
+    for (int e = tid; e < n * n; e += kColsBlock) {
+        const int j = e / n, i = e - j * n;       // R(i, j)
+        double v = 0.0;
+        if (i <= j) v = ((W[i + ldw * i] < 0.0) ? -1.0 : 1.0) * W[i + ldw * j];
+        Rout[((int64_t)b * n + i) + ldr * j] = v;
+    }
+}
+
 // Qout(block rows of b) = Qi(block rows of b) * Qtop(b*n:(b+1)*n, :)  (TSQR combine)
 __global__ void tsqr_combine_kernel(const double* __restrict__ Qi, int64_t m, int n, int nb,
                                     const double* __restrict__ Qtop, int64_t ldt, double* __restrict__ Qout,
@@ -1057,12 +1191,32 @@ cudaError_t tsqr_tri(Handle* h, const double* Rs, int K, int n, double* Q, doubl
 // Tall-skinny QR: one CTA when the matrix is small (about 1 MFLOP or less),
 // else dense Householder leaves of at least n rows spread over the SMs, the
 // tree of triangle pairs, and one combine back to the leaves.
-cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, double* ws, int64_t ws_elems)
+// Dense leaves with 32 < n <= 64 columns (and at least n rows) go through the
+// column-per-thread kernel; structured ones (the Khatri-Rao steps, whose
+// reflectors are mostly empty) keep the warp-per-column kernel, which skips
+// a column's update when its reflector is the identity.
+inline bool use_cols_leaf(bool dense, int64_t mb, int n)
+{
+    return dense && n > 32 && n <= 64 && mb >= n && cols_smem_bytes(mb, n) <= kQrSmemMaxBytes;
+}
+
+void launch_leaves(Handle* h, bool cols, unsigned nb, int64_t mbmax, const double* A, int64_t m, int n, double* Q,
+                   double* R, int64_t ldr)
+{
+    if (cols)
+        hh_qr_cols_kernel<<<nb, kColsBlock, cols_smem_bytes(mbmax, n), h->stream>>>(A, m, m, n, (int)nb, Q, m, R, ldr,
+                                                                                  h->d_status);
+    else
+        hh_qr_blocks_kernel<<<nb, kQrThreads, qr_smem_bytes((int)mbmax, n), h->stream>>>(A, m, m, n, (int)nb, Q, m,
+                                                                                          R, ldr, h->d_status);
+    h->launches++;
+}
+
+cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, double* ws, int64_t ws_elems,
+                 bool dense)
 {
     if (qr_leaf_fits(m, n) && m * n * n <= ((int64_t)1 << 18)) {
-        const size_t smem = qr_smem_bytes((int)m, n);
-        hh_qr_blocks_kernel<<<1, kQrThreads, smem, h->stream>>>(A, m, m, n, 1, Q, m, R, n, h->d_status);
-        h->launches++;
+        launch_leaves(h, use_cols_leaf(dense, m, n), 1, m, A, m, n, Q, R, n);
         return cudaGetLastError();
     }
     const int64_t leaf_rows = std::max<int64_t>({(int64_t)n, 32, (m + h->num_sms - 1) / h->num_sms});
@@ -1072,9 +1226,7 @@ cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double
     const int64_t mbmax = (m + nb - 1) / nb;
     if (!qr_leaf_fits(mbmax, n)) return cudaErrorInvalidValue;
     if (nb == 1) {
-        hh_qr_blocks_kernel<<<1, kQrThreads, qr_smem_bytes((int)m, n), h->stream>>>(A, m, m, n, 1, Q, m, R, n,
-                                                                                      h->d_status);
-        h->launches++;
+        launch_leaves(h, use_cols_leaf(dense, m, n), 1, m, A, m, n, Q, R, n);
         return cudaGetLastError();
     }
     double* Qi = ws;                        // m x n
@@ -1083,9 +1235,7 @@ cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double
     double* rest = Qt + nb * n * n;
     const int64_t used = m * n + 2 * nb * n * n;
     if (used > ws_elems) return cudaErrorInvalidValue;
-    hh_qr_blocks_kernel<<<(unsigned)nb, kQrThreads, qr_smem_bytes((int)mbmax, n), h->stream>>>(
-        A, m, m, n, (int)nb, Qi, m, Rs, nb * n, h->d_status);
-    h->launches++;
+    launch_leaves(h, use_cols_leaf(dense, mbmax, n), (unsigned)nb, mbmax, A, m, n, Qi, Rs, nb * n);
     CPALS_CUDA_TRY(cudaGetLastError());
     CPALS_CUDA_TRY(tsqr_tri(h, Rs, (int)nb, n, Qt, R, rest, ws_elems - used));
     tsqr_combine_kernel<<<grid_for(m * n, 256, h->num_sms), 256, 0, h->stream>>>(Qi, m, n, (int)nb, Qt, nb * n, Q,
@@ -1108,15 +1258,18 @@ cudaError_t qr_kernel_attrs()
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(krp_stair_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)stair_smem_bytes(kStairMaxN));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(hh_qr_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kQrSmemMaxBytes);
         return e;
     }();
     return err;
 }
 
-cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R)
+cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, bool dense)
 {
     CPALS_CUDA_TRY(qr_kernel_attrs());
-    return tsqr(h, A, m, n, Q, R, h->qr_ws, h->qr_ws_elems);
+    return tsqr(h, A, m, n, Q, R, h->qr_ws, h->qr_ws_elems, dense);
 }
 
 // QR of V_n = F_1 (.) F_2 (.) ... (.) F_{N-1} (the R_m of every mode m != n, highest
@@ -1159,7 +1312,7 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
                                                                                               h->d_status);
             h->launches++;
             CPALS_CUDA_TRY(cudaGetLastError());
-            return householder_qr(h, h->KM, (int64_t)R * R, R, Qo, Ro);
+            return householder_qr(h, h->KM, (int64_t)R * R, R, Qo, Ro, false);
         };
         if (implicit) {
             CPALS_CUDA_TRY(step_qr(h->KP + (size_t)(k - 1) * R3));
@@ -1190,7 +1343,7 @@ cudaError_t krp_qr(Handle* h, int n, bool implicit)
     int cnt = 0;
     for (int m = 0; m < h->N; ++m)
         if (m != n) Rl[cnt++] = h->Rf[m];   // ascending: Rl[0] is the fastest (rightmost) factor
-    if (cnt == 1) return householder_qr(h, Rl[0], R, R, implicit ? h->KP : h->Q0, h->R0);
+    if (cnt == 1) return householder_qr(h, Rl[0], R, R, implicit ? h->KP : h->Q0, h->R0, false);
     return fold_qr(h, Rl, cnt, implicit ? nullptr : h->Q0, h->R0, implicit);
 }
 
@@ -1236,7 +1389,7 @@ cudaError_t krp_qr_tree(Handle* h, int n, int slot, bool other_left, const int* 
     // V_n = Own (.) M = (I_S (x) Q_M)(Own (.) R_M)
     if (nown == 0) {
         const int64_t rows = h->hq_rows[slot];
-        if (h->hq_single[slot]) return householder_qr(h, h->hr_ptr[slot], R, R, h->Q0, h->R0);
+        if (h->hq_single[slot]) return householder_qr(h, h->hr_ptr[slot], R, R, h->Q0, h->R0, false);
         CPALS_CUDA_TRY(cudaMemcpyAsync(h->Q0, h->HQ[slot], sizeof(double) * rows * R, cudaMemcpyDeviceToDevice,
                                        h->stream));
         return cudaMemcpyAsync(h->R0, h->hr_ptr[slot], sizeof(double) * R * R, cudaMemcpyDeviceToDevice, h->stream);
