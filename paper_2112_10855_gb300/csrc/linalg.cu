@@ -1272,16 +1272,6 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
     return tsqr(h, A, m, n, Q, R, h->qr_ws, h->qr_ws_elems, dense);
 }
 
-// QR of V_n = F_1 (.) F_2 (.) ... (.) F_{N-1} (the R_m of every mode m != n, highest
-// mode first; Sec. 3.1) without forming V_n.  If B = Q_B R_B is the thin QR
-// of the trailing Khatri-Rao product, then by Eq. kr-id
-//     F (.) B = (I_R (x) Q_B) (F (.) R_B),
-// and I_R (x) Q_B has orthonormal columns, so QR(F (.) B) needs only the QR of
-// the R^2 x R matrix F (.) R_B.  Folding from the lowest mode upward, the QR of V_n
-// takes N-2 QRs of R^2 x R matrices and one Kronecker-structured product per
-// step to build the explicit Q0 (R^{N-1} x R).  The thin QR with diag(R0) >= 0
-// is unique, so this equals the Householder QR of the explicit V_n up to
-// rounding.
 // QR of the Khatri-Rao product Rl[cnt-1] (.) ... (.) Rl[0] of upper-triangular
 // R x R factors (Rl[0] rightmost: its row index runs fastest), cnt >= 2, by
 // the Kronecker fold: if B = Q_B R_B then F (.) B = (I (x) Q_B)(F (.) R_B)
@@ -1335,6 +1325,16 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
     return cudaSuccess;
 }
 
+// QR of V_n = F_1 (.) F_2 (.) ... (.) F_{N-1} (the R_m of every mode m != n, highest
+// mode first; Sec. 3.1) without forming V_n.  If B = Q_B R_B is the thin QR
+// of the trailing Khatri-Rao product, then by Eq. kr-id
+//     F (.) B = (I_R (x) Q_B) (F (.) R_B),
+// and I_R (x) Q_B has orthonormal columns, so QR(F (.) B) needs only the QR of
+// the R^2 x R matrix F (.) R_B.  Folding from the lowest mode upward, the QR of V_n
+// takes N-2 QRs of R^2 x R matrices and one Kronecker-structured product per
+// step to build the explicit Q0 (R^{N-1} x R).  The thin QR with diag(R0) >= 0
+// is unique, so this equals the Householder QR of the explicit V_n up to
+// rounding.
 cudaError_t krp_qr(Handle* h, int n, bool implicit)
 {
     CPALS_CUDA_TRY(qr_kernel_attrs());
