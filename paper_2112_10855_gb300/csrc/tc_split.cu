@@ -38,6 +38,10 @@
 // (cp.async.bulk) into a short ring of operand slots; one thread issues the
 // MMAs with A read from tensor memory; four epilogue warps drain a
 // double-buffered accumulator while the next tile accumulates.
+//
+// The same TMA ring also feeds FP32 FMAs on the CUDA cores
+// (ttm_f32_pipe_kernel, at the end): the FP32 precision's passes over X and
+// the FP32 contractions of intermediates in the mixed precisions.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
