@@ -315,6 +315,9 @@ inline int64_t ttm_ksplit(int64_t ctas_xy, int tpb, int64_t K, int num_sms, int6
         ks = std::min<int64_t>(ks, (part_elems * 16 / 17) / std::max<int64_t>(outn, 1));
         if (ks < 2) ks = 1;
     }
+    // up to 16 splits take one reduction pass instead of two: stay there when
+    // the grid still gives every SM four CTAs
+    if (ks > 16 && ctas_xy * 16 >= 4LL * num_sms) ks = 16;
     const int64_t kchunk = (K + ks - 1) / ks;
     return (K + kchunk - 1) / kchunk;
 }
