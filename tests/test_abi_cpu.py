@@ -77,6 +77,25 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.cpals_launch_count(None) == -1
 
 
+def test_options_match_the_header(lib):
+    # the binding's option setters pass the enum values include/cpals.h declares
+    import inspect
+    import os
+    hdr = open(os.path.join(_build.ROOT, "include", "cpals.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"(CPALS_OPT_[A-Z0-9_]+)\s*=\s*(\d+)", hdr))
+    assert enum == {"CPALS_OPT_DIMTREE": 0, "CPALS_OPT_TC_PIPELINE": 1, "CPALS_OPT_KRP_TREE": 2,
+                    "CPALS_OPT_F32_PIPELINE": 3}
+    setters = {"set_dimtree": "CPALS_OPT_DIMTREE", "set_tc_pipeline": "CPALS_OPT_TC_PIPELINE",
+               "set_krp_tree": "CPALS_OPT_KRP_TREE", "set_f32_pipeline": "CPALS_OPT_F32_PIPELINE"}
+    for name, opt in setters.items():
+        src = inspect.getsource(getattr(cpals.CPALS, name))
+        m = re.search(r"cpals_set_option\(self\._h, (\d+),", src)
+        assert m and int(m.group(1)) == enum[opt], name
+    # a null handle is rejected before the option is looked at
+    for opt in enum.values():
+        assert lib.cpals_set_option(None, opt, 1) == cpals.ERR_ARG
+
+
 def test_splitmix64_matches_published_definition():
     # SplitMix64 seeded with 0: the first output is 0xE220A8397B1DCDAF
     z = inputs._mix64(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))
