@@ -9,6 +9,13 @@
 // decreasing-dimension order (Sec. 3.2), ping-ponging between two workspace
 // buffers; the first one streams X from HBM, the later ones read the shrunken
 // intermediate (R/I of the previous size), which usually stays in L2.
+//
+// Kernel per TTM: FP64 -> ttm_rows_kernel (CTA size chosen per launch);
+// FP32 -> the TMA-ring pipeline of tc_split.cu when 9 <= R <= 64 and
+// L % 4 == 0, else ttm_fiber4_kernel for L == 1, ttm_rows4_kernel for
+// L % 4 == 0, ttm_rows_kernel otherwise; 3xBF16 / 3xTF32 run the pass over X
+// on the tensor cores (tc_split.cu) and their later TTMs like FP32.  Small
+// row counts split K over grid.z with a fixed-order reduction.
 #include <algorithm>
 #include <mutex>
 
