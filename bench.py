@@ -290,9 +290,11 @@ def e2e_double_buffered(cpals, dims, R, Xh, Ah, solve, steps):
     torch.cuda.synchronize()
     turn = [threading.Semaphore(1), threading.Semaphore(0)]
     errors = []
+    device = torch.cuda.current_device()   # a new host thread starts on device 0
 
     def worker(i):
         try:
+            torch.cuda.set_device(device)
             for _ in range(i, steps, 2):
                 turn[i].acquire()
                 if errors:               # the other thread failed: stop
