@@ -21,7 +21,12 @@
  *  - Every call returns a cpals_status.  cpals_last_error() gives a message.
  *  - Work is enqueued on the stream set with cpals_set_stream (default: the
  *    legacy default stream) and is asynchronous, except where a call says it
- *    synchronises.
+ *    synchronises.  Inside a mode update or a sweep the handle also runs work
+ *    on a private high-priority stream (the QR of V_n, the solve operators of
+ *    R0 or S_n): it forks from the caller's stream with an event and joins
+ *    back before the call's last kernel, so every call stays ordered on the
+ *    caller's stream.  Distinct handles may be driven from distinct host
+ *    threads; one handle must not be used by two threads at once.
  *  - Pointer arguments carry a `mem` flag: CPALS_MEM_DEVICE means device
  *    memory that the caller owns; CPALS_MEM_HOST means host memory.  Host
  *    transfers are synchronous with respect to the host.
