@@ -1,0 +1,122 @@
+"""Host logic of bench.py's double-buffered end-to-end loop, on CPU.
+
+The loop drives two handles from two host threads; a copy token alternates
+between them so that one thread copies its step's inputs while the other runs
+its sweep.  Here the handles are fakes that record when each call starts and
+ends, and torch's CUDA calls are stubbed, so the protocol itself is checked:
+every step runs once, the copies never overlap, each copy overlaps the other
+handle's sweep, and a failing handle ends the loop with its error instead of a
+hang."""
+import importlib.util
+import os
+import threading
+import time
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def load_bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+class FakeHandle:
+    log = []
+    lock = threading.Lock()
+    fail_at = None            # (handle id, call count) that raises
+
+    def __init__(self, hid):
+        self.hid = hid
+        self.calls = 0
+
+    def _rec(self, what, dur):
+        t0 = time.perf_counter()
+        time.sleep(dur)
+        with FakeHandle.lock:
+            FakeHandle.log.append((self.hid, what, t0, time.perf_counter()))
+
+    def set_stream(self, s):
+        pass
+
+    def set_tensor(self, X):
+        self.calls += 1
+        if FakeHandle.fail_at == (self.hid, self.calls):
+            raise RuntimeError("planted failure")
+        self._rec("copy", 0.02)
+
+    def set_factors(self, A):
+        pass
+
+    def iterate(self, n, **kw):
+        self._rec("sweep", 0.02)
+        return 1
+
+    def get_factors(self):
+        return None, None
+
+    def fit(self):
+        return 0.5
+
+
+class FakeCpals:
+    def __init__(self):
+        self.made = 0
+
+    def CPALS(self, dims, R, prec):
+        h = FakeHandle(self.made)
+        self.made += 1
+        return h
+
+
+@pytest.fixture
+def bench(monkeypatch):
+    torch = pytest.importorskip("torch")
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: object())
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    FakeHandle.log = []
+    FakeHandle.fail_at = None
+    return load_bench()
+
+
+def test_double_buffered_steps_alternate_and_overlap(bench):
+    steps = 8
+    bench.e2e_double_buffered(FakeCpals(), (4, 4, 4), 2, None, None, "qr", steps)
+    timed = [e for e in FakeHandle.log]
+    # warm-up: one copy and one sweep per handle before the timed loop
+    copies = sorted([e for e in timed if e[1] == "copy"], key=lambda e: e[2])[2:]
+    sweeps = [e for e in timed if e[1] == "sweep"][2:]
+    assert len(copies) == steps and len(sweeps) == steps
+    # each handle took half the steps, alternating
+    assert [c[0] for c in copies] == [i % 2 for i in range(steps)]
+    # copies never overlap each other
+    for a, b in zip(copies, copies[1:]):
+        assert b[2] >= a[3] - 1e-4
+    # every copy after the first overlaps a sweep of the other handle
+    overl = 0
+    for c in copies[1:]:
+        if any(s[0] != c[0] and s[2] < c[3] and c[2] < s[3] for s in sweeps):
+            overl += 1
+    assert overl >= steps - 2
+
+
+def test_double_buffered_failure_propagates_without_hang(bench):
+    FakeHandle.fail_at = (1, 3)     # handle 1's third copy (its second timed step) raises
+    done = []
+
+    def run():
+        try:
+            bench.e2e_double_buffered(FakeCpals(), (4, 4, 4), 2, None, None, "qr", 10)
+        except RuntimeError as e:
+            done.append(str(e))
+
+    t = threading.Thread(target=run)
+    t.start()
+    t.join(timeout=30)
+    assert not t.is_alive(), "the loop hung after a failure"
+    assert done == ["planted failure"]
