@@ -397,6 +397,11 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
         return fail(nullptr, CPALS_ERR_ARG, "%s", "unknown precision");
     for (int m = 0; m < N; ++m)
         if (dims[m] < 1) return fail(nullptr, CPALS_ERR_ARG, "%s", "dims must be >= 1");
+    {
+        int64_t P = 0;
+        if (!cpals::checked_prod(N, dims, &P))
+            return fail(nullptr, CPALS_ERR_ARG, "%s", "prod(dims) does not fit in 64 bits");
+    }
     for (int m = 0; m < N; ++m)
         if (dims[m] < rank)
             return fail(nullptr, CPALS_ERR_ARG, "%s",
@@ -1017,22 +1022,33 @@ int cpals_multi_ttm_static(const int64_t* dims, int N, int rank, int mode, const
                            const double* const* Q, double* Y, void* stream)
 {
     if (!dims || !X || !Q || !Y) return fail(nullptr, CPALS_ERR_ARG, "%s", "a pointer argument is NULL");
-    if (N < 2 || N > cpals::kMaxN) return fail(nullptr, CPALS_ERR_ARG, "%s", "N must be in [2, 8]");
-    if (rank < 1 || rank > cpals::kMaxRank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must be in [1, 64]");
+    if (N < 2 || N > cpals::kMaxN) {
+        snprintf(g_create_err, sizeof(g_create_err), "N must be in [2, %d]", cpals::kMaxN);
+        return CPALS_ERR_ARG;
+    }
+    if (rank < 1 || rank > cpals::kMaxRank) {
+        snprintf(g_create_err, sizeof(g_create_err), "rank must be in [1, %d]", cpals::kMaxRank);
+        return CPALS_ERR_ARG;
+    }
     if (mode < 0 || mode >= N) return fail(nullptr, CPALS_ERR_ARG, "%s", "bad mode");
     for (int m = 0; m < N; ++m) {
         if (dims[m] < rank) return fail(nullptr, CPALS_ERR_ARG, "%s", "rank must not exceed any dim");
         if (m != mode && !Q[m]) return fail(nullptr, CPALS_ERR_ARG, "%s", "a Q pointer is NULL");
     }
-    const int64_t need = cpals::multi_ttm_static_need(N, dims, rank, mode);
-    if (need > cpals::multi_ttm_static_capacity()) {
+    int64_t P = 0;
+    if (!cpals::checked_prod(N, dims, &P))
+        return fail(nullptr, CPALS_ERR_ARG, "%s", "prod(dims) does not fit in 64 bits");
+    cpals::StaticPlan sp{};
+    cudaError_t e = cpals::multi_ttm_static_plan(N, dims, rank, mode, &sp);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "device query");
+    if (!sp.ok) {
         snprintf(g_create_err, sizeof(g_create_err),
                  "problem too large for the static scratch: the two largest TTM intermediates need %lld doubles, "
                  "the fixed array holds %lld",
-                 (long long)need, (long long)cpals::multi_ttm_static_capacity());
+                 (long long)(sp.s0 + sp.s1), (long long)cpals::multi_ttm_static_capacity());
         return CPALS_ERR_ARG;
     }
-    cudaError_t e = cpals::multi_ttm_static(N, dims, rank, mode, X, Q, Y, reinterpret_cast<cudaStream_t>(stream));
+    e = cpals::multi_ttm_static(N, dims, rank, mode, X, Q, Y, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "static Multi-TTM");
     return CPALS_OK;
 }

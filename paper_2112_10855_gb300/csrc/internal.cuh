@@ -7,40 +7,14 @@
 #include <stdio.h>
 
 #include "../../include/cpals.h"
+#include "ttm_plan.h"
 
 namespace cpals {
-
-constexpr int kMaxN = 12;
-constexpr int kMaxRank = 64;
 
 // Device status word values (a subset of cpals_status).
 constexpr int kStatusOk = 0;
 
-// ------------------------------------------------------------------ layout
-// A TTM over mode m of a tensor with (current) dims d views it as
-// [L, K, T] with L = prod_{k<m} d_k, K = d_m, T = prod_{k>m} d_k (Sec. 2.2).
-struct TtmShape {
-    int64_t L, K, T;
-};
-
-inline TtmShape ttm_shape(int N, const int64_t* d, int m) {
-    TtmShape s{1, d[m], 1};
-    for (int k = 0; k < m; ++k) s.L *= d[k];
-    for (int k = m + 1; k < N; ++k) s.T *= d[k];
-    return s;
-}
-
-// Decreasing-dimension TTM order of Sec. 3.2 (ties: higher mode first).
-inline void ttm_order(int N, const int64_t* dims, int n, int* order) {
-    int cnt = 0;
-    for (int m = 0; m < N; ++m)
-        if (m != n) order[cnt++] = m;
-    for (int a = 0; a < cnt; ++a)
-        for (int b = a + 1; b < cnt; ++b) {
-            int x = order[a], y = order[b];
-            if (dims[y] > dims[x] || (dims[y] == dims[x] && y > x)) { order[a] = y; order[b] = x; }
-        }
-}
+// kMaxN, kMaxRank, TtmShape, ttm_shape and ttm_order come from ttm_plan.h.
 
 // ------------------------------------------------------------------ handle
 struct Handle {
@@ -178,7 +152,7 @@ cudaError_t ttm_first(Handle* h, int n);
 cudaError_t multi_ttm_static(int N, const int64_t* dims, int R, int n, const double* X, const double* const* Q,
                              double* Y, cudaStream_t stream);
 int64_t multi_ttm_static_capacity();
-int64_t multi_ttm_static_need(int N, const int64_t* dims, int R, int n);
+cudaError_t multi_ttm_static_plan(int N, const int64_t* dims, int R, int n, StaticPlan* out);
 // First TTM on the tcgen05 tensor cores with split products (FP32 X):
 // 3 x bf16 (kind::f16) or, with tf32 = true, 3 x tf32 (kind::tf32).
 bool tc_supported(int R);

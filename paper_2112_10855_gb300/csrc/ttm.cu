@@ -249,13 +249,9 @@ __global__ void reduce_splits_kernel(const T* __restrict__ part, int ks, int gro
     }
 }
 
-// CTA size: FP32 is bound by HBM and uses 256-row CTAs.  FP64 is bound by
-// the FP64 pipe of each SM, so what counts is the largest number of rows any
-// SM holds: the CTA size (one of kF64Tpb, picked per launch) minimises
-// ceil(CTAs / SMs) x rows per CTA x indices per split, which keeps every SM
-// within a fraction of a percent of the mean at the large passes.
+// CTA size: FP32 is bound by HBM and uses 256-row CTAs; FP64 takes the CTA
+// size of plan_rows_f64 (ttm_plan.h), picked per launch.
 constexpr int kRowsMaxTpb = 256;
-constexpr int kF64Tpb[] = {64, 96, 128};
 // FP32 row-quad kernel: 4 rows per thread; its CTA size (64, 96 or 128
 // threads) is picked per launch from the resident CTAs per SM, so that a pass
 // does not end in a ragged second wave (at 135 registers a thread, 128-thread
@@ -307,43 +303,13 @@ void launch_rows(dim3 grid, int tpb, cudaStream_t st, const T* in, const double*
 #undef CPALS_TPB
 }
 
-// Split of the contracted index: split K when the row blocks alone cannot
-// fill the SMs with about 2048 threads each, keeping >= 8 indices per split
-// and room for the partials and the group sums of the two-level reduction.
-inline int64_t ttm_ksplit(int64_t ctas_xy, int tpb, int64_t K, int num_sms, int64_t outn, int64_t part_elems,
-                          bool have_part)
-{
-    constexpr int64_t kMinSplitK = 8;
-    const int64_t want = (int64_t)num_sms * (2048 / tpb);
-    int64_t ks = 1;
-    if (ctas_xy < want && K >= 2 * kMinSplitK && have_part) {
-        ks = (want + ctas_xy - 1) / ctas_xy;
-        ks = std::min<int64_t>(ks, K / kMinSplitK);
-        ks = std::min<int64_t>(ks, (part_elems * 16 / 17) / std::max<int64_t>(outn, 1));
-        if (ks < 2) ks = 1;
-    }
-    // up to 16 splits take one reduction pass instead of two: stay there when
-    // the grid still gives every SM four CTAs
-    if (ks > 16 && ctas_xy * 16 >= 4LL * num_sms) ks = 16;
-    const int64_t kchunk = (K + ks - 1) / ks;
-    return (K + kchunk - 1) / kchunk;
-}
-
-// Register width per thread: R itself up to 16, then 20, 24, 32 (wider R in chunks of 32).
-inline int ttm_width(int R) {
-    if (R <= 16) return R;
-    if (R <= 20) return 20;
-    if (R <= 24) return 24;
-    return 32;
-}
-
 // Sum the ks K-split partials (part, ks x outn) into out in split order: one
 // pass for up to 16 splits, else groups of 16 and then the group sums.
 template <typename T>
 cudaError_t reduce_ksplit(Handle* h, T* part, int64_t ks, int64_t outn, T* out)
 {
     if (ks <= 1) return cudaSuccess;
-    constexpr int kGroup = 16;
+    constexpr int kGroup = (int)kSplitGroup;
     const int64_t ng = (ks + kGroup - 1) / kGroup;
     auto grid_of = [&](int64_t work) {
         int64_t g = (work + 255) / 256;
@@ -429,15 +395,8 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
     }
     if (sizeof(T) == 8) {
         // FP64: the CTA size with the smallest per-SM share of rows x indices
-        int64_t best = -1;
-        for (int c : kF64Tpb) {
-            const int64_t cx = (rows + c - 1) / c;
-            const int64_t cks = ttm_ksplit(cx * gy, c, s.K, h->num_sms, outn, part_elems, part != nullptr);
-            const int64_t ckc = (s.K + cks - 1) / cks;
-            const int64_t ctas = cx * gy * cks;
-            const int64_t cost = ((ctas + h->num_sms - 1) / h->num_sms) * c * ckc;
-            if (best < 0 || cost < best) { best = cost; tpb = c; gx = cx; ks = cks; }
-        }
+        const RowsPlan p = plan_rows_f64(h->num_sms, s, R, part_elems, part != nullptr);
+        tpb = p.tpb; gx = p.gx; ks = p.ks;
     }
     const int64_t kchunk = (s.K + ks - 1) / ks;
     dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)ks);
@@ -958,25 +917,6 @@ cudaError_t static_scratch(int device, double** scratch, int** status)
 
 int64_t multi_ttm_static_capacity() { return kStaticScratchDoubles; }
 
-// Elements of the two largest TTM intermediates of the Multi-TTM of mode n
-// (the sequence of sizes is non-increasing because R <= every dim).
-int64_t multi_ttm_static_need(int N, const int64_t* dims, int R, int n)
-{
-    int order[kMaxN];
-    ttm_order(N, dims, n, order);
-    int64_t d[kMaxN];
-    int64_t P = 1;
-    for (int m = 0; m < N; ++m) { d[m] = dims[m]; P *= dims[m]; }
-    int64_t s0 = 0, s1 = 0;
-    for (int k = 0; k < N - 1; ++k) {
-        P = P / d[order[k]] * R;
-        d[order[k]] = R;
-        if (k == 0) s0 = P;
-        if (k == 1) s1 = P;
-    }
-    return s0 + s1;
-}
-
 cudaError_t multi_ttm_static(int N, const int64_t* dims, int R, int n, const double* X, const double* const* Q,
                              double* Y, cudaStream_t stream)
 {
@@ -992,25 +932,25 @@ cudaError_t multi_ttm_static(int N, const int64_t* dims, int R, int n, const dou
     for (int m = 0; m < N; ++m) h.dims[m] = dims[m];
     CPALS_CUDA_TRY(cudaDeviceGetAttribute(&h.num_sms, cudaDevAttrMultiProcessorCount, device));
     h.d_status = status;
+    // the scratch layout, with every TTM's split-K partials and group sums
+    // inside the array (the caller has checked sp.ok on the same dims)
+    const StaticPlan sp = plan_multi_ttm_static(N, dims, R, n, h.num_sms, kStaticScratchDoubles);
+    if (!sp.ok) return cudaErrorInvalidValue;
     // the kernels skip their work unless the status word is zero
     CPALS_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), stream));
 
     int order[kMaxN];
     ttm_order(N, dims, n, order);
     int64_t d[kMaxN];
-    int64_t P = 1;
-    for (int m = 0; m < N; ++m) { d[m] = dims[m]; P *= dims[m]; }
-    const int64_t s0 = P / dims[order[0]] * R;
-    const int64_t s1 = (N > 2) ? s0 / dims[order[1]] * R : 0;
-    double* buf[2] = {scratch, scratch + s0};
-    double* part = scratch + s0 + s1;
-    const int64_t part_elems = kStaticScratchDoubles - s0 - s1;
+    for (int m = 0; m < N; ++m) d[m] = dims[m];
+    double* buf[2] = {scratch, scratch + sp.s0};
+    double* part = scratch + sp.s0 + sp.s1;
     const double* in = X;
     int cur = 0;
     for (int k = 0; k < N - 1; ++k) {
         const int m = order[k];
         const TtmShape s = ttm_shape(N, d, m);
-        CPALS_CUDA_TRY(launch_ttm_split<double>(&h, in, Q[m], dims[m], buf[cur], s, R, part, part_elems));
+        CPALS_CUDA_TRY(launch_ttm_split<double>(&h, in, Q[m], dims[m], buf[cur], s, R, part, sp.part_elems));
         d[m] = R;
         in = buf[cur];
         cur ^= 1;
@@ -1022,6 +962,17 @@ cudaError_t multi_ttm_static(int N, const int64_t* dims, int R, int n, const dou
     const int64_t total = dims[n] * RN1;
     unfold_kernel<double><<<grid_for(total, 256, h.num_sms), 256, 0, stream>>>(in, Y, Rn, dims[n], total, status);
     return cudaGetLastError();
+}
+
+// The static Multi-TTM's plan on the current device (for the size check of
+// the C-ABI entry point).
+cudaError_t multi_ttm_static_plan(int N, const int64_t* dims, int R, int n, StaticPlan* out)
+{
+    int device = 0, sms = 0;
+    CPALS_CUDA_TRY(cudaGetDevice(&device));
+    CPALS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    *out = plan_multi_ttm_static(N, dims, R, n, sms, kStaticScratchDoubles);
+    return cudaSuccess;
 }
 
 }  // namespace cpals

@@ -26,8 +26,14 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("dims,R", [((120, 110, 100), 10), ((37, 29, 41), 5), ((12, 11, 10, 9), 3)])
-def test_static_multi_ttm_matches_handle_path_twice(cuda_lib, dims, R):
+@pytest.mark.parametrize("dims,R,modes", [
+    ((120, 110, 100), 10, None), ((37, 29, 41), 5, None), ((12, 11, 10, 9), 3, None),
+    # a long first mode: the first TTM splits its 40000 indices more than 16
+    # ways (two-pass reduction) and the partials fill over 90% of the array
+    # (tests/test_ttm_plan_cpu.py checks that plan on the CPU)
+    ((40000, 10, 10), 10, (1, 2)),
+])
+def test_static_multi_ttm_matches_handle_path_twice(cuda_lib, dims, R, modes):
     rng = np.random.default_rng(sum(dims) * R)
     X = rng.standard_normal(int(np.prod(dims)))
     QR = [oracle.qr(rng.standard_normal((d, R))) for d in dims]
@@ -40,7 +46,7 @@ def test_static_multi_ttm_matches_handle_path_twice(cuda_lib, dims, R):
     h.set_tensor(Xd)
     h.set_factor_qr(Q, Rm)
     stream = torch.cuda.current_stream()
-    for n in range(len(dims)):
+    for n in (range(len(dims)) if modes is None else modes):
         ref, _ = h.multi_ttm(n)
         for call in range(2):
             Y = torch.full((R ** (len(dims) - 1), dims[n]), float("nan"), dtype=torch.float64, device="cuda").t()
