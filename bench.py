@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--solve", choices=["qr", "svd", "normal"], default="qr")
     ap.add_argument("--no-variants", action="store_true", help="skip the SVD/NORMAL/FP32 side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the 120^4 rank-20 FP64/FP32/3xBF16/3xTF32 record of the default run")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--workload", choices=["c2", "c3", "c5a", "c5b", "c4", "sine", "collinear"], default="c2",
                     help="c2: the headline 400^3 rank-10 FP64 workload; c3: 4-way 120^4 rank 20, c5a: 3-way "
@@ -451,6 +453,81 @@ def recovery_rates(args, dims, R, fit_sweeps, solve, rtol, stream):
             "recovered_fraction_at_0.95": {k: float(np.mean(np.asarray(v) >= 0.95)) for k, v in scores.items()},
             "max_abs_score_diff_vs_f64": {k: float(np.abs(np.asarray(v) - f64).max()) for k, v in scores.items()},
             "scores": {k: [round(x, 6) for x in v] for k, v in scores.items()}}
+
+
+def mixed_c3_record(args, stream):
+    """The 4-way 120^4 rank-20 workload (congruence 0.9, 1% noise) with FP64,
+    FP32, 3xBF16 and 3xTF32 passes over X: sweeps/s (CUDA events on the
+    handle's stream, after warm-up), the first TTM of each mode's Multi-TTM
+    (the pass that streams X) timed alone with its GB/s against the measured
+    HBM copy bandwidth, the speed-up over FP64, and the direct fit after the
+    FP64 run's sweeps to convergence (|fit change| < 1e-10, at most
+    --fit-sweeps) from the same start, as a relative gap to FP64's."""
+    import torch
+    from paper_2112_10855_gb300 import cpals, inputs
+    t_gen = time.perf_counter()
+    p = inputs.workload_c3()
+    t_gen = time.perf_counter() - t_gen
+    P, R = int(np.prod(p.dims)), p.rank
+    Xd = torch.from_numpy(p.X).to(torch.cuda.current_device())
+    init = [np.asfortranarray(a) for a in p.init_factors]
+    hbm = measured_peaks().get("hbm_gbs")
+    steps = 20
+    out, sweeps_conv = {}, None
+    for prec in ["f64", "f32", "bf16x3", "tf32x3"]:
+        h = cpals.CPALS(p.dims, R, prec)
+        h.set_stream(stream)
+        h.set_tensor(Xd)
+        h.set_factors(init)
+        h.iterate(max(args.warmup, 3), solve="qr", want_fits=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = h.launch_count()
+        e0.record(stream)
+        h.iterate(steps, solve="qr", want_fits=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        its = steps / (e0.elapsed_time(e1) * 1e-3)
+        launches = (h.launch_count() - l0) / steps
+        ttm_ms = []
+        for n in range(len(p.dims)):
+            h.ttm_first(n)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(5):
+                h.ttm_first(n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ttm_ms.append(e0.elapsed_time(e1) / 5)
+        ms = sum(ttm_ms) / len(ttm_ms)
+        xbytes = (8 if prec == "f64" else 4) * P
+        gbs = xbytes / (ms * 1e-3) / 1e9
+        # the same start, run to FP64's convergence count, then the direct fit
+        h.set_factors(init)
+        if prec == "f64":
+            fits = h.iterate(args.fit_sweeps, tol=1e-10, solve="qr")
+            sweeps_conv = len(fits)
+        else:
+            h.iterate(sweeps_conv, solve="qr", want_fits=False)
+        fit = h.fit(direct=True)
+        del h
+        out[prec] = {"iters_per_s": its, "gpu_launches_per_sweep": launches, "first_ttm_ms": ms,
+                     "first_ttm_gbs": gbs, "first_ttm_frac_hbm": (gbs / hbm) if hbm else None,
+                     "fit_direct": fit}
+    for prec in out:
+        out[prec]["speedup_vs_f64"] = out[prec]["iters_per_s"] / out["f64"]["iters_per_s"]
+        out[prec]["fit_rel_gap_vs_f64"] = abs(out[prec]["fit_direct"] - out["f64"]["fit_direct"]) / \
+            out["f64"]["fit_direct"]
+    del Xd
+    torch.cuda.empty_cache()
+    return {"workload": "4-way 120x120x120x120 (FP64 1.66 GB; FP32 copy 0.83 GB), rank 20, factor columns with "
+                        "congruence 0.9, 1% noise; CP-ALS-QR (QR solve), dimension-tree sweeps",
+            "dims": list(p.dims), "rank": R, "timed_sweeps": steps, "sweeps_to_converge_f64": sweeps_conv,
+            "hbm_peak_gbs": hbm, "hbm_peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+            "first_ttm": "the pass over X of each mode's Multi-TTM, timed alone (events, 5 launches per mode); "
+                         "GB/s = bytes of X read (8P FP64, 4P otherwise) / time",
+            "input_generation_s": t_gen, "precisions": out}
 
 
 def run_batch(args, world, rank):
@@ -853,6 +930,13 @@ def main():
         variants[f"f32_{args.solve}"] = args.steps / (e0.elapsed_time(e1) * 1e-3)
         del hf
 
+    mixed = None
+    if rank == 0 and not args.no_mixed:
+        try:
+            mixed = mixed_c3_record(args, stream)
+        except Exception as exc:     # reported, not fatal to the headline
+            mixed = {"failed": str(exc)[:300]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(p, sweeps=2, solve={"qr": 0, "svd": 1, "normal": 2}[args.solve])
@@ -883,6 +967,7 @@ def main():
             "clocks": clk.summary(),
             "fit_after": fit_now,
             "variants_iters_per_s": variants,
+            "mixed": mixed,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

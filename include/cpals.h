@@ -114,7 +114,10 @@ int cpals_workspace_bytes(const cpals_handle* h, size_t* bytes);
  *    a device FP64 pointer stays borrowed in that case too.
  *  elem = CPALS_ELEM_F32: allowed only with precision F32/BF16X3/TF32X3;
  *    borrowed (DEVICE) or copied (HOST).
- * Also computes ||X||_F^2 in FP64 (Sec. 3.3.1: it is pre-computed once). */
+ * Also computes ||X||_F^2 in FP64 (Sec. 3.3.1: it is pre-computed once).
+ * Synchronises.  A tensor with a NaN or an Inf (||X||^2 not finite) is
+ * refused with CPALS_ERR_ARG, and the handle then holds no tensor
+ * (CPALS_ERR_STATE for the calls that need one) until a valid one is set. */
 int cpals_set_tensor(cpals_handle* h, const void* X, int elem, int mem);
 
 /* Kruskal-tensor input (Sec. 3.3.2).  The data tensor is given in Kruskal
@@ -252,14 +255,32 @@ int cpals_sync(cpals_handle* h);
  *    product of the dims before the contracted mode is a multiple of 4 and
  *    9 <= R <= 64.  0 uses the row-per-thread kernels.  Both sum each output in
  *    order of the contracted index (the row kernels within each K split,
- *    whose sums they add in a fixed order), so only rounding differs. */
+ *    whose sums they add in a fixed order), so only rounding differs.
+ *  CPALS_OPT_TEST_WITHHOLD_COPIES (default 0): a test hook for the failure
+ *    path of the bounded device waits (the paper has no counterpart).  With 1,
+ *    the persistent tensor-core pass over X (BF16X3 / TF32X3, rank >= 16)
+ *    issues no copies of X and its waits give up after 1 ms instead of 1 s,
+ *    with nothing left in flight.  The pass records CPALS_ERR_TIMEOUT in the
+ *    device status word; the rest of the update is skipped and the factors
+ *    stay as they were, and the next synchronising call reports the error.
+ *    Set it back to 0 and the handle works as before. */
 typedef enum {
     CPALS_OPT_DIMTREE = 0,
     CPALS_OPT_TC_PIPELINE = 1,
     CPALS_OPT_KRP_TREE = 2,
-    CPALS_OPT_F32_PIPELINE = 3
+    CPALS_OPT_F32_PIPELINE = 3,
+    CPALS_OPT_TEST_WITHHOLD_COPIES = 4
 } cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
+
+/* Test hook for the allocation-failure path (the paper has no counterpart):
+ * the nth device allocation that a handle makes from now on (counted over
+ * the process, 1 = the next one) fails as if the device were out of memory,
+ * without calling cudaMalloc.  cpals_create then frees what it holds and
+ * returns CPALS_ERR_NOMEM; cpals_set_tensor, whose first call with host
+ * memory or a mixed precision allocates the owned copy of X, returns the same.
+ * 0 disables the hook.  Errors: CPALS_ERR_ARG for nth < 0. */
+int cpals_test_fail_allocation(int nth);
 
 /* Number of kernel launches the handle has issued so far (graph replays count
  * each kernel node once per replay). */

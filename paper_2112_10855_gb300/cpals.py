@@ -78,6 +78,7 @@ def load(path: str | None = None):
     L.cpals_set_option.argtypes = [_vp, C.c_int, C.c_int64]
     L.cpals_launch_count.argtypes = [_vp]
     L.cpals_launch_count.restype = C.c_int64
+    L.cpals_test_fail_allocation.argtypes = [C.c_int]
     L.cpals_multi_ttm_static.argtypes = [i64p, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp), _vp, _vp]
     L.cpals_batch_create.argtypes = [C.c_int, i64p, C.POINTER(C.c_int), C.POINTER(_vp)]
     L.cpals_batch_destroy.argtypes = [_vp]
@@ -201,6 +202,11 @@ class CPALS:
     def set_f32_pipeline(self, on: bool):
         """CPALS_OPT_F32_PIPELINE: TMA-fed CUDA-core kernel for the FP32 TTMs."""
         _check(self._h, load().cpals_set_option(self._h, 3, 1 if on else 0))
+
+    def set_test_withhold_copies(self, on: bool):
+        """CPALS_OPT_TEST_WITHHOLD_COPIES (test hook): the tensor-core pass over X
+        issues no copies and its bounded waits run out after 1 ms."""
+        _check(self._h, load().cpals_set_option(self._h, 4, 1 if on else 0))
 
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
@@ -412,6 +418,15 @@ def multi_ttm_static(X, Q, mode, rank, dims, Y, stream=None):
     raw = getattr(stream, "cuda_stream", stream) or 0
     rc = L.cpals_multi_ttm_static(d, N, int(rank), int(mode), C.c_void_p(X.data_ptr()), ptrs,
                                   C.c_void_p(Y.data_ptr()), C.c_void_p(raw))
+    if rc != OK:
+        raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
+
+
+def test_fail_allocation(nth):
+    """cpals_test_fail_allocation (test hook): the nth device allocation of a
+    handle from now on fails as if the device were out of memory (0 disables)."""
+    L = load()
+    rc = L.cpals_test_fail_allocation(int(nth))
     if rc != OK:
         raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
 

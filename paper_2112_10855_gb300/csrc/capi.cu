@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "internal.cuh"
@@ -35,11 +36,26 @@ int cuda_fail(Handle* h, cudaError_t e, const char* where)
         if (_e != cudaSuccess) return cuda_fail((h), _e, (where)); \
     } while (0)
 
+// Test hook (cpals_test_fail_allocation): the n-th device allocation of a
+// handle from now on fails as if the device were out of memory.
+std::atomic<int> g_fail_alloc_in{0};
+
+cudaError_t device_alloc(void** p, size_t bytes)
+{
+    int n = g_fail_alloc_in.load();
+    while (n > 0 && !g_fail_alloc_in.compare_exchange_weak(n, n - 1)) {}
+    if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 cudaError_t dalloc(Handle* h, T** p, size_t elems)
 {
     const size_t bytes = std::max<size_t>(elems, 1) * sizeof(T);
-    cudaError_t e = cudaMalloc((void**)p, bytes);
+    cudaError_t e = device_alloc((void**)p, bytes);
     if (e == cudaSuccess) h->owned_bytes += bytes;
     return e;
 }
@@ -462,7 +478,7 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
         }
         h->tA_elems = std::max(a, b);
         void* pa = nullptr;
-        ok = cudaMalloc(&pa, tsz * h->tA_elems) == cudaSuccess;
+        ok = device_alloc(&pa, tsz * h->tA_elems) == cudaSuccess;
         h->tA = pa;
         if (ok) h->owned_bytes += tsz * h->tA_elems;
         // per-half QR of the Khatri-Rao products: R^|H1| and R^|H2| rows; the
@@ -475,7 +491,8 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
     }
     if (ok) {
         void* p0 = nullptr; void* p1 = nullptr;
-        ok = cudaMalloc(&p0, tsz * h->tbuf_elems) == cudaSuccess && cudaMalloc(&p1, tsz * h->tbuf_elems) == cudaSuccess;
+        ok = device_alloc(&p0, tsz * h->tbuf_elems) == cudaSuccess &&
+             device_alloc(&p1, tsz * h->tbuf_elems) == cudaSuccess;
         h->tbuf[0] = p0; h->tbuf[1] = p1;
         if (ok) h->owned_bytes += 2 * tsz * h->tbuf_elems;
     }
@@ -606,6 +623,8 @@ int cpals_set_tensor_kruskal(cpals_handle* hh, const double* mu, const double* c
     CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->normX2_host, h->d_normX2, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
                  "norm read");
     CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "set_tensor sync");
+    if (!isfinite(h->normX2_host))
+        return fail(h, CPALS_ERR_ARG, "%s", "X contains NaN or Inf (or values whose squares overflow FP64)");
     h->have_X = true;
     h->last_sweep_solve = -1;
     factors_changed(h);
@@ -685,6 +704,8 @@ int cpals_set_tensor(cpals_handle* hh, const void* X, int elem, int mem)
     CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->normX2_host, h->d_normX2, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
                  "norm read");
     CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "set_tensor sync");
+    if (!isfinite(h->normX2_host))
+        return fail(h, CPALS_ERR_ARG, "%s", "X contains NaN or Inf (or values whose squares overflow FP64)");
     h->have_X = true;
     h->last_sweep_solve = -1;
     return CPALS_OK;
@@ -975,40 +996,29 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
 {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
-    if ((option != CPALS_OPT_DIMTREE && option != CPALS_OPT_TC_PIPELINE && option != CPALS_OPT_KRP_TREE &&
-         option != CPALS_OPT_F32_PIPELINE) ||
-        (value != 0 && value != 1))
-        return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
+    bool* field = nullptr;
+    switch (option) {
+        case CPALS_OPT_DIMTREE: field = &h->dimtree; break;
+        case CPALS_OPT_TC_PIPELINE: field = &h->tc_pipe; break;
+        case CPALS_OPT_KRP_TREE: field = &h->krp_tree; break;
+        case CPALS_OPT_F32_PIPELINE: field = &h->f32_pipe; break;
+        case CPALS_OPT_TEST_WITHHOLD_COPIES: field = &h->test_withhold; break;
+        default: break;
+    }
+    if (!field || (value != 0 && value != 1)) return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
     const bool v = value != 0;
-    if (option == CPALS_OPT_F32_PIPELINE) {
-        if (v != h->f32_pipe) {
-            h->f32_pipe = v;
-            for (int s = 0; s < 4; ++s)         // captured sweeps hold the old kernels
-                if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
-        }
-        return CPALS_OK;
-    }
-    if (option == CPALS_OPT_KRP_TREE) {
-        if (v != h->krp_tree) {
-            h->krp_tree = v;
-            for (int s = 0; s < 4; ++s)         // captured sweeps follow the old schedule
-                if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
-        }
-        return CPALS_OK;
-    }
-    if (option == CPALS_OPT_TC_PIPELINE) {
-        if (v != h->tc_pipe) {
-            h->tc_pipe = v;
-            for (int s = 0; s < 4; ++s)         // captured sweeps hold the old kernels
-                if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
-        }
-        return CPALS_OK;
-    }
-    if (v != h->dimtree) {
-        h->dimtree = v;
-        for (int s = 0; s < 4; ++s)             // captured sweeps follow the old schedule
+    if (v != *field) {
+        *field = v;
+        for (int s = 0; s < 4; ++s)             // captured sweeps hold the old kernels and schedule
             if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
     }
+    return CPALS_OK;
+}
+
+int cpals_test_fail_allocation(int nth)
+{
+    if (nth < 0) return fail(nullptr, CPALS_ERR_ARG, "%s", "nth must be >= 0");
+    g_fail_alloc_in.store(nth);
     return CPALS_OK;
 }
 

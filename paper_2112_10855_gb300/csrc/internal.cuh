@@ -88,6 +88,9 @@ struct Handle {
     // first TTM on the tensor cores through the persistent TMA pipeline when
     // the shape allows it (else one CTA per 128-row tile)
     bool tc_pipe = true;
+    // test hook: the persistent tensor-core pipeline issues no copies of X and
+    // its waits give up after 1 ms (CPALS_OPT_TEST_WITHHOLD_COPIES)
+    bool test_withhold = false;
     // FP64 scratch for split-K partials, reductions and pre-split tensor-core
     // tiles (main stream), and a separate workspace for the TSQR levels, so a QR
     // on the side stream never shares memory with the Multi-TTM

@@ -482,15 +482,17 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* mbar, uint32_t par
 }
 
 // Wait for the phase of `parity` on mbar; false when the CTA's abort flag is
-// raised or after ~1 s (which raises the flag).
-__device__ __forceinline__ bool pipe_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag)
+// raised or after limit_ns (default ~1 s), which raises the flag.
+constexpr uint64_t kPipeWaitNs = 1000000000ull;
+__device__ __forceinline__ bool pipe_wait(uint64_t* mbar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns = kPipeWaitNs)
 {
     if (mbar_try_wait(mbar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_try_wait_sleep(mbar, parity, 100000u)) return true;
         if (*abort_flag) return false;
-        if (global_ns() - t0 > 1000000000ull) { *abort_flag = 1; return false; }
+        if (global_ns() - t0 > limit_ns) { *abort_flag = 1; return false; }
     }
 }
 
@@ -632,7 +634,7 @@ template <int N, bool TF32>
 __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pipe_kernel(
     const __grid_constant__ CUtensorMap xmap, const uint8_t* __restrict__ btiles, float* __restrict__ out,
     int64_t L, int64_t Tn, int R, int BL, int BT, int64_t ntl, int64_t ntiles, int nitems, int SX, int bres,
-    int* __restrict__ status)
+    int* __restrict__ status, uint64_t wait_ns, int withhold)
 {
     using Cfg = PipeCfg<N, TF32>;
     using E = Elem<TF32>;
@@ -692,9 +694,10 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
         if (lane == 0) {
             const uint32_t tx = (uint32_t)rows_used * Cfg::kc * 4u;
             int64_t it = 0;
-            for (; it < items; ++it) {
+            // (the test hook withholds every copy: the consumers' waits run out)
+            for (; it < items && !withhold; ++it) {
                 const int s = (int)(it % SX);
-                if (!pipe_wait(&xempty[s], (uint32_t)((it / SX) & 1) ^ 1u, abort_flag)) break;
+                if (!pipe_wait(&xempty[s], (uint32_t)((it / SX) & 1) ^ 1u, abort_flag, wait_ns)) break;
                 const int64_t tile = blockIdx.x + (it / nitems) * (int64_t)gridDim.x;
                 const int c = (int)(it % nitems);
                 const int64_t tt = tile / ntl, tl = tile - tt * ntl;
@@ -718,7 +721,7 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
             int64_t it = 0;
             for (; it < items; ++it) {
                 const int j = (int)(it % SA);
-                if (!pipe_wait(&aempty[j], (uint32_t)((it / SA) & 1) ^ 1u, abort_flag)) break;
+                if (!pipe_wait(&aempty[j], (uint32_t)((it / SA) & 1) ^ 1u, abort_flag, wait_ns)) break;
                 const int c = (int)(it % nitems);
                 mbar_expect_tx(&bfull[j], Cfg::kBBytes);
                 bulk_load(bslots + (size_t)j * Cfg::kBBytes, btiles + (size_t)c * Cfg::kBBytes, Cfg::kBBytes,
@@ -735,16 +738,16 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
             constexpr uint32_t idesc2 = make_idesc_e<TF32>(kTcRows, 2 * N);
             constexpr uint32_t idesc1 = make_idesc_e<TF32>(kTcRows, N);
             int64_t it = 0;
-            bool ok = !bres || pipe_wait(&bfull[0], 0u, abort_flag);
+            bool ok = !bres || pipe_wait(&bfull[0], 0u, abort_flag, wait_ns);
             for (int64_t t = 0; t < my_tiles && ok; ++t) {
                 const int a = (int)(t & 1);
-                if (!pipe_wait(&accempty[a], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag)) break;
+                if (!pipe_wait(&accempty[a], (uint32_t)((t >> 1) & 1) ^ 1u, abort_flag, wait_ns)) break;
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(a * Cfg::kAccCols);
                 for (int c = 0; c < nitems; ++c, ++it) {
                     const int j = (int)(it % SA);
                     const uint32_t ph = (uint32_t)((it / SA) & 1);
-                    if ((!bres && !pipe_wait(&bfull[j], ph, abort_flag)) || !pipe_wait(&ready[j], ph, abort_flag)) {
+                    if ((!bres && !pipe_wait(&bfull[j], ph, abort_flag, wait_ns)) || !pipe_wait(&ready[j], ph, abort_flag, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -783,8 +786,8 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
         for (int64_t it = 0; it < items; ++it) {
             const int s = (int)(it % SX), j = (int)(it % SA);
             // warp-uniform outcome: tcgen05.st below is warp-collective
-            const bool got = pipe_wait(&xfull[s], (uint32_t)((it / SX) & 1), abort_flag) &&
-                             pipe_wait(&aempty[j], (uint32_t)((it / SA) & 1) ^ 1u, abort_flag);
+            const bool got = pipe_wait(&xfull[s], (uint32_t)((it / SX) & 1), abort_flag, wait_ns) &&
+                             pipe_wait(&aempty[j], (uint32_t)((it / SA) & 1) ^ 1u, abort_flag, wait_ns);
             if (!__all_sync(0xffffffffu, got)) break;
             // rows past the tile's last valid row split row 0's values: their
             // accumulator rows are never stored
@@ -831,7 +834,7 @@ __global__ void __launch_bounds__(PipeCfg<N, TF32>::kThreads, 1) ttm_split_tc_pi
         for (int64_t t = 0; t < my_tiles; ++t) {
             const int a = (int)(t & 1);
             // warp-uniform outcome: tcgen05.ld below is warp-collective
-            if (!__all_sync(0xffffffffu, pipe_wait(&accfull[a], (uint32_t)((t >> 1) & 1), abort_flag))) break;
+            if (!__all_sync(0xffffffffu, pipe_wait(&accfull[a], (uint32_t)((t >> 1) & 1), abort_flag, wait_ns))) break;
             tc_fence_after();
             const int64_t tile = blockIdx.x + t * (int64_t)gridDim.x;
             const int64_t tt = tile / ntl, tl = tile - tt * ntl;
@@ -1100,7 +1103,8 @@ cudaError_t launch_pipe(Handle* h, const float* in, const uint8_t* tiles, float*
     const int SX = Cfg::x_stages(bregion);
     const uint32_t smem = (uint32_t)SX * Cfg::kXBytes + bregion + 1024 + 512;
     ttm_split_tc_pipe_kernel<N, TF32><<<grid, Cfg::kThreads, smem, h->stream>>>(
-        map, tiles, out, s.L, s.T, R, BL, BT, ntl, ntiles, nitems, SX, bres ? 1 : 0, h->d_status);
+        map, tiles, out, s.L, s.T, R, BL, BT, ntl, ntiles, nitems, SX, bres ? 1 : 0, h->d_status,
+        h->test_withhold ? 1000000ull : kPipeWaitNs, h->test_withhold ? 1 : 0);
     h->launches++;
     return cudaGetLastError();
 }

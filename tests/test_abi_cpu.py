@@ -84,9 +84,10 @@ def test_options_match_the_header(lib):
     hdr = open(os.path.join(_build.ROOT, "include", "cpals.h")).read()
     enum = dict((k, int(v)) for k, v in re.findall(r"(CPALS_OPT_[A-Z0-9_]+)\s*=\s*(\d+)", hdr))
     assert enum == {"CPALS_OPT_DIMTREE": 0, "CPALS_OPT_TC_PIPELINE": 1, "CPALS_OPT_KRP_TREE": 2,
-                    "CPALS_OPT_F32_PIPELINE": 3}
+                    "CPALS_OPT_F32_PIPELINE": 3, "CPALS_OPT_TEST_WITHHOLD_COPIES": 4}
     setters = {"set_dimtree": "CPALS_OPT_DIMTREE", "set_tc_pipeline": "CPALS_OPT_TC_PIPELINE",
-               "set_krp_tree": "CPALS_OPT_KRP_TREE", "set_f32_pipeline": "CPALS_OPT_F32_PIPELINE"}
+               "set_krp_tree": "CPALS_OPT_KRP_TREE", "set_f32_pipeline": "CPALS_OPT_F32_PIPELINE",
+               "set_test_withhold_copies": "CPALS_OPT_TEST_WITHHOLD_COPIES"}
     for name, opt in setters.items():
         src = inspect.getsource(getattr(cpals.CPALS, name))
         m = re.search(r"cpals_set_option\(self\._h, (\d+),", src)
@@ -126,3 +127,8 @@ def test_planted_tensor_layout():
     i, j, k = 3, 1, 4
     expect = sum(A[0][i, r] * A[1][j, r] * A[2][k, r] for r in range(2))
     assert abs(T[i, j, k] - expect) < 1e-13
+
+
+def test_allocation_hook_rejects_negative_counts(lib):
+    assert lib.cpals_test_fail_allocation(-1) == cpals.ERR_ARG
+    assert lib.cpals_test_fail_allocation(0) == cpals.OK
