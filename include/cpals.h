@@ -263,15 +263,35 @@ int cpals_sync(cpals_handle* h);
  *    with nothing left in flight.  The pass records CPALS_ERR_TIMEOUT in the
  *    device status word; the rest of the update is skipped and the factors
  *    stay as they were, and the next synchronising call reports the error.
- *    Set it back to 0 and the handle works as before. */
+ *    Set it back to 0 and the handle works as before.
+ *  CPALS_OPT_FUSED_TAIL (default 1): the end of each mode update -- the
+ *    solve (substitution with R0, the SVD or pseudo-inverse operator, or the
+ *    Cholesky factor of S_n), the column normalisation into lambda and A_n,
+ *    and the QR A_n = Q_n R_n (QR/SVD solves) or the Gram A_n^T A_n (normal
+ *    equations) -- runs in one thread-block cluster whose CTAs split the
+ *    rows of A_n.  The factor QR there is CholeskyQR2 (two passes of Gram,
+ *    Cholesky and substitution); it is accepted only when the first pass
+ *    leaves Q1^T Q1 within 1e-2 of the identity (cond(A_n) below about 7e6),
+ *    and otherwise the Householder QR runs as with 0.  Both give the thin QR
+ *    with a positive diagonal of R_n, so only rounding differs.  0 runs the
+ *    separate solve, normalisation and Householder QR kernels. */
 typedef enum {
     CPALS_OPT_DIMTREE = 0,
     CPALS_OPT_TC_PIPELINE = 1,
     CPALS_OPT_KRP_TREE = 2,
     CPALS_OPT_F32_PIPELINE = 3,
-    CPALS_OPT_TEST_WITHHOLD_COPIES = 4
+    CPALS_OPT_TEST_WITHHOLD_COPIES = 4,
+    CPALS_OPT_FUSED_TAIL = 5
 } cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
+
+/* Test hook (the paper has no counterpart): the reciprocal and reciprocal
+ * square root that the factor QR of the fused mode tail uses on its
+ * sequential chain (an FP32 hardware approximation refined by two FP64
+ * Newton-Raphson steps), applied to n device values x (rsqrt gets 0 where
+ * x <= 0).  x, rcp, rsqrt: device arrays of n doubles.  Synchronises the
+ * device.  Errors: CPALS_ERR_ARG, CPALS_ERR_CUDA. */
+int cpals_test_newton_recip(const double* x, int64_t n, double* rcp, double* rsqrt);
 
 /* Test hook for the allocation-failure path (the paper has no counterpart):
  * the nth device allocation that a handle makes from now on (counted over

@@ -79,6 +79,7 @@ def load(path: str | None = None):
     L.cpals_launch_count.argtypes = [_vp]
     L.cpals_launch_count.restype = C.c_int64
     L.cpals_test_fail_allocation.argtypes = [C.c_int]
+    L.cpals_test_newton_recip.argtypes = [_vp, C.c_int64, _vp, _vp]
     L.cpals_multi_ttm_static.argtypes = [i64p, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp), _vp, _vp]
     L.cpals_batch_create.argtypes = [C.c_int, i64p, C.POINTER(C.c_int), C.POINTER(_vp)]
     L.cpals_batch_destroy.argtypes = [_vp]
@@ -207,6 +208,10 @@ class CPALS:
         """CPALS_OPT_TEST_WITHHOLD_COPIES (test hook): the tensor-core pass over X
         issues no copies and its bounded waits run out after 1 ms."""
         _check(self._h, load().cpals_set_option(self._h, 4, 1 if on else 0))
+
+    def set_fused_tail(self, on: bool):
+        """CPALS_OPT_FUSED_TAIL: solve, normalisation and CholeskyQR2 of the factor in one cluster kernel."""
+        _check(self._h, load().cpals_set_option(self._h, 5, 1 if on else 0))
 
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
@@ -429,6 +434,20 @@ def test_fail_allocation(nth):
     rc = L.cpals_test_fail_allocation(int(nth))
     if rc != OK:
         raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
+
+
+def test_newton_recip(x):
+    """cpals_test_newton_recip (test hook): (1/x, 1/sqrt(x)) as the fused mode
+    tail computes them, for a float64 CUDA tensor x."""
+    import torch
+    rcp = torch.empty_like(x)
+    rsq = torch.empty_like(x)
+    L = load()
+    rc = L.cpals_test_newton_recip(C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(rcp.data_ptr()),
+                                   C.c_void_p(rsq.data_ptr()))
+    if rc != OK:
+        raise CPALSError(rc, L.cpals_last_error(None).decode(errors="replace"))
+    return rcp, rsq
 
 
 def probe_fma_peak(ms_target=50.0):

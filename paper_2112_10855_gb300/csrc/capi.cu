@@ -36,6 +36,17 @@ int cuda_fail(Handle* h, cudaError_t e, const char* where)
         if (_e != cudaSuccess) return cuda_fail((h), _e, (where)); \
     } while (0)
 
+// A device allocation: out of memory is CPALS_ERR_NOMEM, anything else CPALS_ERR_CUDA.
+#define ALLOC_OR_FAIL(h, expr, where)                                                              \
+    do {                                                                                           \
+        cudaError_t _e = (expr);                                                                   \
+        if (_e == cudaErrorMemoryAllocation) {                                                     \
+            cudaGetLastError();                                                                    \
+            return fail((h), CPALS_ERR_NOMEM, "%s: device allocation failed", (where));            \
+        }                                                                                          \
+        if (_e != cudaSuccess) return cuda_fail((h), _e, (where));                                 \
+    } while (0)
+
 // Test hook (cpals_test_fail_allocation): the n-th device allocation of a
 // handle from now on fails as if the device were out of memory.
 std::atomic<int> g_fail_alloc_in{0};
@@ -67,7 +78,7 @@ void free_all(Handle* h)
     f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
     f(h->HQ[0]); f(h->HQ[1]); f(h->HR[0]); f(h->HR[1]); f(h->Qin);
-    f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_normX2); f(h->d_fit);
+    f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_gate); f(h->d_normX2); f(h->d_fit);
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->KV[m]); f(h->KC[m]); f(h->KE[m]); }
     f(h->Kmu); f(h->KGV); f(h->KP); f(h->KMw[0]); f(h->KMw[1]);
@@ -123,6 +134,22 @@ int take_status(Handle* h)
 
 inline bool is_normal(int solve) { return solve == CPALS_SOLVE_NORMAL || solve == CPALS_SOLVE_NORMAL_PINV; }
 
+// The Gram of the current factor A_m and, with want_qr, its QR (diag(R_m) >= 0).
+// With CPALS_OPT_FUSED_TAIL they come from the same cluster kernel as the
+// mode updates' (kind 4: the factor as it is), so that factors set from a
+// checkpoint give the same Q_m, R_m and G_m as the run that saved them.
+cudaError_t factor_qr_gram(Handle* h, int m, bool want_qr)
+{
+    const int64_t I = h->dims[m];
+    if (h->fused_tail && cpals::mode_tail_ok(I, h->R)) {
+        CPALS_CUDA_TRY(cpals::mode_tail(h, m, 4, h->A[m], nullptr, want_qr));
+        if (want_qr) CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], I, h->R, h->Q[m], h->Rf[m], true, h->d_gate));
+        return cudaSuccess;
+    }
+    if (want_qr) CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], I, h->R, h->Q[m], h->Rf[m]));
+    return cpals::gram(h, h->A[m], I, h->G[m]);
+}
+
 // Make the derived data (Q_m, R_m for QR/SVD; G_m for NORMAL) of every mode
 // other than `skip` current.
 cudaError_t refresh_derived(Handle* h, int solve, int skip)
@@ -131,7 +158,7 @@ cudaError_t refresh_derived(Handle* h, int solve, int skip)
         if (m == skip) continue;
         if (is_normal(solve)) {
             if (!h->gram_valid[m]) {
-                CPALS_CUDA_TRY(cpals::gram(h, h->A[m], h->dims[m], h->G[m]));
+                CPALS_CUDA_TRY(factor_qr_gram(h, m, false));
                 h->gram_valid[m] = true;
             }
             if (h->kruskal && h->have_X && !h->ke_valid[m]) {
@@ -140,8 +167,9 @@ cudaError_t refresh_derived(Handle* h, int solve, int skip)
             }
         } else {
             if (!h->qr_valid[m]) {
-                CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], h->dims[m], h->R, h->Q[m], h->Rf[m]));
+                CPALS_CUDA_TRY(factor_qr_gram(h, m, true));
                 h->qr_valid[m] = true;
+                h->gram_valid[m] = true;
                 h->kc_valid[m] = false;
             }
             if (h->kruskal && h->have_X && !h->kc_valid[m]) {
@@ -171,6 +199,68 @@ struct TreeQR {
     bool ready;
 };
 
+// The end of a mode update once W_n (or M_n) and the solve operator are ready:
+// the solve, lambda and the normalised A_n, and its QR (QR/SVD solves) or Gram
+// (normal equations).  With CPALS_OPT_FUSED_TAIL the whole tail runs in one
+// thread-block cluster (tail.cu; above rank 32 after the GPU-wide solve
+// kernels), followed by the Householder QR, which runs only if the cluster's
+// CholeskyQR2 was refused; otherwise the separate kernels run.
+cudaError_t finish_update(Handle* h, int n, int solve, double rtol, bool have_operator)
+{
+    const int64_t In = h->dims[n];
+    const bool normal = is_normal(solve);
+    if (h->fused_tail && cpals::mode_tail_ok(In, h->R)) {
+        int kind = 0;
+        const double* Win = normal ? h->M : h->W;
+        const double* Op = h->R0;
+        if (solve == CPALS_SOLVE_SVD || solve == CPALS_SOLVE_NORMAL_PINV) {
+            if (!have_operator) {
+                if (solve == CPALS_SOLVE_SVD) CPALS_CUDA_TRY(cpals::svd_operator(h, rtol));
+                else CPALS_CUDA_TRY(cpals::normal_operator(h, n, true, rtol));
+            }
+            kind = 1;
+            Op = h->T;
+        } else if (solve == CPALS_SOLVE_NORMAL) {
+            if (!have_operator) CPALS_CUDA_TRY(cpals::normal_operator(h, n, false, 0.0));
+            kind = 2;
+            Op = h->T;
+        }
+        if (h->R > 32) {
+            // the R^2 work per row of the solve on every SM, then the cluster from Ahat
+            switch (solve) {
+                case CPALS_SOLVE_QR: CPALS_CUDA_TRY(cpals::solve_qr(h, In)); break;
+                case CPALS_SOLVE_SVD: CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol, true)); break;
+                case CPALS_SOLVE_NORMAL: CPALS_CUDA_TRY(cpals::solve_normal(h, n, true)); break;
+                default: CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol, true)); break;
+            }
+            kind = 3;
+            Win = h->Ahat;
+        }
+        CPALS_CUDA_TRY(cpals::mode_tail(h, n, kind, Win, Op, !normal));
+        if (!normal) CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n], true, h->d_gate));
+        h->gram_valid[n] = true;
+        h->qr_valid[n] = !normal;
+        return cudaSuccess;
+    }
+    switch (solve) {
+        case CPALS_SOLVE_QR: CPALS_CUDA_TRY(cpals::solve_qr(h, In)); break;
+        case CPALS_SOLVE_SVD: CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol, have_operator)); break;
+        case CPALS_SOLVE_NORMAL: CPALS_CUDA_TRY(cpals::solve_normal(h, n, have_operator)); break;
+        default: CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol, have_operator)); break;
+    }
+    CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
+    if (normal) {
+        CPALS_CUDA_TRY(cpals::gram(h, h->A[n], In, h->G[n]));
+        h->gram_valid[n] = true;
+        h->qr_valid[n] = false;
+    } else {
+        CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n]));
+        h->qr_valid[n] = true;
+        h->gram_valid[n] = false;
+    }
+    return cudaSuccess;
+}
+
 // One mode update (Alg. cp-als-qr mode-loop body, or Alg. cp-als for NORMAL).
 cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_partial = false,
                         const TreeQR* tq = nullptr)
@@ -181,29 +271,19 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         // Kruskal input (Sec. 3.3.2): no pass over a dense tensor
         if (is_normal(solve)) {
             CPALS_CUDA_TRY(cpals::kr_mttkrp(h, n));
-            if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n));
-            else CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol));
         } else {
             CPALS_CUDA_TRY(cpals::krp_qr(h, n, true));
             h->krp_mode = n;
             CPALS_CUDA_TRY(cpals::kr_apply_q0(h, n));
-            if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
-            else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol));
         }
-        CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
+        CPALS_CUDA_TRY(finish_update(h, n, solve, rtol, false));
         if (is_normal(solve)) {
-            CPALS_CUDA_TRY(cpals::gram(h, h->A[n], In, h->G[n]));
             CPALS_CUDA_TRY(cpals::kr_refresh_e(h, n));
-            h->gram_valid[n] = true;
             h->ke_valid[n] = true;
-            h->qr_valid[n] = false;
             h->kc_valid[n] = false;
         } else {
-            CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n]));
             CPALS_CUDA_TRY(cpals::kr_refresh_c(h, n));
-            h->qr_valid[n] = true;
             h->kc_valid[n] = true;
-            h->gram_valid[n] = false;
             h->ke_valid[n] = false;
         }
         return cudaSuccess;
@@ -225,8 +305,6 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         if (from_partial) CPALS_CUDA_TRY(cpals::mttkrp_from_partial(h, n));
         else CPALS_CUDA_TRY(cpals::mttkrp(h, n));
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-        if (solve == CPALS_SOLVE_NORMAL) CPALS_CUDA_TRY(cpals::solve_normal(h, n, true));
-        else CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol, true));
     } else {
         // The QR of V_n needs only the R_m and the Multi-TTM only the Q_m: run the
         // QR on the side stream meanwhile and join before W = Y_(n) Q0.
@@ -248,20 +326,8 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         else CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
         CPALS_CUDA_TRY(cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W));
-        if (solve == CPALS_SOLVE_QR) CPALS_CUDA_TRY(cpals::solve_qr(h, In));
-        else CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol, true));
     }
-    CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
-    if (is_normal(solve)) {
-        CPALS_CUDA_TRY(cpals::gram(h, h->A[n], In, h->G[n]));
-        h->gram_valid[n] = true;
-        h->qr_valid[n] = false;
-    } else {
-        CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n]));
-        h->qr_valid[n] = true;
-        h->gram_valid[n] = false;
-    }
-    return cudaSuccess;
+    return finish_update(h, n, solve, rtol, true);
 }
 
 // One sweep over the modes.  For an N >= 3 dense tensor the Multi-TTMs
@@ -456,6 +522,7 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
          dalloc(h, &h->KR[0], (size_t)R * R) == cudaSuccess && dalloc(h, &h->KR[1], (size_t)R * R) == cudaSuccess &&
          dalloc(h, &h->KQb[0], h->RN1 * R) == cudaSuccess && dalloc(h, &h->KQb[1], h->RN1 * R) == cudaSuccess &&
          dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
+         dalloc(h, &h->d_gate, 1) == cudaSuccess &&
          dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
          dalloc(h, &h->d_fit_count, 1) == cudaSuccess;
     // TSQR: leaf Q (m x R), stacked leaf R factors and their Q (2 m x R at most), the
@@ -571,6 +638,7 @@ int cpals_create_kruskal(const int64_t* dims, int N, int rank, int S, cpals_hand
          dalloc(h, &h->Kmu, S) == cudaSuccess && dalloc(h, &h->KGV, (size_t)N * S * S) == cudaSuccess &&
          dalloc(h, &h->KMw[0], (size_t)S * R) == cudaSuccess && dalloc(h, &h->KMw[1], (size_t)S * R) == cudaSuccess &&
          dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
+         dalloc(h, &h->d_gate, 1) == cudaSuccess &&
          dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
          dalloc(h, &h->d_fit_count, 1) == cudaSuccess;
     // Y_(n) is formed (for cpals_multi_ttm) only when it is small
@@ -668,14 +736,14 @@ int cpals_set_tensor(cpals_handle* hh, const void* X, int elem, int mem)
         if (mem == CPALS_MEM_DEVICE) {
             h->X64 = static_cast<const double*>(X);
         } else {
-            if (!h->X64_owned) CUDA_OR_FAIL(h, dalloc(h, &h->X64_owned, h->P), "allocate X");
+            if (!h->X64_owned) ALLOC_OR_FAIL(h, dalloc(h, &h->X64_owned, h->P), "allocate X");
             CUDA_OR_FAIL(h, cudaMemcpyAsync(h->X64_owned, X, sizeof(double) * h->P, cudaMemcpyHostToDevice, h->stream),
                          "copy X");
             h->X64 = h->X64_owned;
         }
     } else {
         if (!h->X32_owned && !(elem == CPALS_ELEM_F32 && mem == CPALS_MEM_DEVICE))
-            CUDA_OR_FAIL(h, dalloc(h, &h->X32_owned, h->P), "allocate FP32 X");
+            ALLOC_OR_FAIL(h, dalloc(h, &h->X32_owned, h->P), "allocate FP32 X");
         if (elem == CPALS_ELEM_F32) {
             if (mem == CPALS_MEM_DEVICE) {
                 h->X32 = static_cast<const float*>(X);
@@ -688,7 +756,7 @@ int cpals_set_tensor(cpals_handle* hh, const void* X, int elem, int mem)
             const double* src = static_cast<const double*>(X);
             if (mem == CPALS_MEM_HOST) {
                 // stage through the owned FP64 buffer
-                if (!h->X64_owned) CUDA_OR_FAIL(h, dalloc(h, &h->X64_owned, h->P), "allocate X staging");
+                if (!h->X64_owned) ALLOC_OR_FAIL(h, dalloc(h, &h->X64_owned, h->P), "allocate X staging");
                 CUDA_OR_FAIL(h, cudaMemcpyAsync(h->X64_owned, X, sizeof(double) * h->P, cudaMemcpyHostToDevice,
                                                 h->stream), "copy X");
                 src = h->X64_owned;
@@ -731,8 +799,7 @@ int cpals_set_factors(cpals_handle* hh, const double* const* A, const double* la
         CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "sync");
     }
     for (int m = 0; m < h->N; ++m) {
-        CUDA_OR_FAIL(h, cpals::householder_qr(h, h->A[m], h->dims[m], R, h->Q[m], h->Rf[m]), "factor QR");
-        CUDA_OR_FAIL(h, cpals::gram(h, h->A[m], h->dims[m], h->G[m]), "factor Gram");
+        CUDA_OR_FAIL(h, factor_qr_gram(h, m, true), "factor QR and Gram");
         h->qr_valid[m] = true;
         h->gram_valid[m] = true;
     }
@@ -1003,6 +1070,7 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
         case CPALS_OPT_KRP_TREE: field = &h->krp_tree; break;
         case CPALS_OPT_F32_PIPELINE: field = &h->f32_pipe; break;
         case CPALS_OPT_TEST_WITHHOLD_COPIES: field = &h->test_withhold; break;
+        case CPALS_OPT_FUSED_TAIL: field = &h->fused_tail; break;
         default: break;
     }
     if (!field || (value != 0 && value != 1)) return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
@@ -1012,6 +1080,15 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
         for (int s = 0; s < 4; ++s)             // captured sweeps hold the old kernels and schedule
             if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
     }
+    return CPALS_OK;
+}
+
+int cpals_test_newton_recip(const double* x, int64_t n, double* rcp, double* rsqrt)
+{
+    if (n < 0 || (n > 0 && (!x || !rcp || !rsqrt))) return fail(nullptr, CPALS_ERR_ARG, "%s", "bad arguments");
+    cudaError_t e = cpals::recip_check(x, n, rcp, rsqrt, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "reciprocal check");
     return CPALS_OK;
 }
 

@@ -105,6 +105,8 @@ struct Handle {
 
     // device scalars
     int* d_status = nullptr;
+    int* d_gate = nullptr;          // fused tail: 1 when the factor QR falls back to Householder
+    bool fused_tail = true;         // CPALS_OPT_FUSED_TAIL
     double* d_normX2 = nullptr;
     double* d_fit = nullptr;        // fit history ring
     int* d_fit_count = nullptr;
@@ -182,7 +184,18 @@ cudaError_t residual_direct(Handle* h, double* d_out);
 // (lda = m), Q is m x n, R is n x n.  A may alias Q.
 // dense = false for structured inputs (Khatri-Rao steps, triangular factors),
 // whose leaves keep the kernel that skips identity reflectors.
-cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, bool dense = true);
+// gate (device int, may be NULL): the kernels return at once while *gate == 0
+// (the fused mode tail writes it: 1 when its CholeskyQR2 was refused).
+cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, bool dense = true,
+                           const int* gate = nullptr);
+// The end of a mode update in one thread-block cluster (tail.cu): the solve
+// (kind 0: Ahat R0^T = W; 1: Ahat = W T; 2: Ahat S = M with S = L L^T; 3: Ahat
+// given in h->Ahat), lambda, A_n, G_n and, with want_qr, Q_n R_n by
+// CholeskyQR2 (h->d_gate = 1 when the Householder QR has to take over).
+bool mode_tail_ok(int64_t I, int R);
+// The tail's Newton-Raphson 1/x and 1/sqrt(x) on n values (for their accuracy test).
+cudaError_t recip_check(const double* x, int64_t n, double* rcp, double* rsq, cudaStream_t st);
+cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double* Op, bool want_qr);
 // QR of V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->Q0, h->R0 (structured, V_n not formed).
 // With implicit = true Q0 is not formed either: the Q factors of the fold steps
 // go to h->KP (for the Kruskal-input path) and only R0 is written.

@@ -10,6 +10,7 @@
 // split over row blocks and then reduced in a fixed order (deterministic).
 #include <algorithm>
 
+#include "dev_common.cuh"
 #include "internal.cuh"
 
 namespace cpals {
@@ -17,13 +18,6 @@ namespace cpals {
 namespace {
 
 constexpr int kQrThreads = 512;
-constexpr double kEps = 2.220446049250313e-16;
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // dlarfg for a column with leading entry alpha and tail sum of squares s:
 // H = I - tau v v^T with v = [1; scale * tail] maps the column to beta e_1
@@ -53,9 +47,9 @@ __device__ __forceinline__ void hh_reflector(double alpha, double s, double* tau
 // made non-negative by flipping the matching row of R and column of Q.
 __global__ void __launch_bounds__(kQrThreads) hh_qr_blocks_kernel(
     const double* __restrict__ A, int64_t lda, int64_t m, int n, int nb, double* __restrict__ Qout,
-    int64_t ldq, double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
+    int64_t ldq, double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status, const int* __restrict__ gate)
 {
-    if (*status != kStatusOk) return;
+    if (*status != kStatusOk || (gate && *gate == 0)) return;
     extern __shared__ double sm[];
     const int b = blockIdx.x;
     const int64_t off = (int64_t)b * m / nb, end = (int64_t)(b + 1) * m / nb;
@@ -184,9 +178,9 @@ inline size_t cols_smem_bytes(int64_t mb, int n)
 
 __global__ void __launch_bounds__(kColsBlock) hh_qr_cols_kernel(
     const double* __restrict__ A, int64_t lda, int64_t m, int n, int nb, double* __restrict__ Qout, int64_t ldq,
-    double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
+    double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status, const int* __restrict__ gate)
 {
-    if (*status != kStatusOk) return;
+    if (*status != kStatusOk || (gate && *gate == 0)) return;
     extern __shared__ double sm[];
     const int b = blockIdx.x;
     const int64_t off = (int64_t)b * m / nb, end = (int64_t)(b + 1) * m / nb;
@@ -302,9 +296,9 @@ __global__ void __launch_bounds__(kColsBlock) hh_qr_cols_kernel(
 // Qout(block rows of b) = Qi(block rows of b) * Qtop(b*n:(b+1)*n, :)  (TSQR combine)
 __global__ void tsqr_combine_kernel(const double* __restrict__ Qi, int64_t m, int n, int nb,
                                     const double* __restrict__ Qtop, int64_t ldt, double* __restrict__ Qout,
-                                    const int* __restrict__ status)
+                                    const int* __restrict__ status, const int* __restrict__ gate)
 {
-    if (*status != kStatusOk) return;
+    if (*status != kStatusOk || (gate && *gate == 0)) return;
     const int64_t total = m * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -345,9 +339,9 @@ constexpr int kTriBlock = kTriThreads + 32;      // + the reflector warp
 
 __global__ void __launch_bounds__(kTriBlock) hh_qr_tri_kernel(
     const double* __restrict__ A, int64_t lda, int K, int n, double* __restrict__ Qout, int64_t ldq,
-    double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status)
+    double* __restrict__ Rout, int64_t ldr, const int* __restrict__ status, const int* __restrict__ gate)
 {
-    if (*status != kStatusOk) return;
+    if (*status != kStatusOk || (gate && *gate == 0)) return;
     extern __shared__ double sm[];
     const int ld = n + 1;             // odd leading dimension: lanes on consecutive columns hit distinct banks
     double* U = sm;                   // upper block
@@ -471,9 +465,9 @@ __global__ void __launch_bounds__(kTriBlock) hh_qr_tri_kernel(
 // p = r / (2n) (the TSQR tree's combine of a level with the level above).
 __global__ void tri_combine_kernel(const double* __restrict__ Qi, int64_t ldqi, int64_t rows, int n,
                                    const double* __restrict__ Qt, int64_t ldt, double* __restrict__ Qout,
-                                   int64_t ldo, const int* __restrict__ status)
+                                   int64_t ldo, const int* __restrict__ status, const int* __restrict__ gate)
 {
-    if (*status != kStatusOk) return;
+    if (*status != kStatusOk || (gate && *gate == 0)) return;
     const int64_t total = rows * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -692,32 +686,6 @@ __global__ void kron_right_apply_kernel(const double* __restrict__ Qa, int64_t S
 // lane updates its entries with x_k -- keeps the chain at R steps of one
 // multiply and one FMA, against ~R^2/2 dependent FMAs for one thread per row.
 constexpr int kSolveWarps = 8;
-
-// One substitution on the warp-distributed row w (slots w0, w1):
-//   back = false: L y = w with L(e, k) = A[e + R k] (lower), from k = 0 up;
-//   back = true:  U x = w with U(e, k) = A[e + R k] (upper), from k = R-1 down,
-//                 or with U = A^T (U(e, k) = A[k + R e]) when trans.
-// d0, d1 are the lanes' reciprocals of the diagonal.
-__device__ __forceinline__ void warp_subst(double& w0, double& w1, const double* A, int R, double d0, double d1,
-                                           bool back, bool trans)
-{
-    const int lane = threadIdx.x & 31;
-    for (int t = 0; t < R; ++t) {
-        const int k = back ? R - 1 - t : t;
-        double xk;
-        if (k < 32) {
-            if (lane == k) w0 *= d0;
-            xk = __shfl_sync(0xffffffffu, w0, k);
-        } else {
-            if (lane == k - 32) w1 *= d1;
-            xk = __shfl_sync(0xffffffffu, w1, k - 32);
-        }
-        const int e0 = lane, e1 = lane + 32;
-        if (e0 < R && (back ? e0 < k : e0 > k)) w0 = fma(-(trans ? A[k + R * e0] : A[e0 + R * k]), xk, w0);
-        if (R > 32 && e1 < R && (back ? e1 < k : e1 > k))
-            w1 = fma(-(trans ? A[k + R * e1] : A[e1 + R * k]), xk, w1);
-    }
-}
 
 // Ahat R0^T = W, i.e. R0 x = w for each row w of W (back substitution).
 // Singularity test: |R0(k,k)| <= R * eps * max_j |R0(j,j)| sets the status
@@ -1160,13 +1128,14 @@ inline unsigned grid_for(int64_t n, int threads, int num_sms)
 // split into blocks of max(2n, 32, m / #SMs) rows.
 // Q (K n x n) and R (n x n) of K >= 2 stacked upper-triangular blocks, by a
 // binary tree of pair QRs.
-cudaError_t tsqr_tri(Handle* h, const double* Rs, int K, int n, double* Q, double* R, double* ws, int64_t ws_elems)
+cudaError_t tsqr_tri(Handle* h, const double* Rs, int K, int n, double* Q, double* R, double* ws, int64_t ws_elems,
+                     const int* gate)
 {
     const int P = (K + 1) / 2;
     const size_t smem = tri_smem_bytes(n);
     if (P == 1) {   // K == 2: the pair's Q is the result
         hh_qr_tri_kernel<<<1, kTriBlock, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Q, (int64_t)K * n, R, n,
-                                                            h->d_status);
+                                                            h->d_status, gate);
         h->launches++;
         return cudaGetLastError();
     }
@@ -1177,13 +1146,13 @@ cudaError_t tsqr_tri(Handle* h, const double* Rs, int K, int n, double* Q, doubl
     const int64_t used = 4 * P * nn;
     if (used > ws_elems) return cudaErrorInvalidValue;
     hh_qr_tri_kernel<<<P, kTriBlock, smem, h->stream>>>(Rs, (int64_t)K * n, K, n, Qi, 2 * (int64_t)P * n, Rs2,
-                                                         (int64_t)P * n, h->d_status);
+                                                         (int64_t)P * n, h->d_status, gate);
     h->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
-    CPALS_CUDA_TRY(tsqr_tri(h, Rs2, P, n, Qt, R, ws + used, ws_elems - used));
+    CPALS_CUDA_TRY(tsqr_tri(h, Rs2, P, n, Qt, R, ws + used, ws_elems - used, gate));
     const int64_t rows = (int64_t)K * n;
     tri_combine_kernel<<<grid_for(rows * n, 256, h->num_sms), 256, 0, h->stream>>>(
-        Qi, 2 * (int64_t)P * n, rows, n, Qt, (int64_t)P * n, Q, rows, h->d_status);
+        Qi, 2 * (int64_t)P * n, rows, n, Qt, (int64_t)P * n, Q, rows, h->d_status, gate);
     h->launches++;
     return cudaGetLastError();
 }
@@ -1201,22 +1170,22 @@ inline bool use_cols_leaf(bool dense, int64_t mb, int n)
 }
 
 void launch_leaves(Handle* h, bool cols, unsigned nb, int64_t mbmax, const double* A, int64_t m, int n, double* Q,
-                   double* R, int64_t ldr)
+                   double* R, int64_t ldr, const int* gate)
 {
     if (cols)
         hh_qr_cols_kernel<<<nb, kColsBlock, cols_smem_bytes(mbmax, n), h->stream>>>(A, m, m, n, (int)nb, Q, m, R, ldr,
-                                                                                  h->d_status);
+                                                                                  h->d_status, gate);
     else
         hh_qr_blocks_kernel<<<nb, kQrThreads, qr_smem_bytes((int)mbmax, n), h->stream>>>(A, m, m, n, (int)nb, Q, m,
-                                                                                          R, ldr, h->d_status);
+                                                                                          R, ldr, h->d_status, gate);
     h->launches++;
 }
 
 cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, double* ws, int64_t ws_elems,
-                 bool dense)
+                 bool dense, const int* gate)
 {
     if (qr_leaf_fits(m, n) && m * n * n <= ((int64_t)1 << 18)) {
-        launch_leaves(h, use_cols_leaf(dense, m, n), 1, m, A, m, n, Q, R, n);
+        launch_leaves(h, use_cols_leaf(dense, m, n), 1, m, A, m, n, Q, R, n, gate);
         return cudaGetLastError();
     }
     const int64_t leaf_rows = std::max<int64_t>({(int64_t)n, 32, (m + h->num_sms - 1) / h->num_sms});
@@ -1226,7 +1195,7 @@ cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double
     const int64_t mbmax = (m + nb - 1) / nb;
     if (!qr_leaf_fits(mbmax, n)) return cudaErrorInvalidValue;
     if (nb == 1) {
-        launch_leaves(h, use_cols_leaf(dense, m, n), 1, m, A, m, n, Q, R, n);
+        launch_leaves(h, use_cols_leaf(dense, m, n), 1, m, A, m, n, Q, R, n, gate);
         return cudaGetLastError();
     }
     double* Qi = ws;                        // m x n
@@ -1235,11 +1204,11 @@ cudaError_t tsqr(Handle* h, const double* A, int64_t m, int n, double* Q, double
     double* rest = Qt + nb * n * n;
     const int64_t used = m * n + 2 * nb * n * n;
     if (used > ws_elems) return cudaErrorInvalidValue;
-    launch_leaves(h, use_cols_leaf(dense, mbmax, n), (unsigned)nb, mbmax, A, m, n, Qi, Rs, nb * n);
+    launch_leaves(h, use_cols_leaf(dense, mbmax, n), (unsigned)nb, mbmax, A, m, n, Qi, Rs, nb * n, gate);
     CPALS_CUDA_TRY(cudaGetLastError());
-    CPALS_CUDA_TRY(tsqr_tri(h, Rs, (int)nb, n, Qt, R, rest, ws_elems - used));
+    CPALS_CUDA_TRY(tsqr_tri(h, Rs, (int)nb, n, Qt, R, rest, ws_elems - used, gate));
     tsqr_combine_kernel<<<grid_for(m * n, 256, h->num_sms), 256, 0, h->stream>>>(Qi, m, n, (int)nb, Qt, nb * n, Q,
-                                                                                  h->d_status);
+                                                                                  h->d_status, gate);
     h->launches++;
     return cudaGetLastError();
 }
@@ -1266,10 +1235,11 @@ cudaError_t qr_kernel_attrs()
     return err;
 }
 
-cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, bool dense)
+cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double* Q, double* R, bool dense,
+                           const int* gate)
 {
     CPALS_CUDA_TRY(qr_kernel_attrs());
-    return tsqr(h, A, m, n, Q, R, h->qr_ws, h->qr_ws_elems, dense);
+    return tsqr(h, A, m, n, Q, R, h->qr_ws, h->qr_ws_elems, dense, gate);
 }
 
 // QR of the Khatri-Rao product Rl[cnt-1] (.) ... (.) Rl[0] of upper-triangular
