@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--recovery-seeds", type=int, default=5,
                     help="c3: planted problems (seeds) on which every precision runs to convergence and is scored "
                          "against the planted factors (factor-match score, Sec. 4.2); 0 skips")
+    ap.add_argument("--precisions", default="f64,f32,bf16x3,tf32x3",
+                    help="c3/c5a/c5b: comma-separated precisions to run")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="c3/c5a/c5b: throughput only (no Multi-TTM error, one-sweep factors or fit to convergence)")
     ap.add_argument("--fit-sweeps", type=int, default=300,
                     help="at most this many sweeps (stop at |fit change| < 1e-10) for the equal-fit comparison")
     return ap.parse_args()
@@ -345,7 +349,8 @@ def run_mixed(args, world, rank):
     hbm = measured_peaks().get("hbm_gbs")
     out = {}
     ref = {}
-    for prec in ["f64", "f32", "bf16x3", "tf32x3"]:
+    precisions = [x for x in args.precisions.split(",") if x]
+    for prec in precisions:
         # throughput
         h = cpals.CPALS(p.dims, R, prec)
         h.set_stream(stream)
@@ -375,6 +380,13 @@ def run_mixed(args, world, rank):
         ms = sum(ttm_ms) / len(ttm_ms)
         xbytes = (8 if prec == "f64" else 4) * P
         del h
+        entry = {"iters_per_s": its, "gpu_launches_per_sweep": launches / args.steps,
+                 "first_ttm_ms": ms, "first_ttm_gbs": xbytes / (ms * 1e-3) / 1e9,
+                 "first_ttm_frac_hbm": (xbytes / (ms * 1e-3) / 1e9 / hbm) if hbm else None,
+                 "first_ttm_tflops": 2.0 * P * R / (ms * 1e-3) / 1e12}
+        if args.no_accuracy:
+            out[prec] = entry
+            continue
         # accuracy: Multi-TTM with identical Q_m, one sweep, and the fit after S sweeps
         ha = cpals.CPALS(p.dims, R, prec)
         ha.set_stream(stream)
@@ -390,14 +402,10 @@ def run_mixed(args, world, rank):
         fit_final = ha.fit(direct=True)
         traj = np.concatenate([fits1, fitsS])
         del ha
-        entry = {"iters_per_s": its, "gpu_launches_per_sweep": launches / args.steps,
-                 "first_ttm_ms": ms, "first_ttm_gbs": xbytes / (ms * 1e-3) / 1e9,
-                 "first_ttm_frac_hbm": (xbytes / (ms * 1e-3) / 1e9 / hbm) if hbm else None,
-                 "first_ttm_tflops": 2.0 * P * R / (ms * 1e-3) / 1e12,
-                 "fit_direct_converged": fit_final, "sweeps_to_converge": sweeps_run}
+        entry.update({"fit_direct_converged": fit_final, "sweeps_to_converge": sweeps_run})
         if prec == "f64":
             ref = {"Y": Ys, "A": A1, "fit": fit_final, "traj": traj}
-        else:
+        elif ref:
             m5 = min(5, len(traj), len(ref["traj"]))
             entry["fit_traj_max_diff_first5"] = float(np.abs(traj[:m5] - ref["traj"][:m5]).max())
             entry["multi_ttm_rel_err_vs_f64"] = max(
@@ -407,18 +415,20 @@ def run_mixed(args, world, rank):
             entry["fit_rel_diff_vs_f64"] = abs(fit_final - ref["fit"]) / abs(ref["fit"])
         out[prec] = entry
     recovery = None
-    if args.workload == "c3" and args.recovery_seeds > 0:
+    if args.workload == "c3" and args.recovery_seeds > 0 and not args.no_accuracy:
         recovery = recovery_rates(args, p.dims, R, fit_sweeps, solve, rtol, stream)
     if rank == 0:
+        head = "bf16x3" if "bf16x3" in out else precisions[0]
         line = {
-            "metric": METRIC, "value": out["bf16x3"]["iters_per_s"], "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": out[head]["iters_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16x3 (value); tf32x3, fp32 and fp64 beside it (tensor cores when R >= 16)",
+            "vs_baseline": None, "dtype": f"{head} (value); the others beside it (tensor cores when R >= 16)",
             "data": "synthetic",
             "config": {"workload": desc, "dims": list(p.dims), "rank": R, "fit_sweeps": fit_sweeps,
                        "solve": solve, "svd_rtol": rtol},
             "precisions": out,
-            "speedup_vs_f64": {k: out[k]["iters_per_s"] / out["f64"]["iters_per_s"] for k in out},
+            "speedup_vs_f64": ({k: out[k]["iters_per_s"] / out["f64"]["iters_per_s"] for k in out}
+                               if "f64" in out else None),
         }
         if recovery is not None:
             line["planted_recovery"] = recovery

@@ -274,14 +274,22 @@ int cpals_sync(cpals_handle* h);
  *    leaves Q1^T Q1 within 1e-2 of the identity (cond(A_n) below about 7e6),
  *    and otherwise the Householder QR runs as with 0.  Both give the thin QR
  *    with a positive diagonal of R_n, so only rounding differs.  0 runs the
- *    separate solve, normalisation and Householder QR kernels. */
+ *    separate solve, normalisation and Householder QR kernels.
+ *  CPALS_OPT_SVD_SHORTCUT (default 1): before the Jacobi SVD of R0 (the SVD
+ *    solve), X = R0^-1 is formed by substitution; when
+ *    ||R0||_F ||X||_F svd_rtol <= 1/4, no singular value can fall below
+ *    svd_rtol * sigma_max (sigma_min >= 1/||X||_F, sigma_max <= ||R0||_F), so
+ *    the truncated solve is W R0^-T exactly and the operator R0^-T is used
+ *    without the SVD.  Otherwise the Jacobi SVD runs as with 0.  The two
+ *    differ only by rounding. */
 typedef enum {
     CPALS_OPT_DIMTREE = 0,
     CPALS_OPT_TC_PIPELINE = 1,
     CPALS_OPT_KRP_TREE = 2,
     CPALS_OPT_F32_PIPELINE = 3,
     CPALS_OPT_TEST_WITHHOLD_COPIES = 4,
-    CPALS_OPT_FUSED_TAIL = 5
+    CPALS_OPT_FUSED_TAIL = 5,
+    CPALS_OPT_SVD_SHORTCUT = 6
 } cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
 

@@ -213,6 +213,10 @@ class CPALS:
         """CPALS_OPT_FUSED_TAIL: solve, normalisation and CholeskyQR2 of the factor in one cluster kernel."""
         _check(self._h, load().cpals_set_option(self._h, 5, 1 if on else 0))
 
+    def set_svd_shortcut(self, on: bool):
+        """CPALS_OPT_SVD_SHORTCUT: skip the Jacobi SVD when a norm bound proves nothing is truncated."""
+        _check(self._h, load().cpals_set_option(self._h, 6, 1 if on else 0))
+
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
 

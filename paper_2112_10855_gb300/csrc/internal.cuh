@@ -106,6 +106,8 @@ struct Handle {
     // device scalars
     int* d_status = nullptr;
     int* d_gate = nullptr;          // fused tail: 1 when the factor QR falls back to Householder
+    int* d_svd_gate = nullptr;      // SVD solve: 1 when truncation is possible and the Jacobi SVD must run
+    bool svd_shortcut = true;       // CPALS_OPT_SVD_SHORTCUT
     bool fused_tail = true;         // CPALS_OPT_FUSED_TAIL
     double* d_normX2 = nullptr;
     double* d_fit = nullptr;        // fit history ring

@@ -746,6 +746,80 @@ __global__ void __launch_bounds__(kSolveWarps * 32) trsm_qr_kernel(
 // FP64 sweeps run on B = R0 V, which is already nearly column-orthogonal, and
 // converge in a few sweeps instead of about twelve.  The result is the SVD of
 // R0 to FP64 accuracy either way.
+// Truncation test ahead of the SVD solve.  The truncated operator
+// T = U pinv(Sigma) V^T of R0 = U Sigma V^T keeps sigma_i > rtol sigma_max
+// (Sec. 3.1).  Since sigma_min >= 1 / ||R0^-1||_F and sigma_max <= ||R0||_F,
+// ||R0||_F ||R0^-1||_F < 1 / rtol proves that nothing is truncated, and then
+// T = U Sigma^-1 V^T = R0^-T exactly.  The kernel forms X = R0^-1 by back
+// substitution (one warp per column, lanes over the rows), and when
+// ||R0||_F ||X||_F rtol <= 1/4 (the margin covers the rounding of X) writes
+// T = X^T and gate = 0, so the Jacobi SVD that follows is skipped; otherwise
+// gate = 1 and the Jacobi SVD forms T.  A zero or non-finite diagonal entry
+// sends R0 to the SVD at once.
+constexpr int kInvWarps = 8;
+__global__ void __launch_bounds__(kInvWarps * 32) svd_shortcut_kernel(const double* __restrict__ R0, int R,
+                                                                      double rtol, double* __restrict__ T,
+                                                                      int* __restrict__ gate,
+                                                                      const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double r0[kMaxRank * kMaxRank];
+    __shared__ double dinv[kMaxRank];
+    __shared__ double wsum[kInvWarps][2];
+    __shared__ int bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < R * R; e += kInvWarps * 32) r0[e] = R0[e];
+    __syncthreads();
+    if (tid < R) {
+        const double d = r0[tid + R * tid];
+        if (!(fabs(d) > 0.0) || !(fabs(d) < INFINITY)) bad = 1;
+        dinv[tid] = 1.0 / d;
+    }
+    __syncthreads();
+    if (bad) {
+        if (tid == 0) *gate = 1;
+        return;
+    }
+    double sx = 0.0, sr = 0.0;
+    const int e0 = lane, e1 = lane + 32;
+    for (int j = warp; j < R; j += kInvWarps) {
+        // X(:, j): R0 x = e_j, from k = j down
+        double w0 = (e0 == j) ? 1.0 : 0.0, w1 = (e1 == j) ? 1.0 : 0.0;
+        for (int k = j; k >= 0; --k) {
+            double xk;
+            if (k < 32) {
+                if (lane == k) w0 *= dinv[k];
+                xk = __shfl_sync(0xffffffffu, w0, k);
+            } else {
+                if (lane == k - 32) w1 *= dinv[k];
+                xk = __shfl_sync(0xffffffffu, w1, k - 32);
+            }
+            if (e0 < k) w0 = fma(-r0[e0 + R * k], xk, w0);
+            if (e1 < k) w1 = fma(-r0[e1 + R * k], xk, w1);
+        }
+        // T = X^T: T(j, i) = X(i, j)
+        if (e0 <= j) { T[j + R * e0] = w0; sx = fma(w0, w0, sx); }
+        if (e1 <= j && e1 < R) { T[j + R * e1] = w1; sx = fma(w1, w1, sx); }
+        if (e0 > j && e0 < R) T[j + R * e0] = 0.0;
+        if (e1 > j && e1 < R) T[j + R * e1] = 0.0;
+        if (e0 <= j) sr = fma(r0[e0 + R * j], r0[e0 + R * j], sr);
+        if (e1 <= j && e1 < R) sr = fma(r0[e1 + R * j], r0[e1 + R * j], sr);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    }
+    if (lane == 0) { wsum[warp][0] = sx; wsum[warp][1] = sr; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kInvWarps; ++w) { a += wsum[w][0]; b += wsum[w][1]; }
+        const double bound = sqrt(a) * sqrt(b);
+        *gate = (bound < INFINITY && bound * rtol <= 0.25) ? 0 : 1;
+    }
+}
+
 constexpr int kJacobiWarps = 8;
 constexpr int kJacobiThreads = 32 * kJacobiWarps;
 constexpr int kJacobiMixedMinR = 32;
@@ -834,9 +908,10 @@ __device__ int jacobi_sweeps(T* B, T* V, int ld, int R, T tol, int max_sweeps, T
 
 __global__ void __launch_bounds__(kJacobiThreads) jacobi_pinv_kernel(const double* __restrict__ R0, int R,
                                                                     double rtol, double* __restrict__ T,
-                                                                    const int* __restrict__ status)
+                                                                    const int* __restrict__ status,
+                                                                    const int* __restrict__ gate)
 {
-    if (*status != kStatusOk) return;
+    if (*status != kStatusOk || (gate && *gate == 0)) return;
     extern __shared__ double jsm[];
     const int ld = R + 1;                     // odd: lanes on different columns hit different banks
     const int Rp = (R + 1) & ~1;
@@ -1401,7 +1476,15 @@ cudaError_t svd_operator(Handle* h, double rtol)
                                             (int)smem));
         attr_set = true;
     }
-    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status);
+    const int* gate = nullptr;
+    if (h->svd_shortcut) {
+        svd_shortcut_kernel<<<1, kInvWarps * 32, 0, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_svd_gate,
+                                                                  h->d_status);
+        h->launches++;
+        CPALS_CUDA_TRY(cudaGetLastError());
+        gate = h->d_svd_gate;
+    }
+    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status, gate);
     h->launches++;
     return cudaGetLastError();
 }
@@ -1429,7 +1512,7 @@ cudaError_t normal_operator(Handle* h, int n, bool pinv, double rtol)
                                             (int)smem));
         attr_set = true;
     }
-    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->S, h->R, rtol, h->T, h->d_status);
+    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->S, h->R, rtol, h->T, h->d_status, nullptr);
     h->launches++;
     return cudaGetLastError();
 }
