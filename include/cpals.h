@@ -354,12 +354,18 @@ int cpals_multi_ttm_static(const int64_t* dims, int N, int rank, int mode, const
 
 /* ---------------------------------------------------------------------
  * Batched problems: many independent 3-way CP-ALS-QR problems of uneven dims
- * and ranks advance together (one persistent kernel per mode update; each
- * CTA runs the whole mode-loop body of Alg. cp-als-qr for one problem at a
- * time: QR of V_n = R_hi (.) R_lo, the FP32 Multi-TTM, W = Y_(n) Q0, the R0
- * substitution, normalisation and the factor QR in FP64, then the efficient
- * fit of Sec. 3.3.1 after the last mode).  The passes over X run in FP32;
- * every small factor is FP64.
+ * and ranks advance together.  A sweep follows the dimension tree of
+ * Sec. 3.3.3 for every problem at once: one pass over all tensors contracts
+ * mode 2 (X x_2 Q_2^T), the updates of modes 0 and 1 finish their
+ * Multi-TTMs from that partial, a second pass contracts mode 1 with the new
+ * Q_1, and the update of mode 2 finishes from it -- two reads of X per sweep.
+ * Every contraction (the passes, the last TTM of each Multi-TTM and
+ * W = Y_(n) Q0) is one launch over all problems whose CTAs take
+ * (problem, row tile) work items from a device queue, in FP32.  The rest of
+ * each mode update of Alg. cp-als-qr -- the R0 substitution, normalisation,
+ * the factor QR and the QR of the next mode's V = R_hi (.) R_lo -- is one
+ * FP64 kernel with a CTA per problem; the efficient fit of Sec. 3.3.1
+ * follows the last mode.
  * --------------------------------------------------------------------- */
 typedef struct cpals_batch cpals_batch;
 
@@ -385,8 +391,11 @@ int cpals_batch_set_factors(cpals_batch* b, const double* const* A, int mem);
 int cpals_batch_get_factors(cpals_batch* b, double* const* A, double* const* lambda, int mem);
 
 /* `iters` sweeps over the three modes for every problem.  The sweep is a
- * captured CUDA graph of three launches.  The first call picks the launch
- * shape by timing one sweep per candidate on a saved copy of the factors.
+ * captured CUDA graph of twelve kernel launches (the QR of V_0, five grouped
+ * TTMs, three grouped W products, three factorisation kernels).  The first
+ * call picks the grouped launches' row tile and the factorisation kernels'
+ * CTA size and count by timing one sweep per candidate on a saved copy of
+ * the factors.
  * fits_host (count values, may be NULL) receives each problem's efficient fit
  * after the last sweep; status_host (count values, may be NULL) receives each
  * problem's status: CPALS_ERR_SINGULAR for a problem whose R0 became
@@ -394,10 +403,10 @@ int cpals_batch_get_factors(cpals_batch* b, double* const* A, double* const* lam
  * after that).  Synchronises. */
 int cpals_batch_iterate(cpals_batch* b, int iters, double* fits_host, int* status_host);
 
-/* Kernel launches issued so far (a graph replay counts its three kernels). */
+/* Kernel launches issued so far (a graph replay counts its twelve kernels). */
 int64_t cpals_batch_launch_count(const cpals_batch* b);
 
-/* The launch shape the first iterate picked (0 before it). */
+/* The factorisation kernels' launch shape the first iterate picked (0 before it). */
 int cpals_batch_launch_shape(const cpals_batch* b, int* grid, int* threads);
 
 /* Measured FMA throughput probe (not part of the method): runs dependent

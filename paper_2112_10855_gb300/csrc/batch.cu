@@ -1,20 +1,31 @@
 // batch.cu -- many independent 3-way CP-ALS-QR problems of uneven dims and
-// ranks advancing together: one persistent kernel per mode update (the body of
-// the mode loop of Alg. cp-als-qr) in which each CTA takes whole problems from
-// a largest-first list and runs, on chip:
-//   1. V_n = R_hi (.) R_lo (the two other R factors, Sec. 3.1) and its Householder
-//      QR V_n = Q0 R0 (FP64, shared memory);
-//   2. the Multi-TTM Y = X x_{m != n} Q_m^T (Eq. multittm) as two single TTMs,
-//      larger dim first (Sec. 3.2), in FP32 through an L2-resident per-problem
-//      scratch;
-//   3. W_n = Y_(n) Q0 (Eq. ls-qr-q0-step), FP64;
-//   4. the substitution Ahat R0^T = W (singular R0 -> per-problem status, factor
-//      kept);
-//   5. column normalisation (2-norm) into A_n and lambda;
-//   6. the Householder QR A_n = Q_n R_n (FP64, shared memory);
-//   7. after the last mode, the efficient fit of Sec. 3.3.1.
-// The sweep (three launches) is captured once into a CUDA graph.  The CTA
-// count (per SM) and the CTA size are picked by timing the first sweep.
+// ranks advancing together.  A sweep follows the dimension tree of Sec. 3.3.3
+// for every problem at once (modes {0, 1} | {2}), so X is read twice:
+//   pass 1:  P = X x_2 Q_2^T                       (all problems, one launch)
+//   mode 0:  Y_(0) from P x_1 Q_1^T, W_0, update
+//   mode 1:  Y_(1) from P x_0 Q_0^T (new Q_0), W_1, update
+//   pass 2:  T = X x_1 Q_1^T (new Q_1)
+//   mode 2:  Y_(2) from T x_0 Q_0^T, W_2, update, efficient fit (Sec. 3.3.1).
+// Every contraction -- the two passes, the last TTM of each Multi-TTM
+// (Eq. multittm) and W_n = Y_(n) Q0 (Eq. ls-qr-q0-step) -- is one launch over
+// all problems whose CTAs take (problem, row tile) work items from a device
+// queue (an atomic counter: no CTA waits on another, so nothing needs a time
+// limit); whatever the mix of sizes, every SM works on every contraction.
+// These run in FP32, W accumulating in FP32 like the Multi-TTM it extends.
+// What is left of a mode update is the FP64 factorisation chain of each
+// problem, one CTA per problem (largest first):
+//   - the substitution Ahat R0^T = W (a singular R0 sets the problem's status
+//     and keeps its factor),
+//   - column normalisation (2-norm) into A_n and lambda,
+//   - the Householder QR A_n = Q_n R_n,
+//   - and, for the next mode, the QR V_{n+1} = Q0 R0 of the Khatri-Rao
+//     product of its two other R factors (Sec. 3.1), by the staircase
+//     Householder QR of a product of two triangular factors (Sec. 3.3.3: no
+//     fill-in).  The QR of V_0 needs only the previous sweep's R_1, R_2, so it
+//     runs on a graph branch beside pass 1.
+// The sweep is captured once into a CUDA graph (twelve kernels).  The first
+// iterate picks the row tile of the grouped contractions and the CTA size
+// and count of the factorisation kernels by timing one sweep per candidate.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +33,7 @@
 #include <numeric>
 #include <vector>
 
+#include "dev_common.cuh"
 #include "internal.cuh"
 
 namespace cpals {
@@ -39,8 +51,11 @@ struct BProb {
     int64_t q[3];     // Q_m (I_m x R)
     int64_t rf[3];    // R_m (R x R)
     int64_t lam;      // lambda (R)
-    int64_t t1;       // first-TTM intermediate (floats)
-    int64_t y;        // Multi-TTM result (floats)
+    int64_t q0, r0;   // Q0 (R^2 x R) and R0 (R x R) of the current mode's V_n
+    int64_t w;        // W_n (up to max_n I_n x R)
+    int64_t p1;       // X x_2 Q_2^T: I0 x I1 x R (floats)
+    int64_t t2;       // X x_1 Q_1^T: I0 x R x I2 (floats)
+    int64_t y;        // Y_(n): up to max_n I_n R^2 (floats)
     double normX2;
 };
 
@@ -125,77 +140,266 @@ __device__ void cta_householder(double* W, int m, int n, double* Q, double* Rout
     __syncthreads();
 }
 
-// One CTA: Out(l, r, t) = sum_k In(l, k, t) * qs[k*R + r] over the [L, K, T] view.
-// Loads are issued eight k at a time so that each thread keeps eight in flight.
-__device__ void cta_ttm_f32(const float* __restrict__ in, int64_t L, int K, int64_t T, const float* qs, int R,
-                            float* __restrict__ out)
+// ---------------------------------------------------------------- grouped contractions
+// One TTM of every problem, viewed as [L, K, T] (Sec. 2.2):
+//   which 0: X  x_2 Q_2^T -> P   [L = I0 I1, K = I2, T = 1]   (pass 1)
+//   which 1: X  x_1 Q_1^T -> T   [L = I0,    K = I1, T = I2]  (pass 2)
+//   which 2: P  x_1 Q_1^T -> Y   [L = I0,    K = I1, T = R]   (mode 0)
+//   which 3: P  x_0 Q_0^T -> Y   [L = 1,     K = I0, T = I1 R] (mode 1)
+//   which 4: T  x_0 Q_0^T -> Y   [L = 1,     K = I0, T = R I2] (mode 2)
+struct BView {
+    int64_t in, out;     // offsets into the input and output arrays
+    int m;               // the contracted mode (its Q_m)
+    int64_t L, T;
+    int K;
+};
+
+__host__ __device__ inline BView view_of(const BProb& pr, int which)
 {
-    const int64_t rows = L * T;
-    for (int64_t f = threadIdx.x; f < rows; f += blockDim.x) {
-        const int64_t t = f / L, l = f - t * L;
-        const float* p = in + l + L * K * t;
-        float acc[kBMaxR];
+    BView v;
+    const int64_t R = pr.R;
+    switch (which) {
+        case 0: v = {pr.x, pr.p1, 2, (int64_t)pr.I[0] * pr.I[1], 1, pr.I[2]}; break;
+        case 1: v = {pr.x, pr.t2, 1, pr.I[0], pr.I[2], pr.I[1]}; break;
+        case 2: v = {pr.p1, pr.y, 1, pr.I[0], R, pr.I[1]}; break;
+        case 3: v = {pr.p1, pr.y, 0, 1, (int64_t)pr.I[1] * R, pr.I[0]}; break;
+        default: v = {pr.t2, pr.y, 0, 1, R * pr.I[2], pr.I[0]}; break;
+    }
+    return v;
+}
+
+// One thread per flattened row f = l + L t of the view, its R FP32
+// accumulators summed in order of k; loads along l are coalesced when L > 1.
+template <int R>
+__device__ __forceinline__ void ttm_row(const float* __restrict__ X, int64_t L, int K, int64_t T, const float* qs,
+                                        int64_t f, float* __restrict__ out)
+{
+    if (f >= L * T) return;
+    const int64_t t = f / L, l = f - t * L;
+    const float* x = X + l + L * (int64_t)K * t;
+    float acc[R];
 #pragma unroll
-        for (int r = 0; r < kBMaxR; ++r) acc[r] = 0.0f;
-        int k = 0;
-        for (; k + 8 <= K; k += 8) {
-            float x[8];
+    for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+    int k = 0;
+    for (; k + 8 <= K; k += 8) {
+        float v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = __ldg(p + L * (k + u));
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(x + L * (int64_t)(k + u));
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float* q = qs + (k + u) * R;
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fmaf(v[u], qs[(k + u) * R + r], acc[r]);
+    }
+    for (; k < K; ++k) {
+        const float v = __ldg(x + L * (int64_t)k);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = fmaf(v, qs[k * R + r], acc[r]);
+    }
+    float* o = out + l + L * (int64_t)R * t;
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[L * r] = acc[r];
+}
+
+struct BItem {
+    int p;
+    int f0;
+};
+
+// The next work item of a grouped launch (thread 0 takes it from the queue).
+__device__ __forceinline__ int next_item(int* counter, int* s_item)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    return *s_item;
+}
+
+__global__ void batch_ttm_kernel(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_items,
+                                 int* __restrict__ counter, int which, const float* __restrict__ Xall,
+                                 float* __restrict__ P1all, float* __restrict__ T2all, float* __restrict__ Yall,
+                                 const double* __restrict__ F, const int* __restrict__ pstatus)
+{
+    __shared__ float qs[128 * kBMaxR];   // Q_m as FP32 [k][r] for K <= 128
+    __shared__ int s_item;
+    int cached = -1;
+    for (;;) {
+        const int it = next_item(counter, &s_item);
+        if (it >= n_items) break;
+        const BItem item = items[it];
+        if (pstatus[item.p] != kStatusOk) continue;
+        const BProb& pr = probs[item.p];
+        const BView v = view_of(pr, which);
+        const int R = pr.R;
+        const float* in = (which <= 1 ? Xall : (which == 4 ? T2all : P1all)) + v.in;
+        float* out = (which == 0 ? P1all : (which == 1 ? T2all : Yall)) + v.out;
+        const double* Q = F + pr.q[v.m];
+        const int64_t f = item.f0 + threadIdx.x;
+        if (v.K <= 128) {
+            if (cached != item.p) {
+                for (int e = threadIdx.x; e < v.K * R; e += blockDim.x) {
+                    const int k = e / R, r = e - k * R;
+                    qs[e] = (float)Q[k + v.K * r];
+                }
+                cached = item.p;
+                __syncthreads();
+            }
+            switch (R) {
+#define CPALS_BT(RV) case RV: ttm_row<RV>(in, v.L, v.K, v.T, qs, f, out); break;
+                CPALS_BT(1) CPALS_BT(2) CPALS_BT(3) CPALS_BT(4) CPALS_BT(5) CPALS_BT(6) CPALS_BT(7) CPALS_BT(8)
+                CPALS_BT(9) CPALS_BT(10) CPALS_BT(11) CPALS_BT(12) CPALS_BT(13) CPALS_BT(14) CPALS_BT(15) CPALS_BT(16)
+#undef CPALS_BT
+                default: break;
+            }
+        } else if (f < v.L * v.T) {
+            // long modes: Q read through L1 in FP64, the same sums in order of k
+            const int64_t t = f / v.L, l = f - t * v.L;
+            const float* x = in + l + v.L * (int64_t)v.K * t;
+            float acc[kBMaxR];
+#pragma unroll
+            for (int r = 0; r < kBMaxR; ++r) acc[r] = 0.0f;
+            for (int k = 0; k < v.K; ++k) {
+                const float xv = __ldg(x + v.L * (int64_t)k);
 #pragma unroll
                 for (int r = 0; r < kBMaxR; ++r)
-                    if (r < R) acc[r] = fmaf(x[u], q[r], acc[r]);
+                    if (r < R) acc[r] = fmaf(xv, (float)__ldg(Q + k + (int64_t)v.K * r), acc[r]);
             }
-        }
-        for (; k < K; ++k) {
-            const float x = __ldg(p + L * k);
-            const float* q = qs + k * R;
+            float* o = out + l + v.L * (int64_t)R * t;
 #pragma unroll
             for (int r = 0; r < kBMaxR; ++r)
-                if (r < R) acc[r] = fmaf(x, q[r], acc[r]);
+                if (r < R) o[v.L * r] = acc[r];
+            cached = -1;
         }
-        float* o = out + l + L * (int64_t)R * t;
-#pragma unroll
-        for (int r = 0; r < kBMaxR; ++r)
-            if (r < R) o[L * r] = acc[r];
     }
 }
 
-// stage Q_m (FP64, I x R column-major) as FP32 [k][r]
-__device__ void stage_q(const double* __restrict__ Qm, int I, int R, float* qs)
+// W_n = Y_(n) Q0 for every problem: one thread per row i of a tile, its R
+// FP32 accumulators summed over the R^2 columns in order.  Y element (i, col),
+// col = a + Rn c, sits at a + Rn (i + In c) with Rn = 1, R, R^2 for n = 0, 1, 2.
+// Q0 (FP64) is staged once per problem as FP32 [col][r].
+template <int R>
+__device__ __forceinline__ void w_row(const float* __restrict__ Y, int In, int Rn, const float* q0f, int i,
+                                      double* __restrict__ W)
 {
-    for (int e = threadIdx.x; e < I * R; e += blockDim.x) {
-        const int k = e / R, r = e - k * R;
-        qs[e] = (float)Qm[k + I * r];
+    if (i >= In) return;
+    constexpr int RR = R * R;
+    const int nc = RR / Rn;
+    float acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+    for (int c = 0; c < nc; ++c) {
+        const float* yr = Y + (int64_t)Rn * (i + (int64_t)In * c);
+        const float* qc = q0f + (int64_t)Rn * c * R;
+        int a = 0;
+        for (; a + 8 <= Rn; a += 8) {
+            float y[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) y[u] = __ldg(yr + a + u);
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = fmaf(y[u], qc[(a + u) * R + r], acc[r]);
+        }
+        for (; a < Rn; ++a) {
+            const float y = __ldg(yr + a);
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fmaf(y, qc[a * R + r], acc[r]);
+        }
     }
-    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) W[i + (int64_t)In * r] = (double)acc[r];
 }
 
+__global__ void batch_w_kernel(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_items,
+                               int* __restrict__ counter, int n, const float* __restrict__ Yall,
+                               double* __restrict__ F, const int* __restrict__ pstatus)
+{
+    __shared__ float q0f[kBMaxR * kBMaxR * kBMaxR];
+    __shared__ int s_item;
+    int cached = -1;
+    for (;;) {
+        const int it = next_item(counter, &s_item);
+        if (it >= n_items) break;
+        const BItem item = items[it];
+        if (pstatus[item.p] != kStatusOk) continue;
+        const BProb& pr = probs[item.p];
+        const int R = pr.R, RR = R * R, In = pr.I[n];
+        if (cached != item.p) {
+            const double* Q0 = F + pr.q0;
+            for (int e = threadIdx.x; e < RR * R; e += blockDim.x) {
+                const int col = e / R, r = e - col * R;
+                q0f[e] = (float)Q0[col + RR * r];
+            }
+            cached = item.p;
+            __syncthreads();
+        }
+        const int Rn = (n == 0) ? 1 : (n == 1 ? R : RR);
+        const int i = item.f0 + threadIdx.x;
+        const float* Y = Yall + pr.y;
+        double* W = F + pr.w;
+        switch (R) {
+#define CPALS_BW(RV) case RV: w_row<RV>(Y, In, Rn, q0f, i, W); break;
+            CPALS_BW(1) CPALS_BW(2) CPALS_BW(3) CPALS_BW(4) CPALS_BW(5) CPALS_BW(6) CPALS_BW(7) CPALS_BW(8)
+            CPALS_BW(9) CPALS_BW(10) CPALS_BW(11) CPALS_BW(12) CPALS_BW(13) CPALS_BW(14) CPALS_BW(15) CPALS_BW(16)
+#undef CPALS_BW
+            default: break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- factorisation chain
 struct BSmem {
-    int64_t regA, regB, r0, rn, w, qst;   // offsets in doubles
+    int64_t regA, regB, r0, rn, w;   // offsets in doubles
     int64_t total;
 };
 
 __host__ __device__ inline BSmem bsmem_layout(int maxR, int maxI)
 {
     BSmem s;
-    const int64_t sa = std::max<int64_t>((int64_t)maxR * maxR * maxR, (int64_t)maxI * maxR);
+    // the staircase QR of V_n needs two compact copies (R(R+1)(2R+1)/6 each) and
+    // the 2 R^2 row indices; the factor QR needs I R
+    const int64_t stair = (int64_t)maxR * (maxR + 1) * (2 * maxR + 1) / 3 + (int64_t)maxR * maxR + 8;
+    const int64_t ir = (int64_t)maxI * maxR;
+    const int64_t sa = ir > stair ? ir : stair;
     s.regA = 0;
     s.regB = s.regA + sa;
-    s.r0 = s.regB + sa;
+    s.r0 = s.regB + ir;
     s.rn = s.r0 + (int64_t)maxR * maxR;
     s.w = s.rn + (int64_t)maxR * maxR;
-    s.qst = s.w + (int64_t)maxI * maxR;
-    s.total = s.qst + ((int64_t)maxI * maxR + 1) / 2 + 128;   // FP32 staging, tau/red
+    s.total = s.w + ir + 128;    // + tau / red
     return s;
 }
 
-__global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restrict__ order, int count, int n,
-                                  int maxR, int maxI, const float* __restrict__ Xall, double* __restrict__ F,
-                                  float* __restrict__ T1all, float* __restrict__ Yall, int* __restrict__ pstatus,
+// V = R_hi (.) R_lo of the mode `next` and its staircase QR into the
+// problem's Q0, R0 (global).  rhi / rlo may point to shared or global memory.
+__device__ void v_qr(const BProb& pr, const double* rhi, const double* rlo, double* F, double* regA, double* tau,
+                     double* red)
+{
+    const int R = pr.R, tot = stair_off(R);
+    int* rows_i = reinterpret_cast<int*>(regA + 2 * tot);
+    stair_qr_block(rhi, rlo, R, regA, regA + tot, tau, red, rows_i, rows_i + R * R, F + pr.q0, F + pr.r0);
+}
+
+// The QR of V_0 = R_2 (.) R_1 of every problem (the start of a sweep).
+__global__ void batch_vqr_kernel(const BProb* __restrict__ probs, const int* __restrict__ order, int count,
+                                 int maxR, int maxI, double* __restrict__ F, const int* __restrict__ pstatus)
+{
+    extern __shared__ double bsm[];
+    const BSmem L = bsmem_layout(maxR, maxI);
+    double* tau = bsm + L.total - 128;
+    double* red = tau + 64;
+    for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
+        const int p = order[idx];
+        if (pstatus[p] != kStatusOk) continue;
+        const BProb pr = probs[p];
+        v_qr(pr, F + pr.rf[2], F + pr.rf[1], F, bsm + L.regA, tau, red);
+    }
+}
+
+// The FP64 end of mode n's update for every problem: substitution,
+// normalisation, factor QR, then the QR of the next mode's V (n < 2) or the
+// efficient fit (n = 2).
+__global__ void batch_tail_kernel(const BProb* __restrict__ probs, const int* __restrict__ order, int count, int n,
+                                  int maxR, int maxI, double* __restrict__ F, int* __restrict__ pstatus,
                                   double* __restrict__ fit_last)
 {
     extern __shared__ double bsm[];
@@ -205,7 +409,6 @@ __global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restri
     double* R0s = bsm + L.r0;
     double* Rns = bsm + L.rn;
     double* Ws = bsm + L.w;
-    float* qst = reinterpret_cast<float*>(bsm + L.qst);
     double* tau = bsm + L.total - 128;
     double* red = tau + 64;
     __shared__ int singular;
@@ -214,24 +417,12 @@ __global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restri
 
     for (int idx = blockIdx.x; idx < count; idx += gridDim.x) {
         const int p = order[idx];
-        BProb pr = probs[p];
         if (pstatus[p] != kStatusOk) continue;       // a failed problem stays as it was
-        const int R = pr.R, In = pr.I[n];
-        int mo[2], cnt = 0;
-        for (int m = 0; m < 3; ++m)
-            if (m != n) mo[cnt++] = m;
-        const int lo = mo[0], hi = mo[1];            // V_n = R_hi (.) R_lo
-        // ---- 1. V_n and its QR (FP64, shared memory)
-        const double* Rhi = F + pr.rf[hi];
-        const double* Rlo = F + pr.rf[lo];
-        const int RR = R * R;
-        for (int e = tid; e < RR * R; e += blockDim.x) {
-            const int c = e / RR, row = e - c * RR;
-            const int i = row / R, j = row - i * R;
-            regA[e] = Rhi[i + R * c] * Rlo[j + R * c];
-        }
+        const BProb pr = probs[p];
+        const int R = pr.R, In = pr.I[n], RR = R * R;
+        for (int e = tid; e < RR; e += blockDim.x) R0s[e] = F[pr.r0 + e];
+        for (int e = tid; e < In * R; e += blockDim.x) Ws[e] = F[pr.w + e];
         __syncthreads();
-        cta_householder(regA, RR, R, regB, R0s, tau, red);   // Q0 in regB (R^2 x R), R0 in R0s
         if (tid == 0) {
             double dmax = 0.0;
             for (int k = 0; k < R; ++k) dmax = fmax(dmax, fabs(R0s[k + R * k]));
@@ -243,68 +434,27 @@ __global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restri
         }
         __syncthreads();
         if (singular) continue;
-        // ---- 2. Multi-TTM: larger contracted dim first (ties: higher mode)
-        int c1 = (pr.I[hi] >= pr.I[lo]) ? hi : lo;
-        int c2 = (c1 == hi) ? lo : hi;
-        int64_t d[3] = {pr.I[0], pr.I[1], pr.I[2]};
-        {
-            stage_q(F + pr.q[c1], pr.I[c1], R, qst);
-            int64_t Lw = 1, Tw = 1;
-            for (int m = 0; m < c1; ++m) Lw *= d[m];
-            for (int m = c1 + 1; m < 3; ++m) Tw *= d[m];
-            cta_ttm_f32(Xall + pr.x, Lw, (int)d[c1], Tw, qst, R, T1all + pr.t1);
-            d[c1] = R;
-            __syncthreads();
-        }
-        {
-            stage_q(F + pr.q[c2], pr.I[c2], R, qst);
-            int64_t Lw = 1, Tw = 1;
-            for (int m = 0; m < c2; ++m) Lw *= d[m];
-            for (int m = c2 + 1; m < 3; ++m) Tw *= d[m];
-            cta_ttm_f32(T1all + pr.t1, Lw, (int)d[c2], Tw, qst, R, Yall + pr.y);
-            d[c2] = R;
-            __syncthreads();
-        }
-        // ---- 3. W = Y_(n) Q0 (FP64); Y element (col, i) at a + Rn*(i + In*c), col = a + Rn*c
-        // one thread per row i with all R accumulators; Q0 rows are shared-memory broadcasts
-        const float* Y = Yall + pr.y;
-        const int Rn = (n == 0) ? 1 : (n == 1 ? R : RR);
-        for (int i = tid; i < In; i += blockDim.x) {
-            double acc[kBMaxR];
-#pragma unroll
-            for (int r = 0; r < kBMaxR; ++r) acc[r] = 0.0;
-            for (int c0 = 0; c0 < RR; c0 += 8) {
-                float y[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int col = c0 + u;
-                    const int a = col % Rn, c = col / Rn;
-                    y[u] = (col < RR) ? __ldg(Y + a + (int64_t)Rn * (i + (int64_t)In * c)) : 0.0f;
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int col = c0 + u;
-                    if (col < RR) {
-#pragma unroll
-                        for (int r = 0; r < kBMaxR; ++r)
-                            if (r < R) acc[r] = fma((double)y[u], regB[col + RR * r], acc[r]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < kBMaxR; ++r)
-                if (r < R) Ws[i + In * r] = acc[r];
-        }
+        // Ahat R0^T = W by substitution, one row per thread (Ahat into regA);
+        // loops unrolled over the largest rank so that x stays in registers
+        if (tid < R) red[16 + tid] = 1.0 / R0s[tid + R * tid];
         __syncthreads();
-        // ---- 4. Ahat R0^T = W by substitution, one row per thread (Ahat into regA)
         for (int i = tid; i < In; i += blockDim.x) {
             double x[kBMaxR];
-            for (int k = R - 1; k >= 0; --k) {
-                double s = Ws[i + In * k];
-                for (int j = k + 1; j < R; ++j) s = fma(-R0s[k + R * j], x[j], s);
-                x[k] = s / R0s[k + R * k];
+#pragma unroll
+            for (int k = kBMaxR - 1; k >= 0; --k) {
+                if (k < R) {
+                    double s = Ws[i + In * k];
+#pragma unroll
+                    for (int j = k + 1; j < kBMaxR; ++j)
+                        if (j < R) s = fma(-R0s[k + R * j], x[j], s);
+                    x[k] = s * red[16 + k];
+                } else {
+                    x[k] = 0.0;
+                }
             }
-            for (int k = 0; k < R; ++k) regA[i + In * k] = x[k];
+#pragma unroll
+            for (int k = 0; k < kBMaxR; ++k)
+                if (k < R) regA[i + In * k] = x[k];
         }
         __syncthreads();
         // efficient-fit inner product <W, Ahat R0^T> (last mode only)
@@ -326,7 +476,7 @@ __global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restri
             }
             __syncthreads();
         }
-        // ---- 5. normalise columns (2-norm): A_n and lambda
+        // normalise columns (2-norm): A_n and lambda
         double* lam = F + pr.lam;
         for (int r = warp; r < R; r += nwarps) {
             double s = 0.0;
@@ -345,14 +495,14 @@ __global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restri
         }
         if (tid < R) lam[tid] = red[32 + tid];
         __syncthreads();
-        // ---- 6. A_n = Q_n R_n (FP64, shared memory)
+        // A_n = Q_n R_n (FP64, shared memory)
         cta_householder(regA, In, R, regB, Rns, tau, red);
         double* Qn = F + pr.q[n];
         double* Rn_g = F + pr.rf[n];
         for (int e = tid; e < In * R; e += blockDim.x) Qn[e] = regB[e];
         for (int e = tid; e < RR; e += blockDim.x) Rn_g[e] = Rns[e];
-        // ---- 7. efficient fit after the last mode (Sec. 3.3.1)
         if (n == 2) {
+            // efficient fit after the last mode (Sec. 3.3.1)
             double s = 0.0;
             for (int e = tid; e < RR; e += blockDim.x) {
                 const int b = e / R, a = e - b * R;
@@ -374,6 +524,11 @@ __global__ void batch_mode_kernel(BProb* __restrict__ probs, const int* __restri
                 if (res2 < 0.0) res2 = 0.0;
                 fit_last[p] = 1.0 - sqrt(res2) / sqrt(pr.normX2);
             }
+        } else {
+            // the next mode's V = R_hi (.) R_lo: mode 1 takes R_2 (.) R_0, mode 2 R_1 (.) R_0
+            __syncthreads();
+            const double* rhi = (n == 0) ? F + pr.rf[2] : F + pr.rf[1];
+            v_qr(pr, (n == 1) ? Rns : rhi, (n == 0) ? Rns : F + pr.rf[0], F, regA, tau, red);
         }
         __syncthreads();
     }
@@ -428,6 +583,10 @@ __global__ void batch_norm_kernel(BProb* __restrict__ probs, int count, const fl
 }  // namespace
 
 // ---------------------------------------------------------------- host side
+constexpr int kTiles[2] = {128, 256};
+constexpr int kTtmWhich = 5;       // grouped TTMs: two passes, three last TTMs
+constexpr int kSweepKernels = 12;  // V_0 QR, five TTMs, three W, three factorisation kernels
+
 struct Batch {
     int count = 0, maxR = 0, maxI = 0;
     std::vector<BProb> probs;
@@ -436,14 +595,22 @@ struct Batch {
     int* d_order = nullptr;
     float* Xall = nullptr;
     double* F = nullptr;
-    float* T1all = nullptr;
+    float* P1all = nullptr;
+    float* T2all = nullptr;
     float* Yall = nullptr;
     int* d_pstatus = nullptr;
     double* d_fit = nullptr;
-    int64_t x_elems = 0, f_elems = 0, t1_elems = 0, y_elems = 0;
+    // work items of the grouped launches per candidate row tile: the five TTMs, then W for modes 0..2
+    BItem* d_items[2][kTtmWhich + 3] = {};
+    int n_items[2][kTtmWhich + 3] = {};
+    int* d_counter = nullptr;            // one queue counter per grouped launch of a sweep
+    int64_t x_elems = 0, f_elems = 0, p1_elems = 0, t2_elems = 0, y_elems = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;         // the QR of V_0 beside pass 1
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
-    int grid = 0, threads = 0;           // autotuned launch shape (0 = not tuned yet)
+    // tuned shape: the grouped launches' tile (threads) and grid; the factorisation kernels' threads and grid
+    int tile = 0, group_grid = 0, grid = 0, threads = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t launches = 0;
     size_t smem = 0;
@@ -457,7 +624,7 @@ cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ran
 {
     b->count = count;
     b->probs.resize(count);
-    int64_t xo = 0, fo = 0, t1o = 0, yo = 0;
+    int64_t xo = 0, fo = 0, p1o = 0, t2o = 0, yo = 0;
     std::vector<double> work(count);
     for (int p = 0; p < count; ++p) {
         BProb& pr = b->probs[p];
@@ -466,50 +633,89 @@ cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ran
         b->maxR = std::max(b->maxR, pr.R);
         for (int m = 0; m < 3; ++m) b->maxI = std::max(b->maxI, pr.I[m]);
         const int64_t P = (int64_t)pr.I[0] * pr.I[1] * pr.I[2];
+        const int64_t R = pr.R;
         pr.x = xo;
         xo += align4(P);
-        for (int m = 0; m < 3; ++m) { pr.a[m] = fo; fo += (int64_t)pr.I[m] * pr.R; }
-        for (int m = 0; m < 3; ++m) { pr.q[m] = fo; fo += (int64_t)pr.I[m] * pr.R; }
-        for (int m = 0; m < 3; ++m) { pr.rf[m] = fo; fo += (int64_t)pr.R * pr.R; }
+        for (int m = 0; m < 3; ++m) { pr.a[m] = fo; fo += pr.I[m] * R; }
+        for (int m = 0; m < 3; ++m) { pr.q[m] = fo; fo += pr.I[m] * R; }
+        for (int m = 0; m < 3; ++m) { pr.rf[m] = fo; fo += R * R; }
         pr.lam = fo;
-        fo += pr.R;
-        int64_t t1max = 0, ymax = 0;
-        for (int n = 0; n < 3; ++n) {
-            int o[2], c = 0;
-            for (int m = 0; m < 3; ++m)
-                if (m != n) o[c++] = m;
-            const int c1 = (pr.I[o[1]] >= pr.I[o[0]]) ? o[1] : o[0];
-            t1max = std::max(t1max, P / pr.I[c1] * pr.R);
-            ymax = std::max(ymax, (int64_t)pr.I[n] * pr.R * pr.R);
-        }
-        pr.t1 = t1o;
-        t1o += align4(t1max);
+        fo += R;
+        pr.q0 = fo;
+        fo += R * R * R;
+        pr.r0 = fo;
+        fo += R * R;
+        pr.w = fo;
+        fo += (int64_t)std::max({pr.I[0], pr.I[1], pr.I[2]}) * R;
+        pr.p1 = p1o;
+        p1o += align4((int64_t)pr.I[0] * pr.I[1] * R);
+        pr.t2 = t2o;
+        t2o += align4((int64_t)pr.I[0] * R * pr.I[2]);
+        int64_t ymax = 0;
+        for (int n = 0; n < 3; ++n) ymax = std::max(ymax, (int64_t)pr.I[n] * R * R);
         pr.y = yo;
         yo += align4(ymax);
         pr.normX2 = 0.0;
-        work[p] = (double)P * pr.R;
+        // the factorisation chain: Householder steps over I_n x R and the staircase of R^2 x R
+        work[p] = (double)R * R * (pr.I[0] + pr.I[1] + pr.I[2]) + 3.0 * R * R * R * R;
     }
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
     std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return work[a] > work[c]; });
-    b->x_elems = xo; b->f_elems = fo; b->t1_elems = t1o; b->y_elems = yo;
+    b->x_elems = xo; b->f_elems = fo; b->p1_elems = p1o; b->t2_elems = t2o; b->y_elems = yo;
     CPALS_CUDA_TRY(cudaMalloc(&b->d_probs, sizeof(BProb) * count));
     CPALS_CUDA_TRY(cudaMalloc(&b->d_order, sizeof(int) * count));
     CPALS_CUDA_TRY(cudaMalloc(&b->Xall, sizeof(float) * std::max<int64_t>(xo, 1)));
     CPALS_CUDA_TRY(cudaMalloc(&b->F, sizeof(double) * std::max<int64_t>(fo, 1)));
-    CPALS_CUDA_TRY(cudaMalloc(&b->T1all, sizeof(float) * std::max<int64_t>(t1o, 1)));
+    CPALS_CUDA_TRY(cudaMalloc(&b->P1all, sizeof(float) * std::max<int64_t>(p1o, 1)));
+    CPALS_CUDA_TRY(cudaMalloc(&b->T2all, sizeof(float) * std::max<int64_t>(t2o, 1)));
     CPALS_CUDA_TRY(cudaMalloc(&b->Yall, sizeof(float) * std::max<int64_t>(yo, 1)));
     CPALS_CUDA_TRY(cudaMalloc(&b->d_pstatus, sizeof(int) * count));
     CPALS_CUDA_TRY(cudaMalloc(&b->d_fit, sizeof(double) * count));
+    CPALS_CUDA_TRY(cudaMalloc(&b->d_counter, sizeof(int) * (kTtmWhich + 3)));
+    CPALS_CUDA_TRY(cudaMemset(b->F, 0, sizeof(double) * std::max<int64_t>(fo, 1)));
     CPALS_CUDA_TRY(cudaMemset(b->d_pstatus, 0, sizeof(int) * count));
     CPALS_CUDA_TRY(cudaMemset(b->d_fit, 0, sizeof(double) * count));
     CPALS_CUDA_TRY(cudaMemcpy(b->d_probs, b->probs.data(), sizeof(BProb) * count, cudaMemcpyHostToDevice));
     CPALS_CUDA_TRY(cudaMemcpy(b->d_order, b->order.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+    // work items: the tiles of each problem's rows, problems with the most
+    // rows first, for each candidate tile
+    for (int ti = 0; ti < 2; ++ti)
+        for (int g = 0; g < kTtmWhich + 3; ++g) {
+            auto rows_of = [&](int p) -> int64_t {
+                const BProb& pr = b->probs[p];
+                if (g < kTtmWhich) {
+                    const BView v = view_of(pr, g);
+                    return v.L * v.T;
+                }
+                return pr.I[g - kTtmWhich];
+            };
+            std::vector<int> by(count);
+            std::iota(by.begin(), by.end(), 0);
+            std::stable_sort(by.begin(), by.end(), [&](int a, int c) {
+                return rows_of(a) * b->probs[a].R > rows_of(c) * b->probs[c].R;
+            });
+            std::vector<BItem> items;
+            for (int p : by) {
+                const int64_t rows = rows_of(p);
+                for (int64_t f0 = 0; f0 < rows; f0 += kTiles[ti]) items.push_back(BItem{p, (int)f0});
+            }
+            b->n_items[ti][g] = (int)items.size();
+            CPALS_CUDA_TRY(cudaMalloc(&b->d_items[ti][g], sizeof(BItem) * std::max<size_t>(items.size(), 1)));
+            CPALS_CUDA_TRY(cudaMemcpy(b->d_items[ti][g], items.data(), sizeof(BItem) * items.size(),
+                                      cudaMemcpyHostToDevice));
+        }
     int dev = 0;
     CPALS_CUDA_TRY(cudaGetDevice(&dev));
     CPALS_CUDA_TRY(cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    int lo = 0, hi = 0;
+    CPALS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    CPALS_CUDA_TRY(cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, hi));
+    CPALS_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    CPALS_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
     b->smem = sizeof(double) * (size_t)bsmem_layout(b->maxR, b->maxI).total;
-    CPALS_CUDA_TRY(cudaFuncSetAttribute(batch_mode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    CPALS_CUDA_TRY(cudaFuncSetAttribute(batch_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+    CPALS_CUDA_TRY(cudaFuncSetAttribute(batch_vqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
     CPALS_CUDA_TRY(cudaFuncSetAttribute(batch_factor_qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)b->smem));
     return cudaSuccess;
@@ -518,8 +724,14 @@ cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ran
 void batch_free(Batch* b)
 {
     auto f = [](void* p) { if (p) cudaFree(p); };
-    f(b->d_probs); f(b->d_order); f(b->Xall); f(b->F); f(b->T1all); f(b->Yall); f(b->d_pstatus); f(b->d_fit);
+    f(b->d_probs); f(b->d_order); f(b->Xall); f(b->F); f(b->P1all); f(b->T2all); f(b->Yall); f(b->d_pstatus);
+    f(b->d_fit); f(b->d_counter);
+    for (int ti = 0; ti < 2; ++ti)
+        for (int g = 0; g < kTtmWhich + 3; ++g) f(b->d_items[ti][g]);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
 }
 
 cudaError_t batch_norms(Batch* b)
@@ -536,20 +748,61 @@ cudaError_t batch_factor_qr(Batch* b)
     return cudaGetLastError();
 }
 
-static cudaError_t batch_sweep(Batch* b, int grid, int threads)
+static cudaError_t grouped_ttm(Batch* b, int ti, int which, int grid)
 {
+    CPALS_CUDA_TRY(cudaMemsetAsync(b->d_counter + which, 0, sizeof(int), b->stream));
+    batch_ttm_kernel<<<grid, kTiles[ti], 0, b->stream>>>(b->d_probs, b->d_items[ti][which], b->n_items[ti][which],
+                                                         b->d_counter + which, which, b->Xall, b->P1all, b->T2all,
+                                                         b->Yall, b->F, b->d_pstatus);
+    b->launches++;
+    return cudaGetLastError();
+}
+
+static cudaError_t grouped_w(Batch* b, int ti, int n, int grid)
+{
+    const int g = kTtmWhich + n;
+    CPALS_CUDA_TRY(cudaMemsetAsync(b->d_counter + g, 0, sizeof(int), b->stream));
+    batch_w_kernel<<<grid, kTiles[ti], 0, b->stream>>>(b->d_probs, b->d_items[ti][g], b->n_items[ti][g],
+                                                       b->d_counter + g, n, b->Yall, b->F, b->d_pstatus);
+    b->launches++;
+    return cudaGetLastError();
+}
+
+static cudaError_t chain(Batch* b, int n, int grid, int threads)
+{
+    batch_tail_kernel<<<grid, threads, b->smem, b->stream>>>(b->d_probs, b->d_order, b->count, n, b->maxR, b->maxI,
+                                                             b->F, b->d_pstatus, b->d_fit);
+    b->launches++;
+    return cudaGetLastError();
+}
+
+// One sweep along the dimension tree.  The QR of V_0 runs on the side stream
+// beside pass 1 (two branches of the captured graph).
+static cudaError_t batch_sweep(Batch* b, int ti, int group_grid, int grid, int threads)
+{
+    CPALS_CUDA_TRY(cudaEventRecord(b->ev_fork, b->stream));
+    CPALS_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+    batch_vqr_kernel<<<grid, threads, b->smem, b->side>>>(b->d_probs, b->d_order, b->count, b->maxR, b->maxI, b->F,
+                                                          b->d_pstatus);
+    b->launches++;
+    CPALS_CUDA_TRY(cudaGetLastError());
+    CPALS_CUDA_TRY(cudaEventRecord(b->ev_join, b->side));
+    CPALS_CUDA_TRY(grouped_ttm(b, ti, 0, group_grid));           // pass 1
+    CPALS_CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
     for (int n = 0; n < 3; ++n) {
-        batch_mode_kernel<<<grid, threads, b->smem, b->stream>>>(b->d_probs, b->d_order, b->count, n, b->maxR,
-                                                                 b->maxI, b->Xall, b->F, b->T1all, b->Yall,
-                                                                 b->d_pstatus, b->d_fit);
-        b->launches++;
-        CPALS_CUDA_TRY(cudaGetLastError());
+        if (n == 2) CPALS_CUDA_TRY(grouped_ttm(b, ti, 1, group_grid));   // pass 2
+        CPALS_CUDA_TRY(grouped_ttm(b, ti, 2 + n, group_grid));            // the last TTM of mode n
+        CPALS_CUDA_TRY(grouped_w(b, ti, n, group_grid));
+        CPALS_CUDA_TRY(chain(b, n, grid, threads));
     }
     return cudaSuccess;
 }
 
-// Pick the launch shape by timing one sweep per candidate on a copy of the
-// factors (restored afterwards), then capture the sweep as a CUDA graph.
+// Pick the launch shapes by timing one sweep per candidate on a copy of the
+// factors (restored afterwards): the grouped launches' row tile (128 or 256
+// rows per work item, as many resident CTAs as fit), and the factorisation
+// kernels' CTA size (128 or 256) and CTAs per SM.  Then capture the sweep as
+// a CUDA graph.
 cudaError_t batch_prepare(Batch* b)
 {
     if (b->graph) return cudaSuccess;
@@ -560,25 +813,40 @@ cudaError_t batch_prepare(Batch* b)
     CPALS_CUDA_TRY(cudaEventCreate(&e0));
     CPALS_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    const int threads_c[2] = {128, 256};
+    int ggrid[2] = {0, 0};
     for (int ti = 0; ti < 2; ++ti) {
-        int occ = 0;
-        CPALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_mode_kernel, threads_c[ti], b->smem));
-        if (occ < 1) continue;
-        for (int per = 1; per <= occ; ++per) {
-            const int grid = std::min(b->count, b->num_sms * per);
-            CPALS_CUDA_TRY(cudaMemcpyAsync(b->F, saved, sizeof(double) * b->f_elems, cudaMemcpyDeviceToDevice,
-                                           b->stream));
-            CPALS_CUDA_TRY(cudaEventRecord(e0, b->stream));
-            CPALS_CUDA_TRY(batch_sweep(b, grid, threads_c[ti]));
-            CPALS_CUDA_TRY(cudaEventRecord(e1, b->stream));
-            CPALS_CUDA_TRY(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CPALS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; b->grid = grid; b->threads = threads_c[ti]; }
-            if (grid == b->count) break;
-        }
+        int o1 = 0, o2 = 0;
+        CPALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_ttm_kernel, kTiles[ti], 0));
+        CPALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, batch_w_kernel, kTiles[ti], 0));
+        ggrid[ti] = std::max(1, std::min(o1, o2)) * b->num_sms;
     }
+    const int threads_c[2] = {128, 256};
+    for (int ti = 0; ti < 2; ++ti)
+        for (int mi = 0; mi < 2; ++mi) {
+            int occ = 0;
+            CPALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_tail_kernel, threads_c[mi],
+                                                                         b->smem));
+            if (occ < 1) continue;
+            for (int per = 1; per <= occ; ++per) {
+                const int grid = std::min(b->count, b->num_sms * per);
+                CPALS_CUDA_TRY(cudaMemcpyAsync(b->F, saved, sizeof(double) * b->f_elems, cudaMemcpyDeviceToDevice,
+                                               b->stream));
+                CPALS_CUDA_TRY(cudaEventRecord(e0, b->stream));
+                CPALS_CUDA_TRY(batch_sweep(b, ti, ggrid[ti], grid, threads_c[mi]));
+                CPALS_CUDA_TRY(cudaEventRecord(e1, b->stream));
+                CPALS_CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CPALS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    b->tile = kTiles[ti];
+                    b->group_grid = ggrid[ti];
+                    b->grid = grid;
+                    b->threads = threads_c[mi];
+                }
+                if (grid == b->count) break;
+            }
+        }
     CPALS_CUDA_TRY(cudaMemcpyAsync(b->F, saved, sizeof(double) * b->f_elems, cudaMemcpyDeviceToDevice, b->stream));
     CPALS_CUDA_TRY(cudaMemsetAsync(b->d_pstatus, 0, sizeof(int) * b->count, b->stream));
     CPALS_CUDA_TRY(cudaStreamSynchronize(b->stream));
@@ -600,7 +868,7 @@ cudaError_t batch_prepare(Batch* b)
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     cudaError_t e2 = cudaSuccess;
     if (e == cudaSuccess) {
-        e2 = batch_sweep(b, b->grid, b->threads);
+        e2 = batch_sweep(b, b->tile == kTiles[0] ? 0 : 1, b->group_grid, b->grid, b->threads);
         e = cudaStreamEndCapture(cap, &g);
     }
     b->stream = saved_stream;
@@ -710,7 +978,7 @@ cudaError_t batch_run(Batch* b, int iters)
     CPALS_CUDA_TRY(batch_prepare(b));
     for (int it = 0; it < iters; ++it) {
         CPALS_CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
-        b->launches += 3;
+        b->launches += kSweepKernels;
     }
     return cudaSuccess;
 }

@@ -1,8 +1,9 @@
 // dev_common.cuh -- device helpers shared by the FP64 linear-algebra
-// translation units (linalg.cu, tail.cu).
+// translation units (linalg.cu, tail.cu, batch.cu).
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace cpals {
 namespace {
@@ -40,6 +41,127 @@ __device__ __forceinline__ void warp_subst(double& w0, double& w1, const double*
         if (R > 32 && e1 < R && (back ? e1 < k : e1 > k))
             w1 = fma(-(trans ? A[k + R * e1] : A[e1 + R * k]), xk, w1);
     }
+}
+
+// ---------------------------------------------------------------- staircase QR of F (.) G
+// Thin QR of the Khatri-Rao product F (.) G of two upper-triangular n x n
+// factors (one step of the QR of V_n, Sec. 3.1 and Eq. kr-id), without
+// forming the n^2 x n product densely.  Row (i, j) (index i n + j, the right
+// factor's row fastest) is zero left of column max(i, j) (Sec. 3.3.3: the
+// columns of a Khatri-Rao product of triangular factors are sparse).  Ordered
+// by that level c = max(i, j) -- level c holds the 2c + 1 rows (c, 0..c),
+// (0..c-1, c) at positions c^2 .. (c+1)^2 - 1 -- the matrix is a staircase:
+// the Householder reflector of column j spans only positions j .. (j+1)^2 - 1,
+// and neither the reflectors nor the explicit Q fill in outside positions
+// < (k+1)^2 of column k.  Column k is stored compactly ((k+1)^2 values), and
+// the QR costs about n^4 / 3 flops instead of 4 n^4.  Householder reflectors
+// in LAPACK's dlarfg form with diag(R) >= 0 (row of R and column of Q
+// flipped together); the thin QR with a positive diagonal is unique, so this
+// is the factorisation a dense Householder QR gives, up to rounding.
+__device__ __forceinline__ int stair_pos(int i, int j)
+{
+    const int c = i > j ? i : j;
+    return c * c + (i == c ? j : c + 1 + i);
+}
+
+__device__ __forceinline__ int stair_off(int k) { return k * (k + 1) * (2 * k + 1) / 6; }
+
+// Block-wide (any block size that is a multiple of 32).  Work space: W and Qs
+// of stair_off(n) doubles each, tau (n), red (32), rowi and rowj (n^2 ints).
+// Writes the explicit Q (n^2 x n, column-major, rows in the Khatri-Rao order
+// i n + j) to Qout and R (n x n) to Rout; both may be shared or global memory.
+__device__ void stair_qr_block(const double* __restrict__ F, const double* __restrict__ G, int n, double* W,
+                               double* Qs, double* tau, double* red, int* rowi, int* rowj, double* Qout,
+                               double* Rout)
+{
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+    for (int p = tid; p < n * n; p += nthr) {
+        const int c = (int)sqrtf((float)p + 0.5f);   // level: c^2 <= p < (c+1)^2
+        const int cc = (c * c > p) ? c - 1 : ((c + 1) * (c + 1) <= p ? c + 1 : c);
+        const int q = p - cc * cc;
+        rowi[p] = (q <= cc) ? cc : q - cc - 1;
+        rowj[p] = (q <= cc) ? q : cc;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k)
+        for (int p = tid; p < (k + 1) * (k + 1); p += nthr)
+            W[stair_off(k) + p] = F[rowi[p] + n * k] * G[rowj[p] + n * k];
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        const int end = (j + 1) * (j + 1);
+        double* wj = W + stair_off(j);
+        if (warp == 0) {
+            double s = 0.0;
+            for (int p = j + 1 + lane; p < end; p += 32) s = fma(wj[p], wj[p], s);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double alpha = wj[j];
+                double t = 0.0, scale = 0.0, beta = alpha;
+                if (s > 0.0) {
+                    const double nrm = sqrt(fma(alpha, alpha, s));
+                    beta = (alpha >= 0.0) ? -nrm : nrm;
+                    const double d = beta - alpha;
+                    const double r = 1.0 / (beta * d);
+                    t = d * d * r;
+                    scale = -beta * r;
+                }
+                tau[j] = t;
+                red[0] = scale;
+                wj[j] = beta;
+            }
+        }
+        __syncthreads();
+        const double tj = tau[j];
+        if (tj != 0.0) {
+            const double scale = red[0];
+            for (int p = j + 1 + tid; p < end; p += nthr) wj[p] *= scale;
+        }
+        __syncthreads();
+        if (tj != 0.0) {
+            for (int k = j + 1 + warp; k < n; k += nwarps) {
+                double* wk = W + stair_off(k);
+                double s = 0.0;
+                for (int p = j + lane; p < end; p += 32) s = fma(p == j ? 1.0 : wj[p], wk[p], s);
+                s = warp_sum(s) * tj;
+                for (int p = j + lane; p < end; p += 32) wk[p] = fma(-s, p == j ? 1.0 : wj[p], wk[p]);
+            }
+        }
+        __syncthreads();
+    }
+    // explicit Q = H_0 ... H_{n-1} [I; 0] (sorted rows), backward accumulation
+    for (int k = 0; k < n; ++k)
+        for (int p = tid; p < (k + 1) * (k + 1); p += nthr) Qs[stair_off(k) + p] = (p == k) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int j = n - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        if (tj != 0.0) {
+            const int end = (j + 1) * (j + 1);
+            const double* wj = W + stair_off(j);
+            for (int k = j + warp; k < n; k += nwarps) {
+                double* qk = Qs + stair_off(k);
+                double s = 0.0;
+                for (int p = j + lane; p < end; p += 32) s = fma(p == j ? 1.0 : wj[p], qk[p], s);
+                s = warp_sum(s) * tj;
+                for (int p = j + lane; p < end; p += 32) qk[p] = fma(-s, p == j ? 1.0 : wj[p], qk[p]);
+            }
+        }
+        __syncthreads();
+    }
+    // sign convention diag(R) >= 0; rows back to the Khatri-Rao order i n + j
+    for (int e = tid; e < n * n * n; e += nthr) {
+        const int k = e / (n * n), rho = e - k * n * n;
+        const int i = rho / n, jj = rho - i * n;
+        const int p = stair_pos(i, jj);
+        const double sgn = (W[stair_off(k) + k] < 0.0) ? -1.0 : 1.0;
+        Qout[rho + (int64_t)n * n * k] = (p < (k + 1) * (k + 1)) ? sgn * Qs[stair_off(k) + p] : 0.0;
+    }
+    for (int e = tid; e < n * n; e += nthr) {
+        const int k = e / n, i = e - k * n;       // R(i, k)
+        double v = 0.0;
+        if (i <= k) v = ((W[stair_off(i) + i] < 0.0) ? -1.0 : 1.0) * W[stair_off(k) + i];
+        Rout[i + n * k] = v;
+    }
+    __syncthreads();
 }
 
 }  // namespace

@@ -492,27 +492,7 @@ constexpr size_t kQrSmemMaxBytes = 200 * 1024;   // one leaf CTA's shared memory
 inline bool qr_leaf_fits(int64_t mb, int n) { return qr_smem_bytes(mb, n) <= kQrSmemMaxBytes; }
 
 // ---------------------------------------------------------------- staircase QR of F (.) G
-// Thin QR of the Khatri-Rao product F (.) G of two upper-triangular n x n
-// factors (one step of the QR of V_n, Sec. 3.1 and Eq. kr-id), without
-// forming the n^2 x n product densely.  Row (i, j) (index i n + j, the right
-// factor's row fastest) is zero left of column max(i, j) (Sec. 3.3.3: the
-// columns of a Khatri-Rao product of triangular factors are sparse).  Ordered
-// by that level c = max(i, j) -- level c holds the 2c + 1 rows (c, 0..c),
-// (0..c-1, c) at positions c^2 .. (c+1)^2 - 1 -- the matrix is a staircase:
-// the Householder reflector of column j spans only positions j .. (j+1)^2 - 1,
-// and neither the reflectors nor the explicit Q fill in outside positions
-// < (k+1)^2 of column k.  Column k is stored compactly ((k+1)^2 values), and
-// the QR costs about n^4 / 3 flops instead of 4 n^4.  Same reflector form and
-// sign convention as hh_qr_blocks_kernel; the thin QR with diag(R) >= 0 is
-// unique, so this is the same factorisation up to rounding.  n <= 32.
-__device__ __forceinline__ int stair_pos(int i, int j)
-{
-    const int c = i > j ? i : j;
-    return c * c + (i == c ? j : c + 1 + i);
-}
-
-__device__ __forceinline__ int stair_off(int k) { return k * (k + 1) * (2 * k + 1) / 6; }
-
+// (stair_qr_block in dev_common.cuh) as a kernel of its own: one CTA.
 constexpr int kStairMaxN = 32;
 
 __global__ void __launch_bounds__(kQrThreads) krp_stair_qr_kernel(
@@ -522,98 +502,12 @@ __global__ void __launch_bounds__(kQrThreads) krp_stair_qr_kernel(
     if (*status != kStatusOk) return;
     extern __shared__ double sm[];
     const int tot = stair_off(n);
-    double* W = sm;                 // compact columns: column k at stair_off(k), (k+1)^2 values
-    double* Qs = W + tot;           // explicit Q, same compact layout (sorted rows)
-    double* tau = Qs + tot;         // n
-    double* red = tau + n;          // 32
+    double* W = sm;
+    double* Qs = W + tot;
+    double* tau = Qs + tot;
+    double* red = tau + n;
     __shared__ int rowi[kStairMaxN * kStairMaxN], rowj[kStairMaxN * kStairMaxN];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kQrThreads / 32;
-    for (int p = tid; p < n * n; p += kQrThreads) {
-        const int c = (int)sqrtf((float)p + 0.5f);   // level: c^2 <= p < (c+1)^2
-        const int cc = (c * c > p) ? c - 1 : ((c + 1) * (c + 1) <= p ? c + 1 : c);
-        const int q = p - cc * cc;
-        rowi[p] = (q <= cc) ? cc : q - cc - 1;
-        rowj[p] = (q <= cc) ? q : cc;
-    }
-    __syncthreads();
-    for (int k = 0; k < n; ++k)
-        for (int p = tid; p < (k + 1) * (k + 1); p += kQrThreads)
-            W[stair_off(k) + p] = F[rowi[p] + n * k] * G[rowj[p] + n * k];
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        const int end = (j + 1) * (j + 1);
-        double* wj = W + stair_off(j);
-        if (warp == 0) {
-            double s = 0.0;
-            for (int p = j + 1 + lane; p < end; p += 32) s = fma(wj[p], wj[p], s);
-            s = warp_sum(s);
-            if (lane == 0) {
-                const double alpha = wj[j];
-                double t = 0.0, scale = 0.0, beta = alpha;
-                if (s > 0.0) {
-                    const double nrm = sqrt(fma(alpha, alpha, s));
-                    beta = (alpha >= 0.0) ? -nrm : nrm;
-                    const double d = beta - alpha;
-                    const double r = 1.0 / (beta * d);
-                    t = d * d * r;
-                    scale = -beta * r;
-                }
-                tau[j] = t;
-                red[0] = scale;
-                wj[j] = beta;
-            }
-        }
-        __syncthreads();
-        const double tj = tau[j];
-        if (tj != 0.0) {
-            const double scale = red[0];
-            for (int p = j + 1 + tid; p < end; p += kQrThreads) wj[p] *= scale;
-        }
-        __syncthreads();
-        if (tj != 0.0) {
-            for (int k = j + 1 + warp; k < n; k += nwarps) {
-                double* wk = W + stair_off(k);
-                double s = 0.0;
-                for (int p = j + lane; p < end; p += 32) s = fma(p == j ? 1.0 : wj[p], wk[p], s);
-                s = warp_sum(s) * tj;
-                for (int p = j + lane; p < end; p += 32) wk[p] = fma(-s, p == j ? 1.0 : wj[p], wk[p]);
-            }
-        }
-        __syncthreads();
-    }
-    // explicit Q = H_0 ... H_{n-1} [I; 0] (sorted rows), backward accumulation
-    for (int k = 0; k < n; ++k)
-        for (int p = tid; p < (k + 1) * (k + 1); p += kQrThreads) Qs[stair_off(k) + p] = (p == k) ? 1.0 : 0.0;
-    __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-        const double tj = tau[j];
-        if (tj != 0.0) {
-            const int end = (j + 1) * (j + 1);
-            const double* wj = W + stair_off(j);
-            for (int k = j + warp; k < n; k += nwarps) {
-                double* qk = Qs + stair_off(k);
-                double s = 0.0;
-                for (int p = j + lane; p < end; p += 32) s = fma(p == j ? 1.0 : wj[p], qk[p], s);
-                s = warp_sum(s) * tj;
-                for (int p = j + lane; p < end; p += 32) qk[p] = fma(-s, p == j ? 1.0 : wj[p], qk[p]);
-            }
-        }
-        __syncthreads();
-    }
-    // sign convention diag(R) >= 0; rows back to the Khatri-Rao order i n + j
-    for (int e = tid; e < n * n * n; e += kQrThreads) {
-        const int k = e / (n * n), rho = e - k * n * n;
-        const int i = rho / n, jj = rho - i * n;
-        const int p = stair_pos(i, jj);
-        const double sgn = (W[stair_off(k) + k] < 0.0) ? -1.0 : 1.0;
-        Qout[rho + (int64_t)n * n * k] = (p < (k + 1) * (k + 1)) ? sgn * Qs[stair_off(k) + p] : 0.0;
-    }
-    for (int e = tid; e < n * n; e += kQrThreads) {
-        const int k = e / n, i = e - k * n;       // R(i, k)
-        double v = 0.0;
-        if (i <= k) v = ((W[stair_off(i) + i] < 0.0) ? -1.0 : 1.0) * W[stair_off(k) + i];
-        Rout[i + n * k] = v;
-    }
+    stair_qr_block(F, G, n, W, Qs, tau, red, rowi, rowj, Qout, Rout);
 }
 
 inline size_t stair_smem_bytes(int n)

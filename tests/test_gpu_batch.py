@@ -1,9 +1,10 @@
 """Batched path (cpals_batch_*): many independent 3-way problems of uneven
-dims and ranks, one persistent kernel per mode update.  Checked against the
-FP64 oracle run on each problem separately, from the same initial factors.
+dims and ranks; per sweep two passes over all tensors (dimension tree) and
+one kernel per mode update.  Checked against the FP64 oracle run on each
+problem separately, from the same initial factors.
 
-Bars: the Multi-TTM runs in FP32 (relative error ~sqrt(I) * 2^-24 per
-contraction), everything else in FP64.  After one sweep the factors agree with
+Bars: the Multi-TTM and W = Y_(n) Q0 run in FP32 (relative error
+~sqrt(I) * 2^-24 per contraction), everything else in FP64.  After one sweep the factors agree with
 the oracle to 1e-4 relative (FP32 error amplified by the solve's
 conditioning).  At convergence (150 sweeps) the direct fit of the factors the
 batch found (FP64 residual against the tensor) agrees with the oracle's to
@@ -116,7 +117,7 @@ def test_batch_autotuner_and_graph(cuda_lib, small_batch):
     assert g >= 1 and t in (128, 256)
     l0 = b.launch_count()
     b.iterate(3)
-    assert b.launch_count() - l0 == 9     # three kernels per replayed sweep
+    assert b.launch_count() - l0 == 36    # twelve kernels per replayed sweep
 
 
 def test_batch_rejects_bad_shapes(cuda_lib):
