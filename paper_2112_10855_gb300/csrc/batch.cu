@@ -51,7 +51,8 @@ struct BProb {
     int64_t q[3];     // Q_m (I_m x R)
     int64_t rf[3];    // R_m (R x R)
     int64_t lam;      // lambda (R)
-    int64_t q0, r0;   // Q0 (R^2 x R) and R0 (R x R) of the current mode's V_n
+    int64_t q0f, r0;  // Q0 of the current mode's V_n as FP32 [col][r] (floats), R0 (R x R, doubles)
+    int64_t qf[3];    // Q_m as FP32 [k][r] (floats): what the contractions read
     int64_t w;        // W_n (up to max_n I_n x R)
     int64_t p1;       // X x_2 Q_2^T: I0 x I1 x R (floats)
     int64_t t2;       // X x_1 Q_1^T: I0 x R x I2 (floats)
@@ -180,13 +181,15 @@ __device__ __forceinline__ void ttm_row(const float* __restrict__ X, int64_t L, 
     float acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+    // sixteen loads in flight per thread: the passes stream X, so the bytes
+    // in flight per SM (not the FMAs) set the rate
     int k = 0;
-    for (; k + 8 <= K; k += 8) {
-        float v[8];
+    for (; k + 16 <= K; k += 16) {
+        float v[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldg(x + L * (int64_t)(k + u));
+        for (int u = 0; u < 16; ++u) v[u] = __ldg(x + L * (int64_t)(k + u));
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
+        for (int u = 0; u < 16; ++u)
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = fmaf(v[u], qs[(k + u) * R + r], acc[r]);
     }
@@ -217,7 +220,7 @@ __device__ __forceinline__ int next_item(int* counter, int* s_item)
 __global__ void batch_ttm_kernel(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_items,
                                  int* __restrict__ counter, int which, const float* __restrict__ Xall,
                                  float* __restrict__ P1all, float* __restrict__ T2all, float* __restrict__ Yall,
-                                 const double* __restrict__ F, const int* __restrict__ pstatus)
+                                 const float* __restrict__ Qf, const int* __restrict__ pstatus)
 {
     __shared__ float qs[128 * kBMaxR];   // Q_m as FP32 [k][r] for K <= 128
     __shared__ int s_item;
@@ -232,14 +235,11 @@ __global__ void batch_ttm_kernel(const BProb* __restrict__ probs, const BItem* _
         const int R = pr.R;
         const float* in = (which <= 1 ? Xall : (which == 4 ? T2all : P1all)) + v.in;
         float* out = (which == 0 ? P1all : (which == 1 ? T2all : Yall)) + v.out;
-        const double* Q = F + pr.q[v.m];
+        const float* Q = Qf + pr.qf[v.m];              // [k][r]
         const int64_t f = item.f0 + threadIdx.x;
         if (v.K <= 128) {
             if (cached != item.p) {
-                for (int e = threadIdx.x; e < v.K * R; e += blockDim.x) {
-                    const int k = e / R, r = e - k * R;
-                    qs[e] = (float)Q[k + v.K * r];
-                }
+                for (int e = threadIdx.x; e < v.K * R; e += blockDim.x) qs[e] = __ldg(Q + e);
                 cached = item.p;
                 __syncthreads();
             }
@@ -251,7 +251,7 @@ __global__ void batch_ttm_kernel(const BProb* __restrict__ probs, const BItem* _
                 default: break;
             }
         } else if (f < v.L * v.T) {
-            // long modes: Q read through L1 in FP64, the same sums in order of k
+            // long modes: Q read through L1, the same sums in order of k
             const int64_t t = f / v.L, l = f - t * v.L;
             const float* x = in + l + v.L * (int64_t)v.K * t;
             float acc[kBMaxR];
@@ -261,7 +261,7 @@ __global__ void batch_ttm_kernel(const BProb* __restrict__ probs, const BItem* _
                 const float xv = __ldg(x + v.L * (int64_t)k);
 #pragma unroll
                 for (int r = 0; r < kBMaxR; ++r)
-                    if (r < R) acc[r] = fmaf(xv, (float)__ldg(Q + k + (int64_t)v.K * r), acc[r]);
+                    if (r < R) acc[r] = fmaf(xv, __ldg(Q + (int64_t)k * R + r), acc[r]);
             }
             float* o = out + l + v.L * (int64_t)R * t;
 #pragma unroll
@@ -275,34 +275,33 @@ __global__ void batch_ttm_kernel(const BProb* __restrict__ probs, const BItem* _
 // W_n = Y_(n) Q0 for every problem: one thread per row i of a tile, its R
 // FP32 accumulators summed over the R^2 columns in order.  Y element (i, col),
 // col = a + Rn c, sits at a + Rn (i + In c) with Rn = 1, R, R^2 for n = 0, 1, 2.
-// Q0 (FP64) is staged once per problem as FP32 [col][r].
+// Q0 is staged once per problem from its FP32 [col][r] copy.
 template <int R>
-__device__ __forceinline__ void w_row(const float* __restrict__ Y, int In, int Rn, const float* q0f, int i,
+__device__ __forceinline__ void w_row(const float* __restrict__ Y, int In, int n, const float* q0f, int i,
                                       double* __restrict__ W)
 {
     if (i >= In) return;
     constexpr int RR = R * R;
-    const int nc = RR / Rn;
     float acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = 0.0f;
-    for (int c = 0; c < nc; ++c) {
-        const float* yr = Y + (int64_t)Rn * (i + (int64_t)In * c);
-        const float* qc = q0f + (int64_t)Rn * c * R;
-        int a = 0;
-        for (; a + 8 <= Rn; a += 8) {
-            float y[8];
+    // eight columns at a time, loads first; col = a + Rn c sits at a + Rn (i + In c)
+    for (int col0 = 0; col0 < RR; col0 += 8) {
+        float y[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) y[u] = __ldg(yr + a + u);
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] = fmaf(y[u], qc[(a + u) * R + r], acc[r]);
+        for (int u = 0; u < 8; ++u) {
+            const int col = col0 + u;
+            int64_t addr;
+            if (n == 0) addr = i + (int64_t)In * col;                                   // Rn = 1
+            else if (n == 1) addr = col % R + (int64_t)R * (i + (int64_t)In * (col / R));  // Rn = R
+            else addr = col + (int64_t)RR * i;                                          // Rn = R^2
+            y[u] = (col < RR) ? __ldg(Y + addr) : 0.0f;
         }
-        for (; a < Rn; ++a) {
-            const float y = __ldg(yr + a);
 #pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = fmaf(y, qc[a * R + r], acc[r]);
+        for (int u = 0; u < 8; ++u) {
+            const int col = (col0 + u < RR) ? col0 + u : RR - 1;   // y is zero past the end
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fmaf(y[u], q0f[col * R + r], acc[r]);
         }
     }
 #pragma unroll
@@ -311,7 +310,7 @@ __device__ __forceinline__ void w_row(const float* __restrict__ Y, int In, int R
 
 __global__ void batch_w_kernel(const BProb* __restrict__ probs, const BItem* __restrict__ items, int n_items,
                                int* __restrict__ counter, int n, const float* __restrict__ Yall,
-                               double* __restrict__ F, const int* __restrict__ pstatus)
+                               const float* __restrict__ Qf, double* __restrict__ F, const int* __restrict__ pstatus)
 {
     __shared__ float q0f[kBMaxR * kBMaxR * kBMaxR];
     __shared__ int s_item;
@@ -324,20 +323,16 @@ __global__ void batch_w_kernel(const BProb* __restrict__ probs, const BItem* __r
         const BProb& pr = probs[item.p];
         const int R = pr.R, RR = R * R, In = pr.I[n];
         if (cached != item.p) {
-            const double* Q0 = F + pr.q0;
-            for (int e = threadIdx.x; e < RR * R; e += blockDim.x) {
-                const int col = e / R, r = e - col * R;
-                q0f[e] = (float)Q0[col + RR * r];
-            }
+            const float* Q0 = Qf + pr.q0f;                 // [col][r]
+            for (int e = threadIdx.x; e < RR * R; e += blockDim.x) q0f[e] = __ldg(Q0 + e);
             cached = item.p;
             __syncthreads();
         }
-        const int Rn = (n == 0) ? 1 : (n == 1 ? R : RR);
         const int i = item.f0 + threadIdx.x;
         const float* Y = Yall + pr.y;
         double* W = F + pr.w;
         switch (R) {
-#define CPALS_BW(RV) case RV: w_row<RV>(Y, In, Rn, q0f, i, W); break;
+#define CPALS_BW(RV) case RV: w_row<RV>(Y, In, n, q0f, i, W); break;
             CPALS_BW(1) CPALS_BW(2) CPALS_BW(3) CPALS_BW(4) CPALS_BW(5) CPALS_BW(6) CPALS_BW(7) CPALS_BW(8)
             CPALS_BW(9) CPALS_BW(10) CPALS_BW(11) CPALS_BW(12) CPALS_BW(13) CPALS_BW(14) CPALS_BW(15) CPALS_BW(16)
 #undef CPALS_BW
@@ -360,9 +355,10 @@ __host__ __device__ inline BSmem bsmem_layout(int maxR, int maxI)
     const int64_t stair = (int64_t)maxR * (maxR + 1) * (2 * maxR + 1) / 3 + (int64_t)maxR * maxR + 8;
     const int64_t ir = (int64_t)maxI * maxR;
     const int64_t sa = ir > stair ? ir : stair;
+    const int64_t sb = ir > (int64_t)maxR * maxR * maxR ? ir : (int64_t)maxR * maxR * maxR;
     s.regA = 0;
     s.regB = s.regA + sa;
-    s.r0 = s.regB + ir;
+    s.r0 = s.regB + sb;
     s.rn = s.r0 + (int64_t)maxR * maxR;
     s.w = s.rn + (int64_t)maxR * maxR;
     s.total = s.w + ir + 128;    // + tau / red
@@ -371,17 +367,33 @@ __host__ __device__ inline BSmem bsmem_layout(int maxR, int maxI)
 
 // V = R_hi (.) R_lo of the mode `next` and its staircase QR into the
 // problem's Q0, R0 (global).  rhi / rlo may point to shared or global memory.
-__device__ void v_qr(const BProb& pr, const double* rhi, const double* rlo, double* F, double* regA, double* tau,
-                     double* red)
+__device__ void v_qr(const BProb& pr, const double* rhi, const double* rlo, double* F, float* Qf, double* regA,
+                     double* qtmp, double* tau, double* red)
 {
-    const int R = pr.R, tot = stair_off(R);
+    const int R = pr.R, RR = R * R, tot = stair_off(R);
     int* rows_i = reinterpret_cast<int*>(regA + 2 * tot);
-    stair_qr_block(rhi, rlo, R, regA, regA + tot, tau, red, rows_i, rows_i + R * R, F + pr.q0, F + pr.r0);
+    stair_qr_block(rhi, rlo, R, regA, regA + tot, tau, red, rows_i, rows_i + RR, qtmp, F + pr.r0);
+    for (int e = threadIdx.x; e < RR * R; e += blockDim.x) {
+        const int col = e / R, r = e - col * R;
+        Qf[pr.q0f + e] = (float)qtmp[col + RR * r];
+    }
+    __syncthreads();
+}
+
+// Q_m (FP64, I x R column-major, shared or global) as the FP32 [k][r] copy.
+__device__ void write_qf(const BProb& pr, int m, const double* Q, float* Qf)
+{
+    const int I = pr.I[m], R = pr.R;
+    for (int e = threadIdx.x; e < I * R; e += blockDim.x) {
+        const int k = e / R, r = e - k * R;
+        Qf[pr.qf[m] + e] = (float)Q[k + I * r];
+    }
 }
 
 // The QR of V_0 = R_2 (.) R_1 of every problem (the start of a sweep).
 __global__ void batch_vqr_kernel(const BProb* __restrict__ probs, const int* __restrict__ order, int count,
-                                 int maxR, int maxI, double* __restrict__ F, const int* __restrict__ pstatus)
+                                 int maxR, int maxI, double* __restrict__ F, float* __restrict__ Qf,
+                                 const int* __restrict__ pstatus)
 {
     extern __shared__ double bsm[];
     const BSmem L = bsmem_layout(maxR, maxI);
@@ -391,7 +403,7 @@ __global__ void batch_vqr_kernel(const BProb* __restrict__ probs, const int* __r
         const int p = order[idx];
         if (pstatus[p] != kStatusOk) continue;
         const BProb pr = probs[p];
-        v_qr(pr, F + pr.rf[2], F + pr.rf[1], F, bsm + L.regA, tau, red);
+        v_qr(pr, F + pr.rf[2], F + pr.rf[1], F, Qf, bsm + L.regA, bsm + L.regB, tau, red);
     }
 }
 
@@ -399,8 +411,8 @@ __global__ void batch_vqr_kernel(const BProb* __restrict__ probs, const int* __r
 // normalisation, factor QR, then the QR of the next mode's V (n < 2) or the
 // efficient fit (n = 2).
 __global__ void batch_tail_kernel(const BProb* __restrict__ probs, const int* __restrict__ order, int count, int n,
-                                  int maxR, int maxI, double* __restrict__ F, int* __restrict__ pstatus,
-                                  double* __restrict__ fit_last)
+                                  int maxR, int maxI, double* __restrict__ F, float* __restrict__ Qf,
+                                  int* __restrict__ pstatus, double* __restrict__ fit_last)
 {
     extern __shared__ double bsm[];
     const BSmem L = bsmem_layout(maxR, maxI);
@@ -501,6 +513,7 @@ __global__ void batch_tail_kernel(const BProb* __restrict__ probs, const int* __
         double* Rn_g = F + pr.rf[n];
         for (int e = tid; e < In * R; e += blockDim.x) Qn[e] = regB[e];
         for (int e = tid; e < RR; e += blockDim.x) Rn_g[e] = Rns[e];
+        write_qf(pr, n, regB, Qf);
         if (n == 2) {
             // efficient fit after the last mode (Sec. 3.3.1)
             double s = 0.0;
@@ -528,7 +541,7 @@ __global__ void batch_tail_kernel(const BProb* __restrict__ probs, const int* __
             // the next mode's V = R_hi (.) R_lo: mode 1 takes R_2 (.) R_0, mode 2 R_1 (.) R_0
             __syncthreads();
             const double* rhi = (n == 0) ? F + pr.rf[2] : F + pr.rf[1];
-            v_qr(pr, (n == 1) ? Rns : rhi, (n == 0) ? Rns : F + pr.rf[0], F, regA, tau, red);
+            v_qr(pr, (n == 1) ? Rns : rhi, (n == 0) ? Rns : F + pr.rf[0], F, Qf, regA, regB, tau, red);
         }
         __syncthreads();
     }
@@ -536,7 +549,7 @@ __global__ void batch_tail_kernel(const BProb* __restrict__ probs, const int* __
 
 // QR of every initial factor: one CTA per (problem, mode).
 __global__ void batch_factor_qr_kernel(BProb* __restrict__ probs, int count, int maxR, int maxI,
-                                       double* __restrict__ F)
+                                       double* __restrict__ F, float* __restrict__ Qf)
 {
     extern __shared__ double bsm[];
     const BSmem L = bsmem_layout(maxR, maxI);
@@ -555,6 +568,7 @@ __global__ void batch_factor_qr_kernel(BProb* __restrict__ probs, int count, int
     cta_householder(regA, I, R, regB, Rs, tau, red);
     for (int e = threadIdx.x; e < I * R; e += blockDim.x) F[pr.q[m] + e] = regB[e];
     for (int e = threadIdx.x; e < R * R; e += blockDim.x) F[pr.rf[m] + e] = Rs[e];
+    write_qf(pr, m, regB, Qf);
 }
 
 // ||X_p||^2 in FP64, one CTA per problem.
@@ -595,6 +609,7 @@ struct Batch {
     int* d_order = nullptr;
     float* Xall = nullptr;
     double* F = nullptr;
+    float* Qf = nullptr;                 // FP32 copies of Q_m ([k][r]) and Q0 ([col][r])
     float* P1all = nullptr;
     float* T2all = nullptr;
     float* Yall = nullptr;
@@ -604,13 +619,13 @@ struct Batch {
     BItem* d_items[2][kTtmWhich + 3] = {};
     int n_items[2][kTtmWhich + 3] = {};
     int* d_counter = nullptr;            // one queue counter per grouped launch of a sweep
-    int64_t x_elems = 0, f_elems = 0, p1_elems = 0, t2_elems = 0, y_elems = 0;
+    int64_t x_elems = 0, f_elems = 0, qf_elems = 0, p1_elems = 0, t2_elems = 0, y_elems = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;         // the QR of V_0 beside pass 1
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
     // tuned shape: the grouped launches' tile (threads) and grid; the factorisation kernels' threads and grid
-    int tile = 0, group_grid = 0, grid = 0, threads = 0;
+    int tile = 0, group_grid = 0, w_grid = 0, grid = 0, threads = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t launches = 0;
     size_t smem = 0;
@@ -624,7 +639,7 @@ cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ran
 {
     b->count = count;
     b->probs.resize(count);
-    int64_t xo = 0, fo = 0, p1o = 0, t2o = 0, yo = 0;
+    int64_t xo = 0, fo = 0, qfo = 0, p1o = 0, t2o = 0, yo = 0;
     std::vector<double> work(count);
     for (int p = 0; p < count; ++p) {
         BProb& pr = b->probs[p];
@@ -641,8 +656,9 @@ cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ran
         for (int m = 0; m < 3; ++m) { pr.rf[m] = fo; fo += R * R; }
         pr.lam = fo;
         fo += R;
-        pr.q0 = fo;
-        fo += R * R * R;
+        for (int m = 0; m < 3; ++m) { pr.qf[m] = qfo; qfo += align4(pr.I[m] * R); }
+        pr.q0f = qfo;
+        qfo += align4(R * R * R);
         pr.r0 = fo;
         fo += R * R;
         pr.w = fo;
@@ -662,11 +678,12 @@ cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ran
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
     std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) { return work[a] > work[c]; });
-    b->x_elems = xo; b->f_elems = fo; b->p1_elems = p1o; b->t2_elems = t2o; b->y_elems = yo;
+    b->x_elems = xo; b->f_elems = fo; b->qf_elems = qfo; b->p1_elems = p1o; b->t2_elems = t2o; b->y_elems = yo;
     CPALS_CUDA_TRY(cudaMalloc(&b->d_probs, sizeof(BProb) * count));
     CPALS_CUDA_TRY(cudaMalloc(&b->d_order, sizeof(int) * count));
     CPALS_CUDA_TRY(cudaMalloc(&b->Xall, sizeof(float) * std::max<int64_t>(xo, 1)));
     CPALS_CUDA_TRY(cudaMalloc(&b->F, sizeof(double) * std::max<int64_t>(fo, 1)));
+    CPALS_CUDA_TRY(cudaMalloc(&b->Qf, sizeof(float) * std::max<int64_t>(qfo, 1)));
     CPALS_CUDA_TRY(cudaMalloc(&b->P1all, sizeof(float) * std::max<int64_t>(p1o, 1)));
     CPALS_CUDA_TRY(cudaMalloc(&b->T2all, sizeof(float) * std::max<int64_t>(t2o, 1)));
     CPALS_CUDA_TRY(cudaMalloc(&b->Yall, sizeof(float) * std::max<int64_t>(yo, 1)));
@@ -724,7 +741,7 @@ cudaError_t batch_build(Batch* b, int count, const int64_t* dims, const int* ran
 void batch_free(Batch* b)
 {
     auto f = [](void* p) { if (p) cudaFree(p); };
-    f(b->d_probs); f(b->d_order); f(b->Xall); f(b->F); f(b->P1all); f(b->T2all); f(b->Yall); f(b->d_pstatus);
+    f(b->d_probs); f(b->d_order); f(b->Xall); f(b->F); f(b->Qf); f(b->P1all); f(b->T2all); f(b->Yall); f(b->d_pstatus);
     f(b->d_fit); f(b->d_counter);
     for (int ti = 0; ti < 2; ++ti)
         for (int g = 0; g < kTtmWhich + 3; ++g) f(b->d_items[ti][g]);
@@ -743,7 +760,8 @@ cudaError_t batch_norms(Batch* b)
 
 cudaError_t batch_factor_qr(Batch* b)
 {
-    batch_factor_qr_kernel<<<3 * b->count, 256, b->smem, b->stream>>>(b->d_probs, b->count, b->maxR, b->maxI, b->F);
+    batch_factor_qr_kernel<<<3 * b->count, 256, b->smem, b->stream>>>(b->d_probs, b->count, b->maxR, b->maxI, b->F,
+                                                                       b->Qf);
     b->launches++;
     return cudaGetLastError();
 }
@@ -753,7 +771,7 @@ static cudaError_t grouped_ttm(Batch* b, int ti, int which, int grid)
     CPALS_CUDA_TRY(cudaMemsetAsync(b->d_counter + which, 0, sizeof(int), b->stream));
     batch_ttm_kernel<<<grid, kTiles[ti], 0, b->stream>>>(b->d_probs, b->d_items[ti][which], b->n_items[ti][which],
                                                          b->d_counter + which, which, b->Xall, b->P1all, b->T2all,
-                                                         b->Yall, b->F, b->d_pstatus);
+                                                         b->Yall, b->Qf, b->d_pstatus);
     b->launches++;
     return cudaGetLastError();
 }
@@ -763,7 +781,7 @@ static cudaError_t grouped_w(Batch* b, int ti, int n, int grid)
     const int g = kTtmWhich + n;
     CPALS_CUDA_TRY(cudaMemsetAsync(b->d_counter + g, 0, sizeof(int), b->stream));
     batch_w_kernel<<<grid, kTiles[ti], 0, b->stream>>>(b->d_probs, b->d_items[ti][g], b->n_items[ti][g],
-                                                       b->d_counter + g, n, b->Yall, b->F, b->d_pstatus);
+                                                       b->d_counter + g, n, b->Yall, b->Qf, b->F, b->d_pstatus);
     b->launches++;
     return cudaGetLastError();
 }
@@ -771,19 +789,19 @@ static cudaError_t grouped_w(Batch* b, int ti, int n, int grid)
 static cudaError_t chain(Batch* b, int n, int grid, int threads)
 {
     batch_tail_kernel<<<grid, threads, b->smem, b->stream>>>(b->d_probs, b->d_order, b->count, n, b->maxR, b->maxI,
-                                                             b->F, b->d_pstatus, b->d_fit);
+                                                             b->F, b->Qf, b->d_pstatus, b->d_fit);
     b->launches++;
     return cudaGetLastError();
 }
 
 // One sweep along the dimension tree.  The QR of V_0 runs on the side stream
 // beside pass 1 (two branches of the captured graph).
-static cudaError_t batch_sweep(Batch* b, int ti, int group_grid, int grid, int threads)
+static cudaError_t batch_sweep(Batch* b, int ti, int group_grid, int w_grid, int grid, int threads)
 {
     CPALS_CUDA_TRY(cudaEventRecord(b->ev_fork, b->stream));
     CPALS_CUDA_TRY(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
     batch_vqr_kernel<<<grid, threads, b->smem, b->side>>>(b->d_probs, b->d_order, b->count, b->maxR, b->maxI, b->F,
-                                                          b->d_pstatus);
+                                                          b->Qf, b->d_pstatus);
     b->launches++;
     CPALS_CUDA_TRY(cudaGetLastError());
     CPALS_CUDA_TRY(cudaEventRecord(b->ev_join, b->side));
@@ -792,7 +810,7 @@ static cudaError_t batch_sweep(Batch* b, int ti, int group_grid, int grid, int t
     for (int n = 0; n < 3; ++n) {
         if (n == 2) CPALS_CUDA_TRY(grouped_ttm(b, ti, 1, group_grid));   // pass 2
         CPALS_CUDA_TRY(grouped_ttm(b, ti, 2 + n, group_grid));            // the last TTM of mode n
-        CPALS_CUDA_TRY(grouped_w(b, ti, n, group_grid));
+        CPALS_CUDA_TRY(grouped_w(b, ti, n, w_grid));
         CPALS_CUDA_TRY(chain(b, n, grid, threads));
     }
     return cudaSuccess;
@@ -807,18 +825,23 @@ cudaError_t batch_prepare(Batch* b)
 {
     if (b->graph) return cudaSuccess;
     double* saved = nullptr;
+    float* saved_qf = nullptr;
     CPALS_CUDA_TRY(cudaMalloc(&saved, sizeof(double) * std::max<int64_t>(b->f_elems, 1)));
+    CPALS_CUDA_TRY(cudaMalloc(&saved_qf, sizeof(float) * std::max<int64_t>(b->qf_elems, 1)));
     CPALS_CUDA_TRY(cudaMemcpyAsync(saved, b->F, sizeof(double) * b->f_elems, cudaMemcpyDeviceToDevice, b->stream));
+    CPALS_CUDA_TRY(cudaMemcpyAsync(saved_qf, b->Qf, sizeof(float) * b->qf_elems, cudaMemcpyDeviceToDevice,
+                                   b->stream));
     cudaEvent_t e0, e1;
     CPALS_CUDA_TRY(cudaEventCreate(&e0));
     CPALS_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int ggrid[2] = {0, 0};
+    int ggrid[2] = {0, 0}, wgrid[2] = {0, 0};
     for (int ti = 0; ti < 2; ++ti) {
         int o1 = 0, o2 = 0;
         CPALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, batch_ttm_kernel, kTiles[ti], 0));
         CPALS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, batch_w_kernel, kTiles[ti], 0));
-        ggrid[ti] = std::max(1, std::min(o1, o2)) * b->num_sms;
+        ggrid[ti] = std::max(1, o1) * b->num_sms;
+        wgrid[ti] = std::max(1, o2) * b->num_sms;
     }
     const int threads_c[2] = {128, 256};
     for (int ti = 0; ti < 2; ++ti)
@@ -831,8 +854,10 @@ cudaError_t batch_prepare(Batch* b)
                 const int grid = std::min(b->count, b->num_sms * per);
                 CPALS_CUDA_TRY(cudaMemcpyAsync(b->F, saved, sizeof(double) * b->f_elems, cudaMemcpyDeviceToDevice,
                                                b->stream));
+                CPALS_CUDA_TRY(cudaMemcpyAsync(b->Qf, saved_qf, sizeof(float) * b->qf_elems,
+                                               cudaMemcpyDeviceToDevice, b->stream));
                 CPALS_CUDA_TRY(cudaEventRecord(e0, b->stream));
-                CPALS_CUDA_TRY(batch_sweep(b, ti, ggrid[ti], grid, threads_c[mi]));
+                CPALS_CUDA_TRY(batch_sweep(b, ti, ggrid[ti], wgrid[ti], grid, threads_c[mi]));
                 CPALS_CUDA_TRY(cudaEventRecord(e1, b->stream));
                 CPALS_CUDA_TRY(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -841,6 +866,7 @@ cudaError_t batch_prepare(Batch* b)
                     best = ms;
                     b->tile = kTiles[ti];
                     b->group_grid = ggrid[ti];
+                    b->w_grid = wgrid[ti];
                     b->grid = grid;
                     b->threads = threads_c[mi];
                 }
@@ -848,9 +874,12 @@ cudaError_t batch_prepare(Batch* b)
             }
         }
     CPALS_CUDA_TRY(cudaMemcpyAsync(b->F, saved, sizeof(double) * b->f_elems, cudaMemcpyDeviceToDevice, b->stream));
+    CPALS_CUDA_TRY(cudaMemcpyAsync(b->Qf, saved_qf, sizeof(float) * b->qf_elems, cudaMemcpyDeviceToDevice,
+                                   b->stream));
     CPALS_CUDA_TRY(cudaMemsetAsync(b->d_pstatus, 0, sizeof(int) * b->count, b->stream));
     CPALS_CUDA_TRY(cudaStreamSynchronize(b->stream));
     cudaFree(saved);
+    cudaFree(saved_qf);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (b->grid == 0) return cudaErrorInvalidConfiguration;
@@ -868,7 +897,7 @@ cudaError_t batch_prepare(Batch* b)
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     cudaError_t e2 = cudaSuccess;
     if (e == cudaSuccess) {
-        e2 = batch_sweep(b, b->tile == kTiles[0] ? 0 : 1, b->group_grid, b->grid, b->threads);
+        e2 = batch_sweep(b, b->tile == kTiles[0] ? 0 : 1, b->group_grid, b->w_grid, b->grid, b->threads);
         e = cudaStreamEndCapture(cap, &g);
     }
     b->stream = saved_stream;
