@@ -55,11 +55,14 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the 120^4 rank-20 FP64/FP32/3xBF16/3xTF32 record of the default run")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--workload", choices=["c2", "c3", "c5a", "c5b", "c4", "sine", "collinear"], default="c2",
+    ap.add_argument("--workload", choices=["c2", "c3", "c5a", "c5b", "c4", "sine", "collinear", "paper41"],
+                    default="c2",
                     help="c2: the headline 400^3 rank-10 FP64 workload; c3: 4-way 120^4 rank 20, c5a: 3-way "
                          "1000^3 rank 64 (SVD solve) and c5b: 5-way 40^5 rank 8, each comparing FP64, FP32, 3xBF16 "
                          "and 3xTF32 passes over X; c4: 512 independent small problems, batched; sine: sine-of-sums "
-                         "tensors in Kruskal form (Sec. 4.3); collinear: the Sec. 4.2 collinearity x noise grid")
+                         "tensors in Kruskal form (Sec. 4.3); collinear: the Sec. 4.2 collinearity x noise grid; "
+                         "paper41: the Sec. 4.1 cubical tensors (700^3, 300^4, 75^5) over a rank sweep with the "
+                         "per-sweep time of the four solves and the component breakdown of Table its_parts")
     ap.add_argument("--trials", type=int, default=10, help="collinear: random starts per grid cell")
     ap.add_argument("--recovery-seeds", type=int, default=5,
                     help="c3: planted problems (seeds) on which every precision runs to convergence and is scored "
@@ -774,6 +777,70 @@ def run_collinear(args, world, rank):
         print(json.dumps(line), flush=True)
 
 
+def run_paper41(args, world, rank):
+    """Sec. 4.1: randomly generated cubical tensors of three, four and five
+    modes (700^3, 300^4, 75^5; entries uniform on [0, 1), generated on the
+    device from a fixed seed; FP64), for a sweep of ranks.  Per (shape, rank)
+    and solve (CP-ALS, CP-ALS-PINV, CP-ALS-QR, CP-ALS-QR-SVD): the time per
+    sweep of the captured sweep (CUDA events, after one warm-up sweep), the
+    slowdown of CP-ALS-QR against CP-ALS, and the component breakdown of
+    Table its_parts from cpals_profile_sweeps (phases serialised on one
+    stream)."""
+    import torch
+    from paper_2112_10855_gb300 import _build, cpals
+    torch.cuda.set_device(0)
+    _build.build()
+    cpals.load()
+    shapes = [((700,) * 3, [5, 10, 20, 40, 64]), ((300,) * 4, [5, 10, 20, 40]), ((75,) * 5, [5, 10, 20])]
+    solves = [("normal", 0.0), ("normal_pinv", 1e-10), ("qr", 0.0), ("svd", 1e-10)]
+    stream = torch.cuda.Stream()
+    results = []
+    t0 = time.time()
+    for dims, ranks in shapes:
+        g = torch.Generator(device="cuda").manual_seed(4101 + len(dims))
+        X = torch.rand(int(np.prod(dims)), dtype=torch.float64, device="cuda", generator=g)
+        for R in ranks:
+            rng = np.random.default_rng(4100 + R)
+            A = [np.asfortranarray(rng.random((d, R))) for d in dims]
+            entry = {"dims": list(dims), "rank": R, "ms_per_sweep": {}, "breakdown_ms": {}}
+            for solve, rtol in solves:
+                h = cpals.CPALS(dims, R, "f64")
+                h.set_stream(stream)
+                h.set_tensor(X)
+                h.set_factors(A)
+                h.iterate(1, solve=solve, svd_rtol=rtol, want_fits=False)
+                torch.cuda.synchronize()
+                k = max(2, min(10, int(3.0e11 / (float(np.prod(dims)) * R * 4))))
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.iterate(k, solve=solve, svd_rtol=rtol, want_fits=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                entry["ms_per_sweep"][solve] = e0.elapsed_time(e1) / k
+                entry["breakdown_ms"][solve] = h.profile_sweeps(2, solve=solve, svd_rtol=rtol)
+                del h
+                torch.cuda.empty_cache()
+            entry["slowdown_qr_vs_normal"] = entry["ms_per_sweep"]["qr"] / entry["ms_per_sweep"]["normal"]
+            results.append(entry)
+            print(json.dumps({"dims": list(dims), "rank": R, "ms_per_sweep": entry["ms_per_sweep"],
+                              "slowdown_qr_vs_normal": entry["slowdown_qr_vs_normal"]}), file=sys.stderr, flush=True)
+        del X
+        torch.cuda.empty_cache()
+    if rank == 0:
+        line = {
+            "metric": "CP-ALS-QR / CP-ALS time per sweep (Sec. 4.1)", "value": float(np.mean(
+                [r["slowdown_qr_vs_normal"] for r in results])), "unit": "ratio (mean over shapes and ranks)",
+            "n_gpus": world, "steps": None, "warmup": 1, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Sec. 4.1: random cubical tensors 700^3, 300^4, 75^5 (uniform [0, 1), FP64), "
+                                   "rank sweep, random initial factors; CP-ALS, CP-ALS-PINV, CP-ALS-QR, "
+                                   "CP-ALS-QR-SVD, dimension-tree sweeps"},
+            "results": results, "wall_s": time.time() - t0,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
@@ -788,6 +855,9 @@ def main():
         return
     if args.workload == "collinear":
         run_collinear(args, world, rank)
+        return
+    if args.workload == "paper41":
+        run_paper41(args, world, rank)
         return
     if args.workload != "c2":
         run_mixed(args, world, rank)

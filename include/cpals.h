@@ -217,6 +217,24 @@ int cpals_solve_mode(cpals_handle* h, int mode, int solve, double svd_rtol);
 int cpals_iterate(cpals_handle* h, int iters, double tol, int solve, double svd_rtol, int* done,
                   double* fits_host);
 
+/* The per-iteration component breakdown of Table its_parts (Sec. 4.1):
+ * runs `sweeps` sweeps (1..16) like cpals_iterate with tol = 0, but eagerly
+ * and with every phase on the handle's stream one after the other (no side
+ * stream, no graph), records CUDA events around each phase, and writes the
+ * mean milliseconds per sweep of five buckets to bucket_ms[0..4]:
+ *   0: the passes over X -- Multi-TTM (QR, SVD) or MTTKRP (normal equations);
+ *   1: the QR of the factor matrices (QR, SVD) or their Grams (normal
+ *      equations); with CPALS_OPT_FUSED_TAIL the fused tail also holds the
+ *      solve and the normalisation;
+ *   2: computing Q0 (the QR of V_n);
+ *   3: applying Q0 (W = Y_(n) Q0);
+ *   4: other (solve operators of R0 or S_n, the solve when not fused, the fit).
+ * The factors advance as in cpals_iterate.  The sum of the buckets exceeds a
+ * graph sweep's time by the overlap and the launch gaps the graph removes.
+ * Synchronises.  Errors: CPALS_ERR_ARG, CPALS_ERR_STATE, CPALS_ERR_CUDA, and
+ * the device errors of a sweep. */
+int cpals_profile_sweeps(cpals_handle* h, int sweeps, int solve, double svd_rtol, double* bucket_ms);
+
 /* fit = 1 - ||X - Xhat|| / ||X||.  direct = 0: the efficient form of
  * Sec. 3.3.1 from the last sweep's W_N, Ahat_N, R0 and R_N (or, after a
  * NORMAL sweep, from M_N and S_N).  It is accurate to about sqrt(eps) and

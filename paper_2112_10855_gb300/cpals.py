@@ -74,6 +74,7 @@ def load(path: str | None = None):
     L.cpals_iterate.argtypes = [_vp, C.c_int, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double)]
     L.cpals_fit.argtypes = [_vp, C.c_int, C.POINTER(C.c_double)]
+    L.cpals_profile_sweeps.argtypes = [_vp, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double)]
     L.cpals_sync.argtypes = [_vp]
     L.cpals_set_option.argtypes = [_vp, C.c_int, C.c_int64]
     L.cpals_launch_count.argtypes = [_vp]
@@ -334,6 +335,13 @@ class CPALS:
         _check(self._h, load().cpals_iterate(self._h, int(iters), float(tol), s, float(svd_rtol),
                                              C.byref(done), fits))
         return np.array(fits[:done.value]) if want_fits else done.value
+
+    def profile_sweeps(self, sweeps=3, solve="qr", svd_rtol=0.0):
+        """cpals_profile_sweeps: mean ms per sweep in the five buckets of Table its_parts
+        (passes over X, factor QR or Gram, computing Q0, applying Q0, other)."""
+        out = (C.c_double * 5)()
+        _check(self._h, load().cpals_profile_sweeps(self._h, int(sweeps), SOLVES[solve], float(svd_rtol), out))
+        return dict(zip(["multi_ttm_or_mttkrp", "factor_qr_or_gram", "compute_q0", "apply_q0", "other"], list(out)))
 
     def fit(self, direct=False):
         f = C.c_double()

@@ -82,6 +82,10 @@ void free_all(Handle* h)
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->KV[m]); f(h->KC[m]); f(h->KE[m]); }
     f(h->Kmu); f(h->KGV); f(h->KP); f(h->KMw[0]); f(h->KMw[1]);
+    for (int i = 0; i < cpals::kProfMax; ++i) {
+        if (h->prof_a[i]) cudaEventDestroy(h->prof_a[i]);
+        if (h->prof_b[i]) cudaEventDestroy(h->prof_b[i]);
+    }
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -132,6 +136,24 @@ int take_status(Handle* h)
     return CPALS_OK;
 }
 
+// Events around one phase of a profiled sweep (no-op unless h->prof).
+struct ProfScope {
+    Handle* h;
+    int i = -1;
+    ProfScope(Handle* hh, int bucket) : h(hh)
+    {
+        if (h->prof && h->prof_n < cpals::kProfMax) {
+            i = h->prof_n++;
+            h->prof_bucket[i] = bucket;
+            cudaEventRecord(h->prof_a[i], h->stream);
+        }
+    }
+    ~ProfScope()
+    {
+        if (i >= 0) cudaEventRecord(h->prof_b[i], h->stream);
+    }
+};
+
 inline bool is_normal(int solve) { return solve == CPALS_SOLVE_NORMAL || solve == CPALS_SOLVE_NORMAL_PINV; }
 
 // The Gram of the current factor A_m and, with want_qr, its QR (diag(R_m) >= 0).
@@ -158,6 +180,7 @@ cudaError_t refresh_derived(Handle* h, int solve, int skip)
         if (m == skip) continue;
         if (is_normal(solve)) {
             if (!h->gram_valid[m]) {
+                ProfScope ps(h, cpals::kProfFactor);
                 CPALS_CUDA_TRY(factor_qr_gram(h, m, false));
                 h->gram_valid[m] = true;
             }
@@ -167,6 +190,7 @@ cudaError_t refresh_derived(Handle* h, int solve, int skip)
             }
         } else {
             if (!h->qr_valid[m]) {
+                ProfScope ps(h, cpals::kProfFactor);
                 CPALS_CUDA_TRY(factor_qr_gram(h, m, true));
                 h->qr_valid[m] = true;
                 h->gram_valid[m] = true;
@@ -215,18 +239,23 @@ cudaError_t finish_update(Handle* h, int n, int solve, double rtol, bool have_op
         const double* Op = h->R0;
         if (solve == CPALS_SOLVE_SVD || solve == CPALS_SOLVE_NORMAL_PINV) {
             if (!have_operator) {
+                ProfScope ps(h, cpals::kProfOther);
                 if (solve == CPALS_SOLVE_SVD) CPALS_CUDA_TRY(cpals::svd_operator(h, rtol));
                 else CPALS_CUDA_TRY(cpals::normal_operator(h, n, true, rtol));
             }
             kind = 1;
             Op = h->T;
         } else if (solve == CPALS_SOLVE_NORMAL) {
-            if (!have_operator) CPALS_CUDA_TRY(cpals::normal_operator(h, n, false, 0.0));
+            if (!have_operator) {
+                ProfScope ps(h, cpals::kProfOther);
+                CPALS_CUDA_TRY(cpals::normal_operator(h, n, false, 0.0));
+            }
             kind = 2;
             Op = h->T;
         }
         if (h->R > 32) {
             // the R^2 work per row of the solve on every SM, then the cluster from Ahat
+            ProfScope ps(h, cpals::kProfOther);
             switch (solve) {
                 case CPALS_SOLVE_QR: CPALS_CUDA_TRY(cpals::solve_qr(h, In)); break;
                 case CPALS_SOLVE_SVD: CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol, true)); break;
@@ -236,19 +265,28 @@ cudaError_t finish_update(Handle* h, int n, int solve, double rtol, bool have_op
             kind = 3;
             Win = h->Ahat;
         }
-        CPALS_CUDA_TRY(cpals::mode_tail(h, n, kind, Win, Op, !normal));
-        if (!normal) CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n], true, h->d_gate));
+        {
+            // the fused tail holds the solve and the normalisation too
+            ProfScope ps(h, cpals::kProfFactor);
+            CPALS_CUDA_TRY(cpals::mode_tail(h, n, kind, Win, Op, !normal));
+            if (!normal)
+                CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[n], In, h->R, h->Q[n], h->Rf[n], true, h->d_gate));
+        }
         h->gram_valid[n] = true;
         h->qr_valid[n] = !normal;
         return cudaSuccess;
     }
-    switch (solve) {
-        case CPALS_SOLVE_QR: CPALS_CUDA_TRY(cpals::solve_qr(h, In)); break;
-        case CPALS_SOLVE_SVD: CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol, have_operator)); break;
-        case CPALS_SOLVE_NORMAL: CPALS_CUDA_TRY(cpals::solve_normal(h, n, have_operator)); break;
-        default: CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol, have_operator)); break;
+    {
+        ProfScope ps(h, cpals::kProfOther);
+        switch (solve) {
+            case CPALS_SOLVE_QR: CPALS_CUDA_TRY(cpals::solve_qr(h, In)); break;
+            case CPALS_SOLVE_SVD: CPALS_CUDA_TRY(cpals::solve_svd(h, In, rtol, have_operator)); break;
+            case CPALS_SOLVE_NORMAL: CPALS_CUDA_TRY(cpals::solve_normal(h, n, have_operator)); break;
+            default: CPALS_CUDA_TRY(cpals::solve_normal_pinv(h, n, rtol, have_operator)); break;
+        }
+        CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
     }
-    CPALS_CUDA_TRY(cpals::normalize_and_refactor(h, n));
+    ProfScope ps(h, cpals::kProfFactor);
     if (normal) {
         CPALS_CUDA_TRY(cpals::gram(h, h->A[n], In, h->G[n]));
         h->gram_valid[n] = true;
@@ -270,10 +308,15 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
     if (h->kruskal) {
         // Kruskal input (Sec. 3.3.2): no pass over a dense tensor
         if (is_normal(solve)) {
+            ProfScope ps(h, cpals::kProfTTM);
             CPALS_CUDA_TRY(cpals::kr_mttkrp(h, n));
         } else {
-            CPALS_CUDA_TRY(cpals::krp_qr(h, n, true));
+            {
+                ProfScope ps(h, cpals::kProfQ0);
+                CPALS_CUDA_TRY(cpals::krp_qr(h, n, true));
+            }
             h->krp_mode = n;
+            ProfScope ps(h, cpals::kProfApplyQ0);
             CPALS_CUDA_TRY(cpals::kr_apply_q0(h, n));
         }
         CPALS_CUDA_TRY(finish_update(h, n, solve, rtol, false));
@@ -297,13 +340,20 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
             CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
             cudaStream_t main = h->stream;
             h->stream = h->side;
-            cudaError_t e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
+            cudaError_t e;
+            {
+                ProfScope ps(h, cpals::kProfOther);
+                e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
+            }
             h->stream = main;
             CPALS_CUDA_TRY(e);
             CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
         }
-        if (from_partial) CPALS_CUDA_TRY(cpals::mttkrp_from_partial(h, n));
-        else CPALS_CUDA_TRY(cpals::mttkrp(h, n));
+        {
+            ProfScope ps(h, cpals::kProfTTM);
+            if (from_partial) CPALS_CUDA_TRY(cpals::mttkrp_from_partial(h, n));
+            else CPALS_CUDA_TRY(cpals::mttkrp(h, n));
+        }
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     } else {
         // The QR of V_n needs only the R_m and the Multi-TTM only the Q_m: run the
@@ -313,21 +363,37 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
             CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
             cudaStream_t main = h->stream;
             h->stream = h->side;
-            cudaError_t e = tq ? cpals::krp_qr_tree(h, n, tq->slot, tq->other_left, tq->own, tq->nown)
-                               : cpals::krp_qr(h, n);
+            cudaError_t e;
+            {
+                ProfScope ps(h, cpals::kProfQ0);
+                e = tq ? cpals::krp_qr_tree(h, n, tq->slot, tq->other_left, tq->own, tq->nown) : cpals::krp_qr(h, n);
+            }
             // the SVD operator of R0 needs nothing else: it follows on the side stream
-            if (e == cudaSuccess && solve == CPALS_SOLVE_SVD) e = cpals::svd_operator(h, rtol);
+            if (e == cudaSuccess && solve == CPALS_SOLVE_SVD) {
+                ProfScope ps(h, cpals::kProfOther);
+                e = cpals::svd_operator(h, rtol);
+            }
             h->stream = main;
             CPALS_CUDA_TRY(e);
             CPALS_CUDA_TRY(cudaEventRecord(h->ev_join, h->side));
         }
         h->krp_mode = n;
-        if (from_partial) CPALS_CUDA_TRY(cpals::multi_ttm_from_partial(h, n));
-        else CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
+        {
+            ProfScope ps(h, cpals::kProfTTM);
+            if (from_partial) CPALS_CUDA_TRY(cpals::multi_ttm_from_partial(h, n));
+            else CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
+        }
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        ProfScope ps(h, cpals::kProfApplyQ0);
         CPALS_CUDA_TRY(cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W));
     }
     return finish_update(h, n, solve, rtol, true);
+}
+
+cudaError_t fit_scoped(Handle* h, int solve)
+{
+    ProfScope ps(h, cpals::kProfOther);
+    return cpals::fit_efficient(h, solve);
 }
 
 // One sweep over the modes.  For an N >= 3 dense tensor the Multi-TTMs
@@ -344,7 +410,7 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
 {
     if (h->N < 3 || !h->dimtree || !h->tA || h->kruskal) {
         for (int n = 0; n < h->N; ++n) CPALS_CUDA_TRY(mode_update(h, n, solve, rtol));
-        return cpals::fit_efficient(h, solve);
+        return fit_scoped(h, solve);
     }
     const int N = h->N, h1 = (N + 1) / 2;
     int H1[cpals::kMaxN], H2[cpals::kMaxN], n1 = 0, n2 = 0;
@@ -354,6 +420,7 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
     }
     // the normal equations use the same halves with the MTTKRP's contractions
     auto pass = [&](const int* modes, int nm) {
+        ProfScope ps(h, cpals::kProfTTM);
         return is_normal(solve) ? cpals::mttkrp_tree_pass(h, modes, nm) : cpals::dimtree_pass(h, modes, nm);
     };
     if (is_normal(solve)) {
@@ -364,7 +431,11 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
             CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
             cudaStream_t main = h->stream;
             h->stream = h->side;
-            cudaError_t e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
+            cudaError_t e;
+            {
+                ProfScope ps(h, cpals::kProfOther);
+                e = cpals::normal_operator(h, n, solve == CPALS_SOLVE_NORMAL_PINV, rtol);
+            }
             h->stream = main;
             CPALS_CUDA_TRY(e);
             return cudaEventRecord(h->ev_join, h->side);
@@ -378,14 +449,14 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
         CPALS_CUDA_TRY(pass(H1, n1));
         for (int k = 0; k < n2; ++k)
             CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true, k == 0 ? &ready : nullptr));
-        return cpals::fit_efficient(h, solve);
+        return fit_scoped(h, solve);
     }
     if (!h->krp_tree) {
         CPALS_CUDA_TRY(pass(H2, n2));
         for (int k = 0; k < n1; ++k) CPALS_CUDA_TRY(mode_update(h, H1[k], solve, rtol, true));
         CPALS_CUDA_TRY(pass(H1, n1));
         for (int k = 0; k < n2; ++k) CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true));
-        return cpals::fit_efficient(h, solve);
+        return fit_scoped(h, solve);
     }
     // The QR of V_n follows the same tree: V_n of an H1 mode is (Khatri-Rao of
     // H2) (.) (the other H1 modes), and the H2 factors do not change while H1
@@ -399,7 +470,11 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
         cudaStream_t main = h->stream;
         h->stream = h->side;
-        cudaError_t e = cpals::krp_qr_half(h, modes, nm, slot);
+        cudaError_t e;
+        {
+            ProfScope ps(h, cpals::kProfQ0);
+            e = cpals::krp_qr_half(h, modes, nm, slot);
+        }
         h->stream = main;
         return e;
     };
@@ -415,8 +490,15 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
     auto early_qr = [&](int n, const TreeQR& tq) -> cudaError_t {
         cudaStream_t main = h->stream;
         h->stream = h->side;
-        cudaError_t e = cpals::krp_qr_tree(h, n, tq.slot, tq.other_left, tq.own, tq.nown);
-        if (e == cudaSuccess && solve == CPALS_SOLVE_SVD) e = cpals::svd_operator(h, rtol);
+        cudaError_t e;
+        {
+            ProfScope ps(h, cpals::kProfQ0);
+            e = cpals::krp_qr_tree(h, n, tq.slot, tq.other_left, tq.own, tq.nown);
+        }
+        if (e == cudaSuccess && solve == CPALS_SOLVE_SVD) {
+            ProfScope ps(h, cpals::kProfOther);
+            e = cpals::svd_operator(h, rtol);
+        }
         h->stream = main;
         CPALS_CUDA_TRY(e);
         return cudaEventRecord(h->ev_join, h->side);
@@ -437,7 +519,7 @@ cudaError_t sweep(Handle* h, int solve, double rtol)
         const TreeQR tq = (k == 0) ? first2 : TreeQR{0, false, own, own_of(H2, n2, H2[k]), false};
         CPALS_CUDA_TRY(mode_update(h, H2[k], solve, rtol, true, &tq));
     }
-    return cpals::fit_efficient(h, solve);
+    return fit_scoped(h, solve);
 }
 
 // FMA throughput probe kernels (dependent chains, 8 independent accumulators).
@@ -1026,6 +1108,41 @@ int cpals_iterate(cpals_handle* hh, int iters, double tol, int solve, double svd
         CUDA_OR_FAIL(h, cudaMemcpyAsync(fits_host, h->d_fit, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream),
                      "fit history read");
     }
+    return take_status(h);
+}
+
+int cpals_profile_sweeps(cpals_handle* hh, int sweeps, int solve, double svd_rtol, double* bucket_ms)
+{
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (sweeps < 1 || sweeps > 16 || !bucket_ms) return fail(h, CPALS_ERR_ARG, "%s", "sweeps in [1, 16], bucket_ms");
+    if (solve < CPALS_SOLVE_QR || solve > CPALS_SOLVE_NORMAL_PINV) return fail(h, CPALS_ERR_ARG, "%s", "bad solve kind");
+    if (!h->have_X || !h->have_factors) return fail(h, CPALS_ERR_STATE, "%s", "tensor and factors must be set");
+    for (int i = 0; i < cpals::kProfMax; ++i) {
+        if (!h->prof_a[i]) CUDA_OR_FAIL(h, cudaEventCreate(&h->prof_a[i]), "profile events");
+        if (!h->prof_b[i]) CUDA_OR_FAIL(h, cudaEventCreate(&h->prof_b[i]), "profile events");
+    }
+    CUDA_OR_FAIL(h, refresh_derived(h, solve, -1), "refresh derived factors");
+    CUDA_OR_FAIL(h, cudaMemsetAsync(h->d_fit_count, 0, sizeof(int), h->stream), "reset fit count");
+    // every phase on the handle's stream, one after the other
+    cudaStream_t side = h->side;
+    h->side = h->stream;
+    h->prof = true;
+    h->prof_n = 0;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < sweeps && e == cudaSuccess; ++k) e = sweep(h, solve, svd_rtol);
+    h->prof = false;
+    h->side = side;
+    CUDA_OR_FAIL(h, e, "profiled sweep");
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream), "profile sync");
+    for (int b = 0; b < cpals::kProfBuckets; ++b) bucket_ms[b] = 0.0;
+    for (int i = 0; i < h->prof_n; ++i) {
+        float ms = 0.f;
+        CUDA_OR_FAIL(h, cudaEventElapsedTime(&ms, h->prof_a[i], h->prof_b[i]), "profile event time");
+        bucket_ms[h->prof_bucket[i]] += ms / sweeps;
+    }
+    if (h->prof_n >= cpals::kProfMax) return fail(h, CPALS_ERR_ARG, "%s", "too many phases: profile fewer sweeps");
+    h->last_sweep_solve = solve;
     return take_status(h);
 }
 

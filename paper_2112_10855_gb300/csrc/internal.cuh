@@ -16,6 +16,13 @@ constexpr int kStatusOk = 0;
 
 // kMaxN, kMaxRank, TtmShape, ttm_shape and ttm_order come from ttm_plan.h.
 
+// Phase buckets of cpals_profile_sweeps (the component breakdown of the
+// paper's Table its_parts): the pass over X (Multi-TTM, or MTTKRP), the
+// factor QR (or Gram), computing Q0 (QR of V_n), applying Q0 (W = Y_(n) Q0),
+// and the rest (solve operators, fit).
+enum { kProfTTM = 0, kProfFactor = 1, kProfQ0 = 2, kProfApplyQ0 = 3, kProfOther = 4, kProfBuckets = 5 };
+constexpr int kProfMax = 1024;
+
 // ------------------------------------------------------------------ handle
 struct Handle {
     int N = 0, R = 0, prec = CPALS_F64;
@@ -121,6 +128,13 @@ struct Handle {
     int64_t graph_nodes[4] = {0, 0, 0, 0};
 
     int64_t launches = 0;
+    // phase timing: while prof is set, an eagerly run sweep records a pair of
+    // events on the handle's stream around each phase (prof_n pairs so far)
+    bool prof = false;
+    int prof_n = 0;
+    int prof_bucket[kProfMax] = {0};
+    cudaEvent_t prof_a[kProfMax] = {nullptr};
+    cudaEvent_t prof_b[kProfMax] = {nullptr};
     // Kruskal-tensor input (Sec. 3.3.2): X = sum_s mu_s v_s^(1) o ... o v_s^(N),
     // V_m = KV[m] (I_m x S); C_m = Q_m^T V_m (R x S) for the QR solves, E_m =
     // V_m^T A_m (S x R) for the normal equations; the Gram V_m^T V_m of each

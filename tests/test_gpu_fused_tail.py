@@ -125,3 +125,24 @@ def test_newton_reciprocals_within_two_ulp(cuda_lib):
     neg = torch.tensor([-2.0, -1e-10, -1e20], dtype=torch.float64, device="cuda")
     r, _ = cpals.test_newton_recip(neg)
     np.testing.assert_allclose(r.cpu().numpy(), 1.0 / neg.cpu().numpy(), rtol=5e-16)
+
+
+@pytest.mark.parametrize("solve", ["qr", "svd", "normal"])
+def test_profiled_sweeps_match_graph_sweeps(cuda_lib, solve):
+    # cpals_profile_sweeps runs the same sweeps eagerly on one stream: the
+    # factors it leaves equal those of cpals_iterate bit for bit, and every
+    # bucket it reports is a non-negative time
+    dims, R = (40, 36, 32), 6
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal(int(np.prod(dims)))
+    A = [np.asfortranarray(rng.standard_normal((d, R))) for d in dims]
+    h1, _ = handles(dims, R, X, A)
+    h2, _ = handles(dims, R, X, A)
+    h1.iterate(2, solve=solve, svd_rtol=1e-10)
+    b = h2.profile_sweeps(2, solve=solve, svd_rtol=1e-10)
+    assert set(b) == {"multi_ttm_or_mttkrp", "factor_qr_or_gram", "compute_q0", "apply_q0", "other"}
+    assert all(v >= 0.0 for v in b.values()) and b["multi_ttm_or_mttkrp"] > 0.0
+    if solve != "normal":
+        assert b["compute_q0"] > 0.0 and b["apply_q0"] > 0.0
+    for a1, a2 in zip(h1.get_factors()[0], h2.get_factors()[0]):
+        np.testing.assert_array_equal(a1, a2)
