@@ -299,7 +299,12 @@ int cpals_sync(cpals_handle* h);
  *    svd_rtol * sigma_max (sigma_min >= 1/||X||_F, sigma_max <= ||R0||_F), so
  *    the truncated solve is W R0^-T exactly and the operator R0^-T is used
  *    without the SVD.  Otherwise the Jacobi SVD runs as with 0.  The two
- *    differ only by rounding. */
+ *    differ only by rounding.
+ *  CPALS_OPT_APPLY_Q0_FP32 (default 1): with CPALS_F32 / BF16X3 / TF32X3,
+ *    the mode updates keep the Multi-TTM's unfolding Y_(n) in FP32 and form
+ *    W_n = Y_(n) Q0 (Eq. ls-qr-q0-step) in FP32, one more contraction of the
+ *    FP32 chain, before the FP64 solve.  0 widens Y_(n) to FP64 and forms W
+ *    in FP64.  The explicit cpals_multi_ttm keeps FP64 either way. */
 typedef enum {
     CPALS_OPT_DIMTREE = 0,
     CPALS_OPT_TC_PIPELINE = 1,
@@ -307,7 +312,8 @@ typedef enum {
     CPALS_OPT_F32_PIPELINE = 3,
     CPALS_OPT_TEST_WITHHOLD_COPIES = 4,
     CPALS_OPT_FUSED_TAIL = 5,
-    CPALS_OPT_SVD_SHORTCUT = 6
+    CPALS_OPT_SVD_SHORTCUT = 6,
+    CPALS_OPT_APPLY_Q0_FP32 = 7
 } cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
 

@@ -218,6 +218,10 @@ class CPALS:
         """CPALS_OPT_SVD_SHORTCUT: skip the Jacobi SVD when a norm bound proves nothing is truncated."""
         _check(self._h, load().cpals_set_option(self._h, 6, 1 if on else 0))
 
+    def set_apply_q0_fp32(self, on: bool):
+        """CPALS_OPT_APPLY_Q0_FP32: mixed precisions form W = Y_(n) Q0 in FP32."""
+        _check(self._h, load().cpals_set_option(self._h, 7, 1 if on else 0))
+
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
 

@@ -75,7 +75,7 @@ void free_all(Handle* h)
 {
     auto f = [](void* p) { if (p) cudaFree(p); };
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->A[m]); f(h->Q[m]); f(h->Rf[m]); f(h->G[m]); }
-    f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->Ahat); f(h->M); f(h->S); f(h->T);
+    f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->W32); f(h->Ahat); f(h->M); f(h->S); f(h->T);
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
     f(h->HQ[0]); f(h->HQ[1]); f(h->HR[0]); f(h->HR[1]); f(h->Qin);
     f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_gate); f(h->d_svd_gate); f(h->d_normX2); f(h->d_fit);
@@ -304,7 +304,6 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
                         const TreeQR* tq = nullptr)
 {
     CPALS_CUDA_TRY(refresh_derived(h, solve, n));
-    const int64_t In = h->dims[n];
     if (h->kruskal) {
         // Kruskal input (Sec. 3.3.2): no pass over a dense tensor
         if (is_normal(solve)) {
@@ -380,12 +379,15 @@ cudaError_t mode_update(Handle* h, int n, int solve, double rtol, bool from_part
         h->krp_mode = n;
         {
             ProfScope ps(h, cpals::kProfTTM);
-            if (from_partial) CPALS_CUDA_TRY(cpals::multi_ttm_from_partial(h, n));
-            else CPALS_CUDA_TRY(cpals::multi_ttm(h, n, h->Q));
+            // mixed precisions: the unfolding stays FP32 for W in FP32
+            h->yn32_mode = h->prec != CPALS_F64 && h->q0_fp32;
+            cudaError_t e = from_partial ? cpals::multi_ttm_from_partial(h, n) : cpals::multi_ttm(h, n, h->Q);
+            h->yn32_mode = false;
+            CPALS_CUDA_TRY(e);
         }
         CPALS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
         ProfScope ps(h, cpals::kProfApplyQ0);
-        CPALS_CUDA_TRY(cpals::gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W));
+        CPALS_CUDA_TRY(cpals::apply_q0(h, n));
     }
     return finish_update(h, n, solve, rtol, true);
 }
@@ -598,6 +600,7 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
     ok = ok && dalloc(h, &h->lambda, R) == cudaSuccess &&
          dalloc(h, &h->Q0, h->RN1 * R) == cudaSuccess && dalloc(h, &h->R0, (size_t)R * R) == cudaSuccess &&
          dalloc(h, &h->Yn, h->Imax * h->RN1) == cudaSuccess && dalloc(h, &h->W, h->Imax * R) == cudaSuccess &&
+         dalloc(h, &h->W32, h->Imax * R) == cudaSuccess &&
          dalloc(h, &h->Ahat, h->Imax * R) == cudaSuccess && dalloc(h, &h->M, h->Imax * R) == cudaSuccess &&
          dalloc(h, &h->S, (size_t)R * R) == cudaSuccess && dalloc(h, &h->T, (size_t)R * R) == cudaSuccess &&
          dalloc(h, &h->KM, (size_t)R * R * R) == cudaSuccess && dalloc(h, &h->KQ, (size_t)R * R * R) == cudaSuccess &&
@@ -1189,6 +1192,7 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
         case CPALS_OPT_TEST_WITHHOLD_COPIES: field = &h->test_withhold; break;
         case CPALS_OPT_FUSED_TAIL: field = &h->fused_tail; break;
         case CPALS_OPT_SVD_SHORTCUT: field = &h->svd_shortcut; break;
+        case CPALS_OPT_APPLY_Q0_FP32: field = &h->q0_fp32; break;
         default: break;
     }
     if (!field || (value != 0 && value != 1)) return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");

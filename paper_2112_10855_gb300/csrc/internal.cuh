@@ -57,6 +57,12 @@ struct Handle {
     double* R0 = nullptr;    // R x R
     double* Yn = nullptr;    // Imax x R^{N-1} (unfolding, FP64)
     double* W = nullptr;     // Imax x R
+    float* W32 = nullptr;    // Imax x R: W in FP32 before widening (mixed precisions)
+    // mixed precisions inside a mode update: the Multi-TTM leaves an FP32
+    // unfolding (yn32, in a TTM buffer) for W = Y_(n) Q0 in FP32
+    bool yn32_mode = false;
+    bool q0_fp32 = true;     // CPALS_OPT_APPLY_Q0_FP32
+    const float* yn32 = nullptr;
     double* Ahat = nullptr;  // Imax x R
     double* M = nullptr;     // Imax x R (MTTKRP)
     double* S = nullptr;     // R x R (Hadamard of Grams)
@@ -230,6 +236,8 @@ cudaError_t krp_qr_tree(Handle* h, int n, int slot, bool other_left, const int* 
 // C (m x n) = A (m x k) B (k x n), FP64, column-major, on the TTM kernel (one thread per output row, R-wide
 // register tile, split-K): used for W = Y_(n) Q0 and W T.
 cudaError_t gemm_rows(Handle* h, const double* A, int64_t m, int64_t k, const double* B, int n, double* C);
+// W_n = Y_(n) Q0 into h->W: FP32 from h->yn32 when the Multi-TTM left it, else FP64 from h->Yn.
+cudaError_t apply_q0(Handle* h, int n);
 // Solve Ahat R0^T = W (QR) or Ahat = W U pinv(S) V^T (SVD) into h->Ahat.
 cudaError_t solve_qr(Handle* h, int64_t In);
 // T = U pinv(Sigma) V^T of R0 (truncated one-sided Jacobi SVD) into h->T; it

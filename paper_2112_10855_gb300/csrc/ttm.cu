@@ -456,6 +456,29 @@ __global__ void unfold_kernel(const T* __restrict__ in, double* __restrict__ Yn,
     }
 }
 
+// The same unfolding in FP32 (no conversion).
+__global__ void unfold32_kernel(const float* __restrict__ in, float* __restrict__ Yn, int64_t Rn, int64_t In,
+                                int64_t total, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = e % Rn;
+        const int64_t q = e / Rn;
+        const int64_t i = q % In;
+        const int64_t c = q / In;
+        Yn[i + In * (a + Rn * c)] = in[e];
+    }
+}
+
+__global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out, int64_t n,
+                             const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = (double)in[e];
+}
+
 // Diagonal contraction of the MTTKRP: after the first TTM one mode (position
 // cpos) holds the rank index r; contracting mode m with A_m(:, r) keeps r:
 //   Out(l, t) = sum_k In(l, k, t) * A(k, r(l, t)).
@@ -550,13 +573,27 @@ cudaError_t ttm_chain(Handle* h, const T* in, int64_t* d, const int* modes_in, i
     return cudaSuccess;
 }
 
-// Final Multi-TTM tensor of mode n (R in every other mode) to the FP64 unfolding Y_(n).
+// Final Multi-TTM tensor of mode n (R in every other mode) to the unfolding
+// Y_(n): FP64 into h->Yn, or -- for an FP32 Multi-TTM inside a mode update
+// with h->yn32_mode -- FP32 into the TTM buffer that does not hold `in`
+// (h->yn32), for W = Y_(n) Q0 in FP32.
 template <typename T>
 cudaError_t unfold_yn(Handle* h, const T* in, int n)
 {
     int64_t Rn = 1;
     for (int m = 0; m < n; ++m) Rn *= h->R;
     const int64_t total = h->dims[n] * h->RN1;
+    if constexpr (sizeof(T) == 4) {
+        if (h->yn32_mode) {
+            float* out = (in == (const T*)h->tbuf[0]) ? (float*)h->tbuf[1] : (float*)h->tbuf[0];
+            unfold32_kernel<<<grid_for(total, 256, h->num_sms), 256, 0, h->stream>>>(in, out, Rn, h->dims[n], total,
+                                                                                    h->d_status);
+            h->launches++;
+            h->yn32 = out;
+            return cudaGetLastError();
+        }
+    }
+    h->yn32 = nullptr;
     unfold_kernel<T><<<grid_for(total, 256, h->num_sms), 256, 0, h->stream>>>(in, h->Yn, Rn, h->dims[n], total,
                                                                                h->d_status);
     h->launches++;
@@ -804,6 +841,28 @@ cudaError_t multi_ttm(Handle* h, int n, const double* const* Q)
 {
     if (h->prec == CPALS_F64) return multi_ttm_impl<double>(h, n, Q);
     return multi_ttm_impl<float>(h, n, Q);
+}
+
+// W_n = Y_(n) Q0 (Eq. ls-qr-q0-step).  After an FP32 Multi-TTM with the
+// FP32 unfolding (h->yn32), the product runs in FP32 like the contractions
+// before it (one more TTM, K = R^{N-1}) and W is widened to FP64 for the
+// solve; otherwise FP64 from h->Yn.
+cudaError_t apply_q0(Handle* h, int n)
+{
+    const int64_t In = h->dims[n];
+    if (h->yn32) {
+        // few rows and a long K: the row kernels with K split over the SMs
+        // (the TMA-ring kernel keeps one CTA per row tile)
+        const TtmShape s{In, h->RN1, 1};
+        CPALS_CUDA_TRY(launch_ttm_split<float>(h, h->yn32, h->Q0, h->RN1, h->W32, s, h->R, (float*)h->scratch,
+                                               h->scratch_elems * 2));
+        const int64_t total = In * h->R;
+        widen_kernel<<<grid_for(total, 256, h->num_sms), 256, 0, h->stream>>>(h->W32, h->W, total, h->d_status);
+        h->launches++;
+        h->yn32 = nullptr;
+        return cudaGetLastError();
+    }
+    return gemm_rows(h, h->Yn, In, h->RN1, h->Q0, h->R, h->W);
 }
 
 // C (m x n) = A (m x k) B (k x n), column-major FP64: a TTM with L = m,

@@ -74,3 +74,27 @@ def test_mixed_converged_fit_matches_fp64_oracle(cuda_lib, name, precision):
     fit = h.fit(direct=True)
     gap = abs(fit - ref["fit_direct"]) / ref["fit_direct"]
     assert gap <= 1e-6, (name, precision, fit, ref["fit_direct"], gap, ref["sweeps"])
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16x3", "tf32x3"])
+def test_w_in_fp32_matches_fp64_w_after_one_sweep(cuda_lib, precision):
+    # W = Y_(n) Q0 formed in FP32 (the default for the mixed precisions)
+    # against the same handle forming it in FP64 from the widened Y_(n).  The
+    # FP32 sum over R^{N-1} = 8000 terms carries ~sqrt(8000) 2^-24 = 5e-6
+    # relative error, which the solve amplifies by the conditioning of R0
+    # (~10 for these factors): the factors after one sweep agree to 1e-4
+    cfg = PROBLEMS["4way_28x28x28x28_r20"]
+    p = inputs.planted(cfg["dims"], cfg["rank"], seed=cfg["seed"], init_seed=cfg["init_seed"], congruence=0.9,
+                       noise=0.01)
+    out = {}
+    for fp32_w in (True, False):
+        h = cpals.CPALS(p.dims, p.rank, precision)
+        h.set_apply_q0_fp32(fp32_w)
+        h.set_tensor(torch.from_numpy(p.X).cuda())
+        h.set_factors([np.asfortranarray(a) for a in p.init_factors])
+        h.iterate(1, solve="qr")
+        out[fp32_w] = h.get_factors()
+    (A1, l1), (A2, l2) = out[True], out[False]
+    err = max(np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(A1, A2))
+    assert err <= 1e-4, err
+    assert np.linalg.norm(l1 - l2) / np.linalg.norm(l2) <= 1e-4
