@@ -120,6 +120,8 @@ struct Handle {
     int* d_status = nullptr;
     int* d_gate = nullptr;          // fused tail: 1 when the factor QR falls back to Householder
     int* d_svd_gate = nullptr;      // SVD solve: 1 when truncation is possible and the Jacobi SVD must run
+    int* d_vgate = nullptr;         // QR of a Khatri-Rao fold step: 1 when the staircase Householder must run
+    double* VG = nullptr;           // R x R: the Gram of a fold step (written by its CholeskyQR2)
     bool svd_shortcut = true;       // CPALS_OPT_SVD_SHORTCUT
     bool fused_tail = true;         // CPALS_OPT_FUSED_TAIL
     double* d_normX2 = nullptr;
@@ -218,6 +220,10 @@ bool mode_tail_ok(int64_t I, int R);
 // The tail's Newton-Raphson 1/x and 1/sqrt(x) on n values (for their accuracy test).
 cudaError_t recip_check(const double* x, int64_t n, double* rcp, double* rsq, cudaStream_t st);
 cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double* Op, bool want_qr);
+// The same kernel's QR alone (CholeskyQR2 with its check) of an explicit
+// rows x R matrix V: Q (rows x R), R (R x R), the Gram V^T V into G (R x R);
+// *gate = 1 when CholeskyQR2 was refused and a Householder QR has to follow.
+cudaError_t cqr2_rows(Handle* h, const double* V, int64_t rows, double* Q, double* Rout, double* G, int* gate);
 // QR of V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->Q0, h->R0 (structured, V_n not formed).
 // With implicit = true Q0 is not formed either: the Q factors of the fold steps
 // go to h->KP (for the Kruskal-input path) and only R0 is written.

@@ -497,9 +497,9 @@ constexpr int kStairMaxN = 32;
 
 __global__ void __launch_bounds__(kQrThreads) krp_stair_qr_kernel(
     const double* __restrict__ F, const double* __restrict__ G, int n, double* __restrict__ Qout,
-    double* __restrict__ Rout, const int* __restrict__ status)
+    double* __restrict__ Rout, const int* __restrict__ status, const int* __restrict__ gate)
 {
-    if (*status != kStatusOk) return;
+    if (*status != kStatusOk || (gate && *gate == 0)) return;
     extern __shared__ double sm[];
     const int tot = stair_off(n);
     double* W = sm;
@@ -1232,8 +1232,19 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
         // QR of F (.) R_B, F = Rl[k]: both factors are upper triangular
         auto step_qr = [&](double* Qo) -> cudaError_t {
             if (R <= kStairMaxN) {
+                const int* gate = nullptr;
+                if (h->fused_tail && mode_tail_ok((int64_t)R * R, R)) {
+                    // CholeskyQR2 of the explicit F (.) R_B in the cluster kernel; the
+                    // staircase Householder QR runs only if that was refused
+                    krp2_kernel<<<grid_for((int64_t)R * R * R, 256, h->num_sms), 256, 0, h->stream>>>(
+                        Rl[k], curR, R, h->KM, h->d_status);
+                    h->launches++;
+                    CPALS_CUDA_TRY(cudaGetLastError());
+                    CPALS_CUDA_TRY(cqr2_rows(h, h->KM, (int64_t)R * R, Qo, Ro, h->VG, h->d_vgate));
+                    gate = h->d_vgate;
+                }
                 krp_stair_qr_kernel<<<1, kQrThreads, stair_smem_bytes(R), h->stream>>>(Rl[k], curR, R, Qo, Ro,
-                                                                                       h->d_status);
+                                                                                       h->d_status, gate);
                 h->launches++;
                 return cudaGetLastError();
             }

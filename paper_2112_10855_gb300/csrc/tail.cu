@@ -514,10 +514,12 @@ bool mode_tail_ok(int64_t I, int R)
     return TailSmem(R, rl, 1).total * sizeof(double) <= kTailSmemMax;
 }
 
-cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double* Op, bool want_qr)
+namespace {
+
+// Launch the cluster kernel for I rows with the arguments of a.
+cudaError_t launch_tail(Handle* h, int64_t I, TailArgs a)
 {
-    const int64_t I = h->dims[n];
-    const int R = h->R;
+    const int R = a.R;
     if (!mode_tail_ok(I, R)) return cudaErrorInvalidValue;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
@@ -529,21 +531,7 @@ cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double*
     });
     CPALS_CUDA_TRY(attr_err);
     int C = tail_cluster(I);
-    TailArgs a;
-    a.W = W;
-    a.Op = Op;
     a.I = I;
-    a.R = R;
-    a.kind = kind;
-    a.want_qr = want_qr ? 1 : 0;
-    a.Ahat = h->Ahat;
-    a.A = h->A[n];
-    a.lambda = h->lambda;
-    a.G = h->G[n];
-    a.Q = h->Q[n];
-    a.Rf = h->Rf[n];
-    a.gate = h->d_gate;
-    a.status = h->d_status;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -558,7 +546,7 @@ cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double*
     for (;;) {
         const int rl = (int)((I + C - 1) / C);
         cfg.gridDim = dim3((unsigned)C);
-        cfg.dynamicSmemBytes = TailSmem(R, rl, kind).total * sizeof(double);
+        cfg.dynamicSmemBytes = TailSmem(R, rl, a.kind).total * sizeof(double);
         attr[0].val.clusterDim.x = (unsigned)C;
         int nclusters = 0;
         if (C <= 8 || (cudaOccupancyMaxActiveClusters(&nclusters, mode_tail_kernel, &cfg) == cudaSuccess &&
@@ -571,6 +559,46 @@ cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double*
     CPALS_CUDA_TRY(cudaLaunchKernelEx(&cfg, mode_tail_kernel, a));
     h->launches++;
     return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double* Op, bool want_qr)
+{
+    TailArgs a;
+    a.W = W;
+    a.Op = Op;
+    a.R = h->R;
+    a.kind = kind;
+    a.want_qr = want_qr ? 1 : 0;
+    a.Ahat = h->Ahat;
+    a.A = h->A[n];
+    a.lambda = h->lambda;
+    a.G = h->G[n];
+    a.Q = h->Q[n];
+    a.Rf = h->Rf[n];
+    a.gate = h->d_gate;
+    a.status = h->d_status;
+    return launch_tail(h, h->dims[n], a);
+}
+
+cudaError_t cqr2_rows(Handle* h, const double* V, int64_t rows, double* Q, double* Rout, double* G, int* gate)
+{
+    TailArgs a;
+    a.W = V;
+    a.Op = nullptr;
+    a.R = h->R;
+    a.kind = 4;
+    a.want_qr = 1;
+    a.Ahat = nullptr;
+    a.A = nullptr;
+    a.lambda = nullptr;
+    a.G = G;
+    a.Q = Q;
+    a.Rf = Rout;
+    a.gate = gate;
+    a.status = h->d_status;
+    return launch_tail(h, rows, a);
 }
 
 }  // namespace cpals
