@@ -163,7 +163,7 @@ inline bool is_normal(int solve) { return solve == CPALS_SOLVE_NORMAL || solve =
 cudaError_t factor_qr_gram(Handle* h, int m, bool want_qr)
 {
     const int64_t I = h->dims[m];
-    if (h->fused_tail && cpals::mode_tail_ok(I, h->R)) {
+    if (h->fused_tail && cpals::mode_tail_ok(I, h->R, 1)) {
         CPALS_CUDA_TRY(cpals::mode_tail(h, m, 4, h->A[m], nullptr, want_qr));
         if (want_qr) CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], I, h->R, h->Q[m], h->Rf[m], true, h->d_gate));
         return cudaSuccess;

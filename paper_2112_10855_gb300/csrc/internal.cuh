@@ -216,7 +216,9 @@ cudaError_t householder_qr(Handle* h, const double* A, int64_t m, int n, double*
 // (kind 0: Ahat R0^T = W; 1: Ahat = W T; 2: Ahat S = M with S = L L^T; 3: Ahat
 // given in h->Ahat), lambda, A_n, G_n and, with want_qr, Q_n R_n by
 // CholeskyQR2 (h->d_gate = 1 when the Householder QR has to take over).
-bool mode_tail_ok(int64_t I, int R);
+// kind: 0..2 solve from W (an R x R operator), 3 from Ahat, 4 the QR of a
+// given matrix; the default asks about every kind.
+bool mode_tail_ok(int64_t I, int R, int kind = 1);
 // The tail's Newton-Raphson 1/x and 1/sqrt(x) on n values (for their accuracy test).
 cudaError_t recip_check(const double* x, int64_t n, double* rcp, double* rsq, cudaStream_t st);
 cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double* Op, bool want_qr);

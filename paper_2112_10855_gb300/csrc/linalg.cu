@@ -1233,7 +1233,7 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
         auto step_qr = [&](double* Qo) -> cudaError_t {
             if (R <= kStairMaxN) {
                 const int* gate = nullptr;
-                if (h->fused_tail && mode_tail_ok((int64_t)R * R, R)) {
+                if (h->fused_tail && mode_tail_ok((int64_t)R * R, R, 4)) {
                     // CholeskyQR2 of the explicit F (.) R_B in the cluster kernel; the
                     // staircase Householder QR runs only if that was refused
                     krp2_kernel<<<grid_for((int64_t)R * R * R, 256, h->num_sms), 256, 0, h->stream>>>(
@@ -1252,7 +1252,13 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
                                                                                               h->d_status);
             h->launches++;
             CPALS_CUDA_TRY(cudaGetLastError());
-            return householder_qr(h, h->KM, (int64_t)R * R, R, Qo, Ro, false);
+            const int* gate = nullptr;
+            if (h->fused_tail && mode_tail_ok((int64_t)R * R, R, 4)) {
+                // CholeskyQR2 in the cluster kernel; the TSQR runs only if that was refused
+                CPALS_CUDA_TRY(cqr2_rows(h, h->KM, (int64_t)R * R, Qo, Ro, h->VG, h->d_vgate));
+                gate = h->d_vgate;
+            }
+            return householder_qr(h, h->KM, (int64_t)R * R, R, Qo, Ro, false, gate);
         };
         if (implicit) {
             CPALS_CUDA_TRY(step_qr(h->KP + (size_t)(k - 1) * R3));

@@ -62,7 +62,7 @@ namespace {
 constexpr int kTailThreads = 512;
 constexpr int kTailWarps = kTailThreads / 32;
 constexpr int kTailMaxCluster = 16;
-constexpr size_t kTailSmemMax = 200 * 1024;
+constexpr size_t kTailSmemMax = 210 * 1024;
 // Q1^T Q1 within this of the identity (entrywise) after the first pass
 constexpr double kCqrCheck = 1e-2;
 
@@ -94,14 +94,18 @@ struct TailSmem {
     {
         nE = R * (R + 1) / 2;
         const size_t RR = (size_t)R * R;
+        // the solve operator (kinds 0..2) also holds R1 later; kinds 3 and 4
+        // have no operator and park R1 in the output R instead
         op = 0;
-        gw = op + RR;
+        gw = op + (kind <= 2 ? RR : 0);
         pa = gw + RR;
         pb = pa + (size_t)nE;
         gp = pb + (size_t)nE;
         piv = gp + (size_t)kTailThreads;   // kTailThreads >= (kTailThreads / R) * R for the column sums
         rows = piv + (size_t)2 * R;
-        rows2 = rows + (size_t)rl * (R + 1);
+        // the stash also stages R2 R1 (R x R) at the end for kinds 3 and 4
+        const size_t stash = (size_t)rl * (R + 1) > RR ? (size_t)rl * (R + 1) : RR;
+        rows2 = rows + stash;
         total = rows2 + (kind == 1 ? (size_t)rl * (R + 1) : 0);
     }
 };
@@ -414,10 +418,16 @@ __global__ void __launch_bounds__(kTailThreads, 1) mode_tail_kernel(TailArgs g)
         if (g.want_qr) {
             // 3. the first CholeskyQR pass: R1 = chol(G_n), Q1 = A_n R1^-1
             qr_ok = block_cholesky(Gw, R, piv, dinv, &flag_bad);
-            for (int e = tid; e < R * R; e += kTailThreads) Mo[e] = Gw[e];   // R1 (the solve operator is spent)
+            // keep R1: in Mo (the solve operator is spent), or in the output R
+            // (CTA 0) when there is no operator buffer
+            if (solve) {
+                for (int e = tid; e < R * R; e += kTailThreads) Mo[e] = Gw[e];
+            } else if (c == 0) {
+                for (int e = tid; e < R * R; e += kTailThreads) g.Rf[e] = Gw[e];
+            }
             __syncthreads();
             if (qr_ok) {
-                subst_rows(rows, ld, rl, Mo, dinv, R, T, false, true);      // R1^T q^T = a^T
+                subst_rows(rows, ld, rl, solve ? Mo : Gw, dinv, R, T, false, true);   // R1^T q^T = a^T
                 __syncthreads();
                 local_gram(rows, rl, R, gp, pa);
             }
@@ -449,11 +459,25 @@ __global__ void __launch_bounds__(kTailThreads, 1) mode_tail_kernel(TailArgs g)
                 g.Q[(r0 + li) + g.I * e] = rows[li * ld + e];
             }
             if (c == 0) {
-                for (int e = tid; e < R * R; e += kTailThreads) {
-                    const int a = e % R, b = e / R;
-                    double s = 0.0;
-                    for (int k = a; k <= b; ++k) s = fma(Gw[a + R * k], Mo[k + R * b], s);
-                    g.Rf[e] = (a <= b) ? s : 0.0;
+                if (solve) {
+                    for (int e = tid; e < R * R; e += kTailThreads) {
+                        const int a = e % R, b = e / R;
+                        double s = 0.0;
+                        for (int k = a; k <= b; ++k) s = fma(Gw[a + R * k], Mo[k + R * b], s);
+                        g.Rf[e] = (a <= b) ? s : 0.0;
+                    }
+                } else {
+                    // R1 from the output R, R2 R1 through the row stash (the
+                    // rows are written out above), then back to the output
+                    __syncthreads();
+                    for (int e = tid; e < R * R; e += kTailThreads) {
+                        const int a = e % R, b = e / R;
+                        double s = 0.0;
+                        for (int k = a; k <= b; ++k) s = fma(Gw[a + R * k], g.Rf[k + R * b], s);
+                        rows[e] = (a <= b) ? s : 0.0;
+                    }
+                    __syncthreads();
+                    for (int e = tid; e < R * R; e += kTailThreads) g.Rf[e] = rows[e];
                 }
             }
         }
@@ -506,12 +530,12 @@ cudaError_t recip_check(const double* x, int64_t n, double* rcp, double* rsq, cu
     return cudaGetLastError();
 }
 
-bool mode_tail_ok(int64_t I, int R)
+bool mode_tail_ok(int64_t I, int R, int kind)
 {
     if (R < 1 || R > kMaxRank || I < 1) return false;
     const int C = tail_cluster(I);
     const int rl = (int)((I + C - 1) / C);
-    return TailSmem(R, rl, 1).total * sizeof(double) <= kTailSmemMax;
+    return TailSmem(R, rl, kind).total * sizeof(double) <= kTailSmemMax;
 }
 
 namespace {
@@ -520,7 +544,7 @@ namespace {
 cudaError_t launch_tail(Handle* h, int64_t I, TailArgs a)
 {
     const int R = a.R;
-    if (!mode_tail_ok(I, R)) return cudaErrorInvalidValue;
+    if (!mode_tail_ok(I, R, a.kind)) return cudaErrorInvalidValue;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
