@@ -494,6 +494,11 @@ inline bool qr_leaf_fits(int64_t mb, int n) { return qr_smem_bytes(mb, n) <= kQr
 // ---------------------------------------------------------------- staircase QR of F (.) G
 // (stair_qr_block in dev_common.cuh) as a kernel of its own: one CTA.
 constexpr int kStairMaxN = 32;
+// Fold steps go through the cluster kernel's CholeskyQR2 from this rank up.
+// Below it the one-CTA staircase kernel is about as fast (38 us at R = 10)
+// and, needing a single SM, runs on the side stream beside a pass over X,
+// while a 16-CTA cluster waits for that pass to free the SMs.
+constexpr int kFoldCqrMinR = 16;
 
 __global__ void __launch_bounds__(kQrThreads) krp_stair_qr_kernel(
     const double* __restrict__ F, const double* __restrict__ G, int n, double* __restrict__ Qout,
@@ -1233,7 +1238,7 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
         auto step_qr = [&](double* Qo) -> cudaError_t {
             if (R <= kStairMaxN) {
                 const int* gate = nullptr;
-                if (h->fused_tail && mode_tail_ok((int64_t)R * R, R, 4)) {
+                if (h->fused_tail && R >= kFoldCqrMinR && mode_tail_ok((int64_t)R * R, R, 4)) {
                     // CholeskyQR2 of the explicit F (.) R_B in the cluster kernel; the
                     // staircase Householder QR runs only if that was refused
                     krp2_kernel<<<grid_for((int64_t)R * R * R, 256, h->num_sms), 256, 0, h->stream>>>(
