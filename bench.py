@@ -235,19 +235,124 @@ def _oracle_replica(task):
     return sweeps / (time.perf_counter() - t0)
 
 
+_ONE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def _replica_map(fn, tasks):
+    """fn over tasks, one spawned process each (spawned, not forked: the
+    parent holds a CUDA context).  The replicas' numpy runs on one thread
+    each, so that one replica's set-up does not crowd another's timed oracle
+    work."""
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in _ONE_THREAD_ENV}
+    os.environ.update({k: "1" for k in _ONE_THREAD_ENV})
+    try:
+        with mp.get_context("spawn").Pool(len(tasks)) as pool:
+            return pool.map(fn, tasks)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
 def cpu_oracle_all_cores(size, rank_, sweeps=1, solve=0):
     """The oracle as it stands (single-threaded plain C) on every host core
     at once: one independent replica per core in spawned processes (spawned,
     not forked, because the parent holds a CUDA context); the aggregate rate
     is the sum of the replicas' sweeps per second."""
-    import multiprocessing as mp
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    with mp.get_context("spawn").Pool(cores) as pool:
-        rates = pool.map(_oracle_replica, [(size, rank_, sweeps, solve)] * cores)
+    rates = _replica_map(_oracle_replica, [(size, rank_, sweeps, solve)] * cores)
     return float(sum(rates)), cores, time.perf_counter() - t0
+
+
+def _sample_problem(kind, size):
+    """The host copy of workload `kind` (seeded generators) for an oracle
+    sample; `size` shrinks the cube of the 3-way rank-64 workload."""
+    from paper_2112_10855_gb300 import inputs
+    if kind == "c3":
+        return inputs.workload_c3(seed=2112)
+    if kind == "c5a":
+        return inputs.workload_c5a(seed=2112, size=size)
+    return inputs.planted((40,) * 5, 8, seed=2112, noise=0.01)
+
+
+def _oracle_sample(task):
+    """One single-threaded oracle replica timing a bounded sample of a
+    workload.  kind "batch": one sweep of each of the first problems of the
+    512-problem batch until `budget` seconds are spent; otherwise `modes` mode
+    updates of the (possibly shrunk) workload.  Returns (seconds, sweeps of
+    the sample done, elements of the sample)."""
+    kind, size, modes, solve, rtol, budget = task
+    import oracle
+    from paper_2112_10855_gb300 import inputs
+    if kind == "batch":
+        dims, ranks = inputs.batch_shapes(512, seed=2112)
+        probs = [inputs.planted(tuple(int(x) for x in dims[q]), int(ranks[q]), seed=2112 + q,
+                                init_seed=10855 + q, noise=0.01) for q in range(len(dims))]
+        t = 0.0
+        elems = 0
+        for pr in probs:
+            o = oracle.OracleCPALS(pr.X, pr.dims, pr.rank)
+            o.set_factors(pr.init_factors)
+            t0 = time.perf_counter()
+            o.iterate(1, solve=solve, rtol=rtol)
+            t += time.perf_counter() - t0
+            elems += pr.X.size
+            if t > budget:
+                break
+        return t, 1.0, elems
+    p = _sample_problem(kind, size)
+    o = oracle.OracleCPALS(p.X, p.dims, p.rank)
+    o.set_factors(p.init_factors)
+    t0 = time.perf_counter()
+    for n in range(modes):
+        o.update_mode(n, solve=solve, rtol=rtol)
+    return time.perf_counter() - t0, modes / len(p.dims), p.X.size
+
+
+def _host_mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def oracle_sample_baseline(kind, total_elems, sample, size=0, modes=1, solve=0, rtol=0.0, budget=20.0):
+    """cpu_baseline of a non-default workload: the oracle as it stands on a
+    bounded sample (`sample` says which), 1 host thread, then one replica per
+    host core in spawned processes, as many as a quarter of the free host
+    memory holds at four copies of the sample's tensor each.  Rates are
+    sweeps of the whole workload per second: the sample's sweeps scaled by
+    its share of the workload's elements (the sweep cost is led by passes over
+    X, linear in the element count)."""
+    import oracle
+    oracle.build()
+    task = (kind, size, modes, solve, rtol, budget)
+    t, sweeps, elems = _oracle_sample(task)
+    rate1 = sweeps / t * elems / total_elems
+    cpu = {"value": rate1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+           "sample_seconds": t, "sample_elements": int(elems), "workload_elements": int(total_elems)}
+    cores = os.cpu_count() or 1
+    per_replica = 4 * 8 * elems
+    replicas = min(cores, int(0.25 * _host_mem_available() // max(per_replica, 1)))
+    if replicas >= 2:
+        t0 = time.perf_counter()
+        res = _replica_map(_oracle_sample, [task] * replicas)
+        agg = sum(sw / tt * el / total_elems for tt, sw, el in res)
+        cpu["all_cores"] = {"value": agg, "unit": UNIT, "cores": replicas, "kind": "oracle",
+                            "sample": f"one replica of the same sample per core ({replicas} of {cores} cores, "
+                                      f"bounded by host memory); sum of the replicas' rates "
+                                      f"({time.perf_counter() - t0:.1f} s wall)"}
+    return cpu
 
 
 def run_reference(args, world, rank):
@@ -464,6 +569,21 @@ def run_mixed(args, world, rank):
         }
         if recovery is not None:
             line["planted_recovery"] = recovery
+        if world == 1 and not args.no_cpu_baseline:
+            sid = {"qr": 0, "svd": 1}[solve]
+            if args.workload == "c5a":
+                line["cpu_baseline"] = oracle_sample_baseline(
+                    "c5a", P, "one mode update (of three) of the same recipe on a 464^3 cube at rank 64, SVD "
+                    "solve, scaled by the element share (1.0e8 of 1e9) to sweeps of the 1000^3 workload",
+                    size=464, modes=1, solve=sid, rtol=rtol)
+            elif args.workload == "c3":
+                line["cpu_baseline"] = oracle_sample_baseline(
+                    "c3", P, "one mode update (of four, all of equal cost on the 120^4 cube) of the same "
+                    "workload", modes=1, solve=sid, rtol=rtol)
+            else:
+                line["cpu_baseline"] = oracle_sample_baseline(
+                    "c5b", P, "one full sweep (five mode updates) of the same workload", modes=5, solve=sid,
+                    rtol=rtol)
         print(json.dumps(line), flush=True)
 
 
@@ -666,6 +786,10 @@ def run_batch(args, world, rank):
             "speedup_batched_vs_per_problem": v_b / v_1,
             "fit_agreement_max_abs_diff_3_sweeps": max(diffs),
         }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_sample_baseline(
+                "batch", total_elems, "one oracle sweep of each of the first problems of the same batch until "
+                "about 20 s are spent, scaled by their share of the batch's elements", budget=20.0)
         print(json.dumps(line), flush=True)
 
 
