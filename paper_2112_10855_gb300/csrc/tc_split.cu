@@ -929,7 +929,9 @@ __global__ void __launch_bounds__(kF32Threads) ttm_f32_pipe_kernel(
     __syncthreads();
     if (skip) return;
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    // 128-byte aligned ring: an offset from the shared array itself, so the
+    // compiler still knows every X and Q read below is a shared-memory load
+    uint8_t* smem = smem_raw + ((128u - ((uint32_t)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u);
     const uint32_t qbytes = qres ? (uint32_t)nitems * C::kQItemBytes : 0u;
     const uint32_t stage = kF32XBytes + (qres ? 0u : C::kQItemBytes);
     uint8_t* qregion = smem;
