@@ -304,7 +304,16 @@ int cpals_sync(cpals_handle* h);
  *    the mode updates keep the Multi-TTM's unfolding Y_(n) in FP32 and form
  *    W_n = Y_(n) Q0 (Eq. ls-qr-q0-step) in FP32, one more contraction of the
  *    FP32 chain, before the FP64 solve.  0 widens Y_(n) to FP64 and forms W
- *    in FP64.  The explicit cpals_multi_ttm keeps FP64 either way. */
+ *    in FP64.  The explicit cpals_multi_ttm keeps FP64 either way.
+ *  CPALS_OPT_WIDE_TAIL (default 1; ranks above 32 with CPALS_OPT_FUSED_TAIL):
+ *    the CholeskyQR2 of the factor QRs (after the GPU-wide solve) and of the
+ *    Khatri-Rao fold steps of the QR of V_n runs as a chain of kernels over
+ *    every SM: Gram partials of row blocks summed in a fixed order, the
+ *    Cholesky factors and their triangular inverses in one CTA, and the row
+ *    products Q1 = A R1^-1, Q = Q1 R2^-1 over all rows.  The first Gram of a
+ *    fold step F (.) R_B is (F^T F) * (R_B^T R_B).  The acceptance check and
+ *    the Householder fallback are those of the cluster kernel.  0 keeps the
+ *    one-cluster kernel (16 SMs).  Results differ only by rounding. */
 typedef enum {
     CPALS_OPT_DIMTREE = 0,
     CPALS_OPT_TC_PIPELINE = 1,
@@ -313,7 +322,8 @@ typedef enum {
     CPALS_OPT_TEST_WITHHOLD_COPIES = 4,
     CPALS_OPT_FUSED_TAIL = 5,
     CPALS_OPT_SVD_SHORTCUT = 6,
-    CPALS_OPT_APPLY_Q0_FP32 = 7
+    CPALS_OPT_APPLY_Q0_FP32 = 7,
+    CPALS_OPT_WIDE_TAIL = 8
 } cpals_option;
 int cpals_set_option(cpals_handle* h, int option, int64_t value);
 

@@ -222,6 +222,10 @@ class CPALS:
         """CPALS_OPT_APPLY_Q0_FP32: mixed precisions form W = Y_(n) Q0 in FP32."""
         _check(self._h, load().cpals_set_option(self._h, 7, 1 if on else 0))
 
+    def set_wide_tail(self, on: bool):
+        """CPALS_OPT_WIDE_TAIL: above rank 32, CholeskyQR2 of the factors and fold steps over every SM."""
+        _check(self._h, load().cpals_set_option(self._h, 8, 1 if on else 0))
+
     def sync(self):
         _check(self._h, load().cpals_sync(self._h))
 

@@ -79,6 +79,7 @@ void free_all(Handle* h)
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
     f(h->HQ[0]); f(h->HQ[1]); f(h->HR[0]); f(h->HR[1]); f(h->Qin);
     f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_gate); f(h->d_svd_gate); f(h->d_vgate); f(h->VG); f(h->d_normX2); f(h->d_fit);
+    f(h->wide[0].base); f(h->wide[1].base);
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->KV[m]); f(h->KC[m]); f(h->KE[m]); }
     f(h->Kmu); f(h->KGV); f(h->KP); f(h->KMw[0]); f(h->KMw[1]);
@@ -90,6 +91,17 @@ void free_all(Handle* h)
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     for (int s = 0; s < 4; ++s) if (h->graph[s]) cudaGraphExecDestroy(h->graph[s]);
+}
+
+// The two workspaces of the GPU-wide CholeskyQR2 (rank above 32 only).
+bool alloc_wide(Handle* h)
+{
+    if (h->R <= 32) return true;
+    for (auto& ws : h->wide) {
+        if (dalloc(h, &ws.base, cpals::wide_ws_elems(h->R, h->num_sms)) != cudaSuccess) return false;
+        cpals::wide_ws_carve(ws, h->R, h->num_sms);
+    }
+    return true;
 }
 
 // Largest TTM intermediate over all modes and steps of the Multi-TTM (and MTTKRP).
@@ -163,7 +175,7 @@ inline bool is_normal(int solve) { return solve == CPALS_SOLVE_NORMAL || solve =
 cudaError_t factor_qr_gram(Handle* h, int m, bool want_qr)
 {
     const int64_t I = h->dims[m];
-    if (h->fused_tail && cpals::mode_tail_ok(I, h->R, 1)) {
+    if (h->fused_tail && (cpals::wide_tail_on(h) || cpals::mode_tail_ok(I, h->R, 1))) {
         CPALS_CUDA_TRY(cpals::mode_tail(h, m, 4, h->A[m], nullptr, want_qr));
         if (want_qr) CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], I, h->R, h->Q[m], h->Rf[m], true, h->d_gate));
         return cudaSuccess;
@@ -233,7 +245,7 @@ cudaError_t finish_update(Handle* h, int n, int solve, double rtol, bool have_op
 {
     const int64_t In = h->dims[n];
     const bool normal = is_normal(solve);
-    if (h->fused_tail && cpals::mode_tail_ok(In, h->R)) {
+    if (h->fused_tail && (cpals::wide_tail_on(h) || cpals::mode_tail_ok(In, h->R))) {
         int kind = 0;
         const double* Win = normal ? h->M : h->W;
         const double* Op = h->R0;
@@ -615,6 +627,7 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
     // tree levels above (4 m x R at most in total)
     h->qr_ws_elems = std::max<int64_t>(8 * big * R + 64 * R * R, 4096);
     ok = ok && dalloc(h, &h->qr_ws, h->qr_ws_elems) == cudaSuccess;
+    ok = ok && alloc_wide(h);
     if (ok) {
         int lo = 0, hi = 0;
         ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
@@ -733,6 +746,7 @@ int cpals_create_kruskal(const int64_t* dims, int N, int rank, int S, cpals_hand
         ok = dalloc(h, &h->Yn, h->Imax * h->RN1) == cudaSuccess;
     h->qr_ws_elems = std::max<int64_t>(8 * big * R + 64 * R * R, 4096);
     ok = ok && dalloc(h, &h->qr_ws, h->qr_ws_elems) == cudaSuccess;
+    ok = ok && alloc_wide(h);
     if (ok) {
         int lo = 0, hi = 0;
         ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
@@ -1195,6 +1209,7 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
         case CPALS_OPT_FUSED_TAIL: field = &h->fused_tail; break;
         case CPALS_OPT_SVD_SHORTCUT: field = &h->svd_shortcut; break;
         case CPALS_OPT_APPLY_Q0_FP32: field = &h->q0_fp32; break;
+        case CPALS_OPT_WIDE_TAIL: field = &h->wide_tail; break;
         default: break;
     }
     if (!field || (value != 0 && value != 1)) return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");

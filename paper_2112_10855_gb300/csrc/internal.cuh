@@ -24,6 +24,20 @@ enum { kProfTTM = 0, kProfFactor = 1, kProfQ0 = 2, kProfApplyQ0 = 3, kProfOther 
 constexpr int kProfMax = 1024;
 
 // ------------------------------------------------------------------ handle
+// Workspace of the GPU-wide CholeskyQR2 (one allocation, carved up): the
+// Gram partials of the row blocks, their group sums, the column sums of
+// squares of the row blocks, lambda, R1, R1^-1 and R2^-1.
+struct WideWs {
+    double* base = nullptr;
+    double* parts = nullptr;
+    double* gparts = nullptr;
+    double* cparts = nullptr;
+    double* lam = nullptr;
+    double* R1 = nullptr;
+    double* X1 = nullptr;
+    double* X2 = nullptr;
+};
+
 struct Handle {
     int N = 0, R = 0, prec = CPALS_F64;
     int64_t dims[kMaxN] = {0};
@@ -124,6 +138,11 @@ struct Handle {
     double* VG = nullptr;           // R x R: the Gram of a fold step (written by its CholeskyQR2)
     bool svd_shortcut = true;       // CPALS_OPT_SVD_SHORTCUT
     bool fused_tail = true;         // CPALS_OPT_FUSED_TAIL
+    bool wide_tail = true;          // CPALS_OPT_WIDE_TAIL
+    // GPU-wide CholeskyQR2 above rank 32 (tail.cu): [0] serves the mode tails
+    // and factor QRs (main stream), [1] the fold steps of the QR of V_n (side
+    // stream), so the two never share memory
+    WideWs wide[2];
     double* d_normX2 = nullptr;
     double* d_fit = nullptr;        // fit history ring
     int* d_fit_count = nullptr;
@@ -225,7 +244,18 @@ cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double*
 // The same kernel's QR alone (CholeskyQR2 with its check) of an explicit
 // rows x R matrix V: Q (rows x R), R (R x R), the Gram V^T V into G (R x R);
 // *gate = 1 when CholeskyQR2 was refused and a Householder QR has to follow.
-cudaError_t cqr2_rows(Handle* h, const double* V, int64_t rows, double* Q, double* Rout, double* G, int* gate);
+// V = F (.) B for upper-triangular R x R factors F, B (a Khatri-Rao fold step,
+// B's row index fastest) may pass them: above rank 32 the first Gram is then
+// (F^T F) * (B^T B) instead of a pass over V.
+cudaError_t cqr2_rows(Handle* h, const double* V, int64_t rows, double* Q, double* Rout, double* G, int* gate,
+                      const double* F = nullptr, const double* B = nullptr);
+// True when the tail of kind 3 or 4 (and cqr2_rows) runs the GPU-wide
+// CholeskyQR2 kernels instead of the cluster kernel (rank above 32); those
+// take any number of rows.
+bool wide_tail_on(const Handle* h);
+// Elements of one GPU-wide CholeskyQR2 workspace for rank R, and carving it up.
+int64_t wide_ws_elems(int R, int num_sms);
+void wide_ws_carve(WideWs& ws, int R, int num_sms);
 // QR of V_n (Khatri-Rao of the R_m, Sec. 3.1) into h->Q0, h->R0 (structured, V_n not formed).
 // With implicit = true Q0 is not formed either: the Q factors of the fold steps
 // go to h->KP (for the Kruskal-input path) and only R0 is written.

@@ -1258,9 +1258,10 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
             h->launches++;
             CPALS_CUDA_TRY(cudaGetLastError());
             const int* gate = nullptr;
-            if (h->fused_tail && mode_tail_ok((int64_t)R * R, R, 4)) {
-                // CholeskyQR2 in the cluster kernel; the TSQR runs only if that was refused
-                CPALS_CUDA_TRY(cqr2_rows(h, h->KM, (int64_t)R * R, Qo, Ro, h->VG, h->d_vgate));
+            if (h->fused_tail && (wide_tail_on(h) || mode_tail_ok((int64_t)R * R, R, 4))) {
+                // CholeskyQR2 (GPU-wide above rank 32, its first Gram from F and R_B); the
+                // TSQR runs only if that was refused
+                CPALS_CUDA_TRY(cqr2_rows(h, h->KM, (int64_t)R * R, Qo, Ro, h->VG, h->d_vgate, Rl[k], curR));
                 gate = h->d_vgate;
             }
             return householder_qr(h, h->KM, (int64_t)R * R, R, Qo, Ro, false, gate);

@@ -520,6 +520,324 @@ __global__ void recip_check_kernel(const double* __restrict__ x, int64_t n, doub
     }
 }
 
+// ------------------------------------------------------------------------
+// GPU-wide CholeskyQR2 (rank above 32).  There the tail's FP64 work per row is
+// R^2, and the cluster's 16 SMs hold a tenth of the GPU's FP64 rate, so the
+// kinds that start from Ahat or A (3, 4) and the fold-step QRs run as a chain
+// of kernels over every SM instead:
+//   colsq   column sums of squares of Ahat per row block            (kind 3)
+//   lambda  lambda_r = sqrt of their sum, in block order             (kind 3)
+//   rows    A_n = Ahat diag(lambda)^-1, and the Gram partial of A_n per row
+//           block (kind 4: of the A_n given)
+//   reduce  the partials summed in 16 fixed groups of blocks
+//   chol    G_n = the sum of the groups; R1 = chol(G_n) and R1^-1 (one CTA)
+//   rows    Q1 = A_n R1^-1 and the Gram partial of Q1 per row block
+//   reduce
+//   chol2   the check on Q1^T Q1, R2 = chol(Q1^T Q1), R2^-1, R_n = R2 R1
+//   rows    Q_n = Q1 R2^-1 (in place)
+// For a fold step V = F (.) B the first Gram is (F^T F) * (B^T B) entrywise
+// (the Gram of a Khatri-Rao product is the Hadamard product of the Grams),
+// O(R^3) work in the chol kernel instead of a pass over V.  Every sum runs in
+// a fixed order over a split of the rows that depends only on the row count,
+// so kind 4 on the A_n that kind 3 wrote repeats its Gram and QR bit for bit.
+// The substitutions use explicit triangular inverses, so each row's products
+// are independent FMAs over the whole GPU; the a-posteriori check and the
+// second pass are those of the cluster kernel.  The gate word is set by the
+// chol kernel (0 accepted so far, 1 refused) and the later kernels return at
+// once when it is 1.
+constexpr int kWideThreads = 256;
+constexpr int kWideChunk = 32;     // rows staged in shared memory at a time
+constexpr int kWideGroups = 16;    // fixed groups of row blocks in the reduction
+constexpr int kWideMaxE = (kMaxRank * (kMaxRank + 1) / 2 + kWideThreads - 1) / kWideThreads;
+
+// Row blocks of the split: about 8 rows each, at most two per SM.
+int wide_blocks(int64_t rows, int num_sms)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, 2LL * num_sms));
+}
+
+__device__ __forceinline__ bool wide_skip(const int* status, const int* gate)
+{
+    if (*(volatile const int*)status != kStatusOk) return true;
+    return gate != nullptr && *(volatile const int*)gate != 0;
+}
+
+// cparts[b][e] = sum over block b's rows of X(r, e)^2 (a warp per column,
+// lanes over rows, a fixed shuffle tree).
+__global__ void __launch_bounds__(kWideThreads) wide_colsq_kernel(const double* __restrict__ X, int64_t I, int R,
+                                                                  int nblk, double* __restrict__ cparts,
+                                                                  const int* __restrict__ status)
+{
+    if (wide_skip(status, nullptr)) return;
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)b * I / nblk, r1 = (int64_t)(b + 1) * I / nblk;
+    for (int e = warp; e < R; e += kWideThreads / 32) {
+        double s = 0.0;
+        for (int64_t r = r0 + lane; r < r1; r += 32) {
+            const double v = X[r + I * e];
+            s = fma(v, v, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) cparts[(size_t)b * R + e] = s;
+    }
+}
+
+// lambda_r = sqrt(sum over the blocks of cparts[b][r]): the blocks in
+// kWideThreads / R contiguous groups, then the groups in order.
+__global__ void __launch_bounds__(kWideThreads) wide_lambda_kernel(const double* __restrict__ cparts, int nblk, int R,
+                                                                   double* __restrict__ lambda_out,
+                                                                   double* __restrict__ lam,
+                                                                   const int* __restrict__ status)
+{
+    if (wide_skip(status, nullptr)) return;
+    __shared__ double red[kWideThreads];
+    const int tid = threadIdx.x, groups = kWideThreads / R, q = tid / R, e = tid - q * R;
+    double s = 0.0;
+    if (q < groups)
+        for (int b = q * nblk / groups; b < (q + 1) * nblk / groups; ++b) s += cparts[(size_t)b * R + e];
+    red[tid] = s;
+    __syncthreads();
+    if (tid < R) {
+        double t = red[tid];
+        for (int g = 1; g < groups; ++g) t += red[g * R + tid];
+        const double l = sqrt(t);
+        lam[tid] = l;
+        if (lambda_out) lambda_out[tid] = l;
+    }
+}
+
+// The row-block kernel.  Block b takes rows [b I / nblk, (b+1) I / nblk) in
+// chunks of kWideChunk rows staged in shared memory (row-major, ld R + 1):
+//   NORM:  a = x / lambda (lambda > 0; else a = x), written to out;
+//   APPLY: a = x X for the upper-triangular X (R x R), written to out (out
+//          may alias src: a block reads a chunk whole before writing it);
+//   GRAM:  parts[b][e] = sum over the rows of a(r, i) a(r, j) for the upper
+//          triangle entry e = (i, j), accumulated in registers over the chunks.
+template <bool NORM, bool APPLY, bool GRAM>
+__global__ void __launch_bounds__(kWideThreads) wide_rows_kernel(const double* src, int64_t I, int R, int nblk,
+                                                                 const double* __restrict__ lam,
+                                                                 const double* __restrict__ Xg, double* out,
+                                                                 double* __restrict__ parts,
+                                                                 const int* __restrict__ gate,
+                                                                 const int* __restrict__ status)
+{
+    if (wide_skip(status, gate)) return;
+    extern __shared__ double wsm[];
+    const int ld = R + 1, tid = threadIdx.x, nE = R * (R + 1) / 2;
+    double* Xs = wsm;                                   // APPLY: X row-major, X(k, c) at Xs[k R + c]
+    double* st = wsm + (APPLY ? R * R : 0);             // the staged input rows
+    double* ot = st + kWideChunk * ld;                  // APPLY: the product rows
+    const int b = blockIdx.x;
+    const int64_t r0 = (int64_t)b * I / nblk, r1 = (int64_t)(b + 1) * I / nblk;
+    if (APPLY)
+        for (int p = tid; p < R * R; p += kWideThreads) {
+            const int k = p / R, c = p - k * R;
+            Xs[p] = Xg[k + R * c];
+        }
+    double acc[kWideMaxE];
+    int ea[kWideMaxE], eb[kWideMaxE];
+    if (GRAM) {
+#pragma unroll
+        for (int j = 0; j < kWideMaxE; ++j) {
+            acc[j] = 0.0;
+            ea[j] = eb[j] = 0;
+            const int e = tid + j * kWideThreads;
+            if (e < nE) tri_index(e, ea[j], eb[j]);
+        }
+    }
+    for (int64_t c0 = r0; c0 < r1; c0 += kWideChunk) {
+        const int rl = (int)(r1 - c0 < kWideChunk ? r1 - c0 : kWideChunk);
+        __syncthreads();                                // the previous chunk is read
+        for (int p = tid; p < rl * R; p += kWideThreads) {
+            const int e = p / rl, li = p - e * rl;
+            double v = src[(c0 + li) + I * e];
+            if (NORM) {
+                const double l = lam[e];
+                v = (l > 0.0) ? v / l : v;
+                out[(c0 + li) + I * e] = v;
+            }
+            st[li * ld + e] = v;
+        }
+        __syncthreads();
+        const double* gs = st;
+        if (APPLY) {
+            for (int p = tid; p < rl * R; p += kWideThreads) {
+                const int c = p / rl, li = p - c * rl;
+                const double* a = st + li * ld;
+                double s = 0.0;
+                for (int k = 0; k <= c; ++k) s = fma(a[k], Xs[k * R + c], s);
+                ot[li * ld + c] = s;
+                out[(c0 + li) + I * c] = s;
+            }
+            __syncthreads();
+            gs = ot;
+        }
+        if (GRAM) {
+#pragma unroll
+            for (int j = 0; j < kWideMaxE; ++j) {
+                if (tid + j * kWideThreads < nE) {
+                    const int ia = ea[j], ib = eb[j];
+                    double s = acc[j];
+                    for (int li = 0; li < rl; ++li) s = fma(gs[li * ld + ia], gs[li * ld + ib], s);
+                    acc[j] = s;
+                }
+            }
+        }
+    }
+    if (GRAM) {
+#pragma unroll
+        for (int j = 0; j < kWideMaxE; ++j) {
+            const int e = tid + j * kWideThreads;
+            if (e < nE) parts[(size_t)b * nE + e] = acc[j];
+        }
+    }
+}
+
+// gparts[g][e] = sum of parts[b][e] over the g-th of kWideGroups contiguous
+// ranges of blocks, in block order.
+__global__ void __launch_bounds__(kWideThreads) wide_reduce_kernel(const double* __restrict__ parts, int nblk, int nE,
+                                                                   double* __restrict__ gparts,
+                                                                   const int* __restrict__ gate,
+                                                                   const int* __restrict__ status)
+{
+    if (wide_skip(status, gate)) return;
+    const int e = blockIdx.x * kWideThreads + threadIdx.x, g = blockIdx.y;
+    if (e >= nE) return;
+    double s = 0.0;
+    for (int b = g * nblk / kWideGroups; b < (g + 1) * nblk / kWideGroups; ++b) s += parts[(size_t)b * nE + e];
+    gparts[(size_t)g * nE + e] = s;
+}
+
+// M (R x R, full symmetric) = the sum of the kWideGroups group partials, in order.
+__device__ void wide_group_sum(const double* gparts, int R, double* M)
+{
+    const int nE = R * (R + 1) / 2;
+    for (int e = threadIdx.x; e < nE; e += kTailThreads) {
+        double s = 0.0;
+        for (int g = 0; g < kWideGroups; ++g) s += gparts[(size_t)g * nE + e];
+        int a, b;
+        tri_index(e, a, b);
+        M[a + R * b] = s;
+        M[b + R * a] = s;
+    }
+}
+
+// X = U^-1 for the upper-triangular U (U(a, b) = U[a + R b], dinv[k] = 1 /
+// U(k, k)), row by row from the bottom: U X = I gives
+//   X(i, c) = (delta_ic - sum_{k > i} U(i, k) X(k, c)) / U(i, i),
+// and once row i is known its contributions U(k, i) X(i, c) are added to the
+// rows k < i (right-looking, in a fixed order).  The strict lower triangle of
+// X stays zero.
+__device__ void block_upper_inverse(const double* U, const double* dinv, int R, double* X)
+{
+    const int tid = threadIdx.x;
+    for (int p = tid; p < R * R; p += kTailThreads) X[p] = 0.0;
+    __syncthreads();
+    for (int i = R - 1; i >= 0; --i) {
+        for (int c = i + tid; c < R; c += kTailThreads) X[i + R * c] = ((c == i ? 1.0 : 0.0) - X[i + R * c]) * dinv[i];
+        __syncthreads();
+        const int m = R - i;
+        for (int p = tid; p < i * m; p += kTailThreads) {
+            const int c = i + p / i, k = p - (c - i) * i;
+            X[k + R * c] = fma(U[k + R * i], X[i + R * c], X[k + R * c]);
+        }
+        __syncthreads();
+    }
+}
+
+// One CTA: the first Gram (group sums, or (F^T F) * (B^T B) for a fold step),
+// written to Gout; with want_qr R1 = chol(Gram) to R1g and R1^-1 to X1g, and
+// the gate word (1 when the Cholesky breaks down).
+__global__ void __launch_bounds__(kTailThreads, 1) wide_chol_kernel(const double* __restrict__ gparts,
+                                                                    const double* __restrict__ F,
+                                                                    const double* __restrict__ B, int R,
+                                                                    double* __restrict__ Gout, int want_qr,
+                                                                    double* __restrict__ R1g,
+                                                                    double* __restrict__ X1g, int* __restrict__ gate,
+                                                                    const int* __restrict__ status)
+{
+    if (wide_skip(status, nullptr)) return;
+    extern __shared__ double wsm[];
+    __shared__ double piv[2 * kMaxRank], dinv[kMaxRank];
+    __shared__ int flag_bad;
+    double* M = wsm;
+    double* X = wsm + R * R;
+    const int tid = threadIdx.x, nE = R * (R + 1) / 2;
+    if (F != nullptr) {
+        // F and B upper triangular: (F^T F)(a, b) = sum_{p <= a} F(p, a) F(p, b) for a <= b
+        for (int e = tid; e < nE; e += kTailThreads) {
+            int a, b;
+            tri_index(e, a, b);
+            double sf = 0.0, sb = 0.0;
+            for (int p = 0; p <= a; ++p) {
+                sf = fma(F[p + R * a], F[p + R * b], sf);
+                sb = fma(B[p + R * a], B[p + R * b], sb);
+            }
+            const double v = sf * sb;
+            M[a + R * b] = v;
+            M[b + R * a] = v;
+        }
+    } else {
+        wide_group_sum(gparts, R, M);
+    }
+    __syncthreads();
+    if (Gout)
+        for (int p = tid; p < R * R; p += kTailThreads) Gout[p] = M[p];
+    if (!want_qr) return;
+    const bool ok = block_cholesky(M, R, piv, dinv, &flag_bad);
+    for (int p = tid; p < R * R; p += kTailThreads) R1g[p] = M[p];
+    if (!ok) {
+        if (tid == 0) *gate = 1;
+        return;
+    }
+    block_upper_inverse(M, dinv, R, X);
+    for (int p = tid; p < R * R; p += kTailThreads) X1g[p] = X[p];
+    if (tid == 0) *gate = 0;
+}
+
+// One CTA: Q1^T Q1 from the group sums; if every entry is within kCqrCheck of
+// the identity and its Cholesky succeeds, R2^-1 to X2g and R_n = R2 R1 to
+// Rout; else the gate word goes to 1.
+__global__ void __launch_bounds__(kTailThreads, 1) wide_chol2_kernel(const double* __restrict__ gparts, int R,
+                                                                     const double* __restrict__ R1g,
+                                                                     double* __restrict__ X2g,
+                                                                     double* __restrict__ Rout,
+                                                                     int* __restrict__ gate,
+                                                                     const int* __restrict__ status)
+{
+    if (wide_skip(status, gate)) return;
+    extern __shared__ double wsm[];
+    __shared__ double piv[2 * kMaxRank], dinv[kMaxRank];
+    __shared__ int flag_bad, flag_check;
+    double* M = wsm;
+    double* X = wsm + R * R;
+    double* R1 = wsm + 2 * R * R;
+    const int tid = threadIdx.x;
+    wide_group_sum(gparts, R, M);
+    for (int p = tid; p < R * R; p += kTailThreads) R1[p] = R1g[p];
+    if (tid == 0) flag_check = 0;
+    __syncthreads();
+    for (int p = tid; p < R * R; p += kTailThreads) {
+        const int a = p % R, b = p / R;
+        if (!(fabs(M[p] - (a == b ? 1.0 : 0.0)) <= kCqrCheck)) flag_check = 1;
+    }
+    __syncthreads();
+    bool ok = flag_check == 0;
+    if (ok) ok = block_cholesky(M, R, piv, dinv, &flag_bad);
+    if (!ok) {
+        if (tid == 0) *gate = 1;
+        return;
+    }
+    block_upper_inverse(M, dinv, R, X);
+    for (int p = tid; p < R * R; p += kTailThreads) {
+        X2g[p] = X[p];
+        const int a = p % R, b = p / R;
+        double s = 0.0;
+        for (int k = a; k <= b; ++k) s = fma(M[a + R * k], R1[k + R * b], s);
+        Rout[p] = (a <= b) ? s : 0.0;
+    }
+}
+
 }  // namespace
 
 cudaError_t recip_check(const double* x, int64_t n, double* rcp, double* rsq, cudaStream_t st)
@@ -587,8 +905,100 @@ cudaError_t launch_tail(Handle* h, int64_t I, TailArgs a)
 
 }  // namespace
 
+bool wide_tail_on(const Handle* h) { return h->wide_tail && h->R > 32 && h->wide[0].base != nullptr; }
+
+int64_t wide_ws_elems(int R, int num_sms)
+{
+    const int64_t nE = (int64_t)R * (R + 1) / 2, nb = 2LL * num_sms;
+    return nb * nE + kWideGroups * nE + nb * R + R + 3LL * R * R;
+}
+
+void wide_ws_carve(WideWs& ws, int R, int num_sms)
+{
+    const int64_t nE = (int64_t)R * (R + 1) / 2, nb = 2LL * num_sms;
+    double* p = ws.base;
+    ws.parts = p; p += nb * nE;
+    ws.gparts = p; p += kWideGroups * nE;
+    ws.cparts = p; p += nb * R;
+    ws.lam = p; p += R;
+    ws.R1 = p; p += (int64_t)R * R;
+    ws.X1 = p; p += (int64_t)R * R;
+    ws.X2 = p;
+}
+
+namespace {
+
+// The GPU-wide chain on h->stream (see the kernels above).  src: I x R;
+// norm: kind 3 (lambda to lambda_out, A_n to Aout); F, B: a fold step's
+// triangular factors (first Gram from them, src = F (.) B).
+cudaError_t wide_cqr2(Handle* h, WideWs& ws, const double* src, int64_t I, bool norm, double* lambda_out,
+                      double* Aout, double* G, bool want_qr, double* Q, double* Rout, int* gate, const double* F,
+                      const double* B)
+{
+    const int R = h->R, nE = R * (R + 1) / 2;
+    if (R > kMaxRank || I < 1) return cudaErrorInvalidValue;
+    const int nblk = wide_blocks(I, h->num_sms);
+    const size_t st_bytes = (size_t)kWideChunk * (R + 1) * sizeof(double);
+    const size_t apply_bytes = (size_t)R * R * sizeof(double) + 2 * st_bytes;
+    const size_t chol_bytes = 2 * (size_t)R * R * sizeof(double);
+    const size_t chol2_bytes = 3 * (size_t)R * R * sizeof(double);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        const int mx = (int)(kMaxRank * kMaxRank * sizeof(double) + 2 * kWideChunk * (kMaxRank + 1) * sizeof(double));
+        attr_err = cudaFuncSetAttribute(wide_rows_kernel<false, true, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(wide_rows_kernel<false, true, false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(wide_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(2 * kMaxRank * kMaxRank * sizeof(double)));
+        if (attr_err == cudaSuccess)
+            attr_err = cudaFuncSetAttribute(wide_chol2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(3 * kMaxRank * kMaxRank * sizeof(double)));
+    });
+    CPALS_CUDA_TRY(attr_err);
+    cudaStream_t st = h->stream;
+    const dim3 rgrid((unsigned)((nE + kWideThreads - 1) / kWideThreads), kWideGroups);
+    const double* qsrc = src;
+    if (F == nullptr) {
+        if (norm) {
+            wide_colsq_kernel<<<nblk, kWideThreads, 0, st>>>(src, I, R, nblk, ws.cparts, h->d_status);
+            wide_lambda_kernel<<<1, kWideThreads, 0, st>>>(ws.cparts, nblk, R, lambda_out, ws.lam, h->d_status);
+            wide_rows_kernel<true, false, true><<<nblk, kWideThreads, st_bytes, st>>>(
+                src, I, R, nblk, ws.lam, nullptr, Aout, ws.parts, nullptr, h->d_status);
+            h->launches += 3;
+            qsrc = Aout;
+        } else {
+            wide_rows_kernel<false, false, true><<<nblk, kWideThreads, st_bytes, st>>>(
+                src, I, R, nblk, nullptr, nullptr, nullptr, ws.parts, nullptr, h->d_status);
+            h->launches++;
+        }
+        wide_reduce_kernel<<<rgrid, kWideThreads, 0, st>>>(ws.parts, nblk, nE, ws.gparts, nullptr, h->d_status);
+        h->launches++;
+    }
+    wide_chol_kernel<<<1, kTailThreads, chol_bytes, st>>>(ws.gparts, F, B, R, G, want_qr ? 1 : 0, ws.R1, ws.X1,
+                                                          gate, h->d_status);
+    h->launches++;
+    if (!want_qr) return cudaGetLastError();
+    wide_rows_kernel<false, true, true><<<nblk, kWideThreads, apply_bytes, st>>>(qsrc, I, R, nblk, nullptr, ws.X1, Q,
+                                                                                ws.parts, gate, h->d_status);
+    wide_reduce_kernel<<<rgrid, kWideThreads, 0, st>>>(ws.parts, nblk, nE, ws.gparts, gate, h->d_status);
+    wide_chol2_kernel<<<1, kTailThreads, chol2_bytes, st>>>(ws.gparts, R, ws.R1, ws.X2, Rout, gate, h->d_status);
+    wide_rows_kernel<false, true, false><<<nblk, kWideThreads, apply_bytes, st>>>(Q, I, R, nblk, nullptr, ws.X2, Q,
+                                                                                 nullptr, gate, h->d_status);
+    h->launches += 4;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double* Op, bool want_qr)
 {
+    if (kind >= 3 && wide_tail_on(h))
+        return wide_cqr2(h, h->wide[0], W, h->dims[n], kind == 3, h->lambda, h->A[n], h->G[n], want_qr, h->Q[n],
+                         h->Rf[n], h->d_gate, nullptr, nullptr);
     TailArgs a;
     a.W = W;
     a.Op = Op;
@@ -606,8 +1016,11 @@ cudaError_t mode_tail(Handle* h, int n, int kind, const double* W, const double*
     return launch_tail(h, h->dims[n], a);
 }
 
-cudaError_t cqr2_rows(Handle* h, const double* V, int64_t rows, double* Q, double* Rout, double* G, int* gate)
+cudaError_t cqr2_rows(Handle* h, const double* V, int64_t rows, double* Q, double* Rout, double* G, int* gate,
+                      const double* F, const double* B)
 {
+    if (wide_tail_on(h))
+        return wide_cqr2(h, h->wide[1], V, rows, false, nullptr, nullptr, G, true, Q, Rout, gate, F, B);
     TailArgs a;
     a.W = V;
     a.Op = nullptr;

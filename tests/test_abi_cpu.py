@@ -86,12 +86,12 @@ def test_options_match_the_header(lib):
     assert enum == {"CPALS_OPT_DIMTREE": 0, "CPALS_OPT_TC_PIPELINE": 1, "CPALS_OPT_KRP_TREE": 2,
                     "CPALS_OPT_F32_PIPELINE": 3, "CPALS_OPT_TEST_WITHHOLD_COPIES": 4,
                     "CPALS_OPT_FUSED_TAIL": 5, "CPALS_OPT_SVD_SHORTCUT": 6,
-                    "CPALS_OPT_APPLY_Q0_FP32": 7}
+                    "CPALS_OPT_APPLY_Q0_FP32": 7, "CPALS_OPT_WIDE_TAIL": 8}
     setters = {"set_dimtree": "CPALS_OPT_DIMTREE", "set_tc_pipeline": "CPALS_OPT_TC_PIPELINE",
                "set_krp_tree": "CPALS_OPT_KRP_TREE", "set_f32_pipeline": "CPALS_OPT_F32_PIPELINE",
                "set_test_withhold_copies": "CPALS_OPT_TEST_WITHHOLD_COPIES",
                "set_fused_tail": "CPALS_OPT_FUSED_TAIL", "set_svd_shortcut": "CPALS_OPT_SVD_SHORTCUT",
-               "set_apply_q0_fp32": "CPALS_OPT_APPLY_Q0_FP32"}
+               "set_apply_q0_fp32": "CPALS_OPT_APPLY_Q0_FP32", "set_wide_tail": "CPALS_OPT_WIDE_TAIL"}
     for name, opt in setters.items():
         src = inspect.getsource(getattr(cpals.CPALS, name))
         m = re.search(r"cpals_set_option\(self\._h, (\d+),", src)
