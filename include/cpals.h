@@ -329,8 +329,9 @@ int cpals_set_option(cpals_handle* h, int option, int64_t value);
 
 /* Test hook (the paper has no counterpart): the reciprocal and reciprocal
  * square root that the factor QR of the fused mode tail uses on its
- * sequential chain (an FP32 hardware approximation refined by two FP64
- * Newton-Raphson steps), applied to n device values x (rsqrt gets 0 where
+ * sequential chain (an FP32 hardware approximation refined in FP64: one
+ * third-order Newton step for the reciprocal, two Newton-Raphson steps for
+ * the reciprocal square root), applied to n device values x (rsqrt gets 0 where
  * x <= 0).  x, rcp, rsqrt: device arrays of n doubles.  Synchronises the
  * device.  Errors: CPALS_ERR_ARG, CPALS_ERR_CUDA. */
 int cpals_test_newton_recip(const double* x, int64_t n, double* rcp, double* rsqrt);

@@ -26,7 +26,8 @@ constexpr int kProfMax = 1024;
 // ------------------------------------------------------------------ handle
 // Workspace of the GPU-wide CholeskyQR2 (one allocation, carved up): the
 // Gram partials of the row blocks, their group sums, the column sums of
-// squares of the row blocks, lambda, R1, R1^-1 and R2^-1.
+// squares of the row blocks, lambda, R1, R1^-1, R2^-1, R2, a fold step's
+// first Gram and the reciprocals of the diagonals of R1 and R2.
 struct WideWs {
     double* base = nullptr;
     double* parts = nullptr;
@@ -36,6 +37,10 @@ struct WideWs {
     double* R1 = nullptr;
     double* X1 = nullptr;
     double* X2 = nullptr;
+    double* R2 = nullptr;
+    double* Gh = nullptr;
+    double* D1 = nullptr;
+    double* D2 = nullptr;
 };
 
 struct Handle {

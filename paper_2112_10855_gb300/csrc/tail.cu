@@ -110,25 +110,24 @@ struct TailSmem {
     }
 };
 
-// 1/d and 1/sqrt(d) to about one ulp: the FP32 hardware approximation
-// (rcp.approx / rsqrt.approx, about 2^-23 relative) refined by two
-// Newton-Raphson steps in FP64 -- y <- y + y (1 - d y) for the reciprocal,
-// y <- y + y (1/2 - (d/2) y^2) for the reciprocal square root -- each of
-// which squares the relative error.  A dependent FP64 operation costs 64
-// cycles on this part, and these are a few of them against the much longer
-// exact division and square root.  Outside the FP32 normal range the exact
-// FP64 operations are used.
+// 1/d and 1/sqrt(d) to about one ulp from the FP32 hardware approximation
+// (rcp.approx / rsqrt.approx, about 2^-23 relative).  The reciprocal takes one
+// third-order step of the Newton iteration for 1/d: with e = 1 - d y,
+// y (1 + e + e^2) = (1 - e^3) / d, so the relative error goes from e to e^3
+// (below 2^-66) in three dependent FMAs.  The reciprocal square root takes
+// two Newton-Raphson steps, y <- y + y (1/2 - (d/2) y^2), each squaring the
+// error.  A dependent FP64 operation costs 64 cycles on this part, and these
+// are a few of them against the much longer exact division and square root.
+// Outside the FP32 normal range the exact FP64 operations are used.
 __device__ __forceinline__ double rcp_nr(double d)
 {
     const double a = fabs(d);
     if (!(a > 1e-36 && a < 1e36)) return 1.0 / d;
     float f;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"((float)d));
-    double y = (double)f;
-    double e = fma(-d, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-d, y, 1.0);
-    return fma(y, e, y);
+    const double y = (double)f;
+    const double e = fma(-d, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 
 __device__ __forceinline__ double rsqrt_nr(double d)
@@ -209,23 +208,45 @@ __device__ void cluster_gram(cg::cluster_group& cluster, double* part, int R, do
 // U(j,k) = M(j,k) / sqrt(d_j), and dinv[j] = 1 / U(j,j).  The strict lower
 // triangle is set to zero.  Returns false (in every thread) on a pivot that
 // is not positive and finite.
+__device__ __forceinline__ void cholesky_pivot(const double* M, int R, int j, double* piv, int* bad)
+{
+    const double d = M[j + R * j];
+    if (!(d > 0.0) || !(d < INFINITY)) *bad = 1;
+    piv[j] = (d > 0.0 && d < INFINITY) ? rcp_nr(d) : 0.0;
+}
+
 __device__ bool block_cholesky(double* M, int R, double* piv, double* dinv, int* bad)
 {
+    // (a, b) of the packed upper-triangle index p (p = b (b + 1) / 2 + a),
+    // a | b << 8, for the trailing triangles of every step
+    __shared__ uint16_t tri_ab[(kMaxRank - 1) * kMaxRank / 2];
     const int tid = threadIdx.x;
-    if (tid == 0) *bad = 0;
+    for (int p = tid; p < (R - 1) * R / 2; p += kTailThreads) {
+        int a, b;
+        tri_index(p, a, b);
+        tri_ab[p] = (uint16_t)(a | (b << 8));
+    }
+    if (tid == 0) {
+        *bad = 0;
+        cholesky_pivot(M, R, 0, piv, bad);
+    }
     __syncthreads();
     for (int j = 0; j < R; ++j) {
-        if (tid == 0) {
-            const double d = M[j + R * j];
-            if (!(d > 0.0) || !(d < INFINITY)) *bad = 1;
-            piv[j] = (d > 0.0 && d < INFINITY) ? rcp_nr(d) : 0.0;
-        }
-        __syncthreads();
         const double inv = piv[j];
         const int m = R - 1 - j;
-        for (int p = tid; p < m * m; p += kTailThreads) {
-            const int a = j + 1 + p % m, b = j + 1 + p / m;
-            if (a <= b) M[a + R * b] = fma(-M[j + R * a] * inv, M[j + R * b], M[a + R * b]);
+        // the pivot row scaled once (M(j, a) / d_j into the strict lower
+        // triangle's column j, which no later step reads), then one FMA per
+        // entry of the trailing upper triangle, packed so that no lane of an
+        // FP64 warp instruction idles.  The thread that updates entry
+        // (j+1, j+1) -- the next pivot, final after this step -- takes its
+        // reciprocal at once, while the other warps are still updating.
+        for (int a = j + 1 + tid; a < R; a += kTailThreads) M[a + R * j] = M[j + R * a] * inv;
+        __syncthreads();
+        for (int p = tid; p < m * (m + 1) / 2; p += kTailThreads) {
+            const int ab = tri_ab[p];
+            const int a = (ab & 0xff) + j + 1, b = (ab >> 8) + j + 1;
+            M[a + R * b] = fma(-M[a + R * j], M[j + R * b], M[a + R * b]);
+            if (p == 0) cholesky_pivot(M, R, j + 1, piv, bad);
         }
         __syncthreads();
     }
@@ -529,7 +550,7 @@ __global__ void recip_check_kernel(const double* __restrict__ x, int64_t n, doub
 //   lambda  lambda_r = sqrt of their sum, in block order             (kind 3)
 //   rows    A_n = Ahat diag(lambda)^-1, and the Gram partial of A_n per row
 //           block (kind 4: of the A_n given)
-//   reduce  the partials summed in 16 fixed groups of blocks
+//   reduce  the partials summed in 8 fixed groups of blocks
 //   chol    G_n = the sum of the groups; R1 = chol(G_n) and R1^-1 (one CTA)
 //   rows    Q1 = A_n R1^-1 and the Gram partial of Q1 per row block
 //   reduce
@@ -547,7 +568,7 @@ __global__ void recip_check_kernel(const double* __restrict__ x, int64_t n, doub
 // once when it is 1.
 constexpr int kWideThreads = 256;
 constexpr int kWideChunk = 32;     // rows staged in shared memory at a time
-constexpr int kWideGroups = 16;    // fixed groups of row blocks in the reduction
+constexpr int kWideGroups = 8;     // fixed groups of row blocks in the reduction
 constexpr int kWideMaxE = (kMaxRank * (kMaxRank + 1) / 2 + kWideThreads - 1) / kWideThreads;
 
 // Row blocks of the split: about 8 rows each, at most two per SM.
@@ -613,15 +634,35 @@ __global__ void __launch_bounds__(kWideThreads) wide_lambda_kernel(const double*
 //          may alias src: a block reads a chunk whole before writing it);
 //   GRAM:  parts[b][e] = sum over the rows of a(r, i) a(r, j) for the upper
 //          triangle entry e = (i, j), accumulated in registers over the chunks.
-template <bool NORM, bool APPLY, bool GRAM>
+//   RPROD: besides, R_n = R2 R1 (both upper triangular): a warp per entry
+//          (a, c), a <= c, lanes over k = a..c and a fixed shuffle tree, the
+//          entries spread over the blocks' warps; the strict lower triangle
+//          of Rout set to zero.
+template <bool NORM, bool APPLY, bool GRAM, bool RPROD>
 __global__ void __launch_bounds__(kWideThreads) wide_rows_kernel(const double* src, int64_t I, int R, int nblk,
                                                                  const double* __restrict__ lam,
                                                                  const double* __restrict__ Xg, double* out,
                                                                  double* __restrict__ parts,
+                                                                 const double* __restrict__ R2g,
+                                                                 const double* __restrict__ R1g,
+                                                                 double* __restrict__ Rout,
                                                                  const int* __restrict__ gate,
                                                                  const int* __restrict__ status)
 {
     if (wide_skip(status, gate)) return;
+    if (RPROD) {
+        const int lane = threadIdx.x & 31, wpb = kWideThreads / 32;
+        for (int e = blockIdx.x * wpb + (threadIdx.x >> 5); e < R * (R + 1) / 2; e += nblk * wpb) {
+            int a, c;
+            tri_index(e, a, c);
+            double s = 0.0;
+            for (int k = a + lane; k <= c; k += 32) s = fma(R2g[a + R * k], R1g[k + R * c], s);
+            s = warp_sum(s);
+            if (lane == 0) Rout[a + R * c] = s;
+        }
+        for (int p = blockIdx.x * kWideThreads + threadIdx.x; p < R * R; p += nblk * kWideThreads)
+            if (p % R > p / R) Rout[p] = 0.0;
+    }
     extern __shared__ double wsm[];
     const int ld = R + 1, tid = threadIdx.x, nE = R * (R + 1) / 2;
     double* Xs = wsm;                                   // APPLY: X row-major, X(k, c) at Xs[k R + c]
@@ -722,38 +763,83 @@ __device__ void wide_group_sum(const double* gparts, int R, double* M)
     }
 }
 
-// X = U^-1 for the upper-triangular U (U(a, b) = U[a + R b], dinv[k] = 1 /
-// U(k, k)), row by row from the bottom: U X = I gives
-//   X(i, c) = (delta_ic - sum_{k > i} U(i, k) X(k, c)) / U(i, i),
-// and once row i is known its contributions U(k, i) X(i, c) are added to the
-// rows k < i (right-looking, in a fixed order).  The strict lower triangle of
-// X stays zero.
-__device__ void block_upper_inverse(const double* U, const double* dinv, int R, double* X)
+// X = U^-1 for the upper-triangular U (U(a, b) = U[a + R b]) given dinv[k] =
+// 1 / U(k, k) (the Cholesky's), one warp per column c of X, the rows split
+// over the lanes (k = lane, lane + 32).  U X = I gives, from the bottom row up,
+//   X(i, c) = delta_ic / U(i, i) - (sum_{k > i} U(i, k) X(k, c)) / U(i, i)
+// (one FMA),
+// and once X(i, c) is known (its lane broadcasts it) every lane adds
+// U(k, i) X(i, c) to its rows k < i: a fixed order, no block barrier.  U goes
+// through shared memory; the strict lower triangle of X is zero.
+constexpr int kInvWarps = 4;
+
+__global__ void __launch_bounds__(kInvWarps * 32) wide_inv_kernel(const double* __restrict__ U,
+                                                                  const double* __restrict__ dinv, int R,
+                                                                  double* __restrict__ X,
+                                                                  const int* __restrict__ gate,
+                                                                  const int* __restrict__ status)
 {
-    const int tid = threadIdx.x;
-    for (int p = tid; p < R * R; p += kTailThreads) X[p] = 0.0;
+    if (wide_skip(status, gate)) return;
+    __shared__ double Us[kMaxRank * kMaxRank];
+    __shared__ double ds[kMaxRank];
+    for (int p = threadIdx.x; p < R * R; p += kInvWarps * 32) Us[p] = U[p];
+    for (int p = threadIdx.x; p < R; p += kInvWarps * 32) ds[p] = dinv[p];
     __syncthreads();
-    for (int i = R - 1; i >= 0; --i) {
-        for (int c = i + tid; c < R; c += kTailThreads) X[i + R * c] = ((c == i ? 1.0 : 0.0) - X[i + R * c]) * dinv[i];
-        __syncthreads();
-        const int m = R - i;
-        for (int p = tid; p < i * m; p += kTailThreads) {
-            const int c = i + p / i, k = p - (c - i) * i;
-            X[k + R * c] = fma(U[k + R * i], X[i + R * c], X[k + R * c]);
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int c = blockIdx.x * kInvWarps + (threadIdx.x >> 5);
+    if (c >= R) return;
+    const int k0 = lane, k1 = lane + 32;
+    double acc0 = 0.0, acc1 = 0.0, x0 = 0.0, x1 = 0.0;
+    for (int i = c; i >= 0; --i) {
+        double xi = 0.0;
+        const double dd = (i == c) ? ds[i] : 0.0;     // delta_ic / U(i, i)
+        if (i == k0) { xi = fma(-acc0, ds[i], dd); x0 = xi; }
+        if (i == k1) { xi = fma(-acc1, ds[i], dd); x1 = xi; }
+        xi = __shfl_sync(0xffffffffu, xi, i & 31);
+        if (k0 < i) acc0 = fma(Us[k0 + R * i], xi, acc0);
+        if (k1 < i) acc1 = fma(Us[k1 + R * i], xi, acc1);
+    }
+    if (k0 < R) X[k0 + R * c] = (k0 <= c) ? x0 : 0.0;
+    if (k1 < R) X[k1 + R * c] = (k1 <= c) ? x1 : 0.0;
+}
+
+// The Gram of a fold step V = F (.) B with F, B upper triangular: G = (F^T F)
+// * (B^T B) entrywise, (F^T F)(a, b) = sum_{p <= a} F(p, a) F(p, b) for a <= b.
+// A warp per upper-triangle entry (lanes over p, a fixed shuffle tree), G
+// written whole (R x R).
+__global__ void __launch_bounds__(kWideThreads) wide_hadamard_kernel(const double* __restrict__ F,
+                                                                     const double* __restrict__ B, int R,
+                                                                     double* __restrict__ G,
+                                                                     const int* __restrict__ status)
+{
+    if (wide_skip(status, nullptr)) return;
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * (kWideThreads / 32) + (threadIdx.x >> 5);
+    if (e >= R * (R + 1) / 2) return;
+    int a, b;
+    tri_index(e, a, b);
+    double sf = 0.0, sb = 0.0;
+    for (int p = lane; p <= a; p += 32) {
+        sf = fma(F[p + R * a], F[p + R * b], sf);
+        sb = fma(B[p + R * a], B[p + R * b], sb);
+    }
+    sf = warp_sum(sf);
+    sb = warp_sum(sb);
+    if (lane == 0) {
+        const double v = sf * sb;
+        G[a + R * b] = v;
+        G[b + R * a] = v;
     }
 }
 
-// One CTA: the first Gram (group sums, or (F^T F) * (B^T B) for a fold step),
-// written to Gout; with want_qr R1 = chol(Gram) to R1g and R1^-1 to X1g, and
-// the gate word (1 when the Cholesky breaks down).
+// One CTA: the first Gram (the group sums, or Gin given whole), written to
+// Gout; with want_qr R1 = chol(Gram) to R1g, the reciprocals of its diagonal
+// to D1g, and the gate word (1 when the Cholesky breaks down).
 __global__ void __launch_bounds__(kTailThreads, 1) wide_chol_kernel(const double* __restrict__ gparts,
-                                                                    const double* __restrict__ F,
-                                                                    const double* __restrict__ B, int R,
+                                                                    const double* __restrict__ Gin, int R,
                                                                     double* __restrict__ Gout, int want_qr,
                                                                     double* __restrict__ R1g,
-                                                                    double* __restrict__ X1g, int* __restrict__ gate,
+                                                                    double* __restrict__ D1g, int* __restrict__ gate,
                                                                     const int* __restrict__ status)
 {
     if (wide_skip(status, nullptr)) return;
@@ -761,22 +847,9 @@ __global__ void __launch_bounds__(kTailThreads, 1) wide_chol_kernel(const double
     __shared__ double piv[2 * kMaxRank], dinv[kMaxRank];
     __shared__ int flag_bad;
     double* M = wsm;
-    double* X = wsm + R * R;
-    const int tid = threadIdx.x, nE = R * (R + 1) / 2;
-    if (F != nullptr) {
-        // F and B upper triangular: (F^T F)(a, b) = sum_{p <= a} F(p, a) F(p, b) for a <= b
-        for (int e = tid; e < nE; e += kTailThreads) {
-            int a, b;
-            tri_index(e, a, b);
-            double sf = 0.0, sb = 0.0;
-            for (int p = 0; p <= a; ++p) {
-                sf = fma(F[p + R * a], F[p + R * b], sf);
-                sb = fma(B[p + R * a], B[p + R * b], sb);
-            }
-            const double v = sf * sb;
-            M[a + R * b] = v;
-            M[b + R * a] = v;
-        }
+    const int tid = threadIdx.x;
+    if (Gin != nullptr) {
+        for (int p = tid; p < R * R; p += kTailThreads) M[p] = Gin[p];
     } else {
         wide_group_sum(gparts, R, M);
     }
@@ -786,22 +859,16 @@ __global__ void __launch_bounds__(kTailThreads, 1) wide_chol_kernel(const double
     if (!want_qr) return;
     const bool ok = block_cholesky(M, R, piv, dinv, &flag_bad);
     for (int p = tid; p < R * R; p += kTailThreads) R1g[p] = M[p];
-    if (!ok) {
-        if (tid == 0) *gate = 1;
-        return;
-    }
-    block_upper_inverse(M, dinv, R, X);
-    for (int p = tid; p < R * R; p += kTailThreads) X1g[p] = X[p];
-    if (tid == 0) *gate = 0;
+    if (tid < R) D1g[tid] = dinv[tid];
+    if (tid == 0) *gate = ok ? 0 : 1;
 }
 
 // One CTA: Q1^T Q1 from the group sums; if every entry is within kCqrCheck of
-// the identity and its Cholesky succeeds, R2^-1 to X2g and R_n = R2 R1 to
-// Rout; else the gate word goes to 1.
+// the identity and its Cholesky succeeds, R2 to R2g and the reciprocals of
+// its diagonal to D2g; else the gate word goes to 1.
 __global__ void __launch_bounds__(kTailThreads, 1) wide_chol2_kernel(const double* __restrict__ gparts, int R,
-                                                                     const double* __restrict__ R1g,
-                                                                     double* __restrict__ X2g,
-                                                                     double* __restrict__ Rout,
+                                                                     double* __restrict__ R2g,
+                                                                     double* __restrict__ D2g,
                                                                      int* __restrict__ gate,
                                                                      const int* __restrict__ status)
 {
@@ -810,11 +877,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) wide_chol2_kernel(const doubl
     __shared__ double piv[2 * kMaxRank], dinv[kMaxRank];
     __shared__ int flag_bad, flag_check;
     double* M = wsm;
-    double* X = wsm + R * R;
-    double* R1 = wsm + 2 * R * R;
     const int tid = threadIdx.x;
     wide_group_sum(gparts, R, M);
-    for (int p = tid; p < R * R; p += kTailThreads) R1[p] = R1g[p];
     if (tid == 0) flag_check = 0;
     __syncthreads();
     for (int p = tid; p < R * R; p += kTailThreads) {
@@ -828,14 +892,8 @@ __global__ void __launch_bounds__(kTailThreads, 1) wide_chol2_kernel(const doubl
         if (tid == 0) *gate = 1;
         return;
     }
-    block_upper_inverse(M, dinv, R, X);
-    for (int p = tid; p < R * R; p += kTailThreads) {
-        X2g[p] = X[p];
-        const int a = p % R, b = p / R;
-        double s = 0.0;
-        for (int k = a; k <= b; ++k) s = fma(M[a + R * k], R1[k + R * b], s);
-        Rout[p] = (a <= b) ? s : 0.0;
-    }
+    for (int p = tid; p < R * R; p += kTailThreads) R2g[p] = M[p];
+    if (tid < R) D2g[tid] = dinv[tid];
 }
 
 }  // namespace
@@ -910,7 +968,7 @@ bool wide_tail_on(const Handle* h) { return h->wide_tail && h->R > 32 && h->wide
 int64_t wide_ws_elems(int R, int num_sms)
 {
     const int64_t nE = (int64_t)R * (R + 1) / 2, nb = 2LL * num_sms;
-    return nb * nE + kWideGroups * nE + nb * R + R + 3LL * R * R;
+    return nb * nE + kWideGroups * nE + nb * R + 3LL * R + 5LL * R * R;
 }
 
 void wide_ws_carve(WideWs& ws, int R, int num_sms)
@@ -923,7 +981,11 @@ void wide_ws_carve(WideWs& ws, int R, int num_sms)
     ws.lam = p; p += R;
     ws.R1 = p; p += (int64_t)R * R;
     ws.X1 = p; p += (int64_t)R * R;
-    ws.X2 = p;
+    ws.X2 = p; p += (int64_t)R * R;
+    ws.R2 = p; p += (int64_t)R * R;
+    ws.Gh = p; p += (int64_t)R * R;
+    ws.D1 = p; p += R;
+    ws.D2 = p;
 }
 
 namespace {
@@ -940,55 +1002,58 @@ cudaError_t wide_cqr2(Handle* h, WideWs& ws, const double* src, int64_t I, bool 
     const int nblk = wide_blocks(I, h->num_sms);
     const size_t st_bytes = (size_t)kWideChunk * (R + 1) * sizeof(double);
     const size_t apply_bytes = (size_t)R * R * sizeof(double) + 2 * st_bytes;
-    const size_t chol_bytes = 2 * (size_t)R * R * sizeof(double);
-    const size_t chol2_bytes = 3 * (size_t)R * R * sizeof(double);
+    const size_t chol_bytes = (size_t)R * R * sizeof(double);
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
         const int mx = (int)(kMaxRank * kMaxRank * sizeof(double) + 2 * kWideChunk * (kMaxRank + 1) * sizeof(double));
-        attr_err = cudaFuncSetAttribute(wide_rows_kernel<false, true, true>,
+        attr_err = cudaFuncSetAttribute(wide_rows_kernel<false, true, true, false>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(wide_rows_kernel<false, true, false>,
+            attr_err = cudaFuncSetAttribute(wide_rows_kernel<false, true, false, true>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(wide_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(2 * kMaxRank * kMaxRank * sizeof(double)));
-        if (attr_err == cudaSuccess)
-            attr_err = cudaFuncSetAttribute(wide_chol2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)(3 * kMaxRank * kMaxRank * sizeof(double)));
     });
     CPALS_CUDA_TRY(attr_err);
     cudaStream_t st = h->stream;
     const dim3 rgrid((unsigned)((nE + kWideThreads - 1) / kWideThreads), kWideGroups);
     const double* qsrc = src;
-    if (F == nullptr) {
+    const double* Gin = nullptr;
+    if (F != nullptr) {
+        const int wpb = kWideThreads / 32;
+        wide_hadamard_kernel<<<(nE + wpb - 1) / wpb, kWideThreads, 0, st>>>(F, B, R, ws.Gh, h->d_status);
+        h->launches++;
+        Gin = ws.Gh;
+    } else {
         if (norm) {
             wide_colsq_kernel<<<nblk, kWideThreads, 0, st>>>(src, I, R, nblk, ws.cparts, h->d_status);
             wide_lambda_kernel<<<1, kWideThreads, 0, st>>>(ws.cparts, nblk, R, lambda_out, ws.lam, h->d_status);
-            wide_rows_kernel<true, false, true><<<nblk, kWideThreads, st_bytes, st>>>(
-                src, I, R, nblk, ws.lam, nullptr, Aout, ws.parts, nullptr, h->d_status);
+            wide_rows_kernel<true, false, true, false><<<nblk, kWideThreads, st_bytes, st>>>(
+                src, I, R, nblk, ws.lam, nullptr, Aout, ws.parts, nullptr, nullptr, nullptr, nullptr, h->d_status);
             h->launches += 3;
             qsrc = Aout;
         } else {
-            wide_rows_kernel<false, false, true><<<nblk, kWideThreads, st_bytes, st>>>(
-                src, I, R, nblk, nullptr, nullptr, nullptr, ws.parts, nullptr, h->d_status);
+            wide_rows_kernel<false, false, true, false><<<nblk, kWideThreads, st_bytes, st>>>(
+                src, I, R, nblk, nullptr, nullptr, nullptr, ws.parts, nullptr, nullptr, nullptr, nullptr,
+                h->d_status);
             h->launches++;
         }
         wide_reduce_kernel<<<rgrid, kWideThreads, 0, st>>>(ws.parts, nblk, nE, ws.gparts, nullptr, h->d_status);
         h->launches++;
     }
-    wide_chol_kernel<<<1, kTailThreads, chol_bytes, st>>>(ws.gparts, F, B, R, G, want_qr ? 1 : 0, ws.R1, ws.X1,
-                                                          gate, h->d_status);
+    const unsigned igrid = (unsigned)((R + kInvWarps - 1) / kInvWarps);
+    wide_chol_kernel<<<1, kTailThreads, chol_bytes, st>>>(ws.gparts, Gin, R, G, want_qr ? 1 : 0, ws.R1, ws.D1, gate,
+                                                          h->d_status);
     h->launches++;
     if (!want_qr) return cudaGetLastError();
-    wide_rows_kernel<false, true, true><<<nblk, kWideThreads, apply_bytes, st>>>(qsrc, I, R, nblk, nullptr, ws.X1, Q,
-                                                                                ws.parts, gate, h->d_status);
+    wide_inv_kernel<<<igrid, kInvWarps * 32, 0, st>>>(ws.R1, ws.D1, R, ws.X1, gate, h->d_status);
+    wide_rows_kernel<false, true, true, false><<<nblk, kWideThreads, apply_bytes, st>>>(
+        qsrc, I, R, nblk, nullptr, ws.X1, Q, ws.parts, nullptr, nullptr, nullptr, gate, h->d_status);
     wide_reduce_kernel<<<rgrid, kWideThreads, 0, st>>>(ws.parts, nblk, nE, ws.gparts, gate, h->d_status);
-    wide_chol2_kernel<<<1, kTailThreads, chol2_bytes, st>>>(ws.gparts, R, ws.R1, ws.X2, Rout, gate, h->d_status);
-    wide_rows_kernel<false, true, false><<<nblk, kWideThreads, apply_bytes, st>>>(Q, I, R, nblk, nullptr, ws.X2, Q,
-                                                                                 nullptr, gate, h->d_status);
-    h->launches += 4;
+    wide_chol2_kernel<<<1, kTailThreads, chol_bytes, st>>>(ws.gparts, R, ws.R2, ws.D2, gate, h->d_status);
+    wide_inv_kernel<<<igrid, kInvWarps * 32, 0, st>>>(ws.R2, ws.D2, R, ws.X2, gate, h->d_status);
+    wide_rows_kernel<false, true, false, true><<<nblk, kWideThreads, apply_bytes, st>>>(
+        Q, I, R, nblk, nullptr, ws.X2, Q, nullptr, ws.R2, ws.R1, Rout, gate, h->d_status);
+    h->launches += 6;
     return cudaGetLastError();
 }
 

@@ -108,8 +108,9 @@ def test_fused_tail_sweeps_match_unfused(cuda_lib, dims, R, solve):
 
 
 def test_newton_reciprocals_within_two_ulp(cuda_lib):
-    # the fused tail's 1/x and 1/sqrt(x) (FP32 seed + two FP64 Newton-Raphson
-    # steps) against the correctly rounded FP64 results, over 40 decades
+    # the fused tail's 1/x and 1/sqrt(x) (FP32 seed + one third-order FP64
+    # Newton step, resp. two Newton-Raphson steps) against the correctly
+    # rounded FP64 results, over 40 decades
     rng = np.random.default_rng(3)
     x = np.concatenate([10.0 ** rng.uniform(-40, 40, 200000), rng.uniform(0.5, 2.0, 100000),
                         [1.0, 2.0, 0.5, 3.0, 1e-36, 1e36, 1.5e-36, 7e35]])
