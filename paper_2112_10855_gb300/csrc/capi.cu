@@ -78,7 +78,7 @@ void free_all(Handle* h)
     f(h->lambda); f(h->Q0); f(h->R0); f(h->Yn); f(h->W); f(h->W32); f(h->Ahat); f(h->M); f(h->S); f(h->T);
     f(h->KM); f(h->KQ); f(h->KR[0]); f(h->KR[1]); f(h->KQb[0]); f(h->KQb[1]);
     f(h->HQ[0]); f(h->HQ[1]); f(h->HR[0]); f(h->HR[1]); f(h->Qin);
-    f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_gate); f(h->d_svd_gate); f(h->d_vgate); f(h->VG); f(h->d_normX2); f(h->d_fit);
+    f(h->tbuf[0]); f(h->tbuf[1]); f(h->tA); f(h->scratch); f(h->d_status); f(h->d_gate); f(h->svd_parts); f(h->d_vgate); f(h->VG); f(h->d_normX2); f(h->d_fit);
     f(h->wide[0].base); f(h->wide[1].base);
     f(h->d_fit_count); f(h->X64_owned); f(h->X32_owned); f(h->qr_ws);
     for (int m = 0; m < cpals::kMaxN; ++m) { f(h->KV[m]); f(h->KC[m]); f(h->KE[m]); }
@@ -619,7 +619,7 @@ int cpals_create(const int64_t* dims, int N, int rank, int precision, cpals_hand
          dalloc(h, &h->KR[0], (size_t)R * R) == cudaSuccess && dalloc(h, &h->KR[1], (size_t)R * R) == cudaSuccess &&
          dalloc(h, &h->KQb[0], h->RN1 * R) == cudaSuccess && dalloc(h, &h->KQb[1], h->RN1 * R) == cudaSuccess &&
          dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
-         dalloc(h, &h->d_gate, 1) == cudaSuccess && dalloc(h, &h->d_svd_gate, 1) == cudaSuccess &&
+         dalloc(h, &h->d_gate, 1) == cudaSuccess && dalloc(h, &h->svd_parts, 2 * (size_t)R) == cudaSuccess &&
          dalloc(h, &h->d_vgate, 1) == cudaSuccess && dalloc(h, &h->VG, (size_t)R * R) == cudaSuccess &&
          dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
          dalloc(h, &h->d_fit_count, 1) == cudaSuccess;
@@ -737,7 +737,7 @@ int cpals_create_kruskal(const int64_t* dims, int N, int rank, int S, cpals_hand
          dalloc(h, &h->Kmu, S) == cudaSuccess && dalloc(h, &h->KGV, (size_t)N * S * S) == cudaSuccess &&
          dalloc(h, &h->KMw[0], (size_t)S * R) == cudaSuccess && dalloc(h, &h->KMw[1], (size_t)S * R) == cudaSuccess &&
          dalloc(h, &h->scratch, h->scratch_elems) == cudaSuccess && dalloc(h, &h->d_status, 1) == cudaSuccess &&
-         dalloc(h, &h->d_gate, 1) == cudaSuccess && dalloc(h, &h->d_svd_gate, 1) == cudaSuccess &&
+         dalloc(h, &h->d_gate, 1) == cudaSuccess && dalloc(h, &h->svd_parts, 2 * (size_t)R) == cudaSuccess &&
          dalloc(h, &h->d_vgate, 1) == cudaSuccess && dalloc(h, &h->VG, (size_t)R * R) == cudaSuccess &&
          dalloc(h, &h->d_normX2, 1) == cudaSuccess && dalloc(h, &h->d_fit, h->fit_cap + 1) == cudaSuccess &&
          dalloc(h, &h->d_fit_count, 1) == cudaSuccess;

@@ -138,7 +138,7 @@ struct Handle {
     // device scalars
     int* d_status = nullptr;
     int* d_gate = nullptr;          // fused tail: 1 when the factor QR falls back to Householder
-    int* d_svd_gate = nullptr;      // SVD solve: 1 when truncation is possible and the Jacobi SVD must run
+    double* svd_parts = nullptr;    // SVD solve: per-column norms of R0^-1 and R0 (the truncation test)
     int* d_vgate = nullptr;         // QR of a Khatri-Rao fold step: 1 when the staircase Householder must run
     double* VG = nullptr;           // R x R: the Gram of a fold step (written by its CholeskyQR2)
     bool svd_shortcut = true;       // CPALS_OPT_SVD_SHORTCUT

@@ -650,21 +650,22 @@ __global__ void __launch_bounds__(kSolveWarps * 32) trsm_qr_kernel(
 // (Sec. 3.1).  Since sigma_min >= 1 / ||R0^-1||_F and sigma_max <= ||R0||_F,
 // ||R0||_F ||R0^-1||_F < 1 / rtol proves that nothing is truncated, and then
 // T = U Sigma^-1 V^T = R0^-T exactly.  The kernel forms X = R0^-1 by back
-// substitution (one warp per column, lanes over the rows), and when
-// ||R0||_F ||X||_F rtol <= 1/4 (the margin covers the rounding of X) writes
-// T = X^T and gate = 0, so the Jacobi SVD that follows is skipped; otherwise
-// gate = 1 and the Jacobi SVD forms T.  A zero or non-finite diagonal entry
-// sends R0 to the SVD at once.
+// substitution, one warp per column over ceil(R / 8) CTAs (lanes over the
+// rows), writes T = X^T and, per column j, ||X(:, j)||^2 and ||R0(:, j)||^2
+// to parts[2 j], parts[2 j + 1].  The Jacobi kernel that follows sums them
+// in column order and, when ||R0||_F ||X||_F rtol <= 1/4 (the margin covers
+// the rounding of X), keeps T and returns; otherwise it forms T by the SVD.
+// A zero or non-finite diagonal entry writes infinite parts, which sends R0
+// to the SVD.
 constexpr int kInvWarps = 8;
 __global__ void __launch_bounds__(kInvWarps * 32) svd_shortcut_kernel(const double* __restrict__ R0, int R,
-                                                                      double rtol, double* __restrict__ T,
-                                                                      int* __restrict__ gate,
+                                                                      double* __restrict__ T,
+                                                                      double* __restrict__ parts,
                                                                       const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     __shared__ double r0[kMaxRank * kMaxRank];
     __shared__ double dinv[kMaxRank];
-    __shared__ double wsum[kInvWarps][2];
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) bad = 0;
@@ -676,47 +677,40 @@ __global__ void __launch_bounds__(kInvWarps * 32) svd_shortcut_kernel(const doub
         dinv[tid] = 1.0 / d;
     }
     __syncthreads();
+    const int j = blockIdx.x * kInvWarps + warp;
+    if (j >= R) return;
     if (bad) {
-        if (tid == 0) *gate = 1;
+        if (lane == 0) { parts[2 * j] = INFINITY; parts[2 * j + 1] = INFINITY; }
         return;
     }
     double sx = 0.0, sr = 0.0;
     const int e0 = lane, e1 = lane + 32;
-    for (int j = warp; j < R; j += kInvWarps) {
-        // X(:, j): R0 x = e_j, from k = j down
-        double w0 = (e0 == j) ? 1.0 : 0.0, w1 = (e1 == j) ? 1.0 : 0.0;
-        for (int k = j; k >= 0; --k) {
-            double xk;
-            if (k < 32) {
-                if (lane == k) w0 *= dinv[k];
-                xk = __shfl_sync(0xffffffffu, w0, k);
-            } else {
-                if (lane == k - 32) w1 *= dinv[k];
-                xk = __shfl_sync(0xffffffffu, w1, k - 32);
-            }
-            if (e0 < k) w0 = fma(-r0[e0 + R * k], xk, w0);
-            if (e1 < k) w1 = fma(-r0[e1 + R * k], xk, w1);
+    // X(:, j): R0 x = e_j, from k = j down
+    double w0 = (e0 == j) ? 1.0 : 0.0, w1 = (e1 == j) ? 1.0 : 0.0;
+    for (int k = j; k >= 0; --k) {
+        double xk;
+        if (k < 32) {
+            if (lane == k) w0 *= dinv[k];
+            xk = __shfl_sync(0xffffffffu, w0, k);
+        } else {
+            if (lane == k - 32) w1 *= dinv[k];
+            xk = __shfl_sync(0xffffffffu, w1, k - 32);
         }
-        // T = X^T: T(j, i) = X(i, j)
-        if (e0 <= j) { T[j + R * e0] = w0; sx = fma(w0, w0, sx); }
-        if (e1 <= j && e1 < R) { T[j + R * e1] = w1; sx = fma(w1, w1, sx); }
-        if (e0 > j && e0 < R) T[j + R * e0] = 0.0;
-        if (e1 > j && e1 < R) T[j + R * e1] = 0.0;
-        if (e0 <= j) sr = fma(r0[e0 + R * j], r0[e0 + R * j], sr);
-        if (e1 <= j && e1 < R) sr = fma(r0[e1 + R * j], r0[e1 + R * j], sr);
+        if (e0 < k) w0 = fma(-r0[e0 + R * k], xk, w0);
+        if (e1 < k) w1 = fma(-r0[e1 + R * k], xk, w1);
     }
+    // T = X^T: T(j, i) = X(i, j)
+    if (e0 <= j) { T[j + R * e0] = w0; sx = fma(w0, w0, sx); }
+    if (e1 <= j && e1 < R) { T[j + R * e1] = w1; sx = fma(w1, w1, sx); }
+    if (e0 > j && e0 < R) T[j + R * e0] = 0.0;
+    if (e1 > j && e1 < R) T[j + R * e1] = 0.0;
+    if (e0 <= j) sr = fma(r0[e0 + R * j], r0[e0 + R * j], sr);
+    if (e1 <= j && e1 < R) sr = fma(r0[e1 + R * j], r0[e1 + R * j], sr);
     for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sr += __shfl_xor_sync(0xffffffffu, sr, o);
     }
-    if (lane == 0) { wsum[warp][0] = sx; wsum[warp][1] = sr; }
-    __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < kInvWarps; ++w) { a += wsum[w][0]; b += wsum[w][1]; }
-        const double bound = sqrt(a) * sqrt(b);
-        *gate = (bound < INFINITY && bound * rtol <= 0.25) ? 0 : 1;
-    }
+    if (lane == 0) { parts[2 * j] = sx; parts[2 * j + 1] = sr; }
 }
 
 constexpr int kJacobiWarps = 8;
@@ -805,12 +799,26 @@ __device__ int jacobi_sweeps(T* B, T* V, int ld, int R, T tol, int max_sweeps, T
     return sweep;
 }
 
+// sc_parts (may be NULL): the truncation test's per-column norms (see
+// svd_shortcut_kernel); when they prove that nothing is truncated, T is
+// already R0^-T and the kernel returns.
 __global__ void __launch_bounds__(kJacobiThreads) jacobi_pinv_kernel(const double* __restrict__ R0, int R,
                                                                     double rtol, double* __restrict__ T,
                                                                     const int* __restrict__ status,
-                                                                    const int* __restrict__ gate)
+                                                                    const double* __restrict__ sc_parts)
 {
-    if (*status != kStatusOk || (gate && *gate == 0)) return;
+    if (*status != kStatusOk) return;
+    if (sc_parts != nullptr) {
+        __shared__ int keep;
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int j = 0; j < R; ++j) { a += sc_parts[2 * j]; b += sc_parts[2 * j + 1]; }
+            const double bound = sqrt(a) * sqrt(b);
+            keep = (bound < INFINITY && bound * rtol <= 0.25) ? 1 : 0;
+        }
+        __syncthreads();
+        if (keep) return;
+    }
     extern __shared__ double jsm[];
     const int ld = R + 1;                     // odd: lanes on different columns hit different banks
     const int Rp = (R + 1) & ~1;
@@ -1049,29 +1057,44 @@ __device__ double block_sum(double v, double* sh)
     return t;   // valid in thread 0
 }
 
-// Final: inner = sum of partials; model norm
+// Model norm, row i of the R x R sum per block (thread j: entry (i, j)):
 //  QR:     <R0^T R0, diag(l) R_N^T R_N diag(l)> = ||R0 diag(l) R_N^T||_F^2
 //          (R0 and R_N upper triangular: entry (i, j) sums k >= max(i, j))
 //  NORMAL: <S_N, diag(l) G_N diag(l)>
+// written to part[i].
+__global__ void fit_norm_kernel(const double* __restrict__ R0orS, const double* __restrict__ RNorG,
+                                const double* __restrict__ lambda, int R, int qr, double* __restrict__ part,
+                                const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    __shared__ double sh[32];
+    const int i = blockIdx.x;
+    double nrm = 0.0;
+    for (int j = threadIdx.x; j < R; j += blockDim.x) {
+        if (qr) {
+            double v = 0.0;
+            for (int k = max(i, j); k < R; ++k) v = fma(R0orS[i + R * k] * lambda[k], RNorG[j + R * k], v);
+            nrm = fma(v, v, nrm);
+        } else {
+            const int e = i + R * j;
+            nrm = fma(R0orS[e] * lambda[i], RNorG[e] * lambda[j], nrm);
+        }
+    }
+    const double t = block_sum(nrm, sh);
+    if (threadIdx.x == 0) part[i] = t;
+}
+
+// Final: inner = the sum of the nparts inner partials, the model norm = the
+// sum of the R row partials after them (fixed orders);
 // fit = 1 - sqrt(max(||X||^2 - 2 inner + nrm, 0)) / ||X||, appended to the ring.
-__global__ void fit_final_kernel(const double* __restrict__ part, int nparts, const double* __restrict__ R0orS,
-                                 const double* __restrict__ RNorG, const double* __restrict__ lambda, int R, int qr,
+__global__ void fit_final_kernel(const double* __restrict__ part, int nparts, int R,
                                  const double* __restrict__ normX2, double* __restrict__ ring, int cap,
                                  int* __restrict__ count, double* __restrict__ last, const int* __restrict__ status)
 {
     if (*status != kStatusOk) return;
     __shared__ double sh[32];
     double nrm = 0.0;
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
-        const int j = e / R, i = e - j * R;
-        if (qr) {
-            double v = 0.0;
-            for (int k = max(i, j); k < R; ++k) v = fma(R0orS[i + R * k] * lambda[k], RNorG[j + R * k], v);
-            nrm = fma(v, v, nrm);
-        } else {
-            nrm = fma(R0orS[e] * lambda[i], RNorG[e] * lambda[j], nrm);
-        }
-    }
+    for (int p = threadIdx.x; p < R; p += blockDim.x) nrm += part[nparts + p];
     double in = 0.0;
     for (int p = threadIdx.x; p < nparts; p += blockDim.x) in += part[p];
     const double tot = block_sum(nrm, sh);
@@ -1393,15 +1416,15 @@ cudaError_t svd_operator(Handle* h, double rtol)
                                             (int)smem));
         attr_set = true;
     }
-    const int* gate = nullptr;
+    const double* parts = nullptr;
     if (h->svd_shortcut) {
-        svd_shortcut_kernel<<<1, kInvWarps * 32, 0, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_svd_gate,
-                                                                  h->d_status);
+        svd_shortcut_kernel<<<(h->R + kInvWarps - 1) / kInvWarps, kInvWarps * 32, 0, h->stream>>>(
+            h->R0, h->R, h->T, h->svd_parts, h->d_status);
         h->launches++;
         CPALS_CUDA_TRY(cudaGetLastError());
-        gate = h->d_svd_gate;
+        parts = h->svd_parts;
     }
-    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status, gate);
+    jacobi_pinv_kernel<<<1, kJacobiThreads, smem, h->stream>>>(h->R0, h->R, rtol, h->T, h->d_status, parts);
     h->launches++;
     return cudaGetLastError();
 }
@@ -1476,11 +1499,12 @@ cudaError_t fit_efficient(Handle* h, int solve)
     const int kgrid = (h->R + kchunk - 1) / kchunk;
     fit_inner_kernel<<<dim3(nb, (unsigned)kgrid), 256, 0, h->stream>>>(qr ? h->W : h->M, h->Ahat, h->R0, I, h->R, qr,
                                                                       kchunk, h->scratch, h->d_status);
-    fit_final_kernel<<<1, 256, 0, h->stream>>>(h->scratch, (int)nb * kgrid, qr ? h->R0 : h->S,
-                                               qr ? h->Rf[n] : h->G[n],
-                                               h->lambda, h->R, qr, h->d_normX2, h->d_fit, h->fit_cap,
+    const int nparts = (int)nb * kgrid;
+    fit_norm_kernel<<<h->R, 64, 0, h->stream>>>(qr ? h->R0 : h->S, qr ? h->Rf[n] : h->G[n], h->lambda, h->R, qr,
+                                                h->scratch + nparts, h->d_status);
+    fit_final_kernel<<<1, 256, 0, h->stream>>>(h->scratch, nparts, h->R, h->d_normX2, h->d_fit, h->fit_cap,
                                                h->d_fit_count, h->d_fit + h->fit_cap, h->d_status);
-    h->launches += 2;
+    h->launches += 3;
     return cudaGetLastError();
 }
 
