@@ -329,7 +329,7 @@ int cpals_set_option(cpals_handle* h, int option, int64_t value);
 
 /* Test hook (the paper has no counterpart): the reciprocal and reciprocal
  * square root that the factor QR of the fused mode tail uses on its
- * sequential chain (an FP32 hardware approximation refined in FP64: one
+ * sequential chain (hardware approximations refined in FP64: one
  * third-order Newton step for the reciprocal, two Newton-Raphson steps for
  * the reciprocal square root), applied to n device values x (rsqrt gets 0 where
  * x <= 0).  x, rcp, rsqrt: device arrays of n doubles.  Synchronises the

@@ -43,8 +43,8 @@
 // many lanes are active, so the substitutions give each row T lanes (T from a
 // cost model: the fewest FP64 instructions on the busiest scheduler), the
 // Cholesky keeps only one reciprocal per step on its sequential chain (square
-// roots at the end), and those reciprocals come from an FP32 seed refined by
-// Newton-Raphson steps.
+// roots at the end), and those reciprocals come from a hardware approximation
+// refined by one third-order Newton step.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -110,22 +110,22 @@ struct TailSmem {
     }
 };
 
-// 1/d and 1/sqrt(d) to about one ulp from the FP32 hardware approximation
-// (rcp.approx / rsqrt.approx, about 2^-23 relative).  The reciprocal takes one
-// third-order step of the Newton iteration for 1/d: with e = 1 - d y,
-// y (1 + e + e^2) = (1 - e^3) / d, so the relative error goes from e to e^3
-// (below 2^-66) in three dependent FMAs.  The reciprocal square root takes
-// two Newton-Raphson steps, y <- y + y (1/2 - (d/2) y^2), each squaring the
-// error.  A dependent FP64 operation costs 64 cycles on this part, and these
+// 1/d and 1/sqrt(d) to about one ulp from the hardware approximations.  The
+// reciprocal starts from rcp.approx.ftz.f64 and takes one third-order step of
+// the Newton iteration for 1/d: with e = 1 - d y, y (1 + e + e^2) =
+// (1 - e^3) / d, so the relative error goes from e to e^3 in three dependent
+// FMAs (the accuracy test checks the result within 2 ulp over 40 decades).
+// The reciprocal square root starts from the FP32 rsqrt.approx (about 2^-23)
+// and takes two Newton-Raphson steps, y <- y + y (1/2 - (d/2) y^2), each
+// squaring the error.  A dependent FP64 operation costs 64 cycles on this part, and these
 // are a few of them against the much longer exact division and square root.
 // Outside the FP32 normal range the exact FP64 operations are used.
 __device__ __forceinline__ double rcp_nr(double d)
 {
     const double a = fabs(d);
     if (!(a > 1e-36 && a < 1e36)) return 1.0 / d;
-    float f;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"((float)d));
-    const double y = (double)f;
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
     const double e = fma(-d, y, 1.0);
     return fma(y, fma(e, e, e), y);
 }

@@ -108,7 +108,7 @@ def test_fused_tail_sweeps_match_unfused(cuda_lib, dims, R, solve):
 
 
 def test_newton_reciprocals_within_two_ulp(cuda_lib):
-    # the fused tail's 1/x and 1/sqrt(x) (FP32 seed + one third-order FP64
+    # the fused tail's 1/x and 1/sqrt(x) (hardware seed + one third-order FP64
     # Newton step, resp. two Newton-Raphson steps) against the correctly
     # rounded FP64 results, over 40 decades
     rng = np.random.default_rng(3)
