@@ -230,6 +230,131 @@ __global__ void __launch_bounds__(128) ttm_fiber4_kernel(
     }
 }
 
+// FP32 TTM over the fastest mode (L = 1) as a tiled GEMM, out(t, r) =
+// sum_k In(k, t) Q(k, r) with every fiber In(:, t) contiguous.  A CTA of 256
+// threads owns 128 fibers and BN columns (BN = 32 or 64, Q zero-padded to
+// BN) and walks its K range in chunks of 32.  The [128 fibers x 32] block is
+// read as 128-byte fiber rows (eight threads per row, 16-byte loads, K % 4
+// == 0) and stored k-major in shared memory; Q's FP32 chunk [32 x BN] sits
+// beside it.  Each thread accumulates BN/8 fibers x 4 columns from two
+// 16-byte reads per k, and the next chunk is loaded into registers while the
+// current one is multiplied.  With a K split (blockIdx.z) each split writes
+// its partial at out + z R T.  The k order per output is ascending within a
+// split, as in the one-thread-per-fiber kernel above.
+constexpr int kFgRows = 128;
+constexpr int kFgK = 32;
+constexpr int kFgThreads = 256;
+constexpr int kFgLd = kFgRows + 4;     // k-major rows of the fiber block, 16-byte aligned
+
+template <int BN>
+__global__ void __launch_bounds__(kFgThreads) ttm_fiber_gemm_kernel(const float* __restrict__ in,
+                                                                    const float* __restrict__ qf,
+                                                                    float* __restrict__ out, int64_t K, int64_t Tn,
+                                                                    int R, int64_t kchunk,
+                                                                    const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    constexpr int TM = BN / 8;                 // fibers per thread
+    constexpr int CG = BN / 4;                 // column groups of 4
+    constexpr int A4 = kFgRows * kFgK / 4 / kFgThreads;   // float4 of the fiber block per thread (4)
+    constexpr int B4 = kFgK * BN / 4 / kFgThreads;        // float4 of the Q chunk per thread (1 or 2)
+    __shared__ __align__(16) float As[kFgK][kFgLd];
+    __shared__ __align__(16) float Bs[kFgK][BN];
+    const int tid = threadIdx.x;
+    const int cg = tid % CG, tg = tid / CG;
+    const int64_t t0 = (int64_t)blockIdx.x * kFgRows;
+    const int64_t kb = (int64_t)blockIdx.z * kchunk;
+    const int64_t ke = (kb + kchunk < K) ? kb + kchunk : K;
+    float acc[TM][4];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    float4 ra[A4], rb[B4];
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < A4; ++u) {
+            const int idx = tid + u * kFgThreads;
+            const int row = idx >> 3, k4 = idx & 7;
+            const int64_t t = t0 + row, k = k0 + 4 * k4;
+            ra[u] = (t < Tn && k < ke) ? __ldg(reinterpret_cast<const float4*>(in + t * K + k))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < B4; ++u) {
+            const int idx = tid + u * kFgThreads;
+            const int kk = idx / CG, c4 = idx - kk * CG;
+            rb[u] = *reinterpret_cast<const float4*>(qf + (k0 + kk) * BN + 4 * c4);
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int u = 0; u < A4; ++u) {
+            const int idx = tid + u * kFgThreads;
+            const int row = idx >> 3, k4 = idx & 7;
+            As[4 * k4 + 0][row] = ra[u].x;
+            As[4 * k4 + 1][row] = ra[u].y;
+            As[4 * k4 + 2][row] = ra[u].z;
+            As[4 * k4 + 3][row] = ra[u].w;
+        }
+#pragma unroll
+        for (int u = 0; u < B4; ++u) {
+            const int idx = tid + u * kFgThreads;
+            const int kk = idx / CG, c4 = idx - kk * CG;
+            *reinterpret_cast<float4*>(&Bs[kk][4 * c4]) = rb[u];
+        }
+    };
+    if (kb < ke) load(kb);
+    for (int64_t k0 = kb; k0 < ke; k0 += kFgK) {
+        __syncthreads();                       // the previous chunk is read
+        store();
+        __syncthreads();
+        if (k0 + kFgK < ke) load(k0 + kFgK);
+#pragma unroll 8
+        for (int k = 0; k < kFgK; ++k) {
+            float a[TM];
+#pragma unroll
+            for (int i = 0; i < TM; i += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(&As[k][tg * TM + i]);
+                a[i] = v.x; a[i + 1] = v.y; a[i + 2] = v.z; a[i + 3] = v.w;
+            }
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[k][4 * cg]);
+#pragma unroll
+            for (int i = 0; i < TM; ++i) {
+                acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+                acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+                acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+                acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
+            }
+        }
+    }
+    float* o = out + (int64_t)blockIdx.z * ((int64_t)R * Tn);
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t t = t0 + tg * TM + i;
+        if (t >= Tn) break;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * cg + j;
+            if (c < R) o[t * R + c] = acc[i][j];
+        }
+    }
+}
+
+// Q (K x R, FP64, ldq) to the FP32 [Kp x BN] copy of the fiber GEMM (zero
+// beyond K and R).
+__global__ void fiber_q_kernel(const double* __restrict__ Q, int64_t ldq, int64_t K, int R, int64_t Kp, int BN,
+                               float* __restrict__ qf, const int* __restrict__ status)
+{
+    if (*status != kStatusOk) return;
+    const int64_t total = Kp * BN;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / BN;
+        const int c = (int)(e - k * BN);
+        qf[e] = (k < K && c < R) ? (float)Q[k + ldq * (int64_t)c] : 0.0f;
+    }
+}
+
 // out[g*n + e] = sum of part[q*n + e] over the splits q of group g (groups of
 // `group` consecutive splits, added in split order).  With one group this is
 // the final sum; with several, a second call adds the group sums in order.
@@ -341,8 +466,43 @@ cudaError_t launch_ttm_split(Handle* h, const T* in, const double* Q, int64_t ld
                       (((uintptr_t)in) & 15) == 0 && (((uintptr_t)out) & 15) == 0 && (((uintptr_t)part) & 15) == 0;
     const int64_t gy = (R + rc - 1) / rc;
     const int64_t outn = rows * R;
-    // FP32 contraction of the fastest mode: one thread per contiguous fiber
+    // FP32 contraction of the fastest mode: a tiled GEMM above rank 16 (its
+    // FP32 copy of Q is carved from the end of the partials' space), else one
+    // thread per contiguous fiber
     const bool fiber = sizeof(T) == 4 && s.L == 1 && (s.K % 4) == 0 && (((uintptr_t)in) & 15) == 0;
+    if (fiber && R > 16 && R <= 64 && part != nullptr) {
+        const int BN = R > 32 ? 64 : 32;
+        const int64_t Kp = (s.K + kFgK - 1) / kFgK * kFgK;
+        const int64_t qelems = (Kp * BN + 3) / 4 * 4;       // floats, 16-byte multiple
+        const int64_t qe_T = (qelems * 4 + (int64_t)sizeof(T) - 1) / (int64_t)sizeof(T);
+        if (part_elems >= qe_T + outn) {
+            float* qf = reinterpret_cast<float*>(part + (part_elems - qe_T));
+            if ((((uintptr_t)qf) & 15) == 0) {
+                const int64_t pe = part_elems - qe_T;
+                const int64_t gx = (s.T + kFgRows - 1) / kFgRows;
+                int64_t ks = ttm_ksplit(gx, kFgThreads, s.K / kFgK, h->num_sms, outn, pe, true);
+                int64_t kc = ((s.K + ks - 1) / ks + kFgK - 1) / kFgK * kFgK;      // whole 32-chunks
+                ks = (s.K + kc - 1) / kc;
+                const unsigned qgrid = (unsigned)std::max<int64_t>(
+                    1, std::min<int64_t>((Kp * BN + 255) / 256, 8LL * h->num_sms));
+                fiber_q_kernel<<<qgrid, 256, 0, h->stream>>>(Q, ldq, s.K, R, Kp, BN, qf, h->d_status);
+                h->launches++;
+                CPALS_CUDA_TRY(cudaGetLastError());
+                const dim3 grid((unsigned)gx, 1, (unsigned)ks);
+                float* dst = reinterpret_cast<float*>(ks > 1 ? part : out);
+                const float* fin = reinterpret_cast<const float*>(in);
+                if (BN == 64)
+                    ttm_fiber_gemm_kernel<64><<<grid, kFgThreads, 0, h->stream>>>(fin, qf, dst, s.K, s.T, R, kc,
+                                                                                  h->d_status);
+                else
+                    ttm_fiber_gemm_kernel<32><<<grid, kFgThreads, 0, h->stream>>>(fin, qf, dst, s.K, s.T, R, kc,
+                                                                                  h->d_status);
+                h->launches++;
+                CPALS_CUDA_TRY(cudaGetLastError());
+                return reduce_ksplit<T>(h, part, ks, outn, out);
+            }
+        }
+    }
     if (fiber) {
         const int rc4 = R > 24 ? 32 : (R + 3) / 4 * 4;
         constexpr int tpbf = 128;
