@@ -17,7 +17,7 @@
 //   - the substitution Ahat R0^T = W (a singular R0 sets the problem's status
 //     and keeps its factor),
 //   - column normalisation (2-norm) into A_n and lambda,
-//   - the Householder QR A_n = Q_n R_n,
+//   - the QR A_n = Q_n R_n (CholeskyQR2 with its check, Householder when refused),
 //   - and, for the next mode, the QR V_{n+1} = Q0 R0 of the Khatri-Rao
 //     product of its two other R factors (Sec. 3.1), by the staircase
 //     Householder QR of a product of two triangular factors (Sec. 3.3.3: no
@@ -139,6 +139,210 @@ __device__ void cta_householder(double* W, int m, int n, double* Q, double* Rout
         Rout[e] = v;
     }
     __syncthreads();
+}
+
+// ---------------------------------------------------------------- CholeskyQR2 in one CTA
+// The factor QR A_n = Q_n R_n by CholeskyQR2 (Fukaya, Nakatsukasa,
+// Yanagisawa, Yamamoto 2014): R1 = chol(A^T A), Q1 = A R1^-1,
+// R2 = chol(Q1^T Q1), Q = Q1 R2^-1, R = R2 R1.  It is accepted when the first
+// Cholesky has no breakdown and every entry of Q1^T Q1 lies within 1e-2 of
+// the identity (which bounds cond(A) near 7e6, where CholeskyQR2 is as
+// accurate as Householder); otherwise the caller runs its Householder QR.
+// The triangular inverses are formed one warp per column, so the products
+// with them are independent FMAs; every sum runs in a fixed order.  (The QR
+// of V stays the staircase Householder QR: CholeskyQR2 would treat the
+// R^2 x R product as dense, about six times the FP64 work, and the batch's
+// factorisation kernels are bound by FP64 throughput.)
+constexpr double kCqrCheckB = 1e-2;
+constexpr int kCqMaxE = kBMaxR * (kBMaxR + 1) / 2;
+constexpr int kCqMaxWarps = 8;                 // factorisation CTAs have at most 256 threads
+constexpr int kCqDoubles = kCqMaxWarps * kCqMaxE + 3 * kBMaxR * kBMaxR + kBMaxR;
+
+struct CqWs {
+    double* part;   // kCqMaxWarps x kCqMaxE Gram partials
+    double* G;      // n x n Gram, then the Cholesky factor
+    double* U1;     // n x n, R1
+    double* X;      // n x n row-major triangular inverse
+    double* d;      // n reciprocals of the diagonal
+};
+
+__device__ CqWs cq_ws(double* base)
+{
+    CqWs w;
+    w.part = base;
+    w.G = w.part + kCqMaxWarps * kCqMaxE;
+    w.U1 = w.G + kBMaxR * kBMaxR;
+    w.X = w.U1 + kBMaxR * kBMaxR;
+    w.d = w.X + kBMaxR * kBMaxR;
+    return w;
+}
+
+// G (n x n, both triangles) = S^T S for the row-major m x n matrix S: warps
+// over contiguous row blocks, lanes over the packed upper-triangle entries,
+// the warps' partials then added in warp order.
+__device__ void cq_gram(const double* S, int m, int n, double* part, double* G)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nE = n * (n + 1) / 2;
+    constexpr int EJ = (kCqMaxE + 31) / 32;
+    int ea[EJ], eb[EJ];
+    double acc[EJ];
+#pragma unroll
+    for (int j = 0; j < EJ; ++j) {
+        acc[j] = 0.0;
+        ea[j] = eb[j] = 0;
+        if (lane + 32 * j < nE) tri_index(lane + 32 * j, ea[j], eb[j]);
+    }
+    for (int i = warp * m / nw; i < (warp + 1) * m / nw; ++i) {
+        const double* row = S + (size_t)i * n;
+#pragma unroll
+        for (int j = 0; j < EJ; ++j)
+            if (lane + 32 * j < nE) acc[j] = fma(row[ea[j]], row[eb[j]], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < EJ; ++j)
+        if (lane + 32 * j < nE) part[warp * nE + lane + 32 * j] = acc[j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nE; e += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += part[w * nE + e];
+        int a, b;
+        tri_index(e, a, b);
+        G[a + n * b] = t;
+        G[b + n * a] = t;
+    }
+    __syncthreads();
+}
+
+// In-place upper Cholesky of G (n x n, n <= 32) on warp 0, square roots
+// deferred to the end: step j subtracts M(j, a) M(j, b) / d_j from the
+// trailing triangle.  Then U(j, k) = M(j, k) / sqrt(d_j), zero below, and
+// d[j] = 1 / U(j, j).  Returns false (in every thread) on a pivot that is not
+// positive and finite.
+__device__ bool cq_cholesky(double* G, int n, double* d, int* flag)
+{
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+        bool bad = false;
+        for (int j = 0; j < n; ++j) {
+            const double piv = G[j + n * j];
+            const bool ok = piv > 0.0 && piv < INFINITY;
+            bad = bad || !ok;
+            const double inv = ok ? rcp_nr(piv) : 0.0;
+            for (int a = j + 1 + lane; a < n; a += 32) G[a + n * j] = G[j + n * a] * inv;
+            __syncwarp();
+            const int m = n - 1 - j;
+            for (int p = lane; p < m * (m + 1) / 2; p += 32) {
+                int a, b;
+                tri_index(p, a, b);
+                a += j + 1;
+                b += j + 1;
+                G[a + n * b] = fma(-G[a + n * j], G[j + n * b], G[a + n * b]);
+            }
+            __syncwarp();
+        }
+        for (int j = lane; j < n; j += 32) {
+            const double piv = G[j + n * j];
+            d[j] = (piv > 0.0 && piv < INFINITY) ? rsqrt_nr(piv) : 1.0;
+        }
+        __syncwarp();
+        for (int p = lane; p < n * n; p += 32) {
+            const int a = p % n, b = p / n;
+            if (a > b) G[p] = 0.0;
+            else if (a == b) G[p] = (G[p] > 0.0 && G[p] < INFINITY) ? G[p] * d[a] : 1.0;
+            else G[p] *= d[a];
+        }
+        if (lane == 0) *flag = bad ? 1 : 0;
+    }
+    __syncthreads();
+    return *flag == 0;
+}
+
+// X = U^-1 (U upper, n x n column-major; d[k] = 1 / U(k, k)) into X row-major
+// (X(k, c) at X[k n + c]), one warp per column, lanes over the rows: from the
+// bottom row up, X(i, c) = delta_ic / U(i, i) - (sum_{k > i} U(i, k) X(k, c))
+// / U(i, i), each known value broadcast and added to the rows above.
+__device__ void cq_inverse(const double* U, const double* d, int n, double* X)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < n; c += nw) {
+        double acc = 0.0, x = 0.0;
+        for (int i = c; i >= 0; --i) {
+            double xi = 0.0;
+            if (lane == i) {
+                xi = fma(-acc, d[i], (i == c) ? d[i] : 0.0);
+                x = xi;
+            }
+            xi = __shfl_sync(0xffffffffu, xi, i);
+            if (lane < i) acc = fma(U[lane + n * i], xi, acc);
+        }
+        if (lane < n) X[lane * n + c] = (lane <= c) ? x : 0.0;
+    }
+    __syncthreads();
+}
+
+// out(i, c) = sum_{k <= c} val(i, k) X(k, c) for the m rows (X row-major,
+// upper), written through store(i, c, value).
+template <typename Val, typename Store>
+__device__ void cq_apply(int m, int n, const double* X, Val val, Store store)
+{
+    for (int p = threadIdx.x; p < m * n; p += blockDim.x) {
+        const int i = p / n, c = p - i * n;
+        double s = 0.0;
+        for (int k = 0; k <= c; ++k) s = fma(val(i, k), X[k * n + c], s);
+        store(i, c, s);
+    }
+    __syncthreads();
+}
+
+// The check on Q1^T Q1 (in G) and the second pass: R2 = chol(Q1^T Q1) in
+// w.G, its inverse in w.X.  False when refused.
+__device__ bool cq_second(CqWs w, int n, int* flag)
+{
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
+        const int a = p % n, b = p / n;
+        if (!(fabs(w.G[p] - (a == b ? 1.0 : 0.0)) <= kCqrCheckB)) *flag = 1;
+    }
+    __syncthreads();
+    if (*flag) return false;
+    if (!cq_cholesky(w.G, n, w.d, flag)) return false;
+    cq_inverse(w.G, w.d, n, w.X);
+    return true;
+}
+
+// R = R2 R1 (upper; R2 in w.G, R1 in w.U1) into Rout (n x n column-major).
+__device__ void cq_rprod(CqWs w, int n, double* Rout)
+{
+    for (int p = threadIdx.x; p < n * n; p += blockDim.x) {
+        const int a = p % n, b = p / n;
+        double s = 0.0;
+        for (int k = a; k <= b; ++k) s = fma(w.G[a + n * k], w.U1[k + n * b], s);
+        Rout[p] = (a <= b) ? s : 0.0;
+    }
+    __syncthreads();
+}
+
+// Factor QR of A (m x n column-major, ld m; left as it is).  S, S2: m x n
+// row-major scratch.  On success Q (m x n column-major) is in S and R in Rout.
+__device__ bool cta_cqr2(const double* A, int m, int n, double* S, double* S2, double* Rout, CqWs w, int* flag)
+{
+    for (int p = threadIdx.x; p < m * n; p += blockDim.x) {
+        const int i = p / n, c = p - i * n;
+        S[p] = A[i + m * c];
+    }
+    __syncthreads();
+    cq_gram(S, m, n, w.part, w.G);
+    if (!cq_cholesky(w.G, n, w.d, flag)) return false;
+    for (int p = threadIdx.x; p < n * n; p += blockDim.x) w.U1[p] = w.G[p];
+    cq_inverse(w.G, w.d, n, w.X);
+    cq_apply(m, n, w.X, [&](int i, int k) { return S[i * n + k]; }, [&](int i, int c, double v) { S2[i * n + c] = v; });
+    cq_gram(S2, m, n, w.part, w.G);
+    if (!cq_second(w, n, flag)) return false;
+    cq_apply(m, n, w.X, [&](int i, int k) { return S2[i * n + k]; }, [&](int i, int c, double v) { S[i + m * c] = v; });
+    cq_rprod(w, n, Rout);
+    return true;
 }
 
 // ---------------------------------------------------------------- grouped contractions
@@ -343,7 +547,7 @@ __global__ void batch_w_kernel(const BProb* __restrict__ probs, const BItem* __r
 
 // ---------------------------------------------------------------- factorisation chain
 struct BSmem {
-    int64_t regA, regB, r0, rn, w;   // offsets in doubles
+    int64_t regA, regB, r0, rn, w, cq;   // offsets in doubles
     int64_t total;
 };
 
@@ -361,7 +565,8 @@ __host__ __device__ inline BSmem bsmem_layout(int maxR, int maxI)
     s.r0 = s.regB + sb;
     s.rn = s.r0 + (int64_t)maxR * maxR;
     s.w = s.rn + (int64_t)maxR * maxR;
-    s.total = s.w + ir + 128;    // + tau / red
+    s.cq = s.w + ir;
+    s.total = s.cq + kCqDoubles + 128;    // + tau / red
     return s;
 }
 
@@ -423,7 +628,8 @@ __global__ void batch_tail_kernel(const BProb* __restrict__ probs, const int* __
     double* Ws = bsm + L.w;
     double* tau = bsm + L.total - 128;
     double* red = tau + 64;
-    __shared__ int singular;
+    const CqWs cw = cq_ws(bsm + L.cq);
+    __shared__ int singular, cq_flag;
     __shared__ double inner_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
@@ -507,13 +713,18 @@ __global__ void batch_tail_kernel(const BProb* __restrict__ probs, const int* __
         }
         if (tid < R) lam[tid] = red[32 + tid];
         __syncthreads();
-        // A_n = Q_n R_n (FP64, shared memory)
-        cta_householder(regA, In, R, regB, Rns, tau, red);
+        // A_n = Q_n R_n (FP64, shared memory): CholeskyQR2 (Q into Ws, the
+        // W stash, which is spent), Householder when it is refused
+        const double* Qs = Ws;
+        if (!cta_cqr2(regA, In, R, Ws, regB, Rns, cw, &cq_flag)) {
+            cta_householder(regA, In, R, regB, Rns, tau, red);
+            Qs = regB;
+        }
         double* Qn = F + pr.q[n];
         double* Rn_g = F + pr.rf[n];
-        for (int e = tid; e < In * R; e += blockDim.x) Qn[e] = regB[e];
+        for (int e = tid; e < In * R; e += blockDim.x) Qn[e] = Qs[e];
         for (int e = tid; e < RR; e += blockDim.x) Rn_g[e] = Rns[e];
-        write_qf(pr, n, regB, Qf);
+        write_qf(pr, n, Qs, Qf);
         if (n == 2) {
             // efficient fit after the last mode (Sec. 3.3.1)
             double s = 0.0;

@@ -110,49 +110,6 @@ struct TailSmem {
     }
 };
 
-// 1/d and 1/sqrt(d) to about one ulp from the hardware approximations.  The
-// reciprocal starts from rcp.approx.ftz.f64 and takes one third-order step of
-// the Newton iteration for 1/d: with e = 1 - d y, y (1 + e + e^2) =
-// (1 - e^3) / d, so the relative error goes from e to e^3 in three dependent
-// FMAs (the accuracy test checks the result within 2 ulp over 40 decades).
-// The reciprocal square root starts from the FP32 rsqrt.approx (about 2^-23)
-// and takes two Newton-Raphson steps, y <- y + y (1/2 - (d/2) y^2), each
-// squaring the error.  A dependent FP64 operation costs 64 cycles on this part, and these
-// are a few of them against the much longer exact division and square root.
-// Outside the FP32 normal range the exact FP64 operations are used.
-__device__ __forceinline__ double rcp_nr(double d)
-{
-    const double a = fabs(d);
-    if (!(a > 1e-36 && a < 1e36)) return 1.0 / d;
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
-    const double e = fma(-d, y, 1.0);
-    return fma(y, fma(e, e, e), y);
-}
-
-__device__ __forceinline__ double rsqrt_nr(double d)
-{
-    if (!(d > 1e-36 && d < 1e36)) return 1.0 / sqrt(d);
-    float f;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(f) : "f"((float)d));
-    double y = (double)f;
-    const double h = 0.5 * d;
-    double e = fma(-h * y, y, 0.5);
-    y = fma(y, e, y);
-    e = fma(-h * y, y, 0.5);
-    return fma(y, e, y);
-}
-
-// Upper-triangle index e -> (a, b) with a <= b, e = b (b + 1) / 2 + a.
-__device__ __forceinline__ void tri_index(int e, int& a, int& b)
-{
-    int q = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    while (q * (q + 1) / 2 > e) --q;
-    while ((q + 1) * (q + 2) / 2 <= e) ++q;
-    b = q;
-    a = e - q * (q + 1) / 2;
-}
-
 // part[e] = sum over the stashed rows of row[a] * row[b] (upper triangle of
 // the local Gram), rows summed in a fixed order per group and the groups in
 // order.

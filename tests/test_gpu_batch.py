@@ -3,6 +3,9 @@ dims and ranks; per sweep two passes over all tensors (dimension tree) and
 one kernel per mode update.  Checked against the FP64 oracle run on each
 problem separately, from the same initial factors.
 
+The factor QRs run CholeskyQR2 with its acceptance check and fall back to
+Householder (an ill-conditioned factor checks that path).
+
 Bars: the Multi-TTM and W = Y_(n) Q0 run in FP32 (relative error
 ~sqrt(I) * 2^-24 per contraction), everything else in FP64.  After one sweep the factors agree with
 the oracle to 1e-4 relative (FP32 error amplified by the solve's
@@ -61,6 +64,34 @@ def test_batch_one_sweep_matches_oracle(cuda_lib, small_batch):
             assert rel(A[p][m], o.factor(m)) <= 1e-4, (p, m, rel(A[p][m], o.factor(m)))
         assert rel(lam[p], o.lam()) <= 1e-4
         assert abs(fits[p] - o.fit_last()) <= 1e-5
+
+
+def test_batch_ill_conditioned_factor_takes_householder(cuda_lib, small_batch):
+    # a problem whose mode-0 factor has two columns 1e-9 apart, started from
+    # the true factors: after mode 0's update cond(A_0) ~ 1e9, past what the
+    # factorisation kernel's CholeskyQR2 accepts, so its Householder QR runs.
+    # A wrongly accepted CholeskyQR2 would leave Q_0 far from orthonormal and
+    # the next modes' updates far from the oracle's.
+    dims, R = (40, 36, 32), 4
+    rng = np.random.default_rng(11)
+    F = [np.linalg.qr(rng.standard_normal((d, R)))[0] for d in dims]
+    F[0][:, 1] = F[0][:, 0] + 1e-9 * rng.standard_normal(dims[0])
+    F = [np.asfortranarray(f) for f in F]
+    X = inputs.cp_full(dims, F, np.ones(R))
+    probs = list(small_batch[:2])
+    b = cpals.CPALSBatch([p.dims for p in probs] + [dims], [p.rank for p in probs] + [R])
+    b.set_tensors([p.X.astype(np.float32) for p in probs] + [X.astype(np.float32)])
+    b.set_factors([p.init_factors for p in probs] + [F])
+    fits, st = b.iterate(1)
+    assert (st == 0).all()
+    A, lam = b.get_factors()
+    o = oracle.OracleCPALS(X.astype(np.float32).astype(np.float64), dims, R)
+    o.set_factors(F)
+    o.iterate(1, solve=oracle.QR)
+    # (no fit check: at fit ~1 on a noise-free tensor the efficient fit's
+    # residual identity cancels to the FP32 rounding level, ~3e-4)
+    for m in range(3):
+        assert rel(A[2][m], o.factor(m)) <= 1e-4, (m, rel(A[2][m], o.factor(m)))
 
 
 def test_batch_converged_fits_match_oracle(cuda_lib, small_batch):
