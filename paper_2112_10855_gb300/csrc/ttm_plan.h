@@ -96,12 +96,18 @@ inline int64_t ttm_ksplit(int64_t ctas_xy, int tpb, int64_t K, int num_sms, int6
     }
 }
 
-// Register width per thread: R itself up to 16, then 20, 24, 32 (wider R in chunks of 32).
+// Register width per thread: R itself up to 16, then 20, 24, 32.  Wider R is
+// cut into ceil(R / 32) equal column blocks, each rounded up to one of those
+// widths (R = 40: 2 x 20, R = 48: 2 x 24, R = 64: 2 x 32), so that no block
+// computes many columns that are not there.
 inline int ttm_width(int R) {
     if (R <= 16) return R;
     if (R <= 20) return 20;
     if (R <= 24) return 24;
-    return 32;
+    if (R <= 32) return 32;
+    const int gy = (R + 31) / 32;
+    const int w = (R + gy - 1) / gy;
+    return w <= 20 ? 20 : (w <= 24 ? 24 : 32);
 }
 
 // CTA sizes of the FP64 row kernel.  FP64 is bound by the FP64 pipe of each
