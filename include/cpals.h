@@ -282,7 +282,7 @@ int cpals_sync(cpals_handle* h);
  *    device status word; the rest of the update is skipped and the factors
  *    stay as they were, and the next synchronising call reports the error.
  *    Set it back to 0 and the handle works as before.
- *  CPALS_OPT_FUSED_TAIL (default 1): the end of each mode update -- the
+ *  CPALS_OPT_FUSED_TAIL (0, 1 or 2; default 2): the end of each mode update -- the
  *    solve (substitution with R0, the SVD or pseudo-inverse operator, or the
  *    Cholesky factor of S_n), the column normalisation into lambda and A_n,
  *    and the QR A_n = Q_n R_n (QR/SVD solves) or the Gram A_n^T A_n (normal
@@ -292,7 +292,11 @@ int cpals_sync(cpals_handle* h);
  *    leaves Q1^T Q1 within 1e-2 of the identity (cond(A_n) below about 7e6),
  *    and otherwise the Householder QR runs as with 0.  Both give the thin QR
  *    with a positive diagonal of R_n, so only rounding differs.  0 runs the
- *    separate solve, normalisation and Householder QR kernels.
+ *    separate solve, normalisation and Householder QR kernels.  2 (the
+ *    default) takes 1 from rank 8 up and 0 below it, where the separate
+ *    kernels measured faster; the choice depends on the rank only, so every
+ *    factor QR of a handle takes the same path.  Values other than 0, 1 and
+ *    2 are CPALS_ERR_ARG.
  *  CPALS_OPT_SVD_SHORTCUT (default 1): before the Jacobi SVD of R0 (the SVD
  *    solve), X = R0^-1 is formed by substitution; when
  *    ||R0||_F ||X||_F svd_rtol <= 1/4, no singular value can fall below

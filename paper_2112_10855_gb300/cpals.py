@@ -210,9 +210,11 @@ class CPALS:
         issues no copies and its bounded waits run out after 1 ms."""
         _check(self._h, load().cpals_set_option(self._h, 4, 1 if on else 0))
 
-    def set_fused_tail(self, on: bool):
-        """CPALS_OPT_FUSED_TAIL: solve, normalisation and CholeskyQR2 of the factor in one cluster kernel."""
-        _check(self._h, load().cpals_set_option(self._h, 5, 1 if on else 0))
+    def set_fused_tail(self, on):
+        """CPALS_OPT_FUSED_TAIL: solve, normalisation and CholeskyQR2 of the factor in the fused kernels
+        (True / False force it; "auto", the default, takes them from rank 8 up)."""
+        v = 2 if on == "auto" else (1 if on else 0)
+        _check(self._h, load().cpals_set_option(self._h, 5, v))
 
     def set_svd_shortcut(self, on: bool):
         """CPALS_OPT_SVD_SHORTCUT: skip the Jacobi SVD when a norm bound proves nothing is truncated."""

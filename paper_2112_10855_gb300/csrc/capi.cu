@@ -175,7 +175,7 @@ inline bool is_normal(int solve) { return solve == CPALS_SOLVE_NORMAL || solve =
 cudaError_t factor_qr_gram(Handle* h, int m, bool want_qr)
 {
     const int64_t I = h->dims[m];
-    if (h->fused_tail && (cpals::wide_tail_on(h) || cpals::mode_tail_ok(I, h->R, 1))) {
+    if (cpals::tail_fused(h) && (cpals::wide_tail_on(h) || cpals::mode_tail_ok(I, h->R, 1))) {
         CPALS_CUDA_TRY(cpals::mode_tail(h, m, 4, h->A[m], nullptr, want_qr));
         if (want_qr) CPALS_CUDA_TRY(cpals::householder_qr(h, h->A[m], I, h->R, h->Q[m], h->Rf[m], true, h->d_gate));
         return cudaSuccess;
@@ -245,7 +245,7 @@ cudaError_t finish_update(Handle* h, int n, int solve, double rtol, bool have_op
 {
     const int64_t In = h->dims[n];
     const bool normal = is_normal(solve);
-    if (h->fused_tail && (cpals::wide_tail_on(h) || cpals::mode_tail_ok(In, h->R))) {
+    if (cpals::tail_fused(h) && (cpals::wide_tail_on(h) || cpals::mode_tail_ok(In, h->R))) {
         int kind = 0;
         const double* Win = normal ? h->M : h->W;
         const double* Op = h->R0;
@@ -1199,6 +1199,17 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
 {
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!h) return fail(nullptr, CPALS_ERR_ARG, "%s", "null handle");
+    if (option == CPALS_OPT_FUSED_TAIL) {
+        if (value < 0 || value > 2) return fail(h, CPALS_ERR_ARG, "%s", "unknown option or value");
+        const bool a = value == 2, f = value == 1;
+        if (a != h->fused_tail_auto || (!a && f != h->fused_tail)) {
+            h->fused_tail_auto = a;
+            if (!a) h->fused_tail = f;
+            for (int s = 0; s < 4; ++s)         // captured sweeps hold the old kernels and schedule
+                if (h->graph[s]) { cudaGraphExecDestroy(h->graph[s]); h->graph[s] = nullptr; }
+        }
+        return CPALS_OK;
+    }
     bool* field = nullptr;
     switch (option) {
         case CPALS_OPT_DIMTREE: field = &h->dimtree; break;
@@ -1206,7 +1217,6 @@ int cpals_set_option(cpals_handle* hh, int option, int64_t value)
         case CPALS_OPT_KRP_TREE: field = &h->krp_tree; break;
         case CPALS_OPT_F32_PIPELINE: field = &h->f32_pipe; break;
         case CPALS_OPT_TEST_WITHHOLD_COPIES: field = &h->test_withhold; break;
-        case CPALS_OPT_FUSED_TAIL: field = &h->fused_tail; break;
         case CPALS_OPT_SVD_SHORTCUT: field = &h->svd_shortcut; break;
         case CPALS_OPT_APPLY_Q0_FP32: field = &h->q0_fp32; break;
         case CPALS_OPT_WIDE_TAIL: field = &h->wide_tail; break;

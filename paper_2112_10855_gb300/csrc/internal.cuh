@@ -142,7 +142,8 @@ struct Handle {
     int* d_vgate = nullptr;         // QR of a Khatri-Rao fold step: 1 when the staircase Householder must run
     double* VG = nullptr;           // R x R: the Gram of a fold step (written by its CholeskyQR2)
     bool svd_shortcut = true;       // CPALS_OPT_SVD_SHORTCUT
-    bool fused_tail = true;         // CPALS_OPT_FUSED_TAIL
+    bool fused_tail = true;         // CPALS_OPT_FUSED_TAIL = 1 / 0
+    bool fused_tail_auto = true;    // CPALS_OPT_FUSED_TAIL = 2 (the default)
     bool wide_tail = true;          // CPALS_OPT_WIDE_TAIL
     // GPU-wide CholeskyQR2 above rank 32 (tail.cu): [0] serves the mode tails
     // and factor QRs (main stream), [1] the fold steps of the QR of V_n (side
@@ -187,6 +188,16 @@ struct Handle {
     size_t owned_bytes = 0;
     char err[512] = {0};
 };
+
+// Whether the end of the mode updates and the factor QRs run in the fused
+// kernels (tail.cu): CPALS_OPT_FUSED_TAIL = 1 always, 0 never, 2 (the
+// default) from rank kFusedTailMinR up.  Below it the separate kernels
+// measured faster (a 4-way 128^4 rank-4 sweep: 3935 against 3260 per second),
+// since a Householder QR of four or five columns is short; from rank 10 the
+// fused kernels win.  The choice depends on the handle's rank only, so every
+// factor QR of a handle takes the same path.
+constexpr int kFusedTailMinR = 8;
+inline bool tail_fused(const Handle* h) { return h->fused_tail_auto ? h->R >= kFusedTailMinR : h->fused_tail; }
 
 // ------------------------------------------------------------------ launchers
 // All launchers enqueue on h->stream, count their launches in h->launches

@@ -1261,7 +1261,7 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
         auto step_qr = [&](double* Qo) -> cudaError_t {
             if (R <= kStairMaxN) {
                 const int* gate = nullptr;
-                if (h->fused_tail && R >= kFoldCqrMinR && mode_tail_ok((int64_t)R * R, R, 4)) {
+                if (tail_fused(h) && R >= kFoldCqrMinR && mode_tail_ok((int64_t)R * R, R, 4)) {
                     // CholeskyQR2 of the explicit F (.) R_B in the cluster kernel; the
                     // staircase Householder QR runs only if that was refused
                     krp2_kernel<<<grid_for((int64_t)R * R * R, 256, h->num_sms), 256, 0, h->stream>>>(
@@ -1281,7 +1281,7 @@ cudaError_t fold_qr(Handle* h, const double* const* Rl, int cnt, double* Qout, d
             h->launches++;
             CPALS_CUDA_TRY(cudaGetLastError());
             const int* gate = nullptr;
-            if (h->fused_tail && (wide_tail_on(h) || mode_tail_ok((int64_t)R * R, R, 4))) {
+            if (tail_fused(h) && (wide_tail_on(h) || mode_tail_ok((int64_t)R * R, R, 4))) {
                 // CholeskyQR2 (GPU-wide above rank 32, its first Gram from F and R_B); the
                 // TSQR runs only if that was refused
                 CPALS_CUDA_TRY(cqr2_rows(h, h->KM, (int64_t)R * R, Qo, Ro, h->VG, h->d_vgate, Rl[k], curR));
