@@ -1,7 +1,8 @@
 """CPU checks of the split-K launch planning (csrc/ttm_plan.h): the partial
 sums and group sums of a K-split TTM always fit the scratch they are given,
-and the Multi-TTM that runs from the fixed array of cpals_multi_ttm_static
-never writes past it.  The planning header is plain C++; it is compiled
+the Multi-TTM that runs from the fixed array of cpals_multi_ttm_static
+never writes past it, and the row kernels' register width covers the rank
+with as few unused columns as the instantiated widths allow.  The planning header is plain C++; it is compiled
 here with g++ and driven over many shapes, without a GPU."""
 import os
 import subprocess
@@ -98,3 +99,19 @@ def test_near_capacity_case_of_the_gpu_test(driver):
     # ways, with the partials filling most of the array
     ok, s0, s1, part, peak, splits = driver([f"s 3 40000 10 10 10 1 {SMS} {CAPACITY}"])[0]
     assert ok == 1 and splits > 16 and peak <= CAPACITY and peak > 0.9 * CAPACITY
+
+
+def test_register_width_covers_the_rank(driver):
+    widths = {R: w for R, (w,) in zip(range(1, 65), driver([f"w {R}" for R in range(1, 65)]))}
+    allowed = set(range(1, 17)) | {20, 24, 32}
+    for R, w in widths.items():
+        gy = -(-R // w)
+        assert w in allowed and gy * w >= R, (R, w)
+        if R <= 32:
+            assert gy == 1 and w == min(x for x in allowed if x >= R), (R, w)
+        else:
+            # the column blocks of the 32-wide tiling, each cut to the next
+            # instantiated width above its share (R = 40 as 2 x 20, not 2 x 32)
+            assert gy == -(-R // 32) and w == min(x for x in (20, 24, 32) if x >= -(-R // gy)), (R, w)
+    assert (widths[10], widths[17], widths[33], widths[40], widths[48], widths[64]) == (10, 20, 20, 20, 24, 32)
+

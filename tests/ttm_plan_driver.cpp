@@ -2,6 +2,7 @@
 // tests of the split-K scratch bound.  Reads commands from stdin, one per line:
 //   k ctas_xy tpb K num_sms outn part_elems   -> "<splits> <scratch elems>"
 //   s N d_0 .. d_{N-1} R n num_sms capacity  -> "<ok> <s0> <s1> <part> <peak> <max splits>"
+//   w R                                      -> "<register width of the row kernels>"
 #include <stdio.h>
 
 #include "ttm_plan.h"
@@ -30,6 +31,10 @@ int main()
             const cpals::StaticPlan p = cpals::plan_multi_ttm_static(N, dims, R, n, sms, cap);
             printf("%d %lld %lld %lld %lld %lld\n", p.ok ? 1 : 0, (long long)p.s0, (long long)p.s1,
                    (long long)p.part_elems, (long long)p.peak, (long long)p.max_splits);
+        } else if (cmd[0] == 'w') {
+            int R;
+            if (scanf("%d", &R) != 1) return 2;
+            printf("%d\n", cpals::ttm_width(R));
         } else {
             return 2;
         }
