@@ -120,3 +120,37 @@ def test_double_buffered_failure_propagates_without_hang(bench):
     t.join(timeout=30)
     assert not t.is_alive(), "the loop hung after a failure"
     assert done == ["planted failure"]
+
+
+def test_oracle_sample_rates_scale_by_elements_and_memory_bounds_replicas(bench, monkeypatch):
+    # the sample timed 2 s for half a sweep over a quarter of the workload's
+    # elements: 0.25 sweeps/s of the sample -> 0.0625 sweeps/s of the workload
+    calls = []
+
+    def fake_sample(task):
+        calls.append(task)
+        return 2.0, 0.5, 250
+
+    monkeypatch.setattr(bench, "_oracle_sample", fake_sample)
+    monkeypatch.setattr(bench, "_replica_map", lambda fn, tasks: [fn(t) for t in tasks])
+    import oracle
+    monkeypatch.setattr(oracle, "build", lambda: None)
+    monkeypatch.setattr(bench.os, "cpu_count", lambda: 16)
+    # room for 3 replicas: a quarter of the free memory over 4 copies of 8-byte elements
+    monkeypatch.setattr(bench, "_host_mem_available", lambda: 4 * 3 * 4 * 8 * 250)
+    cpu = bench.oracle_sample_baseline("c3", 1000, "sample", modes=1)
+    assert cpu["value"] == pytest.approx(0.5 / 2.0 * 250 / 1000)
+    assert cpu["cores"] == 1 and cpu["kind"] == "oracle" and cpu["sample"] == "sample"
+    assert cpu["all_cores"]["cores"] == 3 and cpu["all_cores"]["value"] == pytest.approx(3 * cpu["value"])
+    assert len(calls) == 1 + 3
+    # too little memory for two replicas: no all-cores figure
+    monkeypatch.setattr(bench, "_host_mem_available", lambda: 4 * 1 * 4 * 8 * 250)
+    assert "all_cores" not in bench.oracle_sample_baseline("c3", 1000, "sample", modes=1)
+
+
+def test_replica_map_runs_single_threaded_children_and_restores_env(bench, monkeypatch):
+    monkeypatch.setenv("OMP_NUM_THREADS", "7")
+    monkeypatch.delenv("OPENBLAS_NUM_THREADS", raising=False)
+    out = bench._replica_map(os.getenv, ["OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"])
+    assert out == ["1", "1"]
+    assert os.environ["OMP_NUM_THREADS"] == "7" and "OPENBLAS_NUM_THREADS" not in os.environ
