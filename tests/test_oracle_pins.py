@@ -224,6 +224,29 @@ def test_qr_update_equals_lstsq_on_explicit_Z(dims, R):
         assert rel(o2.last(n)["Ahat"], ref) < 1e-11
 
 
+@pytest.mark.parametrize("dims,R", [((6, 5, 7), 3), ((4, 5, 3, 4), 3), ((5, 4, 3, 3, 4), 2)])
+def test_sweeps_equal_alternating_lstsq(dims, R):
+    # three whole sweeps against ALS written with numpy alone: each mode in
+    # order solved by lstsq on the explicit Khatri-Rao product of the current
+    # (normalised) factors, its columns then normalised, lambda the last
+    # mode's norms -- the sequencing that single-update pins leave open
+    X, A0 = _problem(dims, R, seed=11)
+    A = [np.array(a) for a in A0]
+    lam = np.ones(R)
+    for _ in range(3):
+        for n in range(len(dims)):
+            Ahat = np.linalg.lstsq(F.Z(A, n), F.unfold(X, dims, n).T, rcond=None)[0].T
+            lam = np.linalg.norm(Ahat, axis=0)
+            A[n] = Ahat / np.where(lam > 0, lam, 1.0)
+    o = oracle.OracleCPALS(X, dims, R)
+    o.set_factors(A0)
+    k, _ = o.iterate(3, solve=oracle.QR)
+    assert k == 3
+    for n in range(len(dims)):
+        assert rel(o.factor(n), A[n]) < 1e-10, (n, rel(o.factor(n), A[n]))
+    assert rel(o.lam(), lam) < 1e-10
+
+
 def test_normal_update_equals_qr_update_well_conditioned():
     dims, R = (8, 7, 6), 3
     X, A = _problem(dims, R, seed=3)
