@@ -36,6 +36,8 @@ MUTATIONS = {
     "ttm_order_ties_low_mode": ("(dims[y] == dims[x] && y > x)", "(dims[y] == dims[x] && y < x)"),
     "apply_q0_skipped_in_update": ("orc_matmul(In, RN1, R, st->Y, st->Q0, st->W);",
                                    "orc_matmul(In, R, R, st->Y, st->R0, st->W);"),
+    "factor_qr_left_stale": ("orc_qr(In, R, st->A[n], st->Q[n], st->Rf[n]);",
+                             "/* factor QR not refreshed */"),
 }
 
 PINS = [
@@ -55,6 +57,7 @@ PINS = [
     (P.test_cholesky_solve_against_numpy, ()),
     (P.test_normalize_two_norm, ()),
     (P.test_efficient_fit_matches_direct, ()),
+    (P.test_sweeps_equal_alternating_lstsq, ((6, 5, 7), 3)),
 ]
 
 
