@@ -37,6 +37,11 @@
  *    The word is reported, and then cleared, by the next synchronising call:
  *    cpals_sync, cpals_fit, cpals_iterate, or a get call with host memory.
  *  - A handle is not thread-safe.  Use one handle per host thread.
+ *  - A process drives one GPU.  Kernel attributes (opt-in dynamic shared
+ *    memory, non-portable cluster sizes) are set once per process, on the
+ *    device current at the first call that needs them.  Handles created on a
+ *    second device of the same process are not supported: launches that need
+ *    those attributes fail there with CPALS_ERR_CUDA.  Run one process per GPU.
  */
 #ifndef CPALS_H
 #define CPALS_H
