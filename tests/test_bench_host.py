@@ -6,7 +6,12 @@ its sweep.  Here the handles are fakes that record when each call starts and
 ends, and torch's CUDA calls are stubbed, so the protocol itself is checked:
 every step runs once, the copies never overlap, each copy overlaps the other
 handle's sweep, and a failing handle ends the loop with its error instead of a
-hang."""
+hang.
+
+Also on CPU: the oracle sample scaling and its spawned replicas, the
+parsing of the nvidia-smi clock record (median SM clock, throttle reasons),
+and the guard that reports recorded DRAM traffic only for the kernel text it
+was measured on."""
 import importlib.util
 import os
 import threading
@@ -154,3 +159,48 @@ def test_replica_map_runs_single_threaded_children_and_restores_env(bench, monke
     out = bench._replica_map(os.getenv, ["OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"])
     assert out == ["1", "1"]
     assert os.environ["OMP_NUM_THREADS"] == "7" and "OPENBLAS_NUM_THREADS" not in os.environ
+
+
+def test_clock_summary_takes_median_and_throttle_reasons(bench, tmp_path):
+    # nvidia-smi rows: index, clocks.sm, clocks.max.sm, power.draw, active mask,
+    # then the four named reasons; a malformed row and a "[N/A]" row are skipped
+    path = tmp_path / "clocks.csv"
+    path.write_text("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "garbage line\n"
+                    "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "0, 1500, 2100, 1399.9, 0x8, Active, Not Active, Not Active, Not Active\n")
+    clk = bench.ClockSampler(0)
+    clk.path = str(path)
+    s = clk.summary()
+    assert s == {"sm_mhz": 2025.0, "sm_max_mhz": 2100.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 4}
+    assert not path.exists()            # the temporary record is removed
+
+
+def test_clock_summary_without_samples_is_none(bench, tmp_path):
+    path = tmp_path / "empty.csv"
+    path.write_text("")
+    clk = bench.ClockSampler(0)
+    clk.path = str(path)
+    assert clk.summary() is None
+    assert bench.ClockSampler(0).summary() is None       # sampler never started
+
+
+def test_kernel_source_spans_template_line_to_closing_brace(bench):
+    src = bench.kernel_source("ttm_rows_kernel")
+    lines = src.split("\n")
+    assert lines[0].startswith("template") and "__global__" in lines[1]
+    assert lines[-1] == "}" and src.count("__global__") == 1
+    assert bench.kernel_source("no_such_kernel") == ""
+
+
+def test_recorded_traffic_needs_the_recorded_kernel_text(bench, monkeypatch):
+    # the committed summary holds the DRAM bytes and the hash of the kernel
+    # text they were taken on; any other text gives no traffic figure
+    t = bench.recorded_traffic()
+    assert isinstance(t, int) and 512_000_000 <= t <= 530_000_000
+    real = bench.kernel_source
+    monkeypatch.setattr(bench, "kernel_source", lambda name: real(name) + "\n// changed")
+    assert bench.recorded_traffic() is None
+    assert bench.recorded_traffic("no_such_profile.md") is None
