@@ -499,8 +499,11 @@ __global__ void recip_check_kernel(const double* __restrict__ x, int64_t n, doub
 }
 
 // ------------------------------------------------------------------------
-// GPU-wide CholeskyQR2 (rank above 32).  There the tail's FP64 work per row is
-// R^2, and the cluster's 16 SMs hold a tenth of the GPU's FP64 rate, so the
+// GPU-wide CholeskyQR2 (rank above 32): the normalisation and factor QR
+// A_n = Q_n R_n that close a mode update of Alg. cp-als-qr, and the QR of each
+// Kronecker fold step of V_n (Eq. kr-id, Sec. 3.3.3), by the CholeskyQR2 of
+// Fukaya, Nakatsukasa, Yanagisawa and Yamamoto (2014) with the cluster
+// kernel's acceptance check.  There the tail's FP64 work per row is R^2, and the cluster's 16 SMs hold a tenth of the GPU's FP64 rate, so the
 // kinds that start from Ahat or A (3, 4) and the fold-step QRs run as a chain
 // of kernels over every SM instead:
 //   colsq   column sums of squares of Ahat per row block            (kind 3)

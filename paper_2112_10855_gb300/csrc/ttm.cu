@@ -230,8 +230,9 @@ __global__ void __launch_bounds__(128) ttm_fiber4_kernel(
     }
 }
 
-// FP32 TTM over the fastest mode (L = 1) as a tiled GEMM, out(t, r) =
-// sum_k In(k, t) Q(k, r) with every fiber In(:, t) contiguous.  A CTA of 256
+// FP32 TTM over the fastest mode (L = 1) as a tiled GEMM: one single TTM of
+// the Multi-TTM (Eq. multittm, Sec. 3.2) when the contracted mode is mode 0,
+// out(t, r) = sum_k In(k, t) Q(k, r) with every fiber In(:, t) contiguous.  A CTA of 256
 // threads owns 128 fibers and BN columns (BN = 32 or 64, Q zero-padded to
 // BN) and walks its K range in chunks of 32.  The [128 fibers x 32] block is
 // read as 128-byte fiber rows (eight threads per row, 16-byte loads, K % 4
