@@ -1,5 +1,6 @@
-// tc_split.cu -- the first TTM of the Multi-TTM (the pass that streams X) on
-// the tcgen05 tensor cores with split-precision products:
+// tc_split.cu -- the first TTM of the Multi-TTM (Eq. multittm; the pass that
+// streams X, which dominates a mode update at small rank, Sec. 3.2) on the
+// tcgen05 tensor cores with split-precision products:
 //     Out(l, r, t) = sum_k X(l, k, t) * Q(k, r)            (Y = X x_m Q_m^T)
 // X is the FP32 copy of the tensor.  Each x and each q are split into two
 // parts of the operand type, x = x_hi + x_lo (x_hi = round(x),
