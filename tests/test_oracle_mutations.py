@@ -38,6 +38,17 @@ MUTATIONS = {
                                    "orc_matmul(In, R, R, st->Y, st->R0, st->W);"),
     "factor_qr_left_stale": ("orc_qr(In, R, st->A[n], st->Q[n], st->Rf[n]);",
                              "/* factor QR not refreshed */"),
+    "svd_no_truncation": ("int keep = S[j] > rtol * S[0] && S[j] > 0.0;", "int keep = S[j] > 0.0;"),
+    "svd_U_in_place_of_V": ("for (int64_t j = 0; j < R; ++j) s += WU[i + I * j] * V[k + R * j];",
+                            "for (int64_t j = 0; j < R; ++j) s += WU[i + I * j] * U[k + R * j];"),
+    "hadamard_gram_summed": ("for (int64_t k = 0; k < R * R; ++k) st->S[k] *= st->G[m][k];",
+                             "for (int64_t k = 0; k < R * R; ++k) st->S[k] += st->G[m][k];"),
+    "direct_residual_drops_lambda": ("double p = lambda[r];", "double p = 1.0;"),
+    "fit_qr_R0_not_transposed": ("for (int64_t j = 0; j < R; ++j) s += AhatN[i + IN * j] * R0[k + R * j];",
+                                 "for (int64_t j = 0; j < R; ++j) s += AhatN[i + IN * j] * R0[j + R * k];"),
+    "fit_normal_drops_one_lambda": ("nrm += SN[a + R * b] * lambda[a] * GN[a + R * b] * lambda[b];",
+                                    "nrm += SN[a + R * b] * lambda[a] * GN[a + R * b];"),
+    "lambda_accumulates_over_modes": ("        lambda[r] = l;\n", "        lambda[r] *= l;\n"),
 }
 
 PINS = [
@@ -58,6 +69,7 @@ PINS = [
     (P.test_normalize_two_norm, ()),
     (P.test_efficient_fit_matches_direct, ()),
     (P.test_sweeps_equal_alternating_lstsq, ((6, 5, 7), 3)),
+    (P.test_svd_solve_truncation_matches_pinv, ()),
 ]
 
 
