@@ -49,6 +49,9 @@ MUTATIONS = {
     "fit_normal_drops_one_lambda": ("nrm += SN[a + R * b] * lambda[a] * GN[a + R * b] * lambda[b];",
                                     "nrm += SN[a + R * b] * lambda[a] * GN[a + R * b];"),
     "lambda_accumulates_over_modes": ("        lambda[r] = l;\n", "        lambda[r] *= l;\n"),
+    "score_keeps_sign": ("term *= (n1 > 0.0 && n2 > 0.0) ? fabs(d) / sqrt(n1 * n2) : 0.0;",
+                         "term *= (n1 > 0.0 && n2 > 0.0) ? d / sqrt(n1 * n2) : 0.0;"),
+    "score_identity_permutation_only": ("while (i < R) {", "while (0) {"),
 }
 
 PINS = [
@@ -70,6 +73,7 @@ PINS = [
     (P.test_efficient_fit_matches_direct, ()),
     (P.test_sweeps_equal_alternating_lstsq, ((6, 5, 7), 3)),
     (P.test_svd_solve_truncation_matches_pinv, ()),
+    (P.test_score_invariances, ()),
 ]
 
 
