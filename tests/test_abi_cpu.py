@@ -1,6 +1,8 @@
 """CPU-only checks of the boundary: the C-ABI library builds for sm_103a, loads,
 exports every entry point declared in include/cpals.h, and rejects bad
-arguments before touching the GPU.  Also pins the seeded input generator."""
+arguments before touching the GPU.  Without the library, or without a GPU,
+the binding raises: there is no host fallback.  Also pins the seeded input
+generator."""
 import ctypes as C
 import re
 
@@ -136,3 +138,23 @@ def test_planted_tensor_layout():
 def test_allocation_hook_rejects_negative_counts(lib):
     assert lib.cpals_test_fail_allocation(-1) == cpals.ERR_ARG
     assert lib.cpals_test_fail_allocation(0) == cpals.OK
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    monkeypatch.setattr(cpals, "_lib", None)
+    with pytest.raises(RuntimeError, match="not found"):
+        cpals.load(str(tmp_path / "libcpals.so"))
+
+
+def test_no_host_fallback_without_a_gpu(lib):
+    # valid arguments and no usable GPU: creation fails with the CUDA error
+    # instead of computing anything on the host
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(cpals.CPALSError) as e:
+        cpals.CPALS((4, 4, 4), 2, "f64")
+    assert e.value.code == cpals.ERR_CUDA
+    with pytest.raises(cpals.CPALSError) as e:
+        cpals.CPALSBatch([(16, 16, 16)], [2])
+    assert e.value.code == cpals.ERR_CUDA
