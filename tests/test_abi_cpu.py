@@ -158,3 +158,53 @@ def test_no_host_fallback_without_a_gpu(lib):
     with pytest.raises(cpals.CPALSError) as e:
         cpals.CPALSBatch([(16, 16, 16)], [2])
     assert e.value.code == cpals.ERR_CUDA
+
+
+def _static_call(lib, dims, N, rank, mode, null_q=None, null=None):
+    d = (C.c_int64 * len(dims))(*dims)
+    # non-null dummy addresses: every case here is rejected before any device access
+    q = (C.c_void_p * len(dims))(*[0x1000 * (m + 1) for m in range(len(dims))])
+    if null_q is not None:
+        q[null_q] = None
+    X, Y = C.c_void_p(0x100000), C.c_void_p(0x200000)
+    args = {"dims": d, "X": X, "Q": q, "Y": Y}
+    if null is not None:
+        args[null] = None
+    return lib.cpals_multi_ttm_static(args["dims"], N, rank, mode, args["X"], args["Q"], args["Y"], None)
+
+
+@pytest.mark.parametrize("dims,N,rank,mode,null_q,null", [
+    ((10, 10, 10), 1, 3, 0, None, None),         # N < 2
+    ((3,) * 13, 13, 2, 0, None, None),           # N above the maximum
+    ((10, 10, 10), 3, 0, 0, None, None),         # rank 0
+    ((10, 10, 10), 3, 65, 0, None, None),        # rank above the maximum
+    ((10, 10, 10), 3, 3, 3, None, None),         # mode out of range
+    ((10, 10, 10), 3, 3, -1, None, None),        # negative mode
+    ((10, 2, 10), 3, 3, 0, None, None),          # rank above a dim
+    ((10, 10, 10), 3, 3, 0, 2, None),            # a Q_m the Multi-TTM needs is NULL
+    ((10, 10, 10), 3, 3, 0, None, "X"),          # X NULL
+    ((10, 10, 10), 3, 3, 0, None, "Y"),          # Y NULL
+    ((10, 10, 10), 3, 3, 0, None, "Q"),          # Q array NULL
+    ((10, 10, 10), 3, 3, 0, None, "dims"),       # dims NULL
+    ((1 << 40, 1 << 30, 64), 3, 3, 2, None, None),   # prod(dims) overflows int64
+])
+def test_static_entry_rejects_bad_arguments_on_the_host(lib, dims, N, rank, mode, null_q, null):
+    assert _static_call(lib, dims, N, rank, mode, null_q, null) == cpals.ERR_ARG
+    assert lib.cpals_last_error(None)
+
+
+@pytest.mark.parametrize("count,dims,ranks", [
+    (0, [], []),                                  # no problems
+    (1, [16, 16, 16], [0]),                       # rank 0
+    (1, [16, 16, 16], [17]),                      # rank above the batched maximum
+    (2, [16, 16, 16, 16, 3, 16], [4, 4]),         # a dim below the rank
+    (1, [16, 5000, 16], [4]),                     # a dim above 4096
+    (1, [4096, 4096, 4096], [16]),                # working set beyond one CTA's shared memory
+])
+def test_batch_create_rejects_bad_arguments_on_the_host(lib, count, dims, ranks):
+    d = (C.c_int64 * max(len(dims), 1))(*dims)
+    r = (C.c_int * max(len(ranks), 1))(*ranks)
+    out = C.c_void_p()
+    assert lib.cpals_batch_create(count, d, r, C.byref(out)) == cpals.ERR_ARG
+    assert not out.value
+    assert lib.cpals_last_error(None)
