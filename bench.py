@@ -210,15 +210,21 @@ def workload(size, rank, seed):
     return inputs.workload_c2(seed=seed, init_seed=10855 + seed - 2112, size=size, rank=rank)
 
 
-def cpu_oracle_rate(p, sweeps=2, solve=0):
-    """The oracle as it stands (1 host thread), `sweeps` full sweeps."""
+def cpu_oracle_rate(p, solve=0, target_s=12.0, max_sweeps=20):
+    """The oracle as it stands (1 host thread): full sweeps, timed together,
+    as many as fill about target_s (at least 2, at most max_sweeps; the first
+    sweep's time sets the count).  Returns (sweeps/s, seconds, sweeps)."""
     import oracle
     o = oracle.OracleCPALS(p.X, p.dims, p.rank)
     o.set_factors(p.init_factors)
     t0 = time.perf_counter()
-    o.iterate(sweeps, solve=solve)
+    k1, _ = o.iterate(1, solve=solve)
+    first = time.perf_counter() - t0
+    more = max(1, min(max_sweeps - 1, int(target_s / max(first, 1e-9)) - 1))
+    k2, _ = o.iterate(more, solve=solve)
     dt = time.perf_counter() - t0
-    return sweeps / dt, dt
+    n = abs(k1) + abs(k2)
+    return n / dt, dt, n
 
 
 def _oracle_replica(task):
@@ -1179,9 +1185,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         solve_id = {"qr": 0, "svd": 1, "normal": 2}[args.solve]
-        rate, dt = cpu_oracle_rate(p, sweeps=2, solve=solve_id)
+        rate, dt, n = cpu_oracle_rate(p, solve=solve_id)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"2 full sweeps of the same workload ({dt:.1f} s), plain C FP64, 1 host thread"}
+               "sample": f"{n} full sweeps of the same workload ({dt:.1f} s), plain C FP64, 1 host thread"}
         try:
             agg, cores, wall = cpu_oracle_all_cores(p.dims[0], R, sweeps=1, solve=solve_id)
             cpu["all_cores"] = {"value": agg, "unit": UNIT, "cores": cores, "kind": "oracle",

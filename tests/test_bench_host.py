@@ -204,3 +204,16 @@ def test_recorded_traffic_needs_the_recorded_kernel_text(bench, monkeypatch):
     monkeypatch.setattr(bench, "kernel_source", lambda name: real(name) + "\n// changed")
     assert bench.recorded_traffic() is None
     assert bench.recorded_traffic("no_such_profile.md") is None
+
+
+def test_single_thread_oracle_sample_is_bounded(bench):
+    # the 1-thread oracle sample times whole sweeps: at least 2, at most the
+    # cap, as many as the first sweep's time says fit the target
+    from paper_2112_10855_gb300 import inputs
+    p = inputs.workload_c2(size=24, rank=3)
+    rate, dt, n = bench.cpu_oracle_rate(p, target_s=0.0)
+    assert n == 2 and dt > 0 and abs(rate - n / dt) < 1e-9 * rate
+    rate, dt, n = bench.cpu_oracle_rate(p, target_s=1e9, max_sweeps=7)
+    assert n == 7 and abs(rate - n / dt) < 1e-9 * rate
+    rate, dt, n = bench.cpu_oracle_rate(p, target_s=0.3, max_sweeps=10000)
+    assert 2 <= n < 10000 and dt >= 0.1
