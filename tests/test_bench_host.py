@@ -217,3 +217,23 @@ def test_single_thread_oracle_sample_is_bounded(bench):
     assert n == 7 and abs(rate - n / dt) < 1e-9 * rate
     rate, dt, n = bench.cpu_oracle_rate(p, target_s=0.3, max_sweeps=10000)
     assert 2 <= n < 10000 and dt >= 0.1
+
+
+def test_profile_commands_use_flags_the_bench_accepts(bench, monkeypatch):
+    # every committed ncu summary names the command that made it; its bench.py
+    # part must still parse, so the command can be run again as written
+    import glob
+    import re
+    import shlex
+    import sys
+    found = 0
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read()
+        assert re.search(r"^Commands? ", text, re.M), f"{path}: no command"
+        joined = text.replace("\\\n", " ")
+        for m in re.finditer(r"python bench\.py([^\n`]*)", joined):
+            argv = ["bench.py"] + shlex.split(m.group(1))
+            monkeypatch.setattr(sys, "argv", argv)
+            bench.parse()       # argparse exits on an unknown flag or a bad value
+            found += 1
+    assert found >= 8
