@@ -37,6 +37,13 @@
  *    The word is reported, and then cleared, by the next synchronising call:
  *    cpals_sync, cpals_fit, cpals_iterate, or a get call with host memory.
  *  - A handle is not thread-safe.  Use one handle per host thread.
+ *  - Errors of a call that lists none of its own: CPALS_ERR_ARG for a NULL
+ *    handle, a mode outside [0, N), a bad mem flag or a NULL pointer that the
+ *    call needs; CPALS_ERR_STATE when the call needs a tensor or factors that
+ *    were not set; CPALS_ERR_NOMEM or CPALS_ERR_CUDA when an allocation or a
+ *    CUDA call fails.  A call with mem = CPALS_MEM_HOST synchronises, so it
+ *    also reports a device error recorded by earlier work (CPALS_ERR_SINGULAR,
+ *    CPALS_ERR_TIMEOUT).
  *  - A process drives one GPU.  Kernel attributes (opt-in dynamic shared
  *    memory, non-portable cluster sizes) are set once per process, on the
  *    device current at the first call that needs them.  Handles created on a
@@ -358,8 +365,9 @@ int cpals_test_fail_allocation(int nth);
  * each kernel node once per replay). */
 int64_t cpals_launch_count(const cpals_handle* h);
 
-/* Multi-TTM Y_(n) = X_(n) (Q_{N-1} (x) ... (x) Q_0, without `mode`) for
- * callers that cannot allocate device memory.  The paper has no counterpart
+/* Multi-TTM Y_(n) = X_(n) (Q_{N-1} (x) ... (x) Q_0, without `mode`) of
+ * Eq. multittm (Alg. cp-als-qr, Multi-TTM step) for callers that cannot
+ * allocate device memory.  The paper has no counterpart
  * to this entry point.  Such callers include a host framework that hands all
  * device memory to its own pool allocator, a process that runs under a hard
  * device-memory budget, and a latency-critical loop where the implicit
