@@ -71,6 +71,18 @@ void orc_matmul_tn(int64_t m, int64_t k, int64_t n, const double* A, const doubl
 /* Householder QR (Sec. 2.1: compact/thin QR A = QR, Q with the shape of */
 /* A, R square), explicit Q, diag(R) >= 0.                              */
 /* ------------------------------------------------------------------ */
+/* Multiply-adds of the two O(m n^2) loop nests of orc_qr (the reflector
+ * applications to W and to Q), summed over calls: the flop-count pin of
+ * Eq. QRcost reads it.  The oracle is single-threaded. */
+static int64_t g_qr_madds = 0;
+
+int64_t orc_qr_madds(int reset)
+{
+    int64_t v = g_qr_madds;
+    if (reset) g_qr_madds = 0;
+    return v;
+}
+
 void orc_qr(int64_t m, int64_t n, const double* A, double* Q, double* R)
 {
     double* W = (double*)malloc(sizeof(double) * (size_t)(m * n));
@@ -98,6 +110,7 @@ void orc_qr(int64_t m, int64_t n, const double* A, double* Q, double* R)
             for (int64_t i = j; i < m; ++i) s += V[i + m * j] * W[i + m * k];
             s *= beta[j];
             for (int64_t i = j; i < m; ++i) W[i + m * k] -= s * V[i + m * j];
+            g_qr_madds += 2 * (m - j);
         }
         W[j + m * j] = alpha;
         for (int64_t i = j + 1; i < m; ++i) W[i + m * j] = 0.0;
@@ -105,16 +118,21 @@ void orc_qr(int64_t m, int64_t n, const double* A, double* Q, double* R)
     /* R = upper triangle of W */
     for (int64_t j = 0; j < n; ++j)
         for (int64_t i = 0; i < n; ++i) R[i + n * j] = (i <= j) ? W[i + m * j] : 0.0;
-    /* Q = H_0 H_1 ... H_{n-1} [I_n; 0], accumulated backwards */
+    /* Q = H_0 H_1 ... H_{n-1} [I_n; 0], accumulated backwards.  When H_j is
+     * applied, columns k < j are still e_k, zero in rows j..m-1 where v_j
+     * lives, so H_j leaves them as they are and only columns j..n-1 change.
+     * With the loop above this is the 4 m n^2 - (4/3) n^3 flops of a
+     * Householder QR with explicit Q (Sec. 3.2, Eq. QRcost). */
     for (int64_t j = 0; j < n; ++j)
         for (int64_t i = 0; i < m; ++i) Q[i + m * j] = (i == j) ? 1.0 : 0.0;
     for (int64_t j = n - 1; j >= 0; --j) {
         if (beta[j] == 0.0) continue;
-        for (int64_t k = 0; k < n; ++k) {
+        for (int64_t k = j; k < n; ++k) {
             double s = 0.0;
             for (int64_t i = j; i < m; ++i) s += V[i + m * j] * Q[i + m * k];
             s *= beta[j];
             for (int64_t i = j; i < m; ++i) Q[i + m * k] -= s * V[i + m * j];
+            g_qr_madds += 2 * (m - j);
         }
     }
     /* sign convention: diag(R) >= 0 */

@@ -82,6 +82,7 @@ def lib():
 
 def _configure(L):
     L.orc_multi_ttm.restype = C.c_int64
+    L.orc_qr_madds.restype = C.c_int64
     L.orc_trsm_qr.restype = C.c_int
     L.orc_svd_solve.restype = C.c_int
     L.orc_cholesky_solve.restype = C.c_int
@@ -132,13 +133,18 @@ def _ptr_array(mats):
     return arr
 
 
-def qr(A):
+def qr(A, return_madds=False):
+    """Householder QR with explicit Q and diag(R) >= 0.  return_madds: also
+    the multiply-adds of its two O(m n^2) loop nests (Eq. QRcost pin)."""
     A = _f(A)
     m, n = A.shape
     Q = np.zeros((m, n), order="F")
     R = np.zeros((n, n), order="F")
-    lib().orc_qr(C.c_int64(m), C.c_int64(n), _p(A), _p(Q), _p(R))
-    return Q, R
+    L = lib()
+    L.orc_qr_madds(1)
+    L.orc_qr(C.c_int64(m), C.c_int64(n), _p(A), _p(Q), _p(R))
+    madds = L.orc_qr_madds(1)
+    return (Q, R, madds) if return_madds else (Q, R)
 
 
 def krp(mats):

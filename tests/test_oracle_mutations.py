@@ -52,6 +52,7 @@ MUTATIONS = {
     "score_keeps_sign": ("term *= (n1 > 0.0 && n2 > 0.0) ? fabs(d) / sqrt(n1 * n2) : 0.0;",
                          "term *= (n1 > 0.0 && n2 > 0.0) ? d / sqrt(n1 * n2) : 0.0;"),
     "score_identity_permutation_only": ("while (i < R) {", "while (0) {"),
+    "qr_q_misses_reflector_column": ("for (int64_t k = j; k < n; ++k) {", "for (int64_t k = j + 1; k < n; ++k) {"),
 }
 
 PINS = [

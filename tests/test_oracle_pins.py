@@ -33,6 +33,32 @@ def test_qr_matches_lapack_with_sign_convention(m, n):
     assert rel(Q, Qn) < 1e-12 and rel(R, Rn) < 1e-12
 
 
+@pytest.mark.parametrize("m,n", [(1, 1), (12, 5), (36, 6), (64, 4), (400, 10), (125, 5), (33, 33)])
+def test_qr_flop_count(m, n):
+    # Eq. QRcost and the factor-QR cost of Sec. 3.2: a Householder QR of an
+    # m x n matrix with Q formed explicitly costs 4 m n^2 + O(n^3) flops; with
+    # V_n (m = R^{N-1}, n = R) that is 4 R^{N+1} + O(R^3), with a factor
+    # (m = I_n, n = R) 4 I_n R^2 + O(R^3).  Counted exactly (one multiply-add =
+    # 2 flops): reflector j updates n-1-j columns of A and n-j columns of Q,
+    # each over m-j rows with a dot product and an update, so
+    # flops = 4 m n^2 - (4/3) n^3 + 2 n^2 - (2/3) n.
+    A = RNG.standard_normal((m, n))
+    Q, R, madds = oracle.qr(A, return_madds=True)
+    assert 3 * (2 * madds) == 12 * m * n * n - 4 * n ** 3 + 6 * n * n - 2 * n
+    assert abs(2 * madds - 4 * m * n * n) <= 4 * n ** 3
+    assert rel(Q @ R, A) < 1e-14
+
+
+def test_qr_flop_count_skips_identity_reflectors():
+    # a zero column gives H_j = I, which is neither applied nor counted
+    m, n, z = 9, 4, 2
+    A = RNG.standard_normal((m, n))
+    A[:, z] = 0.0
+    _, _, madds = oracle.qr(A, return_madds=True)
+    full = sum(2 * (2 * n - 1 - 2 * j) * (m - j) for j in range(n))
+    assert madds == full - 2 * (2 * n - 1 - 2 * z) * (m - z)
+
+
 def test_qr_zero_column():
     A = RNG.standard_normal((9, 4))
     A[:, 2] = 0.0
