@@ -331,6 +331,29 @@ def test_trsm_against_solve():
         oracle.trsm_qr(W, R1)
 
 
+def test_trsm_singularity_threshold():
+    # the reading of the QR solve's singularity test: R0 is singular when some
+    # |R0(k,k)| <= R * eps * max_j |R0(j,j)|; just above the bound it solves,
+    # at or below it (or NaN) it refuses
+    R = 6
+    eps = np.finfo(np.float64).eps
+    R0 = np.triu(RNG.standard_normal((R, R))) + 3 * np.eye(R)
+    R0[1, 1] = 10.0
+    dmax = np.abs(np.diag(R0)).max()
+    W = RNG.standard_normal((5, R))
+    bound = R * eps * dmax
+    for k in (0, 4):
+        ok = R0.copy(); ok[k, k] = 2.0 * bound
+        A = oracle.trsm_qr(W, ok)
+        # nearly singular: a small backward error, not a small residual
+        assert np.isfinite(A).all()
+        assert np.linalg.norm(A @ ok.T - W) <= 1e-13 * np.linalg.norm(A) * np.linalg.norm(ok)
+        for v in (bound, 0.5 * bound, -0.5 * bound, 0.0, np.nan):
+            bad = R0.copy(); bad[k, k] = v
+            with pytest.raises(np.linalg.LinAlgError):
+                oracle.trsm_qr(W, bad)
+
+
 def test_jacobi_svd_against_lapack():
     for n in (1, 2, 5, 10, 17):
         A = RNG.standard_normal((n, n))
